@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the Quantum Flow sweep on one GB300: one step = one full sweep (dressing of the
+pool, every active space gathered + folded + solved by the batched Davidson kernel, CI -> CC
+increments merged by owner, mean energy and convergence reductions).
+
+Default workload: the 82-orbital synthetic system (10 occupied, 72 virtual, xi = 5) with all
+C(10,3) C(72,3) = 7,156,800 (3,3) active spaces per sweep, mixed precision (FP32 sigma-vectors,
+FP64 dressing / projected eigenproblem / energy / amplitude update).  Warm-up sweeps move the
+pool from empty to a mid-flow state before the timed sweeps; the plain FP64 GPU form of the
+same sweep is timed beside it, and the FP64 oracle is timed on the host cores on a bounded
+sample (cpu_baseline).  The inputs (W: 362 MB) are larger than the 126 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload n82]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_04186_gb300 import synth  # noqa: E402
+
+METRIC = "QFlow sweep time (s) + active spaces/s vs plain FP64 GPU form at |ΔE|≤1e-6 Eh"
+UNIT = "active spaces/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+FP64_PEAK_TFLOPS = 1.25                              # GB300 FP64 (nominal)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="n82", choices=sorted(synth.SYSTEMS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed sweeps of the plain FP64 form (0 = skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=800, help="spaces solved by the oracle for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---- per-space flop accounting of the solve kernel (6e6o, 400 determinants) ------------------
+
+def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12, kmax: int = 8) -> float:
+    """Algorithmic flops of the batched Davidson for spaces that ran `iters` iterations.
+
+    sigma: per determinant 2 * (NSG*NSG) for the alpha-beta double sum + 2 * 2 * NS for the
+    same-spin string products + 2 for the diagonal  -> 400 * (288 + 80 + 2) = 148,000 flop.
+    Setup: same-spin string operator NS*NSG*(1+NSG)*2, start sigma, 2 dot products.
+    Iteration with subspace k: residual 400*(4k+4), Gram-Schmidt 2 passes 400*(4k),
+    norm+scale 400*3, sigma, projected row/column 400*2*(2k+1).  k runs 1..kmax-1 then restarts.
+    """
+    sig = ndet * (2 * nsg * nsg + 4 * ns + 2)
+    setup = ns * nsg * (1 + nsg) * 2 + sig + 4 * ndet
+    # flops of m iterations: follow the subspace size sequence of the kernel
+    m_max = int(iters.max()) if iters.size else 0
+    cum = np.zeros(m_max + 1)
+    k, tot = 1, 0.0
+    for m in range(1, m_max + 1):
+        if k == kmax:
+            tot += ndet * (4 * kmax + 6)          # restart: Ritz vector + its sigma combination + norms
+            k = 1
+        tot += ndet * (4 * k + 4) + ndet * 8 * k + ndet * 3 + sig + ndet * 2 * (2 * k + 1)
+        k += 1
+        cum[m] = tot
+    return float(setup * iters.size + cum[np.clip(iters, 0, m_max)].sum())
+
+
+# ---- clocks ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- CPU oracle leg -------------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    from oracle import cas
+    out = []
+    for c, h, w in args:
+        out.append(cas.solve_problem(3, 3, c, h, w)[0])
+    return out
+
+
+def oracle_sweep_sample(name: str, sample: int, pool, seed: int = 7):
+    """Time the oracle on a bounded sample of one sweep: full dressing + `sample` spaces."""
+    from oracle import cas, flow, hbar
+    eps, h, g, sp = synth.system_inputs(name)
+    s = synth.SYSTEMS[name]
+    no, nv = s.nocc, s.n - s.nocc
+    t1, t2 = synth.random_amplitudes(no, nv, seed, 0.005, 0.01)
+    t0 = time.perf_counter()
+    e0, F, W = hbar.hbar2(h, g, t1, t2, no)
+    t_dress = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(len(sp), size=min(sample, len(sp)), replace=False)
+    t0 = time.perf_counter()
+    probs = [cas.space_problem(e0, F, W, *flow.space_orbitals(sp[k])) for k in pick]
+    nproc = getattr(pool, "_processes", 1)
+    chunks = [probs[i::nproc] for i in range(nproc)]
+    pool.map(_oracle_worker, chunks)
+    t_solve = time.perf_counter() - t0
+    per_space = t_solve / len(pick)
+    sweep_s = t_dress + per_space * len(sp)
+    return {"value": len(sp) / sweep_s, "sweep_s_extrapolated": sweep_s, "dress_s": t_dress,
+            "solve_s_sample": t_solve, "sample": len(pick), "nspaces": len(sp)}
+
+
+def log(msg: str):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _warm_worker(_):
+    from oracle import cas
+    cas.coupling(3, 3)  # build the determinant coupling maps once per worker
+    return 0
+
+
+def make_pool():
+    n = host_cores()
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"          # one BLAS thread per worker: the pool already uses every core
+    pool = ctx.Pool(n)
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    pool.map(_warm_worker, range(n))
+    return pool, n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pool, cores = make_pool()
+    s = synth.SYSTEMS[args.workload]
+    sample = max(64, args.cpu_sample // 3)
+    for _ in range(args.warmup):
+        oracle_sweep_sample(args.workload, sample, pool)
+    vals, secs = [], []
+    for k in range(args.steps):
+        r = oracle_sweep_sample(args.workload, sample, pool, seed=11 + k)
+        vals.append(r["value"])
+        secs.append(r["sweep_s_extrapolated"])
+    pool.close()
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {s.n} orbitals ({s.nocc} occ), all (3,3) spaces", "precision": "fp64",
+                   "note": "each step: full oracle dressing + a seeded sample of spaces solved on all host cores; "
+                           "sweep time extrapolated linearly in the number of spaces"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} spaces per step of {r['nspaces']} + full dressing, extrapolated"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU leg ---------------------------------------------------------------------------------------
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = cores = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pool, cores = make_pool()   # before the first GPU call
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2606_04186_gb300 import qflow
+    qflow.lib()
+    name = args.workload
+    s = synth.SYSTEMS[name]
+    eps, h, g, sp = synth.system_inputs(name)
+    no, nv = s.nocc, s.n - s.nocc
+    log(f"inputs ready: {name}, {len(sp)} spaces")
+    t_init = time.perf_counter()
+    fl = qflow.Flow(h, g, no, sp, precision=args.precision)
+    t_init = time.perf_counter() - t_init
+    stream = torch.cuda.ExternalStream(fl.stream())
+    log(f"init {t_init:.1f} s")
+    # every timed step is the third sweep of the flow: the pool after two sweeps from empty is
+    # restored before each step (outside the timed events)
+    e_hist = []
+    for _ in range(2):
+        fl.sweep(raise_on_fail=False)
+        e_hist.append(fl.energy())
+        log(f"sweep {len(e_hist)}: E = {e_hist[-1]:.10f}, phases {fl.last_sweep_info()[0]}")
+    p2 = fl.amplitudes()
+    for _ in range(max(3, args.warmup)):
+        fl.set_amplitudes(*p2)
+        fl.sweep(raise_on_fail=False)
+    e3 = fl.energy()
+    log(f"warm-up done: sweep-3 E = {e3:.10f}, phases {fl.last_sweep_info()[0]}")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    phases, launches, codes = [], 0, []
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            fl.set_amplitudes(*p2)
+            starts[k].record(stream)
+            de, dt, nf, code = fl.sweep(raise_on_fail=False)
+            ends[k].record(stream)
+            codes.append(code)
+            ph, nl = fl.last_sweep_info()
+            phases.append(ph)
+            launches += nl
+        barrier()
+    elapsed_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    log(f"timed {args.steps} sweeps: {elapsed_ms:.1f} ms")
+    it, st = fl.stats()
+    e_mean = fl.energy()
+    if dist is not None:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    sweep_ms = elapsed_ms / args.steps
+    value = world * len(sp) / (sweep_ms / 1e3)
+    ph = np.array(phases)
+    solve_ms = float(ph[:, 1].mean())
+    flops = solver_flops(it.astype(np.int64))
+    achieved = flops / (solve_ms / 1e3) / 1e12
+    peak = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
+
+    # end-to-end through the public API with host buffers: pool H2D (pinned), sweep,
+    # per-space energies + pool D2H, every step
+    t1h = torch.empty((no, nv), dtype=torch.float64).pin_memory()
+    t2h = torch.empty((no, no, nv, nv), dtype=torch.float64).pin_memory()
+    t1h.numpy()[...] = p2[0]
+    t2h.numpy()[...] = p2[1]
+    ebuf = torch.empty(len(sp), dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        qflow.lib().qflow_set_amplitudes(fl._h, t1h.data_ptr(), t2h.data_ptr())
+        fl.sweep(raise_on_fail=False)
+        ec = qflow.C.c_double()
+        qflow.lib().qflow_energy(fl._h, qflow.C.byref(ec), ebuf.data_ptr())
+        qflow.lib().qflow_amplitudes(fl._h, t1h.data_ptr(), t2h.data_ptr())
+        t1h.numpy()[...] = p2[0]   # next step starts from the same pool again (host side, untimed work
+        t2h.numpy()[...] = p2[1]   # of a few MB; part of the end-to-end wall time)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
+    log(f"e2e {e2e_s:.3f} s per step")
+    pool_bytes = 8 * (t1h.numel() + t2h.numel())
+    fl.close()
+
+    # plain FP64 GPU form of the same sweep (pool after the same number of sweeps as the first
+    # warm-up of the mixed run: compare energies after sweep 2)
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision == "mixed":
+        f64 = qflow.Flow(h, g, no, sp, precision="fp64")
+        s64 = torch.cuda.ExternalStream(f64.stream())
+        ms = []
+        for k in range(args.fp64_steps):
+            f64.set_amplitudes(*p2)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a.record(s64)
+            f64.sweep(raise_on_fail=False)
+            b.record(s64)
+            barrier()
+            ms.append(a.elapsed_time(b))
+            log(f"fp64 sweep: {ms[-1]:.1f} ms, phases {f64.last_sweep_info()[0]}")
+        ms64 = statistics.median(ms)
+        e64 = f64.energy()
+        ph64, _ = f64.last_sweep_info()
+        it64, _ = f64.stats()
+        fp64 = {"sweep_s": ms64 / 1e3, "spaces_per_s": len(sp) / (ms64 / 1e3), "solve_ms": float(ph64[1]),
+                "dress_ms": float(ph64[0]), "davidson_iters_mean": float(it64.mean()),
+                "solve_tflops": solver_flops(it64.astype(np.int64)) / (ph64[1] / 1e3) / 1e12,
+                "e_sweep3": e64, "mixed_minus_fp64_e_sweep3": e3 - e64}
+        f64.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if pool is not None:
+        log("oracle sample")
+        r = oracle_sweep_sample(name, args.cpu_sample, pool)
+        log(f"oracle: {r}")
+        pool.close()
+        cpu = {"value": r["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"full dressing + {r['sample']} of {r['nspaces']} spaces on a spawn pool, sweep time "
+                         f"extrapolated ({r['sweep_s_extrapolated']:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": sweep_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} (3,3) spaces",
+                   "precision": args.precision, "sweep_s": sweep_ms / 1e3, "l2": "inputs larger than L2 (W = "
+                   f"{8 * s.n ** 4 / 1e6:.0f} MB)", "replicas": world, "e_sweep3": e_mean,
+                   "step": "third sweep of the flow (pool after two sweeps restored before each step)",
+                   "init_s": t_init},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": f"solve_kernel<3,{'float' if args.precision == 'mixed' else 'double'}>",
+                     "flops_per_launch": flops, "launch_ms": solve_ms,
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "mixed"
+                     else "GB300 FP64 nominal"},
+        "phase_ms": {"dress": float(ph[:, 0].mean()), "solve": solve_ms, "merge": float(ph[:, 2].mean())},
+        "davidson_iters_mean": float(it.mean()), "failed_spaces": int((st != 0).sum()),
+        "sweep_codes": sorted(set(int(c) for c in codes)),
+        "fp64_form": fp64,
+        "speedup_vs_fp64": (fp64["sweep_s"] / (sweep_ms / 1e3)) if fp64 else None,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * len(sp) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": pool_bytes,
+                "d2h_bytes_per_step": pool_bytes + 8 * len(sp), "sweep_s": e2e_s},
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

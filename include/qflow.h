@@ -1,0 +1,185 @@
+/*
+ * qflow.h -- C ABI of the GB300-native singles-and-doubles Quantum Flow sweep.
+ *
+ * The paper (arXiv 2606.04186) defines one flow cycle as: downfold the Hamiltonian into every
+ * active space with the current global amplitude pool (Eqs. 5-8, N = 1), solve each space,
+ * write the amplitudes each space owns back into the pool, barrier (Numerical
+ * Implementation).  This library runs that cycle on one GPU:
+ *   (a) dressing: H-bar = e^{-T} H e^{T} (SES-CC reading of the flow's sigma), normal ordered
+ *       with respect to the closed-shell reference, truncated to <= two-body: E0, F[n][n],
+ *       W[n][n][n][n] with W[p][q][r][s] = coefficient of {E_pq E_rs}/2 (creators p, r;
+ *       annihilators q, s; pair symmetry W[p][q][r][s] = W[r][s][p][q]);
+ *   (b) per space: gather the active block of (E0, F, W), fold the active occupied orbitals
+ *       (rewrite relative to the space's vacuum), find the Phi-dominant right eigenpair of the
+ *       determinant operator (Sz = 0) with a batched Davidson solver;
+ *   (c) per space: increment X1 = C1, X2 = C2 - C1*C1 from the normalised CI vector; every
+ *       amplitude takes t_old + X from its owner space only (first space in ascending
+ *       Delta-eps order that contains all its indices; Jacobi sweep); E_QFlow = mean E(i).
+ *
+ * Conventions used by every entry point
+ *   n       spatial orbitals (1 <= n <= 128), orbitals 0..nocc-1 doubly occupied.
+ *   h       [n][n] row-major FP64 core Hamiltonian.
+ *   eri     [n][n][n][n] row-major FP64 two-electron integrals (pq|rs), chemists' order.
+ *   t1      [nocc][nvir] FP64, t1[i][a] = t_i^a (a counted from nocc).
+ *   t2      [nocc][nocc][nvir][nvir] FP64 alpha-beta amplitude t_ij^ab = t2[i][j][a][b];
+ *           the library keeps t2[i][j][a][b] == t2[j][i][b][a].
+ *   spaces  qflow_space[nspaces]; (no, nv) in {(1,1), (2,2), (3,3)}; orb[] holds the no
+ *           occupied then the nv virtual absolute orbital indices, each group strictly
+ *           ascending; unused slots are -1.
+ *
+ * Errors: every int-returning call returns QFLOW_OK (0) or a negative qflow_status; nothing
+ * throws across the ABI.  QFLOW_WARN_UNCOVERED (a positive bit) is or-ed into the return of
+ * qflow_init / qflow_plan when some amplitude has no owner (it keeps its value).
+ * Ownership: the library copies every input at the call; output buffers are owned by the
+ * caller.  A handle owns all its device memory and one CUDA stream; it is not thread safe.
+ */
+#ifndef QFLOW_H
+#define QFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QFLOW_OK = 0,
+  QFLOW_ERR_ARG = -1,        /* invalid argument (sizes, space list, null pointer)        */
+  QFLOW_ERR_CUDA = -2,       /* a CUDA runtime call failed                                 */
+  QFLOW_ERR_OOM = -3,        /* device allocation failed                                   */
+  QFLOW_ERR_NOCONV = -4,     /* some space's Davidson solver hit its iteration limit       */
+  QFLOW_ERR_ROOT = -5,       /* selected root complex or |c_Phi| < 1e-3                    */
+  QFLOW_ERR_NONFINITE = -6,  /* NaN/Inf in an energy or amplitude                          */
+  QFLOW_ERR_STATE = -7,      /* call out of order (e.g. energy before the first sweep)     */
+  QFLOW_WARN_UNCOVERED = 1   /* bit: some amplitudes have no owner space                   */
+} qflow_status;
+
+typedef enum {
+  QFLOW_PREC_FP64 = 0,   /* plain: every step in FP64                                        */
+  QFLOW_PREC_MIXED = 1   /* FP32 sigma-vectors and 400-length vector algebra, FP64 projected
+                            eigenproblem, FP64 dressing, energy and amplitude update          */
+} qflow_precision;
+
+typedef struct {
+  int32_t no, nv;
+  int32_t orb[6];
+} qflow_space;
+
+typedef struct {
+  int32_t precision;          /* qflow_precision                                            */
+  int32_t max_iter;           /* Davidson iteration limit per space (default 60)            */
+  double tol;                 /* Davidson residual 2-norm (default 1e-9 fp64, 1e-6 mixed)   */
+  int32_t diis;               /* 0 = off, else DIIS history length on the pool (<= 8)       */
+  int32_t guess;              /* 0 = Phi, 1 = previous sweep's root of the same space (keeps
+                                 one CI vector per space on the device: 400 x 4 B per 6e6o
+                                 space in mixed precision, x 8 B in FP64)                   */
+  int32_t reserved[8];
+} qflow_options;
+
+/* Fill *opt with the defaults above for the given precision. */
+void qflow_default_options(qflow_options* opt, int32_t precision);
+
+/* ---- host-only planning (no GPU needed) ------------------------------------------------- */
+
+/* Order and ownership of a space list (Algorithm 1's final sort; owner rule of the Numerical
+ * Implementation).  eps_p = h_pp + sum_{k<nocc} [2 (pp|kk) - (pk|kp)] summed k ascending;
+ * Delta-eps = (sum eps_v, ascending) - (sum eps_o, ascending); ties broken by size class,
+ * occupied tuple, virtual tuple, input position.
+ *   perm[nspaces]                      out: sorted position -> input index
+ *   owner1[nocc*nvir]                  out: sorted index of the owner of t1[i][a], or -1
+ *   owner2[nocc*nocc*nvir*nvir]        out: owner of t2[i][j][a][b] (== owner of t2[j][i][b][a])
+ *   n_uncovered                        out (nullable): amplitudes with no owner
+ * Any output pointer may be NULL except perm. */
+int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
+               int64_t nspaces, int64_t* perm, int32_t* owner1, int32_t* owner2, int64_t* n_uncovered);
+
+/* ---- handle API: one flow on one GPU ---------------------------------------------------- */
+
+typedef struct qflow_ctx* qflow_handle;
+
+/* Copy h, eri (host pointers) and the space list to the current CUDA device, plan the sweep,
+ * start from an empty pool.  opt may be NULL (plain FP64, Jacobi, no DIIS, Phi guess). */
+int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n, int32_t nocc,
+               const qflow_space* spaces, int64_t nspaces, const qflow_options* opt);
+
+/* One sweep (barrier to barrier).  Outputs (nullable): change of E_QFlow since the previous
+ * sweep (+inf after the first), max |t_new - t_old| over the pool, number of spaces whose
+ * solver did not finish with status 0.  Returns QFLOW_ERR_NOCONV / ROOT / NONFINITE when some
+ * space failed (its owned amplitudes then keep their old value). */
+int qflow_sweep(qflow_handle hnd, double* d_e, double* max_dt, int32_t* nfailed);
+
+/* E_QFlow of the last sweep and (nullable) the per-space energies in sorted order. */
+int qflow_energy(qflow_handle hnd, double* e_mean, double* e_per_space);
+
+/* Copy the pool to host buffers t1[nocc*nvir], t2[nocc*nocc*nvir*nvir]. */
+int qflow_amplitudes(qflow_handle hnd, double* t1, double* t2);
+
+/* Overwrite the pool from host buffers (warm start, fixed-point tests). */
+int qflow_set_amplitudes(qflow_handle hnd, const double* t1, const double* t2);
+
+/* Sorted position -> caller's input index (int64[nspaces]). */
+int qflow_space_order(qflow_handle hnd, int64_t* perm);
+
+/* Per-space solver diagnostics of the last sweep, sorted order (nullable outputs):
+ * Davidson iterations and status (0 ok, 1 no convergence, 2 root, 3 non-finite,
+ * 4 invalid space). */
+int qflow_space_stats(qflow_handle hnd, int32_t* iterations, int32_t* status);
+
+/* The dressed integrals of the current pool (what the next sweep will use): e0 (1),
+ * F[n*n], W[n^4] copied to host buffers (any may be NULL). */
+int qflow_dressed(qflow_handle hnd, double* e0, double* F, double* W);
+
+/* Timing of the last sweep from CUDA events recorded on the handle's stream:
+ * phase_ms[3] = dressing, per-space solve, merge reductions (milliseconds); and the number
+ * of kernels the sweep launched.  Either output may be NULL. */
+int qflow_last_sweep_info(qflow_handle hnd, double* phase_ms, int64_t* kernel_launches);
+
+/* Stream the handle works on (a cudaStream_t). */
+void* qflow_stream(qflow_handle hnd);
+
+void qflow_destroy(qflow_handle hnd);
+const char* qflow_strerror(int code);
+
+/* ---- device-level steps (device pointers, caller-allocated, stream-ordered) --------------
+ * These run one step of the sweep on buffers the caller owns.  All pointers are device
+ * pointers except where noted; `stream` is a cudaStream_t (NULL = default stream).  The
+ * calls are asynchronous; errors of the launch are returned, errors of the kernels surface at
+ * the next synchronisation.                                                                 */
+
+/* Scratch bytes qflow_dress_device needs for n orbitals. */
+size_t qflow_dress_workspace(int32_t n, int32_t nocc);
+
+/* Step (a): e0[1], F[n*n], W[n^4] of H-bar_<=2 for the pool (t1, t2); FP64.
+ * work: qflow_dress_workspace(n, nocc) bytes of device scratch. */
+int qflow_dress_device(const double* h, const double* eri, const double* t1, const double* t2, int32_t n,
+                       int32_t nocc, double* e0, double* F, double* W, void* work, size_t work_bytes,
+                       void* stream);
+
+/* Steps (b)+(c) for a list of spaces of one size class (all (k,k), k = size_class in 1..3)
+ * given dressed integrals (e0, F, W) on the device:
+ *   spaces    qflow_space[nspaces] on the device (already in sorted order); a space whose
+ *             (no, nv) is not (k, k) or whose orbitals are out of range gets status 4 and is
+ *             skipped
+ *   owner1/2  int32 owner maps (sorted indices, see qflow_plan), device; may be NULL, then no
+ *             amplitude is written
+ *   space_base  sorted index of spaces[0] (owners are compared with space_base + k)
+ *   t1_old/t2_old  pool read by every space; t1_new/t2_new receive t_old + X for owned
+ *             amplitudes (the caller initialises them, e.g. with a copy of the old pool)
+ *   energy[nspaces], status[nspaces], iters[nspaces]: outputs (iters may be NULL)
+ *   guess     NULL or device [nspaces][C(2k,k)^2] start vectors in the path's working
+ *             precision (double for QFLOW_PREC_FP64, float for QFLOW_PREC_MIXED), any scale
+ *             (an all-zero vector means Phi); receives the converged root (Phi coefficient 1)
+ *             when save_root != 0
+ *   precision qflow_precision; max_iter, tol as in qflow_options. */
+int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* F, const double* W,
+                       int32_t size_class, const qflow_space* spaces, int64_t nspaces, int64_t space_base, const int32_t* owner1,
+                       const int32_t* owner2, const double* t1_old, const double* t2_old, double* t1_new,
+                       double* t2_new, double* energy, int32_t* status, int32_t* iters, void* guess,
+                       int32_t save_root, int32_t precision, int32_t max_iter, double tol, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFLOW_H */

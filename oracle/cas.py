@@ -162,3 +162,12 @@ def solve_space(e0: float, F: np.ndarray, W: np.ndarray, occ, vir):
     e, vec, status = phi_root(mat, phi)
     x1, x2 = increment(no, nv, vec)
     return e, x1, x2, status
+
+
+def solve_problem(no: int, nv: int, c: float, h: np.ndarray, w: np.ndarray):
+    """Energy, increment and status of one space given its folded (c, h, w) block."""
+    mat = cas_matrix(no, nv, c, h, w)
+    _, _, _, phi = coupling(no, nv)
+    e, vec, status = phi_root(mat, phi)
+    x1, x2 = increment(no, nv, vec)
+    return e, x1, x2, status

@@ -1,0 +1,439 @@
+// Step (a) of a flow sweep: the dressed one- and two-body integrals that define every active
+// space's downfolded Hamiltonian (Eqs. 5-8, N = 1, SES-CC reading):
+//   H-bar = e^{-T} H e^{T},  T = T1 + T2 = the current global amplitude pool,
+// normal ordered with respect to the closed-shell reference and truncated to <= two-body:
+//   E0, F[p][q], W[p][q][r][s] (creators p, r; annihilators q, s; W[pqrs] = W[rspq]).
+//
+// Construction (plain FP64, one thread per output element in every kernel):
+//   1. T1 exactly: orbital similarity transform of the integrals; creators by (1 - K),
+//      annihilators by (1 + K), K_ai = t_i^a (K^2 = 0) -> h~, g~ (four in-place passes).
+//   2. f~ = h~ + sum_k [2 g~_pqkk - g~_pkkq], E~ = <Phi|H~|Phi>.
+//   3. T2 through its connected contractions with H~ (one- and two-body parts of [H~, T2];
+//      the quadratic term 1/2 [[H~,T2],T2] only reaches the doubly excited (vo|vo) block).
+// Index names: occupied i j k l m n, virtual a b e f (absolute index nocc + a).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qflow_internal.h"
+
+namespace qf {
+namespace {
+
+struct Dims {
+  int n, o, v;
+};
+
+__device__ __forceinline__ size_t gi(const Dims& d, int p, int q, int r, int s) {
+  return (((size_t)p * d.n + q) * d.n + r) * d.n + s;
+}
+__device__ __forceinline__ size_t ti(const Dims& d, int i, int j, int a, int b) {
+  return (((size_t)i * d.o + j) * d.v + a) * d.v + b;
+}
+
+constexpr int TPB = 256;
+inline unsigned blocks_for(size_t m) { return (unsigned)((m + TPB - 1) / TPB); }
+
+__global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst, size_t m) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m; x += (size_t)gridDim.x * blockDim.x)
+    dst[x] = src[x];
+}
+
+// Creator index `pos` (0 or 2): rows p >= nocc get  - sum_i t1[i][p-nocc] * row_i.
+__global__ void k_t1_creator(double* __restrict__ W, const double* __restrict__ t1, Dims d, int pos) {
+  const size_t m = (size_t)d.v * d.n * d.n * d.n;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m; x += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(x / ((size_t)d.n * d.n * d.n));
+    const size_t rest = x % ((size_t)d.n * d.n * d.n);
+    const int u = (int)(rest / ((size_t)d.n * d.n)), w = (int)((rest / d.n) % d.n), z = (int)(rest % d.n);
+    double acc = 0.0;
+    if (pos == 0) {
+      for (int i = 0; i < d.o; ++i) acc += t1[i * d.v + a] * W[gi(d, i, u, w, z)];
+      W[gi(d, d.o + a, u, w, z)] -= acc;
+    } else {
+      for (int i = 0; i < d.o; ++i) acc += t1[i * d.v + a] * W[gi(d, u, w, i, z)];
+      W[gi(d, u, w, d.o + a, z)] -= acc;
+    }
+  }
+}
+
+// Annihilator index `pos` (1 or 3): rows q < nocc get  + sum_a t1[q][a] * row_(nocc+a).
+__global__ void k_t1_annihilator(double* __restrict__ W, const double* __restrict__ t1, Dims d, int pos) {
+  const size_t m = (size_t)d.o * d.n * d.n * d.n;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m; x += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(x / ((size_t)d.n * d.n * d.n));
+    const size_t rest = x % ((size_t)d.n * d.n * d.n);
+    const int u = (int)(rest / ((size_t)d.n * d.n)), w = (int)((rest / d.n) % d.n), z = (int)(rest % d.n);
+    double acc = 0.0;
+    if (pos == 1) {
+      for (int a = 0; a < d.v; ++a) acc += t1[q * d.v + a] * W[gi(d, u, d.o + a, w, z)];
+      W[gi(d, u, q, w, z)] += acc;
+    } else {
+      for (int a = 0; a < d.v; ++a) acc += t1[q * d.v + a] * W[gi(d, u, w, z, d.o + a)];
+      W[gi(d, u, w, z, q)] += acc;
+    }
+  }
+}
+
+// h~ = (1 - K) h (1 + K)
+__global__ void k_h_tilde(const double* __restrict__ h, const double* __restrict__ t1, double* __restrict__ ht, Dims d) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.n * d.n) return;
+  const int r = x / d.n, s = x % d.n;
+  // (h (1+K))_{p s} = h_ps + [s occ] sum_a h_{p,nocc+a} t1[s][a]
+  auto hk = [&](int p) {
+    double v = h[p * d.n + s];
+    if (s < d.o)
+      for (int a = 0; a < d.v; ++a) v += h[p * d.n + d.o + a] * t1[s * d.v + a];
+    return v;
+  };
+  double v = hk(r);
+  if (r >= d.o)
+    for (int i = 0; i < d.o; ++i) v -= t1[i * d.v + (r - d.o)] * hk(i);
+  ht[x] = v;
+}
+
+// f~ = h~ + sum_k [2 g~_pqkk - g~_pkkq]
+__global__ void k_fock(const double* __restrict__ ht, const double* __restrict__ W, double* __restrict__ F, Dims d) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.n * d.n) return;
+  const int p = x / d.n, q = x % d.n;
+  double v = ht[x];
+  for (int k = 0; k < d.o; ++k) v += 2.0 * W[gi(d, p, q, k, k)] - W[gi(d, p, k, k, q)];
+  F[x] = v;
+}
+
+// E0 = sum_k 2 h~_kk + sum_kl [2 g~_kkll - g~_kllk] + sum_ijab g~_iajb (2 t_ij^ab - t_ij^ba).
+// One block; fixed-order reduction.
+__global__ void k_energy(const double* __restrict__ ht, const double* __restrict__ W, const double* __restrict__ t2,
+                         double* __restrict__ e0, Dims d) {
+  __shared__ double red[TPB];
+  double acc = 0.0;
+  const size_t m = (size_t)d.o * d.o * d.v * d.v;
+  for (size_t x = threadIdx.x; x < m; x += blockDim.x) {
+    const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
+    const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
+    acc += W[gi(d, i, d.o + a, j, d.o + b)] * (2.0 * t2[x] - t2[ti(d, i, j, b, a)]);
+  }
+  for (int x = threadIdx.x; x < d.o * d.o; x += blockDim.x) {
+    const int k = x / d.o, l = x % d.o;
+    acc += 2.0 * W[gi(d, k, k, l, l)] - W[gi(d, k, l, l, k)];
+  }
+  for (int k = threadIdx.x; k < d.o; k += blockDim.x) acc += 2.0 * ht[k * d.n + k];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *e0 = red[0];
+}
+
+// u = 2 t_ij^ab - t_ij^ba
+__device__ __forceinline__ double U(const double* t2, const Dims& d, int i, int j, int a, int b) {
+  return 2.0 * t2[ti(d, i, j, a, b)] - t2[ti(d, i, j, b, a)];
+}
+
+// Foo[m][i] = f~_mi + sum_nef g~_menf u_in^ef ;  Fvv[a][e] = f~_ae - sum_mnf g~_menf u_mn^af
+__global__ void k_foo_fvv(const double* __restrict__ F, const double* __restrict__ W, const double* __restrict__ t2,
+                          double* __restrict__ foo, double* __restrict__ fvv, Dims d) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < d.o * d.o) {
+    const int m = x / d.o, i = x % d.o;
+    double v = F[m * d.n + i];
+    for (int nn = 0; nn < d.o; ++nn)
+      for (int e = 0; e < d.v; ++e)
+        for (int f = 0; f < d.v; ++f) v += W[gi(d, m, d.o + e, nn, d.o + f)] * U(t2, d, i, nn, e, f);
+    foo[x] = v;
+  } else if (x < d.o * d.o + d.v * d.v) {
+    const int y = x - d.o * d.o, a = y / d.v, e = y % d.v;
+    double v = F[(d.o + a) * d.n + d.o + e];
+    for (int m = 0; m < d.o; ++m)
+      for (int nn = 0; nn < d.o; ++nn)
+        for (int f = 0; f < d.v; ++f) v -= W[gi(d, m, d.o + e, nn, d.o + f)] * U(t2, d, m, nn, a, f);
+    fvv[y] = v;
+  }
+}
+
+// Woooo[k][i][l][j] = g~_kilj + sum_ef g~_kelf t_ij^ef
+__global__ void k_woooo(const double* __restrict__ W, const double* __restrict__ t2, double* __restrict__ wo, Dims d) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.o * d.o * d.o * d.o) return;
+  const int k = x / (d.o * d.o * d.o), i = (x / (d.o * d.o)) % d.o, l = (x / d.o) % d.o, j = x % d.o;
+  double v = W[gi(d, k, i, l, j)];
+  for (int e = 0; e < d.v; ++e)
+    for (int f = 0; f < d.v; ++f) v += W[gi(d, k, d.o + e, l, d.o + f)] * t2[ti(d, i, j, e, f)];
+  wo[x] = v;
+}
+
+// R1[a][i] = f~_ai + sum_me f~_me u_im^ae + sum_mef g~_aemf u_im^ef - sum_mne g~_mine u_mn^ae
+__global__ void k_r1(const double* __restrict__ F, const double* __restrict__ W, const double* __restrict__ t2,
+                     double* __restrict__ r1, Dims d) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.v * d.o) return;
+  const int a = x / d.o, i = x % d.o;
+  double v = F[(d.o + a) * d.n + i];
+  for (int m = 0; m < d.o; ++m)
+    for (int e = 0; e < d.v; ++e) {
+      v += F[m * d.n + d.o + e] * U(t2, d, i, m, a, e);
+      for (int f = 0; f < d.v; ++f) v += W[gi(d, d.o + a, d.o + e, m, d.o + f)] * U(t2, d, i, m, e, f);
+      for (int nn = 0; nn < d.o; ++nn) v -= W[gi(d, m, i, nn, d.o + e)] * U(t2, d, m, nn, a, e);
+    }
+  r1[x] = v;
+}
+
+// Ring intermediates for the quadratic doubles terms, each [i][a][n][f] (o v o v):
+//   A = sum_me u_im^ae g~_menf,  B = sum_me u_im^ae g~_mfne,  Cq = sum_me t_im^ae g~_mfne,
+//   D[j][a][n][f] = sum_me t_jm^ea g~_mfne
+__global__ void k_rings(const double* __restrict__ W, const double* __restrict__ t2, double* __restrict__ A,
+                        double* __restrict__ B, double* __restrict__ Cq, double* __restrict__ D, Dims d) {
+  const size_t m_all = (size_t)d.o * d.v * d.o * d.v;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int i = (int)(x / ((size_t)d.v * d.o * d.v)), a = (int)((x / ((size_t)d.o * d.v)) % d.v);
+  const int nn = (int)((x / d.v) % d.o), f = (int)(x % d.v);
+  double sa = 0, sb = 0, sc = 0, sd = 0;
+  for (int m = 0; m < d.o; ++m)
+    for (int e = 0; e < d.v; ++e) {
+      const double g1 = W[gi(d, m, d.o + e, nn, d.o + f)];
+      const double g2 = W[gi(d, m, d.o + f, nn, d.o + e)];
+      const double t = t2[ti(d, i, m, a, e)];
+      const double u = 2.0 * t - t2[ti(d, i, m, e, a)];
+      sa += u * g1;
+      sb += u * g2;
+      sc += t * g2;
+      sd += t2[ti(d, i, m, e, a)] * g2;
+    }
+  A[x] = sa;
+  B[x] = sb;
+  Cq[x] = sc;
+  D[x] = sd;
+}
+
+// R2[i][j][a][b] = <Phi_{ij}^{ab}|H-bar|Phi> (alpha-beta), from bare g~ blocks and dressed
+// Foo, Fvv, Woooo.
+__global__ void k_r2(const double* __restrict__ W, const double* __restrict__ t2, const double* __restrict__ foo,
+                     const double* __restrict__ fvv, const double* __restrict__ wo, const double* __restrict__ A,
+                     const double* __restrict__ B, const double* __restrict__ Cq, const double* __restrict__ D,
+                     double* __restrict__ r2, Dims d) {
+  const size_t m_all = (size_t)d.o * d.o * d.v * d.v;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
+  const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
+  const int A_ = d.o + a, B_ = d.o + b;
+  double v = W[gi(d, A_, i, B_, j)];
+  for (int e = 0; e < d.v; ++e)
+    v += fvv[b * d.v + e] * t2[ti(d, i, j, a, e)] + fvv[a * d.v + e] * t2[ti(d, i, j, e, b)];
+  for (int m = 0; m < d.o; ++m)
+    v -= foo[m * d.o + j] * t2[ti(d, i, m, a, b)] + foo[m * d.o + i] * t2[ti(d, m, j, a, b)];
+  for (int m = 0; m < d.o; ++m)
+    for (int nn = 0; nn < d.o; ++nn) v += wo[((m * d.o + i) * d.o + nn) * d.o + j] * t2[ti(d, m, nn, a, b)];
+  // particle-particle ladder
+  for (int e = 0; e < d.v; ++e)
+    for (int f = 0; f < d.v; ++f) v += W[gi(d, A_, d.o + e, B_, d.o + f)] * t2[ti(d, i, j, e, f)];
+  // linear rings
+  for (int m = 0; m < d.o; ++m)
+    for (int e = 0; e < d.v; ++e) {
+      const int E_ = d.o + e;
+      v += W[gi(d, m, E_, B_, j)] * U(t2, d, i, m, a, e);
+      v -= W[gi(d, m, j, B_, E_)] * t2[ti(d, i, m, a, e)];
+      v -= W[gi(d, m, i, B_, E_)] * t2[ti(d, j, m, e, a)];
+      v -= W[gi(d, m, j, A_, E_)] * t2[ti(d, i, m, e, b)];
+      v += W[gi(d, m, E_, A_, i)] * U(t2, d, j, m, b, e);
+      v -= W[gi(d, m, i, A_, E_)] * t2[ti(d, j, m, b, e)];
+    }
+  // quadratic rings through the intermediates
+  const size_t ovov_i = (size_t)d.v * d.o * d.v, ovov_a = (size_t)d.o * d.v;
+  for (int nn = 0; nn < d.o; ++nn)
+    for (int f = 0; f < d.v; ++f) {
+      const size_t ia = i * ovov_i + a * ovov_a + (size_t)nn * d.v + f;
+      const size_t ja = j * ovov_i + a * ovov_a + (size_t)nn * d.v + f;
+      v += A[ia] * U(t2, d, j, nn, b, f) - B[ia] * t2[ti(d, j, nn, b, f)] + Cq[ia] * t2[ti(d, j, nn, f, b)] +
+           D[ja] * t2[ti(d, i, nn, f, b)];
+    }
+  r2[x] = v;
+}
+
+// W[a,e,b,f] += sum_mn g~_menf t_mn^ab  (vvvv block, in place; reads only the ovov block)
+__global__ void k_vvvv(double* __restrict__ W, const double* __restrict__ t2, Dims d) {
+  const size_t m_all = (size_t)d.v * d.v * d.v * d.v;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int a = (int)(x / ((size_t)d.v * d.v * d.v)), e = (int)((x / ((size_t)d.v * d.v)) % d.v);
+  const int b = (int)((x / d.v) % d.v), f = (int)(x % d.v);
+  double v = 0.0;
+  for (int m = 0; m < d.o; ++m)
+    for (int nn = 0; nn < d.o; ++nn) v += W[gi(d, m, d.o + e, nn, d.o + f)] * t2[ti(d, m, nn, a, b)];
+  W[gi(d, d.o + a, d.o + e, d.o + b, d.o + f)] += v;
+}
+
+// (ov|vo) and its pair partner (vo|ov):
+//   W[m,e,b,j] = g~_mebj + sum_nf g~_menf u_jn^bf - sum_nf g~_mfne t_jn^bf
+__global__ void k_ovvo(double* __restrict__ W, const double* __restrict__ t2, Dims d) {
+  const size_t m_all = (size_t)d.o * d.v * d.v * d.o;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int m = (int)(x / ((size_t)d.v * d.v * d.o)), e = (int)((x / ((size_t)d.v * d.o)) % d.v);
+  const int b = (int)((x / d.o) % d.v), j = (int)(x % d.o);
+  double v = W[gi(d, m, d.o + e, d.o + b, j)];
+  for (int nn = 0; nn < d.o; ++nn)
+    for (int f = 0; f < d.v; ++f)
+      v += W[gi(d, m, d.o + e, nn, d.o + f)] * U(t2, d, j, nn, b, f) -
+           W[gi(d, m, d.o + f, nn, d.o + e)] * t2[ti(d, j, nn, b, f)];
+  W[gi(d, m, d.o + e, d.o + b, j)] = v;
+  W[gi(d, d.o + b, j, m, d.o + e)] = v;
+}
+
+// (oo|vv) and (vv|oo):  W[i,j,a,b] = g~_ijab - sum_nf g~_ifnb t_jn^fa
+__global__ void k_oovv(double* __restrict__ W, const double* __restrict__ t2, Dims d) {
+  const size_t m_all = (size_t)d.o * d.o * d.v * d.v;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
+  const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
+  double v = W[gi(d, i, j, d.o + a, d.o + b)];
+  for (int nn = 0; nn < d.o; ++nn)
+    for (int f = 0; f < d.v; ++f) v -= W[gi(d, i, d.o + f, nn, d.o + b)] * t2[ti(d, j, nn, f, a)];
+  W[gi(d, i, j, d.o + a, d.o + b)] = v;
+  W[gi(d, d.o + a, d.o + b, i, j)] = v;
+}
+
+// (oo|vo) and (vo|oo):
+//   W[m,i,b,j] = g~_mibj + sum_e f~_me t_ij^eb + sum_ef g~_mebf t_ij^ef
+//              + sum_ne [g~_mine u_jn^be - g~_meni t_jn^be - g~_menj t_in^eb]
+__global__ void k_oovo(double* __restrict__ W, const double* __restrict__ F, const double* __restrict__ t2, Dims d) {
+  const size_t m_all = (size_t)d.o * d.o * d.v * d.o;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int m = (int)(x / ((size_t)d.o * d.v * d.o)), i = (int)((x / ((size_t)d.v * d.o)) % d.o);
+  const int b = (int)((x / d.o) % d.v), j = (int)(x % d.o);
+  const int B_ = d.o + b;
+  double v = W[gi(d, m, i, B_, j)];
+  for (int e = 0; e < d.v; ++e) {
+    const int E_ = d.o + e;
+    v += F[m * d.n + E_] * t2[ti(d, i, j, e, b)];
+    for (int f = 0; f < d.v; ++f) v += W[gi(d, m, E_, B_, d.o + f)] * t2[ti(d, i, j, e, f)];
+    for (int nn = 0; nn < d.o; ++nn)
+      v += W[gi(d, m, i, nn, E_)] * U(t2, d, j, nn, b, e) - W[gi(d, m, E_, nn, i)] * t2[ti(d, j, nn, b, e)] -
+           W[gi(d, m, E_, nn, j)] * t2[ti(d, i, nn, e, b)];
+  }
+  W[gi(d, m, i, B_, j)] = v;
+  W[gi(d, B_, j, m, i)] = v;
+}
+
+// (vv|vo) and (vo|vv):
+//   W[a,e,b,i] = g~_aebi - sum_m f~_me t_mi^ab + sum_mn g~_meni t_mn^ab
+//              + sum_mf [g~_mfae u_mi^fb - g~_mebf t_mi^af - g~_meaf t_mi^fb]
+__global__ void k_vvvo(double* __restrict__ W, const double* __restrict__ F, const double* __restrict__ t2, Dims d) {
+  const size_t m_all = (size_t)d.v * d.v * d.v * d.o;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int a = (int)(x / ((size_t)d.v * d.v * d.o)), e = (int)((x / ((size_t)d.v * d.o)) % d.v);
+  const int b = (int)((x / d.o) % d.v), i = (int)(x % d.o);
+  const int A_ = d.o + a, E_ = d.o + e, B_ = d.o + b;
+  double v = W[gi(d, A_, E_, B_, i)];
+  for (int m = 0; m < d.o; ++m) {
+    v -= F[m * d.n + E_] * t2[ti(d, m, i, a, b)];
+    for (int nn = 0; nn < d.o; ++nn) v += W[gi(d, m, E_, nn, i)] * t2[ti(d, m, nn, a, b)];
+    for (int f = 0; f < d.v; ++f) {
+      const int F_ = d.o + f;
+      v += W[gi(d, m, F_, A_, E_)] * U(t2, d, m, i, f, b) - W[gi(d, m, E_, B_, F_)] * t2[ti(d, m, i, a, f)] -
+           W[gi(d, m, E_, A_, F_)] * t2[ti(d, m, i, f, b)];
+    }
+  }
+  W[gi(d, A_, E_, B_, i)] = v;
+  W[gi(d, B_, i, A_, E_)] = v;
+}
+
+// Write the dressed oooo, vo|vo blocks and the oo / vv / vo Fock blocks.
+__global__ void k_finalize(double* __restrict__ W, double* __restrict__ F, const double* __restrict__ foo,
+                           const double* __restrict__ fvv, const double* __restrict__ r1, const double* __restrict__ wo,
+                           const double* __restrict__ r2, Dims d) {
+  const size_t n_r2 = (size_t)d.o * d.o * d.v * d.v;
+  const size_t n_wo = (size_t)d.o * d.o * d.o * d.o;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x < n_r2) {
+    const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
+    const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
+    W[gi(d, d.o + a, i, d.o + b, j)] = r2[x];
+  } else if (x < n_r2 + n_wo) {
+    const int y = (int)(x - n_r2);
+    const int k = y / (d.o * d.o * d.o), i = (y / (d.o * d.o)) % d.o, l = (y / d.o) % d.o, j = y % d.o;
+    W[gi(d, k, i, l, j)] = wo[y];
+  } else if (x < n_r2 + n_wo + (size_t)d.o * d.o) {
+    const int y = (int)(x - n_r2 - n_wo);
+    F[(y / d.o) * d.n + (y % d.o)] = foo[y];
+  } else if (x < n_r2 + n_wo + (size_t)d.o * d.o + (size_t)d.v * d.v) {
+    const int y = (int)(x - n_r2 - n_wo - (size_t)d.o * d.o);
+    F[(d.o + y / d.v) * d.n + d.o + (y % d.v)] = fvv[y];
+  } else if (x < n_r2 + n_wo + (size_t)d.o * d.o + (size_t)d.v * d.v + (size_t)d.v * d.o) {
+    const int y = (int)(x - n_r2 - n_wo - (size_t)d.o * d.o - (size_t)d.v * d.v);
+    F[(d.o + y / d.o) * d.n + (y % d.o)] = r1[y];
+  }
+}
+
+struct Work {
+  double *ht, *foo, *fvv, *wo, *r1, *r2, *A, *B, *Cq, *D;
+};
+
+size_t carve(void* base, int n, int o, Work* w) {
+  const int v = n - o;
+  const size_t sizes[] = {(size_t)n * n, (size_t)o * o, (size_t)v * v, (size_t)o * o * o * o, (size_t)v * o,
+                          (size_t)o * o * v * v, (size_t)o * v * o * v, (size_t)o * v * o * v, (size_t)o * v * o * v,
+                          (size_t)o * v * o * v};
+  double** ptrs[] = {&w->ht, &w->foo, &w->fvv, &w->wo, &w->r1, &w->r2, &w->A, &w->B, &w->Cq, &w->D};
+  size_t off = 0;
+  for (int k = 0; k < 10; ++k) {
+    if (base) *ptrs[k] = reinterpret_cast<double*>(static_cast<char*>(base) + off);
+    off += ((sizes[k] * sizeof(double) + 255) / 256) * 256;
+  }
+  return off;
+}
+
+}  // namespace
+
+size_t dress_workspace_bytes(int n, int nocc) {
+  Work w;
+  return carve(nullptr, n, nocc, &w);
+}
+
+int dress_launch_count(int n, int nocc) { return (n - nocc > 0 && nocc > 0) ? 19 : 4; }
+
+cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
+                         double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st) {
+  Work w;
+  if (work_bytes < carve(nullptr, n, nocc, &w)) return cudaErrorInvalidValue;
+  carve(work, n, nocc, &w);
+  Dims d{n, nocc, n - nocc};
+  const size_t n4 = (size_t)n * n * n * n;
+  const size_t o = nocc, v = n - nocc;
+  k_copy<<<blocks_for(n4) > 65535u * 8 ? 65535u * 8 : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
+  if (v > 0 && o > 0) {
+    const size_t mc = v * n * n * n, ma = o * n * n * n;
+    k_t1_creator<<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
+    k_t1_creator<<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
+    k_t1_annihilator<<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
+    k_t1_annihilator<<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 3);
+  }
+  k_h_tilde<<<blocks_for((size_t)n * n), TPB, 0, st>>>(h, t1, w.ht, d);
+  k_fock<<<blocks_for((size_t)n * n), TPB, 0, st>>>(w.ht, W, F, d);
+  k_energy<<<1, TPB, 0, st>>>(w.ht, W, t2, e0, d);
+  if (v > 0 && o > 0) {
+    k_foo_fvv<<<blocks_for(o * o + v * v), TPB, 0, st>>>(F, W, t2, w.foo, w.fvv, d);
+    k_woooo<<<blocks_for(o * o * o * o), TPB, 0, st>>>(W, t2, w.wo, d);
+    k_r1<<<blocks_for(v * o), TPB, 0, st>>>(F, W, t2, w.r1, d);
+    k_rings<<<blocks_for(o * v * o * v), TPB, 0, st>>>(W, t2, w.A, w.B, w.Cq, w.D, d);
+    k_r2<<<blocks_for(o * o * v * v), TPB, 0, st>>>(W, t2, w.foo, w.fvv, w.wo, w.A, w.B, w.Cq, w.D, w.r2, d);
+    // blocks that read only unmodified bare blocks may now be overwritten
+    k_vvvv<<<blocks_for(v * v * v * v), TPB, 0, st>>>(W, t2, d);
+    k_ovvo<<<blocks_for(o * v * v * o), TPB, 0, st>>>(W, t2, d);
+    k_oovv<<<blocks_for(o * o * v * v), TPB, 0, st>>>(W, t2, d);
+    k_oovo<<<blocks_for(o * o * v * o), TPB, 0, st>>>(W, F, t2, d);
+    k_vvvo<<<blocks_for(v * v * v * o), TPB, 0, st>>>(W, F, t2, d);
+    const size_t nf = o * o * v * v + o * o * o * o + o * o + v * v + v * o;
+    k_finalize<<<blocks_for(nf), TPB, 0, st>>>(W, F, w.foo, w.fvv, w.r1, w.wo, w.r2, d);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace qf

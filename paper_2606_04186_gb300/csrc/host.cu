@@ -1,0 +1,531 @@
+// C ABI of the flow: planning (ordering + ownership), the handle that owns one flow's device
+// state, and the device-level step entry points.  Declarations and contracts: include/qflow.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <limits>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "qflow_internal.h"
+
+using qf::SolveArgs;
+
+namespace {
+
+// ---- validation and planning -------------------------------------------------------------
+
+int validate(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* sp, int64_t ns) {
+  if (!h || !eri || !sp || n < 2 || n > 128 || nocc < 1 || nocc >= n || ns < 0) return QFLOW_ERR_ARG;
+  for (int64_t k = 0; k < ns; ++k) {
+    const qflow_space& s = sp[k];
+    if (s.no != s.nv || s.no < 1 || s.no > 3 || s.no > nocc || s.nv > n - nocc) return QFLOW_ERR_ARG;
+    for (int t = 0; t < s.no + s.nv; ++t) {
+      const int o = s.orb[t];
+      const bool occ = t < s.no;
+      if (occ && (o < 0 || o >= nocc)) return QFLOW_ERR_ARG;
+      if (!occ && (o < nocc || o >= n)) return QFLOW_ERR_ARG;
+      if (t > 0 && t != s.no && s.orb[t - 1] >= o) return QFLOW_ERR_ARG;
+    }
+  }
+  return QFLOW_OK;
+}
+
+// eps_p = h_pp + sum_k [2 (pp|kk) - (pk|kp)], k ascending (no contraction: -ffp-contract=off).
+std::vector<double> fock_diagonal(const double* h, const double* eri, int n, int nocc) {
+  std::vector<double> e(n);
+  const size_t n1 = n, n2 = n1 * n1, n3 = n2 * n1;
+  for (int p = 0; p < n; ++p) {
+    double acc = h[(size_t)p * n + p];
+    for (int k = 0; k < nocc; ++k) {
+      const double j = eri[p * n3 + p * n2 + (size_t)k * n1 + k];
+      const double x = eri[p * n3 + (size_t)k * n2 + (size_t)k * n1 + p];
+      volatile double t = 2.0 * j;  // keep the FP64 rounding sequence of the definition
+      acc = acc + (t - x);
+    }
+    e[p] = acc;
+  }
+  return e;
+}
+
+struct Plan {
+  std::vector<int64_t> perm;
+  std::vector<int32_t> own1, own2;
+  int64_t uncovered = 0;
+};
+
+void make_plan(const double* h, const double* eri, int n, int nocc, const qflow_space* sp, int64_t ns, Plan* pl,
+               bool want_owners) {
+  const int nv = n - nocc;
+  std::vector<double> eps = fock_diagonal(h, eri, n, nocc);
+  std::vector<double> de(ns);
+  for (int64_t k = 0; k < ns; ++k) {
+    double sv = 0.0, so = 0.0;
+    for (int t = 0; t < sp[k].nv; ++t) sv = sv + eps[sp[k].orb[sp[k].no + t]];
+    for (int t = 0; t < sp[k].no; ++t) so = so + eps[sp[k].orb[t]];
+    de[k] = sv - so;
+  }
+  pl->perm.resize(ns);
+  std::iota(pl->perm.begin(), pl->perm.end(), (int64_t)0);
+  std::sort(pl->perm.begin(), pl->perm.end(), [&](int64_t a, int64_t b) {
+    if (de[a] != de[b]) return de[a] < de[b];
+    const qflow_space &x = sp[a], &y = sp[b];
+    if (x.no != y.no) return x.no < y.no;
+    for (int t = 0; t < x.no; ++t)
+      if (x.orb[t] != y.orb[t]) return x.orb[t] < y.orb[t];
+    for (int t = 0; t < x.nv; ++t)
+      if (x.orb[x.no + t] != y.orb[y.no + t]) return x.orb[x.no + t] < y.orb[y.no + t];
+    return a < b;
+  });
+  if (!want_owners) return;
+  pl->own1.assign((size_t)nocc * nv, -1);
+  pl->own2.assign((size_t)nocc * nocc * nv * nv, -1);
+  int64_t left = (int64_t)pl->own1.size() + (int64_t)pl->own2.size();
+  for (int64_t s = 0; s < ns && left > 0; ++s) {
+    const qflow_space& q = sp[pl->perm[s]];
+    for (int i = 0; i < q.no; ++i)
+      for (int a = 0; a < q.nv; ++a) {
+        int32_t& o = pl->own1[(size_t)q.orb[i] * nv + (q.orb[q.no + a] - nocc)];
+        if (o < 0) {
+          o = (int32_t)s;
+          --left;
+        }
+      }
+    for (int i = 0; i < q.no; ++i)
+      for (int j = 0; j < q.no; ++j)
+        for (int a = 0; a < q.nv; ++a)
+          for (int b = 0; b < q.nv; ++b) {
+            const int I = q.orb[i], J = q.orb[j], A = q.orb[q.no + a] - nocc, B = q.orb[q.no + b] - nocc;
+            int32_t& o = pl->own2[(((size_t)I * nocc + J) * nv + A) * nv + B];
+            if (o < 0) {
+              o = (int32_t)s;
+              --left;
+            }
+          }
+  }
+  pl->uncovered = 0;
+  for (int32_t o : pl->own1) pl->uncovered += (o < 0);
+  for (int32_t o : pl->own2) pl->uncovered += (o < 0);
+}
+
+}  // namespace
+
+// ---- handle --------------------------------------------------------------------------------
+
+struct qflow_ctx {
+  int32_t n = 0, nocc = 0, nvir = 0;
+  int64_t nspaces = 0;
+  qflow_options opt{};
+  cudaStream_t stream = nullptr;
+  std::vector<int64_t> perm;
+  int64_t cls_count[4] = {0, 0, 0, 0};  // spaces per size class k = 1..3 (grouped on device)
+  int64_t cls_off[4] = {0, 0, 0, 0};
+  // device buffers
+  double *h = nullptr, *eri = nullptr;
+  double *pool = nullptr, *pool_new = nullptr;  // [t1 | t2]
+  double *e0 = nullptr, *F = nullptr, *W = nullptr;
+  double* energy = nullptr;
+  int32_t *status = nullptr, *iters = nullptr;
+  int32_t *own1 = nullptr, *own2 = nullptr;
+  qflow_space* spaces = nullptr;  // grouped by class, sorted within a class
+  int64_t* sorted_index = nullptr;
+  void* dwork = nullptr;
+  size_t dwork_bytes = 0;
+  void* rwork = nullptr;
+  double* red = nullptr;  // [4] reduction results
+  double* red_host = nullptr;  // pinned
+  double e_mean = 0.0;
+  bool have_energy = false;
+  int64_t n_t1 = 0, n_t2 = 0;
+  void* guess[4] = {nullptr, nullptr, nullptr, nullptr};  // previous roots per size class (opt.guess == 1)
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase marks of the last sweep
+  int64_t last_launches = 0;                                  // kernels launched by the last sweep
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+}
+
+void free_ctx(qflow_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->h, c->eri, c->pool, c->pool_new, c->e0, c->F, c->W, c->energy, c->status, c->iters,
+                  c->own1, c->own2, c->spaces, c->sorted_index, c->dwork, c->rwork, c->red};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : c->guess)
+    if (p) cudaFree(p);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QFLOW_OK;
+  if (e == cudaErrorMemoryAllocation) return QFLOW_ERR_OOM;
+  return QFLOW_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qflow_default_options(qflow_options* opt, int32_t precision) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = precision;
+  opt->max_iter = 60;
+  opt->tol = (precision == QFLOW_PREC_MIXED) ? 1e-6 : 1e-9;
+  opt->diis = 0;
+  opt->guess = 0;
+}
+
+int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
+               int64_t nspaces, int64_t* perm, int32_t* owner1, int32_t* owner2, int64_t* n_uncovered) {
+  if (!perm) return QFLOW_ERR_ARG;
+  int v = validate(h, eri, n, nocc, spaces, nspaces);
+  if (v != QFLOW_OK) return v;
+  Plan pl;
+  try {
+    make_plan(h, eri, n, nocc, spaces, nspaces, &pl, owner1 || owner2 || n_uncovered);
+  } catch (const std::bad_alloc&) {
+    return QFLOW_ERR_OOM;
+  }
+  memcpy(perm, pl.perm.data(), sizeof(int64_t) * (size_t)nspaces);
+  if (owner1) memcpy(owner1, pl.own1.data(), sizeof(int32_t) * pl.own1.size());
+  if (owner2) memcpy(owner2, pl.own2.data(), sizeof(int32_t) * pl.own2.size());
+  if (n_uncovered) *n_uncovered = pl.uncovered;
+  return (pl.uncovered > 0) ? QFLOW_WARN_UNCOVERED : QFLOW_OK;
+}
+
+int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n, int32_t nocc,
+               const qflow_space* spaces, int64_t nspaces, const qflow_options* opt) {
+  if (!out) return QFLOW_ERR_ARG;
+  *out = nullptr;
+  int v = validate(h, eri, n, nocc, spaces, nspaces);
+  if (v != QFLOW_OK) return v;
+  qflow_ctx* c = new (std::nothrow) qflow_ctx();
+  if (!c) return QFLOW_ERR_OOM;
+  if (opt) c->opt = *opt; else qflow_default_options(&c->opt, QFLOW_PREC_FP64);
+  if (c->opt.precision != QFLOW_PREC_FP64 && c->opt.precision != QFLOW_PREC_MIXED) {
+    delete c;
+    return QFLOW_ERR_ARG;
+  }
+  if (c->opt.max_iter <= 0) c->opt.max_iter = 60;
+  if (!(c->opt.tol > 0.0)) c->opt.tol = (c->opt.precision == QFLOW_PREC_MIXED) ? 1e-6 : 1e-9;
+  c->n = n;
+  c->nocc = nocc;
+  c->nvir = n - nocc;
+  c->nspaces = nspaces;
+  c->n_t1 = (int64_t)nocc * c->nvir;
+  c->n_t2 = (int64_t)nocc * nocc * c->nvir * c->nvir;
+  Plan pl;
+  try {
+    make_plan(h, eri, n, nocc, spaces, nspaces, &pl, true);
+  } catch (const std::bad_alloc&) {
+    delete c;
+    return QFLOW_ERR_OOM;
+  }
+  c->perm = pl.perm;
+  // group by size class, sorted order within each class
+  std::vector<qflow_space> grouped((size_t)nspaces);
+  std::vector<int64_t> gidx((size_t)nspaces);
+  for (int64_t s = 0; s < nspaces; ++s) c->cls_count[spaces[pl.perm[s]].no]++;
+  c->cls_off[1] = 0;
+  c->cls_off[2] = c->cls_count[1];
+  c->cls_off[3] = c->cls_count[1] + c->cls_count[2];
+  int64_t fill[4] = {0, c->cls_off[1], c->cls_off[2], c->cls_off[3]};
+  for (int64_t s = 0; s < nspaces; ++s) {
+    const qflow_space& q = spaces[pl.perm[s]];
+    grouped[fill[q.no]] = q;
+    gidx[fill[q.no]] = s;
+    fill[q.no]++;
+  }
+  const size_t n1 = n, n4 = n1 * n1 * n1 * n1;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  c->dwork_bytes = qf::dress_workspace_bytes(n, nocc);
+  const size_t npool = (size_t)(c->n_t1 + c->n_t2);
+  if (e == cudaSuccess) e = dalloc(&c->h, n1 * n1);
+  if (e == cudaSuccess) e = dalloc(&c->eri, n4);
+  if (e == cudaSuccess) e = dalloc(&c->pool, npool);
+  if (e == cudaSuccess) e = dalloc(&c->pool_new, npool);
+  if (e == cudaSuccess) e = dalloc(&c->e0, 1);
+  if (e == cudaSuccess) e = dalloc(&c->F, n1 * n1);
+  if (e == cudaSuccess) e = dalloc(&c->W, n4);
+  if (e == cudaSuccess) e = dalloc(&c->energy, (size_t)std::max<int64_t>(nspaces, 1));
+  if (e == cudaSuccess) e = dalloc(&c->status, (size_t)std::max<int64_t>(nspaces, 1));
+  if (e == cudaSuccess) e = dalloc(&c->iters, (size_t)std::max<int64_t>(nspaces, 1));
+  if (e == cudaSuccess) e = dalloc(&c->own1, (size_t)c->n_t1);
+  if (e == cudaSuccess) e = dalloc(&c->own2, (size_t)c->n_t2);
+  if (e == cudaSuccess) e = dalloc(&c->spaces, (size_t)std::max<int64_t>(nspaces, 1));
+  if (e == cudaSuccess) e = dalloc(&c->sorted_index, (size_t)std::max<int64_t>(nspaces, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->dwork, c->dwork_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->rwork, qf::mean_maxdiff_workspace(nspaces, (int64_t)npool));
+  if (e == cudaSuccess) e = dalloc(&c->red, 4);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->red_host), 4 * sizeof(double));
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+  if (c->opt.guess == 1) {
+    const size_t ndet[4] = {0, 4, 36, 400};
+    const size_t esz = (c->opt.precision == QFLOW_PREC_MIXED) ? sizeof(float) : sizeof(double);
+    for (int k = 1; k <= 3 && e == cudaSuccess; ++k) {
+      if (c->cls_count[k] == 0) continue;
+      const size_t bytes = (size_t)c->cls_count[k] * ndet[k] * esz;
+      e = cudaMalloc(&c->guess[k], bytes);
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->guess[k], 0, bytes, c->stream);  // zero = start from Phi
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h, h, sizeof(double) * n1 * n1, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->eri, eri, sizeof(double) * n4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->pool, 0, sizeof(double) * npool, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->own1, pl.own1.data(), sizeof(int32_t) * pl.own1.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->own2, pl.own2.data(), sizeof(int32_t) * pl.own2.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && nspaces > 0)
+    e = cudaMemcpyAsync(c->spaces, grouped.data(), sizeof(qflow_space) * (size_t)nspaces, cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess && nspaces > 0)
+    e = cudaMemcpyAsync(c->sorted_index, gidx.data(), sizeof(int64_t) * (size_t)nspaces, cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_status(e);
+  }
+  *out = c;
+  return (pl.uncovered > 0) ? QFLOW_WARN_UNCOVERED : QFLOW_OK;
+}
+
+int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
+  if (!c) return QFLOW_ERR_ARG;
+  const size_t npool = (size_t)(c->n_t1 + c->n_t2);
+  int64_t launches = 0;
+  cudaError_t e = cudaEventRecord(c->ev[0], c->stream);
+  if (e == cudaSuccess)
+    e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
+                         c->dwork_bytes, c->stream);
+  launches += qf::dress_launch_count(c->n, c->nocc);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev[1], c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->pool_new, c->pool, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
+  for (int k = 1; k <= 3 && e == cudaSuccess; ++k) {
+    if (c->cls_count[k] == 0) continue;
+    SolveArgs a{};
+    a.n = c->n;
+    a.nocc = c->nocc;
+    a.nvir = c->nvir;
+    a.e0 = c->e0;
+    a.F = c->F;
+    a.W = c->W;
+    a.spaces = c->spaces + c->cls_off[k];
+    a.nspaces = c->cls_count[k];
+    a.space_base = 0;
+    a.sorted_index = c->sorted_index + c->cls_off[k];
+    a.owner1 = c->own1;
+    a.owner2 = c->own2;
+    a.t1_old = c->pool;
+    a.t2_old = c->pool + c->n_t1;
+    a.t1_new = c->pool_new;
+    a.t2_new = c->pool_new + c->n_t1;
+    a.energy = c->energy;
+    a.status = c->status;
+    a.iters = c->iters;
+    a.guess = c->guess[k];
+    a.save_root = c->guess[k] ? 1 : 0;
+    a.max_iter = c->opt.max_iter;
+    a.tol = c->opt.tol;
+    e = qf::launch_solve(k, c->opt.precision, a, c->stream);
+    ++launches;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev[2], c->stream);
+  if (e == cudaSuccess)
+    e = qf::launch_reduce(c->energy, c->status, c->nspaces, c->pool, c->pool_new, (int64_t)npool, c->red, c->rwork,
+                          c->stream);
+  launches += 2;
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev[3], c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->red_host, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  c->last_launches = launches;
+  std::swap(c->pool, c->pool_new);
+  const double em = c->red_host[0];
+  const double de = c->have_energy ? em - c->e_mean : std::numeric_limits<double>::infinity();
+  c->e_mean = em;
+  c->have_energy = true;
+  if (d_e) *d_e = de;
+  if (max_dt) *max_dt = c->red_host[1];
+  const int32_t nf = (int32_t)c->red_host[2];
+  if (nfailed) *nfailed = nf;
+  if (!isfinite(em) || !isfinite(c->red_host[1])) return QFLOW_ERR_NONFINITE;
+  if (nf > 0) {
+    const int worst = (int)c->red_host[3];
+    if (worst == qf::kSpaceNonFinite) return QFLOW_ERR_NONFINITE;
+    if (worst == qf::kSpaceRoot) return QFLOW_ERR_ROOT;
+    return QFLOW_ERR_NOCONV;
+  }
+  return QFLOW_OK;
+}
+
+int qflow_energy(qflow_handle c, double* e_mean, double* e_per_space) {
+  if (!c) return QFLOW_ERR_ARG;
+  if (!c->have_energy) return QFLOW_ERR_STATE;
+  if (e_mean) *e_mean = c->e_mean;
+  if (e_per_space && c->nspaces > 0) {
+    cudaError_t e = cudaMemcpyAsync(e_per_space, c->energy, sizeof(double) * (size_t)c->nspaces,
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_status(e);
+  }
+  return QFLOW_OK;
+}
+
+int qflow_amplitudes(qflow_handle c, double* t1, double* t2) {
+  if (!c) return QFLOW_ERR_ARG;
+  cudaError_t e = cudaSuccess;
+  if (t1) e = cudaMemcpyAsync(t1, c->pool, sizeof(double) * (size_t)c->n_t1, cudaMemcpyDeviceToHost, c->stream);
+  if (t2 && e == cudaSuccess)
+    e = cudaMemcpyAsync(t2, c->pool + c->n_t1, sizeof(double) * (size_t)c->n_t2, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+int qflow_set_amplitudes(qflow_handle c, const double* t1, const double* t2) {
+  if (!c || !t1 || !t2) return QFLOW_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(c->pool, t1, sizeof(double) * (size_t)c->n_t1, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->pool + c->n_t1, t2, sizeof(double) * (size_t)c->n_t2, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+int qflow_space_order(qflow_handle c, int64_t* perm) {
+  if (!c || !perm) return QFLOW_ERR_ARG;
+  memcpy(perm, c->perm.data(), sizeof(int64_t) * c->perm.size());
+  return QFLOW_OK;
+}
+
+int qflow_space_stats(qflow_handle c, int32_t* iterations, int32_t* status) {
+  if (!c) return QFLOW_ERR_ARG;
+  if (!c->have_energy) return QFLOW_ERR_STATE;
+  cudaError_t e = cudaSuccess;
+  if (iterations && c->nspaces > 0)
+    e = cudaMemcpyAsync(iterations, c->iters, sizeof(int32_t) * (size_t)c->nspaces, cudaMemcpyDeviceToHost, c->stream);
+  if (status && c->nspaces > 0 && e == cudaSuccess)
+    e = cudaMemcpyAsync(status, c->status, sizeof(int32_t) * (size_t)c->nspaces, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+int qflow_dressed(qflow_handle c, double* e0, double* F, double* W) {
+  if (!c) return QFLOW_ERR_ARG;
+  const size_t n1 = c->n, n4 = n1 * n1 * n1 * n1;
+  cudaError_t e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W,
+                                   c->dwork, c->dwork_bytes, c->stream);
+  if (e0 && e == cudaSuccess) e = cudaMemcpyAsync(e0, c->e0, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (F && e == cudaSuccess) e = cudaMemcpyAsync(F, c->F, sizeof(double) * n1 * n1, cudaMemcpyDeviceToHost, c->stream);
+  if (W && e == cudaSuccess) e = cudaMemcpyAsync(W, c->W, sizeof(double) * n4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+void* qflow_stream(qflow_handle c) { return c ? (void*)c->stream : nullptr; }
+
+int qflow_last_sweep_info(qflow_handle c, double* phase_ms, int64_t* kernel_launches) {
+  if (!c) return QFLOW_ERR_ARG;
+  if (!c->have_energy) return QFLOW_ERR_STATE;
+  if (phase_ms) {
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]);
+      if (e != cudaSuccess) return cuda_status(e);
+      phase_ms[k] = ms;
+    }
+  }
+  if (kernel_launches) *kernel_launches = c->last_launches;
+  return QFLOW_OK;
+}
+
+void qflow_destroy(qflow_handle c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+const char* qflow_strerror(int code) {
+  switch (code) {
+    case QFLOW_OK: return "ok";
+    case QFLOW_ERR_ARG: return "invalid argument";
+    case QFLOW_ERR_CUDA: return "CUDA runtime error";
+    case QFLOW_ERR_OOM: return "out of device memory";
+    case QFLOW_ERR_NOCONV: return "Davidson solver did not converge for some space";
+    case QFLOW_ERR_ROOT: return "no real Phi-dominant root for some space";
+    case QFLOW_ERR_NONFINITE: return "non-finite energy or amplitude";
+    case QFLOW_ERR_STATE: return "call out of order";
+    case QFLOW_WARN_UNCOVERED: return "some amplitudes have no owner space";
+    default: return "unknown qflow status";
+  }
+}
+
+size_t qflow_dress_workspace(int32_t n, int32_t nocc) {
+  if (n < 2 || n > 128 || nocc < 1 || nocc >= n) return 0;
+  return qf::dress_workspace_bytes(n, nocc);
+}
+
+int qflow_dress_device(const double* h, const double* eri, const double* t1, const double* t2, int32_t n,
+                       int32_t nocc, double* e0, double* F, double* W, void* work, size_t work_bytes, void* stream) {
+  if (!h || !eri || !t1 || !t2 || !e0 || !F || !W || !work || n < 2 || n > 128 || nocc < 1 || nocc >= n)
+    return QFLOW_ERR_ARG;
+  if (work_bytes < qf::dress_workspace_bytes(n, nocc)) return QFLOW_ERR_ARG;
+  return cuda_status(qf::launch_dress(h, eri, t1, t2, n, nocc, e0, F, W, work, work_bytes, (cudaStream_t)stream));
+}
+
+int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* F, const double* W,
+                       int32_t size_class, const qflow_space* spaces, int64_t nspaces, int64_t space_base, const int32_t* owner1,
+                       const int32_t* owner2, const double* t1_old, const double* t2_old, double* t1_new,
+                       double* t2_new, double* energy, int32_t* status, int32_t* iters, void* guess,
+                       int32_t save_root, int32_t precision, int32_t max_iter, double tol, void* stream) {
+  if (n < 2 || n > 128 || nocc < 1 || nocc >= n || nspaces < 0 || !e0 || !F || !W || !energy || !status)
+    return QFLOW_ERR_ARG;
+  if (nspaces > 0 && !spaces) return QFLOW_ERR_ARG;
+  if ((owner1 || owner2) && (!t1_old || !t2_old || !t1_new || !t2_new)) return QFLOW_ERR_ARG;
+  if (precision != QFLOW_PREC_FP64 && precision != QFLOW_PREC_MIXED) return QFLOW_ERR_ARG;
+  if (max_iter <= 0 || !(tol > 0.0)) return QFLOW_ERR_ARG;
+  if (size_class < 1 || size_class > 3 || size_class > nocc || size_class > n - nocc) return QFLOW_ERR_ARG;
+  if (nspaces == 0) return QFLOW_OK;
+  SolveArgs a{};
+  a.n = n;
+  a.nocc = nocc;
+  a.nvir = n - nocc;
+  a.e0 = e0;
+  a.F = F;
+  a.W = W;
+  a.spaces = spaces;
+  a.nspaces = nspaces;
+  a.space_base = space_base;
+  a.sorted_index = nullptr;
+  a.owner1 = owner1;
+  a.owner2 = owner2;
+  a.t1_old = t1_old;
+  a.t2_old = t2_old;
+  a.t1_new = t1_new;
+  a.t2_new = t2_new;
+  a.energy = energy;
+  a.status = status;
+  a.iters = iters;
+  a.guess = guess;
+  a.save_root = save_root;
+  a.max_iter = max_iter;
+  a.tol = tol;
+  return cuda_status(qf::launch_solve(size_class, precision, a, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of ``libqflow.so`` (argument marshalling only).
+
+Every step of the sweep runs in the library's CUDA kernels; this module converts NumPy
+arrays / torch device tensors to pointers and return codes to exceptions.  It never falls
+back to any other implementation: if the library is missing it raises.
+
+Space lists are int32 arrays of shape (nspaces, 8) laid out exactly like ``qflow_space``
+(no, nv, orb[6]), as produced by ``paper_2606_04186_gb300.synth``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqflow.so")
+
+PREC = {"fp64": 0, "mixed": 1}
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_ROOT, ERR_NONFINITE, ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+WARN_UNCOVERED = 1
+
+
+class QFlowError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("diis", C.c_int32), ("guess", C.c_int32), ("reserved", C.c_int32 * 8)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2606_04186_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    P, I32, I64, D, V = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_void_p
+    sig = {
+        "qflow_default_options": (None, [P, I32]),
+        "qflow_plan": (I32, [P, P, I32, I32, P, I64, P, P, P, P]),
+        "qflow_init": (I32, [P, P, P, I32, I32, P, I64, P]),
+        "qflow_sweep": (I32, [P, P, P, P]),
+        "qflow_energy": (I32, [P, P, P]),
+        "qflow_amplitudes": (I32, [P, P, P]),
+        "qflow_set_amplitudes": (I32, [P, P, P]),
+        "qflow_space_order": (I32, [P, P]),
+        "qflow_space_stats": (I32, [P, P, P]),
+        "qflow_dressed": (I32, [P, P, P, P]),
+        "qflow_stream": (V, [P]),
+        "qflow_last_sweep_info": (I32, [P, P, P]),
+        "qflow_destroy": (None, [P]),
+        "qflow_strerror": (C.c_char_p, [C.c_int]),
+        "qflow_dress_workspace": (C.c_size_t, [I32, I32]),
+        "qflow_dress_device": (I32, [P, P, P, P, I32, I32, P, P, P, P, C.c_size_t, P]),
+        "qflow_solve_device": (I32, [I32, I32, P, P, P, I32, P, I64, I64, P, P, P, P, P, P, P, P, P, P, I32, I32,
+                                     I32, D, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return lib().qflow_strerror(int(code)).decode()
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _spaces(sp) -> np.ndarray:
+    sp = np.ascontiguousarray(sp, dtype=np.int32)
+    if sp.ndim != 2 or sp.shape[1] != 8:
+        raise ValueError("spaces must be an int32 array of shape (nspaces, 8)")
+    return sp
+
+
+def _check(code: int, where: str, allow=(OK, WARN_UNCOVERED)) -> int:
+    if code not in allow:
+        raise QFlowError(code, where)
+    return code
+
+
+def plan(h, eri, nocc: int, spaces):
+    """(perm, owner1[o,v], owner2[o,o,v,v], n_uncovered) from the library's host planner."""
+    h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
+    n = h.shape[0]
+    nv = n - nocc
+    perm = np.empty(len(sp), dtype=np.int64)
+    o1 = np.empty((nocc, nv), dtype=np.int32)
+    o2 = np.empty((nocc, nocc, nv, nv), dtype=np.int32)
+    unc = C.c_int64(0)
+    _check(lib().qflow_plan(_ptr(h), _ptr(eri), n, nocc, _ptr(sp), len(sp), _ptr(perm), _ptr(o1), _ptr(o2),
+                            C.byref(unc)), "qflow_plan")
+    return perm, o1, o2, unc.value
+
+
+def default_options(precision: str = "fp64") -> Options:
+    o = Options()
+    lib().qflow_default_options(C.byref(o), PREC[precision])
+    return o
+
+
+class Flow:
+    """One flow on the current CUDA device (handle API of the library)."""
+
+    def __init__(self, h, eri, nocc: int, spaces, precision: str = "fp64", max_iter: int | None = None,
+                 tol: float | None = None, guess: str = "phi"):
+        h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
+        self.n, self.nocc = h.shape[0], nocc
+        self.nvir = self.n - nocc
+        self.nspaces = len(sp)
+        opt = default_options(precision)
+        if max_iter is not None:
+            opt.max_iter = max_iter
+        if tol is not None:
+            opt.tol = tol
+        opt.guess = {"phi": 0, "previous": 1}[guess]
+        self._h = C.c_void_p()
+        code = lib().qflow_init(C.byref(self._h), _ptr(h), _ptr(eri), self.n, nocc, _ptr(sp), len(sp), C.byref(opt))
+        self.init_status = _check(code, "qflow_init")
+
+    def close(self):
+        if self._h:
+            lib().qflow_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, raise_on_fail: bool = True):
+        de, dt, nf = C.c_double(), C.c_double(), C.c_int32()
+        code = lib().qflow_sweep(self._h, C.byref(de), C.byref(dt), C.byref(nf))
+        if raise_on_fail:
+            _check(code, "qflow_sweep")
+        return de.value, dt.value, nf.value, code
+
+    def energy(self, per_space: bool = False):
+        e = C.c_double()
+        arr = np.empty(self.nspaces) if per_space else None
+        _check(lib().qflow_energy(self._h, C.byref(e), _ptr(arr) if per_space else None), "qflow_energy")
+        return (e.value, arr) if per_space else e.value
+
+    def amplitudes(self):
+        t1 = np.empty((self.nocc, self.nvir))
+        t2 = np.empty((self.nocc, self.nocc, self.nvir, self.nvir))
+        _check(lib().qflow_amplitudes(self._h, _ptr(t1), _ptr(t2)), "qflow_amplitudes")
+        return t1, t2
+
+    def set_amplitudes(self, t1, t2):
+        t1, t2 = _f64(t1), _f64(t2)
+        _check(lib().qflow_set_amplitudes(self._h, _ptr(t1), _ptr(t2)), "qflow_set_amplitudes")
+
+    def order(self) -> np.ndarray:
+        perm = np.empty(self.nspaces, dtype=np.int64)
+        _check(lib().qflow_space_order(self._h, _ptr(perm)), "qflow_space_order")
+        return perm
+
+    def stats(self):
+        it = np.empty(self.nspaces, dtype=np.int32)
+        st = np.empty(self.nspaces, dtype=np.int32)
+        _check(lib().qflow_space_stats(self._h, _ptr(it), _ptr(st)), "qflow_space_stats")
+        return it, st
+
+    def dressed(self):
+        e0 = np.empty(1)
+        F = np.empty((self.n, self.n))
+        W = np.empty((self.n,) * 4)
+        _check(lib().qflow_dressed(self._h, _ptr(e0), _ptr(F), _ptr(W)), "qflow_dressed")
+        return float(e0[0]), F, W
+
+    def last_sweep_info(self):
+        ph = np.empty(3)
+        nl = C.c_int64()
+        _check(lib().qflow_last_sweep_info(self._h, _ptr(ph), C.byref(nl)), "qflow_last_sweep_info")
+        return ph, nl.value
+
+    def stream(self) -> int:
+        return lib().qflow_stream(self._h) or 0
+
+
+# ---- device-level steps on torch CUDA tensors ------------------------------------------------
+
+def _dptr(t) -> int:
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device steps take contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def dress_device(h, eri, t1, t2, nocc: int, e0, F, W, work, stream: int = 0):
+    """Step (a) on torch float64 CUDA tensors; `work` is a uint8 CUDA tensor of
+    ``dress_workspace(n, nocc)`` bytes."""
+    n = h.shape[0]
+    _check(lib().qflow_dress_device(_dptr(h), _dptr(eri), _dptr(t1), _dptr(t2), n, nocc, _dptr(e0), _dptr(F),
+                                    _dptr(W), _dptr(work), work.numel(), stream or None), "qflow_dress_device")
+
+
+def dress_workspace(n: int, nocc: int) -> int:
+    return int(lib().qflow_dress_workspace(n, nocc))
+
+
+def solve_device(n: int, nocc: int, e0, F, W, size_class: int, spaces, energy, status, iters=None,
+                 owner1=None, owner2=None, t1_old=None, t2_old=None, t1_new=None, t2_new=None,
+                 guess=None, save_root: bool = False, space_base: int = 0, precision: str = "fp64",
+                 max_iter: int = 60, tol: float | None = None, stream: int = 0):
+    """Steps (b)+(c) for one size class on torch CUDA tensors (spaces: int32 [ns, 8])."""
+    if tol is None:
+        tol = 1e-6 if precision == "mixed" else 1e-9
+    opt = lambda t: _dptr(t) if t is not None else None  # noqa: E731
+    _check(lib().qflow_solve_device(n, nocc, _dptr(e0), _dptr(F), _dptr(W), size_class, _dptr(spaces),
+                                    spaces.shape[0], space_base, opt(owner1), opt(owner2), opt(t1_old),
+                                    opt(t2_old), opt(t1_new), opt(t2_new), _dptr(energy), _dptr(status),
+                                    opt(iters), opt(guess), int(save_root), PREC[precision], max_iter, tol,
+                                    stream or None), "qflow_solve_device")

@@ -1,0 +1,70 @@
+"""The C-ABI library loads here (no GPU) and exports every entry point include/qflow.h declares;
+its host planner reproduces the oracle's ordering and ownership bit for bit."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import ccsd, flow
+from paper_2606_04186_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def qf():
+    from paper_2606_04186_gb300 import build, qflow
+    if not os.path.exists(qflow.LIB_PATH):
+        build.build()
+    qflow.lib()
+    return qflow
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "qflow.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qflow_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(qf):
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    L = ctypes.CDLL(qf.LIB_PATH)
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_strerror_and_defaults(qf):
+    assert qf.strerror(0) == "ok"
+    o = qf.default_options("mixed")
+    assert o.precision == 1 and o.tol == 1e-6 and o.max_iter == 60
+
+
+@pytest.mark.parametrize("name", ["n10", "n24", "n40"])
+def test_plan_matches_oracle(qf, name):
+    eps, h, g, sp = synth.system_inputs(name)
+    s = synth.SYSTEMS[name]
+    perm, o1, o2, unc = qf.plan(h, g, s.nocc, sp)
+    fd = ccsd.fock_diagonal(h, g, s.nocc)
+    perm_ref = flow.sort_spaces(sp, fd)
+    assert np.array_equal(perm, perm_ref)
+    r1, r2 = flow.owner_maps(sp[perm_ref], s.nocc, s.n - s.nocc)
+    assert np.array_equal(o1, r1) and np.array_equal(o2, r2)
+    assert unc == int((r1 < 0).sum() + (r2 < 0).sum())
+
+
+def test_plan_rejects_bad_spaces(qf):
+    eps, h, g, sp = synth.system_inputs("n10")
+    bad = sp.copy()
+    bad[0, 2] = 5          # an "occupied" index that is virtual
+    with pytest.raises(qf.QFlowError):
+        qf.plan(h, g, 3, bad)
+    bad = sp.copy()
+    bad[0, 0] = 2          # (2,3) is not a supported size class
+    with pytest.raises(qf.QFlowError):
+        qf.plan(h, g, 3, bad)
+    empty = sp[:0]
+    perm, o1, o2, unc = qf.plan(h, g, 3, empty)
+    assert perm.size == 0 and unc == o1.size + o2.size

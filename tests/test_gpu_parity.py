@@ -1,0 +1,204 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: plain FP64 path |dE| <= 1e-8 Eh per space and max |dt| <= 1e-7 (the flow's own
+convergence thresholds); mixed path (FP32 sigma) |dE| <= 1e-6 Eh and |dt| <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import cas, ccsd, flow, hbar
+from paper_2606_04186_gb300 import synth
+
+from gpu_util import dev, library
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-8, 1e-7), "mixed": (1e-6, 1e-5)}
+
+
+@pytest.fixture(scope="module")
+def qf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return library()
+
+
+def _pool(no, nv, seed=3, s1=0.01, s2=0.02):
+    return synth.random_amplitudes(no, nv, seed, s1, s2)
+
+
+@pytest.mark.parametrize("name", ["n10", "n24"])
+def test_dress_matches_oracle(qf, name):
+    import torch
+    eps, h, g, _ = synth.system_inputs(name, with_spaces=False)
+    s = synth.SYSTEMS[name]
+    no, nv = s.nocc, s.n - s.nocc
+    t1, t2 = _pool(no, nv)
+    e0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F = torch.zeros((s.n, s.n), dtype=torch.float64, device="cuda")
+    W = torch.zeros((s.n,) * 4, dtype=torch.float64, device="cuda")
+    work = torch.zeros(qf.dress_workspace(s.n, no), dtype=torch.uint8, device="cuda")
+    qf.dress_device(dev(h), dev(g), dev(t1), dev(t2), no, e0, F, W, work)
+    torch.cuda.synchronize()
+    e0r, Fr, Wr = hbar.hbar2(h, g, t1, t2, no)
+    assert abs(e0.item() - e0r) < 1e-11
+    assert np.abs(F.cpu().numpy() - Fr).max() < 1e-11
+    assert np.abs(W.cpu().numpy() - Wr).max() < 1e-11
+
+
+def _solve_on_gpu(qf, n, no, e0, F, W, k, spaces, own1, own2, t1, t2, precision):
+    import torch
+    ns = len(spaces)
+    energy = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    status = torch.full((ns,), -1, dtype=torch.int32, device="cuda")
+    iters = torch.zeros(ns, dtype=torch.int32, device="cuda")
+    t1o, t2o = dev(t1), dev(t2)
+    t1n, t2n = t1o.clone(), t2o.clone()
+    qf.solve_device(n, no, dev(np.array([e0])), dev(F), dev(W), k, dev(spaces), energy, status, iters,
+                    owner1=dev(own1.astype(np.int32)), owner2=dev(own2.astype(np.int32)), t1_old=t1o, t2_old=t2o,
+                    t1_new=t1n, t2_new=t2n, precision=precision)
+    torch.cuda.synchronize()
+    return (energy.cpu().numpy(), status.cpu().numpy(), iters.cpu().numpy(), t1n.cpu().numpy(), t2n.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_solver_on_oracle_hbar(qf, k, precision):
+    eps, h, g, _ = synth.system_inputs("n10", with_spaces=False)
+    n, no = 10, 3
+    t1, t2 = _pool(no, n - no, 7)
+    e0, F, W = hbar.hbar2(h, g, t1, t2, no)
+    sp = synth.all_spaces(n, no, k, k)
+    perm = flow.sort_spaces(sp, ccsd.fock_diagonal(h, g, no))
+    sps = sp[perm]
+    own1, own2 = flow.owner_maps(sps, no, n - no)
+    E, st, it, t1n, t2n = _solve_on_gpu(qf, n, no, e0, F, W, k, sps, own1, own2, t1, t2, precision)
+    ref = flow.solve_all(e0, F, W, sps)
+    Er = np.array([r[0] for r in ref])
+    t1r, t2r = flow.merge(t1, t2, sps, ref, own1, own2, no)
+    te, tt = TOL[precision]
+    assert (st == 0).all(), st
+    assert np.abs(E - Er).max() < te
+    assert np.abs(t1n - t1r).max() < tt and np.abs(t2n - t2r).max() < tt
+    assert np.abs(t2n - t2n.transpose(1, 0, 3, 2)).max() < 1e-12
+    assert it.max() < 60
+
+
+def test_solver_skips_malformed_and_empty(qf):
+    import torch
+    eps, h, g, _ = synth.system_inputs("n10", with_spaces=False)
+    e0, F, W = hbar.hbar2(h, g, np.zeros((3, 7)), np.zeros((3, 3, 7, 7)), 3)
+    sp = synth.all_spaces(10, 3)[:4].copy()
+    sp[1, 0] = 2           # wrong size class
+    sp[2, 5] = 2           # virtual slot holding an occupied index
+    E, st, it, _, _ = _solve_on_gpu(qf, 10, 3, e0, F, W, 3, sp, np.full((3, 7), -1), np.full((3, 3, 7, 7), -1),
+                                    np.zeros((3, 7)), np.zeros((3, 3, 7, 7)), "fp64")
+    assert list(st) == [0, 4, 4, 0]
+    energy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    qf.solve_device(10, 3, dev(np.array([e0])), dev(F), dev(W), 3, dev(sp[:0]), energy, status)
+
+
+def test_flow_sweeps_match_oracle_fp64(qf):
+    eps, h, g, sp = synth.system_inputs("n10")
+    ref = flow.Flow(h, g, 3, sp)
+    gpu = qf.Flow(h, g, 3, sp, precision="fp64")
+    assert np.array_equal(gpu.order(), ref.perm)
+    for sweep in range(4):
+        er, der, dtr, _ = ref.sweep()
+        de, dt, nf, code = gpu.sweep()
+        e, per = gpu.energy(per_space=True)
+        t1, t2 = gpu.amplitudes()
+        assert nf == 0 and code == 0
+        assert abs(e - er) < 1e-9
+        assert np.abs(per - ref.energies).max() < 1e-9
+        assert np.abs(t1 - ref.t1).max() < 1e-9 and np.abs(t2 - ref.t2).max() < 1e-9
+        if sweep:
+            assert abs(de - der) < 1e-9 and abs(dt - dtr) < 1e-9
+    gpu.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_flow_converges_to_ccsd(qf, precision):
+    eps, h, g, sp = synth.system_inputs("n10")
+    e_cc, t1c, t2c, _ = ccsd.ccsd(h, g, 3, tol=1e-13)
+    gpu = qf.Flow(h, g, 3, sp, precision=precision)
+    for _ in range(40):
+        de, dt, nf, code = gpu.sweep()
+        if abs(de) < 1e-10 and dt < 1e-9:
+            break
+    te, tt = TOL[precision]
+    assert abs(gpu.energy() - e_cc) < (1e-9 if precision == "fp64" else te)
+    t1, t2 = gpu.amplitudes()
+    assert np.abs(t2 - t2c).max() < (1e-8 if precision == "fp64" else tt)
+    gpu.close()
+
+
+def test_ccsd_fixed_point_n24(qf):
+    eps, h, g, sp = synth.system_inputs("n24")
+    e_cc, t1c, t2c, _ = ccsd.ccsd(h, g, 5, tol=1e-12)
+    gpu = qf.Flow(h, g, 5, sp, precision="fp64")
+    gpu.set_amplitudes(t1c, t2c)
+    de, dt, nf, code = gpu.sweep()
+    e, per = gpu.energy(per_space=True)
+    assert nf == 0 and dt < 1e-9
+    assert np.abs(per - e_cc).max() < 1e-9
+    gpu.close()
+
+
+@pytest.mark.parametrize("name,precision", [("n24", "fp64"), ("n24", "mixed"), ("n40", "fp64")])
+def test_sampled_spaces_full_list(qf, name, precision):
+    """Full space lists on the GPU; a seeded sample of spaces recomputed by the oracle."""
+    eps, h, g, sp = synth.system_inputs(name)
+    s = synth.SYSTEMS[name]
+    no, nv = s.nocc, s.n - s.nocc
+    t1, t2 = _pool(no, nv, 11, 0.01, 0.015)
+    gpu = qf.Flow(h, g, no, sp, precision=precision)
+    gpu.set_amplitudes(t1, t2)
+    gpu.sweep()
+    e, per = gpu.energy(per_space=True)
+    t1n, t2n = gpu.amplitudes()
+    perm = gpu.order()
+    sps = sp[perm]
+    e0, F, W = hbar.hbar2(h, g, t1, t2, no)
+    own1, own2 = flow.owner_maps(sps, no, nv)
+    rng = np.random.default_rng(5)
+    te, tt = TOL[precision]
+    for s_idx in rng.choice(len(sps), size=40, replace=False):
+        occ, vir = flow.space_orbitals(sps[s_idx])
+        er, x1, x2, st = cas.solve_space(e0, F, W, occ, vir)
+        assert abs(per[s_idx] - er) < te
+        va = [a - no for a in vir]
+        for ii, i in enumerate(occ):
+            for aa, a in enumerate(va):
+                if own1[i, a] == s_idx:
+                    assert abs(t1n[i, a] - (t1[i, a] + x1[ii, aa])) < tt
+            for jj, j in enumerate(occ):
+                for aa, a in enumerate(va):
+                    for bb, b in enumerate(va):
+                        if own2[i, j, a, b] == s_idx:
+                            assert abs(t2n[i, j, a, b] - (t2[i, j, a, b] + x2[ii, jj, aa, bb])) < tt
+    # amplitudes nobody owns keep their value; mean energy is the mean of the space energies
+    assert abs(e - per.mean()) < 1e-12 * max(1.0, abs(e))
+    unowned1 = own1 < 0
+    assert np.array_equal(t1n[unowned1], t1[unowned1])
+    gpu.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_previous_root_guess_same_result_fewer_iterations(qf, precision):
+    eps, h, g, sp = synth.system_inputs("n24")
+    a = qf.Flow(h, g, 5, sp, precision=precision, guess="phi")
+    b = qf.Flow(h, g, 5, sp, precision=precision, guess="previous")
+    te, tt = TOL[precision]
+    for sweep in range(3):
+        a.sweep()
+        b.sweep()
+        ea, pa = a.energy(per_space=True)
+        eb, pb = b.energy(per_space=True)
+        assert np.abs(pa - pb).max() < te
+    ia, _ = a.stats()
+    ib, _ = b.stats()
+    assert ib.mean() < ia.mean()
+    a.close()
+    b.close()
