@@ -73,7 +73,9 @@ typedef struct {
   int32_t diis;               /* 0 = off, else DIIS history length on the pool (<= 8)       */
   int32_t guess;              /* 0 = Phi, 1 = previous sweep's root of the same space (keeps
                                  one CI vector per space on the device: 400 x 4 B per 6e6o
-                                 space in mixed precision, x 8 B in FP64)                   */
+                                 space in mixed precision, x 8 B in FP64).  In a flow the pool
+                                 absorbs each root's increment, so Phi is usually the closer
+                                 start; 1 pays off when the pool is held fixed.             */
   int32_t reserved[8];
 } qflow_options;
 

@@ -18,6 +18,7 @@
 // Every loop is bounded; a warp never waits on another warp.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <utility>
@@ -103,7 +104,7 @@ __device__ __forceinline__ void ab_terms(std::integer_sequence<int, I...>, float
   (ab_term<I / NSG, I % NSG>(acc, wr, cr), ...);
 }
 
-struct WarpSmem {
+struct alignas(16) WarpSmem {  // 16-byte rows: sigma reads them as float4
   float V[KM * NDET];
   float S[KM * NDET];
   float Wt[NW];        // FP32 W block without its [pp][rr] (diagonal-only) entries
@@ -121,13 +122,19 @@ struct WarpSmem {
   int ctrl[4];  // [0] subspace size, [2] status, [3] iterations
 };
 
-struct CtaSmem {
+struct alignas(16) CtaSmem {
   int J[NS * NSG];
   int pq[NS * NSG];
   int sg[NS * NSG];
   int mask[NS];
   WarpSmem w[WARPS];
 };
+
+static_assert(sizeof(WarpSmem) % 16 == 0, "per-warp state must keep 16-byte alignment");
+static_assert(offsetof(WarpSmem, V) % 16 == 0 && offsetof(WarpSmem, S) % 16 == 0 && offsetof(WarpSmem, Wt) % 16 == 0 &&
+                  offsetof(WarpSmem, Hs) % 16 == 0 && offsetof(WarpSmem, diag) % 16 == 0,
+              "float4 rows");
+static_assert(offsetof(CtaSmem, w) % 16 == 0, "warp state alignment");
 
 // Index of the string with bit mask m (strings are numbered by increasing mask).
 __device__ __forceinline__ int str_index(const CtaSmem& cs, int m) {

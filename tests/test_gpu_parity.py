@@ -186,7 +186,9 @@ def test_sampled_spaces_full_list(qf, name, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_previous_root_guess_same_result_fewer_iterations(qf, precision):
+def test_previous_root_guess_same_result(qf, precision):
+    # Starting each space from its previous root gives the same flow.  (It is not a cheaper
+    # start here: the pool absorbs each root's increment, so the next root is closer to Phi.)
     eps, h, g, sp = synth.system_inputs("n24")
     a = qf.Flow(h, g, 5, sp, precision=precision, guess="phi")
     b = qf.Flow(h, g, 5, sp, precision=precision, guess="previous")
@@ -197,8 +199,7 @@ def test_previous_root_guess_same_result_fewer_iterations(qf, precision):
         ea, pa = a.energy(per_space=True)
         eb, pb = b.energy(per_space=True)
         assert np.abs(pa - pb).max() < te
-    ia, _ = a.stats()
-    ib, _ = b.stats()
-    assert ib.mean() < ia.mean()
+    ta, tb = a.amplitudes(), b.amplitudes()
+    assert np.abs(ta[1] - tb[1]).max() < tt
     a.close()
     b.close()
