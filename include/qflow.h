@@ -52,6 +52,7 @@ typedef enum {
   QFLOW_ERR_ROOT = -5,       /* selected root complex or |c_Phi| < 1e-3                    */
   QFLOW_ERR_NONFINITE = -6,  /* NaN/Inf in an energy or amplitude                          */
   QFLOW_ERR_STATE = -7,      /* call out of order (e.g. energy before the first sweep)     */
+  QFLOW_ERR_TOO_LARGE = -8,  /* problem needs more scratch than qflow_dress_device_static has */
   QFLOW_WARN_UNCOVERED = 1   /* bit: some amplitudes have no owner space                   */
 } qflow_status;
 
@@ -179,6 +180,32 @@ int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* 
                        const int32_t* owner2, const double* t1_old, const double* t2_old, double* t1_new,
                        double* t2_new, double* energy, int32_t* status, int32_t* iters, void* guess,
                        int32_t save_root, int32_t precision, int32_t max_iter, double tol, void* stream);
+
+/* ---- allocation-free dressing ---------------------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc: applications whose device memory belongs to another allocator (an arena or pool
+ * that must account for every byte), code that must not risk the implicit device
+ * synchronisation an allocation may cause, or services with a fixed pre-reserved budget.
+ *
+ * qflow_dress_device_static computes exactly what qflow_dress_device computes (same kernels,
+ * same arguments except the workspace) but takes its scratch from a static device array of
+ * QFLOW_STATIC_SCRATCH_BYTES bytes inside the library, so the call allocates nothing (no
+ * cudaMalloc, no cudaFree, no allocating library routine).  The array is held by every GPU
+ * that loads the library until the process exits.
+ *   - Limit: the call returns QFLOW_ERR_TOO_LARGE when qflow_dress_workspace(n, nocc) exceeds
+ *     QFLOW_STATIC_SCRATCH_BYTES (4 MiB, e.g. 40 orbitals with 6 occupied fit, 82 do not).
+ *   - Set-up: the first call on a device looks up the device address of the array on that
+ *     device (with it current); make that first call before any stream capture.
+ *   - Sharing: every call on a device uses the same array, which keeps the last call's data;
+ *     the kernels write every scratch element before reading it, so nothing needs clearing.
+ *     Calls whose work overlaps on the GPU (other streams, other threads) race on the array:
+ *     order them on one stream or serialise them.
+ * Other arguments, layouts and errors: as qflow_dress_device. */
+#define QFLOW_STATIC_SCRATCH_BYTES (4u * 1024u * 1024u)
+int qflow_dress_device_static(const double* h, const double* eri, const double* t1, const double* t2, int32_t n,
+                              int32_t nocc, double* e0, double* F, double* W, void* stream);
+/* Size of that static scratch array in bytes. */
+size_t qflow_static_scratch_bytes(void);
 
 #ifdef __cplusplus
 }

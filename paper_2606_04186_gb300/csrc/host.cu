@@ -471,6 +471,7 @@ const char* qflow_strerror(int code) {
     case QFLOW_ERR_NONFINITE: return "non-finite energy or amplitude";
     case QFLOW_ERR_STATE: return "call out of order";
     case QFLOW_WARN_UNCOVERED: return "some amplitudes have no owner space";
+    case QFLOW_ERR_TOO_LARGE: return "problem exceeds the static scratch of the allocation-free entry point";
     default: return "unknown qflow status";
   }
 }

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libqflow.so")
 PREC = {"fp64": 0, "mixed": 1}
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_ROOT, ERR_NONFINITE, ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+ERR_TOO_LARGE = -8
 WARN_UNCOVERED = 1
 
 
@@ -62,6 +63,8 @@ def lib() -> C.CDLL:
         "qflow_destroy": (None, [P]),
         "qflow_strerror": (C.c_char_p, [C.c_int]),
         "qflow_dress_workspace": (C.c_size_t, [I32, I32]),
+        "qflow_dress_device_static": (I32, [P, P, P, P, I32, I32, P, P, P, P]),
+        "qflow_static_scratch_bytes": (C.c_size_t, []),
         "qflow_dress_device": (I32, [P, P, P, P, I32, I32, P, P, P, P, C.c_size_t, P]),
         "qflow_solve_device": (I32, [I32, I32, P, P, P, I32, P, I64, I64, P, P, P, P, P, P, P, P, P, P, I32, I32,
                                      I32, D, P]),
@@ -214,6 +217,18 @@ def dress_device(h, eri, t1, t2, nocc: int, e0, F, W, work, stream: int = 0):
     n = h.shape[0]
     _check(lib().qflow_dress_device(_dptr(h), _dptr(eri), _dptr(t1), _dptr(t2), n, nocc, _dptr(e0), _dptr(F),
                                     _dptr(W), _dptr(work), work.numel(), stream or None), "qflow_dress_device")
+
+
+def dress_device_static(h, eri, t1, t2, nocc: int, e0, F, W, stream: int = 0):
+    """Step (a) without any allocation: scratch comes from the library's static device array
+    (see qflow_dress_device_static in include/qflow.h for the size limit and sharing rules)."""
+    n = h.shape[0]
+    _check(lib().qflow_dress_device_static(_dptr(h), _dptr(eri), _dptr(t1), _dptr(t2), n, nocc, _dptr(e0),
+                                           _dptr(F), _dptr(W), stream or None), "qflow_dress_device_static")
+
+
+def static_scratch_bytes() -> int:
+    return int(lib().qflow_static_scratch_bytes())
 
 
 def dress_workspace(n: int, nocc: int) -> int:
