@@ -249,6 +249,27 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     gidx[fill[q.no]] = s;
     fill[q.no]++;
   }
+  // Within a class the solve visits spaces in orbital-tuple order (occupied tuple, then virtual
+  // tuple) so that warps running at the same time gather overlapping rows of W from L2; the
+  // Delta-eps position of each space travels with it in gidx (owners, energies, statistics).
+  for (int k = 1; k <= 3; ++k) {
+    const int64_t b = c->cls_off[k], e = b + c->cls_count[k];
+    std::vector<int64_t> ord((size_t)(e - b));
+    std::iota(ord.begin(), ord.end(), b);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
+      for (int t = 0; t < 2 * k; ++t)
+        if (grouped[x].orb[t] != grouped[y].orb[t]) return grouped[x].orb[t] < grouped[y].orb[t];
+      return gidx[x] < gidx[y];
+    });
+    std::vector<qflow_space> gs(ord.size());
+    std::vector<int64_t> gi(ord.size());
+    for (size_t t = 0; t < ord.size(); ++t) {
+      gs[t] = grouped[ord[t]];
+      gi[t] = gidx[ord[t]];
+    }
+    std::copy(gs.begin(), gs.end(), grouped.begin() + b);
+    std::copy(gi.begin(), gi.end(), gidx.begin() + b);
+  }
   const size_t n1 = n, n4 = n1 * n1 * n1 * n1;
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   c->dwork_bytes = qf::dress_workspace_bytes(n, nocc);

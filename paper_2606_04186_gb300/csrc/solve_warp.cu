@@ -29,9 +29,9 @@ namespace qf {
 namespace {
 
 constexpr int NS = 20, NSG = 12, NDET = 400, NORB = 6, NF = 36, NW = 1296;
-constexpr int KM = 6;        // Davidson subspace limit (restart on the Ritz vector)
+constexpr int KM = 4;        // Davidson subspace limit (restart on the Ritz vector)
 constexpr int WARPS = 4;     // spaces (warps) per CTA
-constexpr int PERL = (NDET + 31) / 32;  // determinant slots per lane (13)
+constexpr int NPAIR = NF * (NF + 1) / 2;  // unique (pq, rs) pairs of the pair-symmetric W block
 
 struct Tab {
   int mask[NS];
@@ -110,16 +110,18 @@ struct alignas(16) WarpSmem {  // 16-byte rows: sigma reads them as float4
   float Wt[NW];        // FP32 W block without its [pp][rr] (diagonal-only) entries
   float Hs[NS * NS];   // same-spin string operator, zero diagonal
   float diag[NDET];    // operator diagonal minus E_Phi
-  double F[NF], h[NF], J[NF], K[NF];
-  double hsd[NS];
+  float hp[NF];        // h' = h - 1/2 sum_r W_prrq (off-diagonal part used in FP32)
+  double F[NF], J[NF], K[NF];  // F block; J_pr = W_pprr, K_pr = W_prrp (FP64)
+  double hd[6];        // folded one-body diagonal h_pp (FP64)
+  double hsd[NS];      // same-spin string diagonal (FP64)
+  float dh[NS];        // hsd[I] - hsd[0] (FP64 difference, rounded); Hs[I][0] on the Phi path
+  float jb[6 * NS];    // jb[p][Ib] = sum_{r in Ib} J_pr
   double G[KM * KM];
   double y[KM];
-  double x1[9];
-  double x2[81];
   float yf[KM];
   double ecore, eshift, theta;
   int orb[6];
-  int ctrl[4];  // [0] subspace size, [2] status, [3] iterations
+  int ctrl[4];  // [0] subspace size, [1] valid, [2] status, [3] iterations
 };
 
 struct alignas(16) CtaSmem {
@@ -127,6 +129,7 @@ struct alignas(16) CtaSmem {
   int pq[NS * NSG];
   int sg[NS * NSG];
   int mask[NS];
+  unsigned short pair[NF * (NF + 1) / 2];  // (P, R) with P <= R, packed P | R << 8
   WarpSmem w[WARPS];
 };
 
@@ -344,6 +347,9 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
         }
       }
     }
+    int t = 0;
+    for (int P = 0; P < NF; ++P)
+      for (int R = P; R < NF; ++R) cs.pair[t++] = (unsigned short)(P | (R << 8));
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
   const double tol = a.tol;
 
   for (int64_t s = (int64_t)blockIdx.x * WARPS + warp; s < a.nspaces; s += (int64_t)gridDim.x * WARPS) {
-    // ---- validate + gather + fold (FP64 where it matters) ---------------------------------
+    // ---- validate -------------------------------------------------------------------------
     if (lane == 0) {
       const qflow_space& q = a.spaces[s];
       int ok = (q.no == 3 && q.nv == 3);
@@ -377,38 +383,67 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
       __syncwarp();
       continue;
     }
-    for (int idx = lane; idx < NW; idx += 32) {
-      const int p = idx / 216, q = (idx / 36) % 6, r = (idx / 6) % 6, u = idx % 6;
-      const double w = a.W[(size_t)ws.orb[p] * n3 + (size_t)ws.orb[q] * n2 + (size_t)ws.orb[r] * n1 + ws.orb[u]];
-      if (p == q && r == u) ws.J[p * 6 + r] = w;
-      if (q == r && u == p) ws.K[p * 6 + r] = w;
-      ws.Wt[idx] = (p == q && r == u) ? 0.f : (float)w;  // [pp][rr] reaches only the diagonal
+    // ---- gather: 666 unique elements of the pair-symmetric W block, all loads in flight ----
+    {
+      size_t rowp[6];
+#pragma unroll
+      for (int t = 0; t < 6; ++t) rowp[t] = (size_t)ws.orb[t];
+      constexpr int PER = (NPAIR + 31) / 32;  // 21
+      double wv[PER];
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int t = lane + 32 * k;
+        wv[k] = 0.0;
+        if (t < NPAIR) {
+          const int pr = cs.pair[t], P = pr & 255, R = pr >> 8;
+          wv[k] = a.W[rowp[P / 6] * n3 + rowp[P % 6] * n2 + rowp[R / 6] * n1 + rowp[R % 6]];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int t = lane + 32 * k;
+        if (t < NPAIR) {
+          const int pr = cs.pair[t], P = pr & 255, R = pr >> 8;
+          const int p = P / 6, q = P % 6, r = R / 6, u = R % 6;
+          const double w = wv[k];
+          const bool jj = (p == q && r == u);  // W_pprr: reaches only the diagonal
+          const float wf = jj ? 0.f : (float)w;
+          ws.Wt[P * NF + R] = wf;
+          ws.Wt[R * NF + P] = wf;
+          if (jj) {
+            ws.J[p * 6 + r] = w;
+            ws.J[r * 6 + p] = w;
+          }
+          if (q == r && u == p) {  // W_prrp = K_pr (and its pair partner K_rp)
+            ws.K[p * 6 + r] = w;
+            ws.K[r * 6 + p] = w;
+          }
+        }
+      }
+      for (int idx = lane; idx < NF; idx += 32) ws.F[idx] = a.F[rowp[idx / 6] * n1 + rowp[idx % 6]];
     }
-    for (int idx = lane; idx < NF; idx += 32) ws.F[idx] = a.F[(size_t)ws.orb[idx / 6] * n1 + ws.orb[idx % 6]];
     __syncwarp();
+    // ---- fold (vacuum order over the active orbitals) -------------------------------------
+    // diagonal h_pp = F_pp - sum_k (2 J_pk - K_pk) in FP64; off-diagonal h' in FP32 from Wt
+    if (lane < 6) {
+      double v = ws.F[lane * 7];
+      for (int k = 0; k < 3; ++k) v -= 2.0 * ws.J[lane * 6 + k] - ws.K[lane * 6 + k];
+      ws.hd[lane] = v;
+    }
     for (int idx = lane; idx < NF; idx += 32) {
       const int p = idx / 6, q = idx % 6;
-      double v = ws.F[idx];
-      for (int k = 0; k < 3; ++k) {
-        const double wqk = a.W[(size_t)ws.orb[p] * n3 + (size_t)ws.orb[q] * n2 + (size_t)ws.orb[k] * n1 + ws.orb[k]];
-        const double wkq = a.W[(size_t)ws.orb[p] * n3 + (size_t)ws.orb[k] * n2 + (size_t)ws.orb[k] * n1 + ws.orb[q]];
-        v -= 2.0 * wqk - wkq;
-      }
-      ws.h[idx] = v;  // folded one-body, vacuum order
+      float v = (float)ws.F[idx];
+      for (int k = 0; k < 3; ++k) v -= 2.f * ws.Wt[idx * NF + k * 7] - ws.Wt[(p * 6 + k) * NF + k * 6 + q];
+      for (int r = 0; r < 6; ++r) v -= 0.5f * ws.Wt[(p * 6 + r) * NF + r * 6 + q];
+      ws.hp[idx] = (p == q) ? 0.f : v;  // diagonal replacements are handled in FP64
     }
     __syncwarp();
-    if (lane == 0) {
-      double ec = *a.e0;
-      for (int k = 0; k < 3; ++k) ec -= ws.h[k * 6 + k] + ws.F[k * 6 + k];
-      ws.ecore = ec;
-    }
-    // same-spin string diagonal in FP64: sum_{p in I} h_pp + 1/2 sum_{p,r in I} (J_pr - K_pr)
-    if (lane < NS) {
+    if (lane < NS) {  // same-spin string diagonal: sum_{p in I} h_pp + 1/2 sum_{p,r in I} (J_pr - K_pr)
       const int m = cs.mask[lane];
       double v = 0.0;
       for (int p = 0; p < 6; ++p) {
         if (!((m >> p) & 1)) continue;
-        v += ws.h[p * 6 + p];
+        v += ws.hd[p];
         for (int r = 0; r < 6; ++r)
           if ((m >> r) & 1) v += 0.5 * (ws.J[p * 6 + r] - ws.K[p * 6 + r]);
       }
@@ -416,29 +451,93 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
     }
     __syncwarp();
     if (lane == 0) {
-      double v = ws.ecore + 2.0 * ws.hsd[0];
-      const int m = cs.mask[0];
-      for (int p = 0; p < 6; ++p)
-        for (int r = 0; r < 6; ++r)
-          if (((m >> p) & 1) && ((m >> r) & 1)) v += ws.J[p * 6 + r];
-      ws.eshift = v;
+      double ec = *a.e0;
+      for (int k = 0; k < 3; ++k) ec -= ws.hd[k] + ws.F[k * 7];
+      ws.ecore = ec;
+      double v = ec + 2.0 * ws.hsd[0];
+      for (int p = 0; p < 3; ++p)
+        for (int r = 0; r < 3; ++r) v += ws.J[p * 6 + r];
+      ws.eshift = v;  // <Phi|H|Phi>
+      ws.ctrl[0] = 1;
+      ws.ctrl[2] = kSpaceNoConv;
+      ws.ctrl[3] = 0;
+      ws.theta = 0.0;
+      ws.G[0] = 0.0;
+      ws.y[0] = 1.0;
+      ws.yf[0] = 1.f;
     }
     __syncwarp();
-    for (int d = lane; d < NDET; d += 32) {
-      const int ia = d / NS, ib = d % NS;
-      const int ma = cs.mask[ia], mb = cs.mask[ib];
-      double v = ws.ecore + ws.hsd[ia] + ws.hsd[ib];
-      for (int p = 0; p < 6; ++p) {
-        if (!((ma >> p) & 1)) continue;
-        for (int r = 0; r < 6; ++r)
-          if ((mb >> r) & 1) v += ws.J[p * 6 + r];
+    // ---- Phi fast path: sigma(Phi) = column 0 of H (0 at Phi after the shift) --------------
+    // Only determinants connected to Phi by single or double replacements are nonzero.  If the
+    // residual of Phi is already below the tolerance the root is Phi, the increment is zero and
+    // the space is done without building the full string operator or the diagonal.
+    const bool phi_start = (guess_in == nullptr);
+    if (phi_start) {
+      if (lane < NS) {  // hcol[I] = Hs[I][0]: same-spin coupling of string I to the Phi string
+        const int I = lane;
+        float hc = 0.f;
+        if (I != 0) {
+          for (int u = 0; u < NSG; ++u) {
+            const int e = I * NSG + u;
+            const int pq = cs.pq[e], Kk = cs.J[e];
+            const float s1 = (float)cs.sg[e];
+            if (Kk == 0) hc = fmaf(s1, ws.hp[pq], hc);
+            for (int v = 0; v < NSG; ++v) {
+              const int e2 = Kk * NSG + v;
+              if (cs.J[e2] == 0) hc = fmaf(0.5f * s1 * (float)cs.sg[e2], ws.Wt[pq * NF + cs.pq[e2]], hc);
+            }
+          }
+        }
+        ws.dh[I] = hc;  // (dh is rebuilt below if the full operator is needed)
       }
-      ws.diag[d] = (float)(v - ws.eshift);
-      float g0 = (d == 0) ? 1.f : 0.f;
-      if (guess_in) g0 = guess_in[(size_t)s * NDET + d];
-      ws.V[d] = g0;
+      __syncwarp();
+      float rr = 0.f;
+      if (lane < NS) {
+        const int Ia = lane;
+        float col[NS];
+#pragma unroll
+        for (int b = 0; b < NS; ++b) col[b] = 0.f;
+        if (Ia != 0) col[0] = ws.dh[Ia];
+        else
+          for (int b = 1; b < NS; ++b) col[b] = ws.dh[b];
+        for (int u = 0; u < NSG; ++u) {
+          const int e = Ia * NSG + u;
+          if (cs.J[e] != 0) continue;
+          const float su = (float)cs.sg[e];
+          const int pq = cs.pq[e];
+#pragma unroll
+          for (int b = 0; b < NS; ++b) {
+            float acc = 0.f;
+            for (int v = 0; v < NSG; ++v) {
+              const int e2 = b * NSG + v;
+              if (cs.J[e2] == 0) acc = fmaf((float)cs.sg[e2], ws.Wt[pq * NF + cs.pq[e2]], acc);
+            }
+            col[b] = fmaf(su, acc, col[b]);
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+          const float cv = (Ia == 0 && b == 0) ? 0.f : col[b];
+          ws.S[Ia * NS + b] = cv;
+          ws.V[Ia * NS + b] = (Ia == 0 && b == 0) ? 1.f : 0.f;
+          rr = fmaf(cv, cv, rr);
+        }
+      }
+      const double rphi = sqrt((double)wsum(rr));
+      __syncwarp();
+      if (rphi < tol && isfinite(rphi)) {  // converged at Phi: E = <Phi|H|Phi>, X = 0
+        if (lane == 0) {
+          a.energy[oidx] = ws.eshift;
+          a.status[oidx] = kSpaceOk;
+          if (a.iters) a.iters[oidx] = 0;
+        }
+        if (guess_out)
+          for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (d == 0) ? 1.f : 0.f;
+        __syncwarp();
+        continue;
+      }
     }
-    // off-diagonal same-spin string operator (FP32): row I owned by lane I
+    // ---- same-spin string operator, off-diagonal (row I owned by lane I) ---------------------
     if (lane < NS) {
       const int I = lane;
       for (int j = 0; j < NS; ++j) ws.Hs[I * NS + j] = 0.f;
@@ -446,46 +545,52 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
         const int e = I * NSG + u;
         const int pq = cs.pq[e], Kk = cs.J[e];
         const float s1 = (float)cs.sg[e];
-        if (Kk != I) {  // one-body h'_pq = h_pq - 1/2 sum_r W_prrq, p != q
-          const int p = pq / 6, q = pq % 6;
-          double hp = ws.h[pq];
-          for (int r = 0; r < 6; ++r)
-            hp -= 0.5 * a.W[(size_t)ws.orb[p] * n3 + (size_t)ws.orb[r] * n2 + (size_t)ws.orb[r] * n1 + ws.orb[q]];
-          ws.Hs[I * NS + Kk] += s1 * (float)hp;
-        }
+        if (Kk != I) ws.Hs[I * NS + Kk] += s1 * ws.hp[pq];
         for (int v = 0; v < NSG; ++v) {
           const int e2 = Kk * NSG + v;
           const int J2 = cs.J[e2];
-          if (J2 == I) continue;  // the diagonal is kept in FP64 elsewhere
+          if (J2 == I) continue;  // the diagonal is kept in FP64
           ws.Hs[I * NS + J2] += 0.5f * s1 * (float)cs.sg[e2] * ws.Wt[pq * NF + cs.pq[e2]];
         }
       }
     }
-    if (lane == 0) {
-      ws.ctrl[0] = 1;
-      ws.ctrl[2] = kSpaceNoConv;
-      ws.ctrl[3] = 0;
+    // the diagonal (needed by sigma and the preconditioner) relative to <Phi|H|Phi>: string
+    // parts as FP64 differences, the alpha-beta Coulomb sum J(Ia, Ib) in FP32 via row sums
+    if (lane < NS) ws.dh[lane] = (float)(ws.hsd[lane] - ws.hsd[0]);
+    for (int t = lane; t < 6 * NS; t += 32) {  // jb[p][Ib] = sum_{r in Ib} J_pr
+      const int p = t / NS, b = t % NS, mb = cs.mask[b];
+      float v = 0.f;
+      for (int r = 0; r < 6; ++r)
+        if ((mb >> r) & 1) v += (float)ws.J[p * 6 + r];
+      ws.jb[t] = v;
     }
     __syncwarp();
-    // normalise start vector, S0 = sigma(V0), G00
-    {
+    for (int d = lane; d < NDET; d += 32) {
+      const int ia = d / NS, ib = d % NS;
+      const int ma = cs.mask[ia];
+      float jj = 0.f, j0 = 0.f;
+      for (int p = 0; p < 6; ++p) {
+        if ((ma >> p) & 1) jj += ws.jb[p * NS + ib];
+        if (p < 3) j0 += ws.jb[p * NS + 0];
+      }
+      ws.diag[d] = (d == 0) ? 0.f : ws.dh[ia] + ws.dh[ib] + (jj - j0);
+      if (!phi_start) ws.V[d] = guess_in[(size_t)s * NDET + d];
+    }
+    __syncwarp();
+    if (!phi_start) {
       float p = 0.f;
       for (int d = lane; d < NDET; d += 32) p = fmaf(ws.V[d], ws.V[d], p);
       const float nr = sqrtf(wsum(p));
       const float inv = (nr > 0.f) ? 1.f / nr : 0.f;
       for (int d = lane; d < NDET; d += 32) ws.V[d] = (nr > 0.f) ? ws.V[d] * inv : ((d == 0) ? 1.f : 0.f);
       __syncwarp();
-    }
-    sigma_warp(cs, ws, ws.V, ws.S, lane);
-    {
-      float p = 0.f;
-      for (int d = lane; d < NDET; d += 32) p = fmaf(ws.V[d], ws.S[d], p);
-      p = wsum(p);
+      sigma_warp(cs, ws, ws.V, ws.S, lane);
+      float g = 0.f;
+      for (int d = lane; d < NDET; d += 32) g = fmaf(ws.V[d], ws.S[d], g);
+      g = wsum(g);
       if (lane == 0) {
-        ws.G[0] = p;
-        ws.theta = p;
-        ws.y[0] = 1.0;
-        ws.yf[0] = 1.f;
+        ws.G[0] = g;
+        ws.theta = g;
       }
       __syncwarp();
     }
@@ -651,13 +756,15 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
     const double inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.0 / c0 : 0.0;
     if (guess_out && st == kSpaceOk)
       for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (float)((double)ws.S[d] * inv0);
+    double* x1 = reinterpret_cast<double*>(ws.V);  // V is free now: 9 + 81 doubles of scratch
+    double* x2 = x1 + 9;
     if (lane < 9) {
       const int i = lane / 3, aa = lane % 3;
       double sg;
       const int J = phi_single(cs, i, 3 + aa, &sg);
       const double ca = sg * (double)ws.S[J * NS] * inv0;
       const double cb = sg * (double)ws.S[J] * inv0;
-      ws.x1[lane] = 0.5 * (ca + cb);
+      x1[lane] = 0.5 * (ca + cb);
     }
     __syncwarp();
     for (int idx = lane; idx < 81; idx += 32) {
@@ -665,20 +772,20 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
       double sa, sb;
       const int ja = phi_single(cs, i, 3 + aa, &sa);
       const int jb = phi_single(cs, j, 3 + b, &sb);
-      ws.x2[idx] = sa * sb * (double)ws.S[ja * NS + jb] * inv0 - ws.x1[i * 3 + aa] * ws.x1[j * 3 + b];
+      x2[idx] = sa * sb * (double)ws.S[ja * NS + jb] * inv0 - x1[i * 3 + aa] * x1[j * 3 + b];
     }
     __syncwarp();
     if (st == kSpaceOk && a.owner1 && lane < 9) {
       const int i = lane / 3, aa = lane % 3;
       const size_t g = (size_t)ws.orb[i] * a.nvir + (ws.orb[3 + aa] - a.nocc);
-      if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + ws.x1[lane];
+      if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + x1[lane];
     }
     if (st == kSpaceOk && a.owner2) {
       for (int idx = lane; idx < 81; idx += 32) {
         const int i = idx / 27, j = (idx / 9) % 3, aa = (idx / 3) % 3, b = idx % 3;
         const size_t g = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[3 + aa] - a.nocc)) * a.nvir +
                          (ws.orb[3 + b] - a.nocc);
-        if (a.owner2[g] == sidx) a.t2_new[g] = a.t2_old[g] + 0.5 * (ws.x2[idx] + ws.x2[((j * 3 + i) * 3 + b) * 3 + aa]);
+        if (a.owner2[g] == sidx) a.t2_new[g] = a.t2_old[g] + 0.5 * (x2[idx] + x2[((j * 3 + i) * 3 + b) * 3 + aa]);
       }
     }
     if (lane == 0) {
