@@ -71,7 +71,10 @@ typedef struct {
   int32_t precision;          /* qflow_precision                                            */
   int32_t max_iter;           /* Davidson iteration limit per space (default 60)            */
   double tol;                 /* Davidson residual 2-norm (default 1e-9 fp64, 1e-6 mixed)   */
-  int32_t diis;               /* 0 = off, else DIIS history length on the pool (<= 8)       */
+  int32_t diis;               /* 0 = off, else Pulay DIIS on the pool with a history of 2..8
+                                 sweeps (FP64, on the device; not in the paper: it accelerates
+                                 the sweep iteration without moving its fixed point).  The
+                                 history restarts at qflow_set_amplitudes.                  */
   int32_t guess;              /* 0 = Phi, 1 = previous sweep's root of the same space (keeps
                                  one CI vector per space on the device: 400 x 4 B per 6e6o
                                  space in mixed precision, x 8 B in FP64).  In a flow the pool

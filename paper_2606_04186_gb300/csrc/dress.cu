@@ -390,7 +390,18 @@ size_t carve(void* base, int n, int o, Work* w) {
   return off;
 }
 
+__global__ void k_to_f32(const double* __restrict__ W, float* __restrict__ W32, size_t m) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m; x += (size_t)gridDim.x * blockDim.x)
+    W32[x] = (float)W[x];
+}
+
 }  // namespace
+
+cudaError_t launch_to_f32(const double* W, float* W32, size_t count, cudaStream_t st) {
+  const unsigned g = blocks_for(count) > 152u * 64u ? 152u * 64u : blocks_for(count);
+  k_to_f32<<<g, TPB, 0, st>>>(W, W32, count);
+  return cudaGetLastError();
+}
 
 size_t dress_workspace_bytes(int n, int nocc) {
   Work w;

@@ -142,6 +142,8 @@ struct qflow_ctx {
   bool have_energy = false;
   int64_t n_t1 = 0, n_t2 = 0;
   void* guess[4] = {nullptr, nullptr, nullptr, nullptr};  // previous roots per size class (opt.guess == 1)
+  void* diis = nullptr;                                   // DIIS ring (opt.diis > 0)
+  float* W32 = nullptr;                                   // FP32 copy of W (mixed precision)
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase marks of the last sweep
   int64_t last_launches = 0;                                  // kernels launched by the last sweep
 };
@@ -161,6 +163,8 @@ void free_ctx(qflow_ctx* c) {
     if (p) cudaFree(p);
   for (void* p : c->guess)
     if (p) cudaFree(p);
+  if (c->diis) cudaFree(c->diis);
+  if (c->W32) cudaFree(c->W32);
   if (c->red_host) cudaFreeHost(c->red_host);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -220,6 +224,10 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     return QFLOW_ERR_ARG;
   }
   if (c->opt.max_iter <= 0) c->opt.max_iter = 60;
+  if (c->opt.diis < 0 || c->opt.diis > QFLOW_DIIS_MAX || c->opt.diis == 1) {
+    delete c;
+    return QFLOW_ERR_ARG;
+  }
   if (!(c->opt.tol > 0.0)) c->opt.tol = (c->opt.precision == QFLOW_PREC_MIXED) ? 1e-6 : 1e-9;
   c->n = n;
   c->nocc = nocc;
@@ -293,6 +301,11 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   if (e == cudaSuccess) e = dalloc(&c->red, 4);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->red_host), 4 * sizeof(double));
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+  if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) e = dalloc(&c->W32, n4);
+  if (c->opt.diis > 0 && e == cudaSuccess) {
+    e = cudaMalloc(&c->diis, qf::diis_workspace_bytes(c->opt.diis, (int64_t)npool));
+    if (e == cudaSuccess) e = qf::diis_reset(c->diis, c->opt.diis, (int64_t)npool, c->stream);
+  }
   if (c->opt.guess == 1) {
     const size_t ndet[4] = {0, 4, 36, 400};
     const size_t esz = (c->opt.precision == QFLOW_PREC_MIXED) ? sizeof(float) : sizeof(double);
@@ -334,6 +347,10 @@ int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
     e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
                          c->dwork_bytes, c->stream);
   launches += qf::dress_launch_count(c->n, c->nocc);
+  if (e == cudaSuccess && c->W32) {
+    e = qf::launch_to_f32(c->W, c->W32, (size_t)c->n * c->n * c->n * c->n, c->stream);
+    ++launches;
+  }
   if (e == cudaSuccess) e = cudaEventRecord(c->ev[1], c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->pool_new, c->pool, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
@@ -359,12 +376,17 @@ int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
     a.energy = c->energy;
     a.status = c->status;
     a.iters = c->iters;
+    a.W32 = c->W32;
     a.guess = c->guess[k];
     a.save_root = c->guess[k] ? 1 : 0;
     a.max_iter = c->opt.max_iter;
     a.tol = c->opt.tol;
     e = qf::launch_solve(k, c->opt.precision, a, c->stream);
     ++launches;
+  }
+  if (e == cudaSuccess && c->diis) {
+    e = qf::launch_diis(c->diis, c->opt.diis, c->pool, c->pool_new, (int64_t)npool, c->stream);
+    launches += 4;
   }
   if (e == cudaSuccess) e = cudaEventRecord(c->ev[2], c->stream);
   if (e == cudaSuccess)
@@ -424,6 +446,7 @@ int qflow_set_amplitudes(qflow_handle c, const double* t1, const double* t2) {
   cudaError_t e = cudaMemcpyAsync(c->pool, t1, sizeof(double) * (size_t)c->n_t1, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->pool + c->n_t1, t2, sizeof(double) * (size_t)c->n_t2, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && c->diis) e = qf::diis_reset(c->diis, c->opt.diis, c->n_t1 + c->n_t2, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_status(e);
 }

@@ -7,6 +7,8 @@
 
 #include "../../include/qflow.h"
 
+#define QFLOW_DIIS_MAX 8
+
 namespace qf {
 
 // Per-space solver status codes written by the solve kernels.
@@ -30,6 +32,7 @@ struct SolveArgs {
   double* energy;
   int32_t* status;
   int32_t* iters;
+  const float* W32;  // nullable FP32 copy of W (mixed path)
   void* guess;  // start vectors / saved roots: double (FP64 path) or float (mixed path)
   int32_t save_root;
   int32_t max_iter;
@@ -39,7 +42,11 @@ struct SolveArgs {
 // Launch the batched solver for spaces of size class k (1, 2 or 3) in the given precision.
 cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st);
 // Warp-per-space mixed-precision solver for (3,3) spaces (solve_warp.cu).
-cudaError_t launch_solve_warp33(const SolveArgs& a, const float* guess_in, float* guess_out, cudaStream_t st);
+// W32: optional FP32 copy of W (same layout); NULL reads and converts the FP64 W.
+cudaError_t launch_solve_warp33(const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
+                                cudaStream_t st);
+// FP32 copy of the dressed two-body integrals for the mixed-precision solver.
+cudaError_t launch_to_f32(const double* W, float* W32, size_t count, cudaStream_t st);
 
 // Dressing (step a) on caller-provided device buffers; returns a CUDA error code.
 size_t dress_workspace_bytes(int n, int nocc);
@@ -51,5 +58,11 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
 size_t mean_maxdiff_workspace(int64_t nspaces, int64_t nt);
 cudaError_t launch_reduce(const double* energy, const int32_t* status, int64_t nspaces, const double* t_old,
                           const double* t_new, int64_t nt, double* out4, void* work, cudaStream_t st);
+
+// Pool DIIS (diis.cu): workspace size for a ring of m vectors of length N, the per-sweep step
+// (t_new is replaced by the extrapolation once two vectors are stored) and the history reset.
+size_t diis_workspace_bytes(int m, int64_t N);
+cudaError_t launch_diis(void* work, int m, const double* t_old, double* t_new, int64_t N, cudaStream_t st);
+cudaError_t diis_reset(void* work, int m, int64_t N, cudaStream_t st);
 
 }  // namespace qf

@@ -615,7 +615,7 @@ cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t 
     case 2: return mixed ? launch_k<2, float>(a, st) : launch_k<2, double>(a, st);
     case 3:
       if (mixed)
-        return launch_solve_warp33(a, static_cast<const float*>(a.guess),
+        return launch_solve_warp33(a, a.W32, static_cast<const float*>(a.guess),
                                    a.save_root ? static_cast<float*>(a.guess) : nullptr, st);
       return launch_k<3, double>(a, st);
     default: return cudaErrorInvalidValue;

@@ -116,10 +116,10 @@ struct alignas(16) WarpSmem {  // 16-byte rows: sigma reads them as float4
   double hsd[NS];      // same-spin string diagonal (FP64)
   float dh[NS];        // hsd[I] - hsd[0] (FP64 difference, rounded); Hs[I][0] on the Phi path
   float jb[6 * NS];    // jb[p][Ib] = sum_{r in Ib} J_pr
-  double G[KM * KM];
-  double y[KM];
-  float yf[KM];
-  double ecore, eshift, theta;
+  float G[KM * KM];    // projected matrix, G[i*KM+j] = V_i . S_j
+  float yf[KM];        // Ritz coefficients
+  float theta;         // Ritz value relative to eshift
+  double ecore, eshift;
   int orb[6];
   int ctrl[4];  // [0] subspace size, [1] valid, [2] status, [3] iterations
 };
@@ -164,8 +164,8 @@ __device__ __forceinline__ float wsum(float v) {
 }
 
 // sigma = H c restricted to off-diagonal couplings plus the shifted diagonal.
-__device__ __forceinline__ void sigma_warp(const CtaSmem& cs, const WarpSmem& ws, const float* __restrict__ c,
-                                           float* __restrict__ out, int lane) {
+__device__ __noinline__ void sigma_warp(const CtaSmem& cs, const WarpSmem& ws, const float* __restrict__ c,
+                                        float* __restrict__ out, int lane) {
   if (lane < NS) {
     const int Ia = lane;
     float acc[NS];
@@ -256,57 +256,58 @@ __device__ __forceinline__ void sigma_warp(const CtaSmem& cs, const WarpSmem& ws
   __syncwarp();
 }
 
-// Phi-tracking eigenpair of the k x k projected matrix (FP64, lane 0): shifted inverse
-// iteration from the previous Ritz value, then Rayleigh-quotient refinement.
-__device__ void small_eig(const double* G, int k, double shift, double* y, double* theta) {
-  double a[KM * KM], z[KM];
+// Phi-tracking eigenpair of the k x k projected matrix (lane 0): shifted inverse iteration
+// from the previous Ritz value, then Rayleigh-quotient refinement.  The projected matrix is
+// built from FP32 vectors, so it is solved in FP32 too.
+__device__ __noinline__ void small_eig(const float* G, int k, float shift, float* y, float* theta) {
+  float a[KM * KM], z[KM];
   for (int phase = 0; phase < 5; ++phase) {
-    const double sg = (phase < 2) ? shift : *theta;
+    const float sg = (phase < 2) ? shift : *theta;
     for (int i = 0; i < k; ++i)
-      for (int j = 0; j < k; ++j) a[i * KM + j] = G[i * KM + j] - ((i == j) ? sg : 0.0);
+      for (int j = 0; j < k; ++j) a[i * KM + j] = G[i * KM + j] - ((i == j) ? sg : 0.f);
     for (int i = 0; i < k; ++i) z[i] = y[i];
     for (int col = 0; col < k; ++col) {
       int piv = col;
-      double best = fabs(a[col * KM + col]);
+      float best = fabsf(a[col * KM + col]);
       for (int r = col + 1; r < k; ++r)
-        if (fabs(a[r * KM + col]) > best) {
-          best = fabs(a[r * KM + col]);
+        if (fabsf(a[r * KM + col]) > best) {
+          best = fabsf(a[r * KM + col]);
           piv = r;
         }
       if (piv != col) {
         for (int j = 0; j < k; ++j) {
-          const double t = a[col * KM + j];
+          const float t = a[col * KM + j];
           a[col * KM + j] = a[piv * KM + j];
           a[piv * KM + j] = t;
         }
-        const double t = z[col];
+        const float t = z[col];
         z[col] = z[piv];
         z[piv] = t;
       }
-      double p = a[col * KM + col];
-      if (fabs(p) < 1e-300) p = (p < 0.0) ? -1e-300 : 1e-300;
+      float p = a[col * KM + col];
+      if (fabsf(p) < 1e-30f) p = (p < 0.f) ? -1e-30f : 1e-30f;
       a[col * KM + col] = p;
-      const double ip = 1.0 / p;
+      const float ip = 1.f / p;
       for (int r = col + 1; r < k; ++r) {
-        const double f = a[r * KM + col] * ip;
+        const float f = a[r * KM + col] * ip;
         for (int j = col + 1; j < k; ++j) a[r * KM + j] -= f * a[col * KM + j];
         z[r] -= f * z[col];
       }
     }
     for (int r = k - 1; r >= 0; --r) {
-      double s = z[r];
+      float s = z[r];
       for (int j = r + 1; j < k; ++j) s -= a[r * KM + j] * z[j];
       z[r] = s / a[r * KM + r];
     }
-    double nrm = 0.0;
+    float nrm = 0.f;
     for (int i = 0; i < k; ++i) nrm += z[i] * z[i];
-    nrm = sqrt(nrm);
-    if (!(nrm > 0.0) || !isfinite(nrm)) break;
-    const double sgn = (z[0] < 0.0) ? -1.0 : 1.0;
-    for (int i = 0; i < k; ++i) y[i] = sgn * z[i] / nrm;
-    double num = 0.0;
+    nrm = sqrtf(nrm);
+    if (!(nrm > 0.f) || !isfinite(nrm)) break;
+    const float sc = ((z[0] < 0.f) ? -1.f : 1.f) / nrm;
+    for (int i = 0; i < k; ++i) y[i] = sc * z[i];
+    float num = 0.f;
     for (int i = 0; i < k; ++i) {
-      double gy = 0.0;
+      float gy = 0.f;
       for (int j = 0; j < k; ++j) gy += G[i * KM + j] * y[j];
       num += y[i] * gy;
     }
@@ -314,7 +315,8 @@ __device__ void small_eig(const double* G, int k, double shift, double* y, doubl
   }
 }
 
-__global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, const float* __restrict__ guess_in,
+__global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, const float* __restrict__ W32,
+                                                                 const float* __restrict__ guess_in,
                                                                  float* __restrict__ guess_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CtaSmem& cs = *reinterpret_cast<CtaSmem*>(smem_raw);
@@ -356,8 +358,9 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
   WarpSmem& ws = cs.w[warp];
   const int n = a.n;
   const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
-  const double tol = a.tol;
+  const float tol = (float)a.tol;
 
+#pragma unroll 1
   for (int64_t s = (int64_t)blockIdx.x * WARPS + warp; s < a.nspaces; s += (int64_t)gridDim.x * WARPS) {
     // ---- validate -------------------------------------------------------------------------
     if (lane == 0) {
@@ -383,20 +386,35 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
       __syncwarp();
       continue;
     }
-    // ---- gather: 666 unique elements of the pair-symmetric W block, all loads in flight ----
+    // ---- gather ------------------------------------------------------------------------------
+    // FP32 couplings: the 666 unique elements of the pair-symmetric W block (all loads in
+    // flight); FP64: J_pr = W_pprr, K_pr = W_prrp and the F block (energy-carrying parts).
     {
-      size_t rowp[6];
+      size_t ro[6];
 #pragma unroll
-      for (int t = 0; t < 6; ++t) rowp[t] = (size_t)ws.orb[t];
+      for (int t = 0; t < 6; ++t) ro[t] = (size_t)ws.orb[t];
       constexpr int PER = (NPAIR + 31) / 32;  // 21
-      double wv[PER];
+      float wv[PER];
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
         const int t = lane + 32 * k;
-        wv[k] = 0.0;
+        wv[k] = 0.f;
         if (t < NPAIR) {
           const int pr = cs.pair[t], P = pr & 255, R = pr >> 8;
-          wv[k] = a.W[rowp[P / 6] * n3 + rowp[P % 6] * n2 + rowp[R / 6] * n1 + rowp[R % 6]];
+          const size_t g = ro[P / 6] * n3 + ro[P % 6] * n2 + ro[R / 6] * n1 + ro[R % 6];
+          wv[k] = W32 ? W32[g] : (float)a.W[g];
+        }
+      }
+      double jv[2], kv[2], fv[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int t = lane + 32 * k;
+        jv[k] = kv[k] = fv[k] = 0.0;
+        if (t < NF) {
+          const size_t p = ro[t / 6], r = ro[t % 6];
+          jv[k] = a.W[p * n3 + p * n2 + r * n1 + r];
+          kv[k] = a.W[p * n3 + r * n2 + r * n1 + p];
+          fv[k] = a.F[p * n1 + r];
         }
       }
 #pragma unroll
@@ -404,38 +422,37 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
         const int t = lane + 32 * k;
         if (t < NPAIR) {
           const int pr = cs.pair[t], P = pr & 255, R = pr >> 8;
-          const int p = P / 6, q = P % 6, r = R / 6, u = R % 6;
-          const double w = wv[k];
-          const bool jj = (p == q && r == u);  // W_pprr: reaches only the diagonal
-          const float wf = jj ? 0.f : (float)w;
+          const bool jj = (P / 6 == P % 6) && (R / 6 == R % 6);  // W_pprr: reaches only the diagonal
+          const float wf = jj ? 0.f : wv[k];
           ws.Wt[P * NF + R] = wf;
           ws.Wt[R * NF + P] = wf;
-          if (jj) {
-            ws.J[p * 6 + r] = w;
-            ws.J[r * 6 + p] = w;
-          }
-          if (q == r && u == p) {  // W_prrp = K_pr (and its pair partner K_rp)
-            ws.K[p * 6 + r] = w;
-            ws.K[r * 6 + p] = w;
-          }
         }
       }
-      for (int idx = lane; idx < NF; idx += 32) ws.F[idx] = a.F[rowp[idx / 6] * n1 + rowp[idx % 6]];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int t = lane + 32 * k;
+        if (t < NF) {
+          ws.J[t] = jv[k];
+          ws.K[t] = kv[k];
+          ws.F[t] = fv[k];
+        }
+      }
     }
     __syncwarp();
     // ---- fold (vacuum order over the active orbitals) -------------------------------------
-    // diagonal h_pp = F_pp - sum_k (2 J_pk - K_pk) in FP64; off-diagonal h' in FP32 from Wt
+    // h_pp = F_pp - sum_k (2 J_pk - K_pk) in FP64; off-diagonal h' = h - 1/2 sum_r W_prrq in FP32
     if (lane < 6) {
       double v = ws.F[lane * 7];
       for (int k = 0; k < 3; ++k) v -= 2.0 * ws.J[lane * 6 + k] - ws.K[lane * 6 + k];
       ws.hd[lane] = v;
     }
+#pragma unroll 1
     for (int idx = lane; idx < NF; idx += 32) {
       const int p = idx / 6, q = idx % 6;
       float v = (float)ws.F[idx];
       for (int k = 0; k < 3; ++k) v -= 2.f * ws.Wt[idx * NF + k * 7] - ws.Wt[(p * 6 + k) * NF + k * 6 + q];
       for (int r = 0; r < 6; ++r) v -= 0.5f * ws.Wt[(p * 6 + r) * NF + r * 6 + q];
-      ws.hp[idx] = (p == q) ? 0.f : v;  // diagonal replacements are handled in FP64
+      ws.hp[idx] = (p == q) ? 0.f : v;
     }
     __syncwarp();
     if (lane < NS) {  // same-spin string diagonal: sum_{p in I} h_pp + 1/2 sum_{p,r in I} (J_pr - K_pr)
@@ -461,9 +478,8 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
       ws.ctrl[0] = 1;
       ws.ctrl[2] = kSpaceNoConv;
       ws.ctrl[3] = 0;
-      ws.theta = 0.0;
-      ws.G[0] = 0.0;
-      ws.y[0] = 1.0;
+      ws.theta = 0.f;
+      ws.G[0] = 0.f;
       ws.yf[0] = 1.f;
     }
     __syncwarp();
@@ -473,59 +489,58 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
     // the space is done without building the full string operator or the diagonal.
     const bool phi_start = (guess_in == nullptr);
     if (phi_start) {
-      if (lane < NS) {  // hcol[I] = Hs[I][0]: same-spin coupling of string I to the Phi string
+      if (lane < NS) {  // dh[I] <- Hs[I][0]: same-spin coupling of string I to the Phi string
         const int I = lane;
         float hc = 0.f;
         if (I != 0) {
+#pragma unroll 1
           for (int u = 0; u < NSG; ++u) {
             const int e = I * NSG + u;
             const int pq = cs.pq[e], Kk = cs.J[e];
             const float s1 = (float)cs.sg[e];
             if (Kk == 0) hc = fmaf(s1, ws.hp[pq], hc);
+#pragma unroll 1
             for (int v = 0; v < NSG; ++v) {
               const int e2 = Kk * NSG + v;
               if (cs.J[e2] == 0) hc = fmaf(0.5f * s1 * (float)cs.sg[e2], ws.Wt[pq * NF + cs.pq[e2]], hc);
             }
           }
         }
-        ws.dh[I] = hc;  // (dh is rebuilt below if the full operator is needed)
+        ws.dh[I] = hc;
+      }
+      for (int d = lane; d < NDET; d += 32) {
+        ws.S[d] = 0.f;
+        ws.V[d] = (d == 0) ? 1.f : 0.f;
       }
       __syncwarp();
-      float rr = 0.f;
       if (lane < NS) {
         const int Ia = lane;
-        float col[NS];
-#pragma unroll
-        for (int b = 0; b < NS; ++b) col[b] = 0.f;
-        if (Ia != 0) col[0] = ws.dh[Ia];
+        if (Ia != 0) ws.S[Ia * NS] = ws.dh[Ia];
         else
-          for (int b = 1; b < NS; ++b) col[b] = ws.dh[b];
+          for (int b = 1; b < NS; ++b) ws.S[b] = ws.dh[b];
+        // alpha-beta: replacements (pq) into Ia from the Phi string times (rs) into Ib from it
+#pragma unroll 1
         for (int u = 0; u < NSG; ++u) {
           const int e = Ia * NSG + u;
           if (cs.J[e] != 0) continue;
           const float su = (float)cs.sg[e];
           const int pq = cs.pq[e];
-#pragma unroll
+#pragma unroll 1
           for (int b = 0; b < NS; ++b) {
             float acc = 0.f;
             for (int v = 0; v < NSG; ++v) {
               const int e2 = b * NSG + v;
               if (cs.J[e2] == 0) acc = fmaf((float)cs.sg[e2], ws.Wt[pq * NF + cs.pq[e2]], acc);
             }
-            col[b] = fmaf(su, acc, col[b]);
+            if (Ia * NS + b != 0) ws.S[Ia * NS + b] += su * acc;
           }
         }
-#pragma unroll
-        for (int b = 0; b < NS; ++b) {
-          const float cv = (Ia == 0 && b == 0) ? 0.f : col[b];
-          ws.S[Ia * NS + b] = cv;
-          ws.V[Ia * NS + b] = (Ia == 0 && b == 0) ? 1.f : 0.f;
-          rr = fmaf(cv, cv, rr);
-        }
       }
-      const double rphi = sqrt((double)wsum(rr));
       __syncwarp();
-      if (rphi < tol && isfinite(rphi)) {  // converged at Phi: E = <Phi|H|Phi>, X = 0
+      float rr = 0.f;
+      for (int d = lane; d < NDET; d += 32) rr = fmaf(ws.S[d], ws.S[d], rr);
+      const float rphi = sqrtf(wsum(rr));
+      if (rphi < tol) {  // converged at Phi: E = <Phi|H|Phi>, X = 0
         if (lane == 0) {
           a.energy[oidx] = ws.eshift;
           a.status[oidx] = kSpaceOk;
@@ -540,12 +555,15 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
     // ---- same-spin string operator, off-diagonal (row I owned by lane I) ---------------------
     if (lane < NS) {
       const int I = lane;
+#pragma unroll 1
       for (int j = 0; j < NS; ++j) ws.Hs[I * NS + j] = 0.f;
+#pragma unroll 1
       for (int u = 0; u < NSG; ++u) {
         const int e = I * NSG + u;
         const int pq = cs.pq[e], Kk = cs.J[e];
         const float s1 = (float)cs.sg[e];
         if (Kk != I) ws.Hs[I * NS + Kk] += s1 * ws.hp[pq];
+#pragma unroll 1
         for (int v = 0; v < NSG; ++v) {
           const int e2 = Kk * NSG + v;
           const int J2 = cs.J[e2];
@@ -554,10 +572,11 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
         }
       }
     }
-    // the diagonal (needed by sigma and the preconditioner) relative to <Phi|H|Phi>: string
-    // parts as FP64 differences, the alpha-beta Coulomb sum J(Ia, Ib) in FP32 via row sums
+    // the diagonal relative to <Phi|H|Phi>: string parts as FP64 differences, the alpha-beta
+    // Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
     if (lane < NS) ws.dh[lane] = (float)(ws.hsd[lane] - ws.hsd[0]);
-    for (int t = lane; t < 6 * NS; t += 32) {  // jb[p][Ib] = sum_{r in Ib} J_pr
+#pragma unroll 1
+    for (int t = lane; t < 6 * NS; t += 32) {
       const int p = t / NS, b = t % NS, mb = cs.mask[b];
       float v = 0.f;
       for (int r = 0; r < 6; ++r)
@@ -565,6 +584,7 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
       ws.jb[t] = v;
     }
     __syncwarp();
+#pragma unroll 1
     for (int d = lane; d < NDET; d += 32) {
       const int ia = d / NS, ib = d % NS;
       const int ma = cs.mask[ia];
@@ -595,9 +615,10 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
       __syncwarp();
     }
     // ---- Davidson ----------------------------------------------------------------------------
+#pragma unroll 1
     for (int it = 0; it < a.max_iter; ++it) {
       int k = ws.ctrl[0];
-      if (k == KM) {
+      if (k == KM) {  // restart on the Ritz vector
         float pv = 0.f, ps = 0.f;
         for (int d = lane; d < NDET; d += 32) {
           float xv = 0.f, sv = 0.f;
@@ -617,17 +638,17 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
           ws.V[d] *= inv;
           ws.S[d] *= inv;
         }
+        __syncwarp();
         if (lane == 0) {
-          ws.G[0] = (double)ps / (double)pv;
+          ws.G[0] = ps / pv;
           ws.theta = ws.G[0];
-          ws.y[0] = 1.0;
           ws.yf[0] = 1.f;
           ws.ctrl[0] = 1;
         }
         __syncwarp();
         k = 1;
       }
-      const float th = (float)ws.theta;
+      const float th = ws.theta;
       float rr = 0.f;
       float* vk = ws.V + k * NDET;
       for (int d = lane; d < NDET; d += 32) {
@@ -642,8 +663,8 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
         if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
         vk[d] = r / den;
       }
-      const double rnorm = sqrt((double)wsum(rr));
-      if (!isfinite(rnorm) || !isfinite(ws.theta)) {
+      const float rnorm = sqrtf(wsum(rr));
+      if (!isfinite(rnorm) || !isfinite(th)) {
         if (lane == 0) ws.ctrl[2] = kSpaceNonFinite;
         __syncwarp();
         break;
@@ -684,7 +705,7 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
       const float vn = sqrtf(wsum(nn));
       if (!(vn > 1e-6f)) {
         if (lane == 0) {
-          ws.ctrl[2] = (rnorm < 100.0 * tol) ? kSpaceOk : kSpaceNoConv;
+          ws.ctrl[2] = (rnorm < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
           ws.ctrl[3] = it;
         }
         __syncwarp();
@@ -723,14 +744,11 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
         }
         ws.G[k * KM + k] = gkk;
         const int kk = k + 1;
-        double yn[KM];
-        for (int j = 0; j < kk; ++j) yn[j] = (j < k) ? ws.y[j] : 0.0;
-        double thn = ws.theta;
-        small_eig(ws.G, kk, ws.theta - 1e-2, yn, &thn);
-        for (int j = 0; j < kk; ++j) {
-          ws.y[j] = yn[j];
-          ws.yf[j] = (float)yn[j];
-        }
+        float yn[KM];
+        for (int j = 0; j < kk; ++j) yn[j] = (j < k) ? ws.yf[j] : 0.f;
+        float thn = ws.theta;
+        small_eig(ws.G, kk, ws.theta - 1e-2f, yn, &thn);
+        for (int j = 0; j < kk; ++j) ws.yf[j] = yn[j];
         ws.theta = thn;
         ws.ctrl[0] = kk;
         ws.ctrl[3] = it + 1;
@@ -748,48 +766,51 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
     }
     xx = wsum(xx);
     __syncwarp();
-    const double xn = sqrt((double)xx);
-    const double c0 = (double)ws.S[0];
+    const float xn = sqrtf(xx);
+    const float c0 = ws.S[0];
     int st = ws.ctrl[2];
-    if (st == kSpaceOk && !(fabs(c0) >= 1e-3 * xn)) st = kSpaceRoot;
+    if (st == kSpaceOk && !(fabsf(c0) >= 1e-3f * xn)) st = kSpaceRoot;
     if (!isfinite(c0) || !isfinite(ws.theta)) st = kSpaceNonFinite;
-    const double inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.0 / c0 : 0.0;
+    const float inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.f / c0 : 0.f;
     if (guess_out && st == kSpaceOk)
-      for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (float)((double)ws.S[d] * inv0);
-    double* x1 = reinterpret_cast<double*>(ws.V);  // V is free now: 9 + 81 doubles of scratch
-    double* x2 = x1 + 9;
+      for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = ws.S[d] * inv0;
+    float* x1 = ws.V;  // V is free now: 9 + 81 floats of scratch
+    float* x2 = x1 + 9;
     if (lane < 9) {
       const int i = lane / 3, aa = lane % 3;
       double sg;
       const int J = phi_single(cs, i, 3 + aa, &sg);
-      const double ca = sg * (double)ws.S[J * NS] * inv0;
-      const double cb = sg * (double)ws.S[J] * inv0;
-      x1[lane] = 0.5 * (ca + cb);
+      const float f = (sg < 0.0) ? -inv0 : inv0;
+      x1[lane] = 0.5f * f * (ws.S[J * NS] + ws.S[J]);
     }
     __syncwarp();
+#pragma unroll 1
     for (int idx = lane; idx < 81; idx += 32) {
       const int i = idx / 27, j = (idx / 9) % 3, aa = (idx / 3) % 3, b = idx % 3;
       double sa, sb;
       const int ja = phi_single(cs, i, 3 + aa, &sa);
       const int jb = phi_single(cs, j, 3 + b, &sb);
-      x2[idx] = sa * sb * (double)ws.S[ja * NS + jb] * inv0 - x1[i * 3 + aa] * x1[j * 3 + b];
+      const float f = ((sa < 0.0) != (sb < 0.0)) ? -inv0 : inv0;
+      x2[idx] = f * ws.S[ja * NS + jb] - x1[i * 3 + aa] * x1[j * 3 + b];
     }
     __syncwarp();
     if (st == kSpaceOk && a.owner1 && lane < 9) {
       const int i = lane / 3, aa = lane % 3;
       const size_t g = (size_t)ws.orb[i] * a.nvir + (ws.orb[3 + aa] - a.nocc);
-      if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + x1[lane];
+      if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + (double)x1[lane];
     }
     if (st == kSpaceOk && a.owner2) {
+#pragma unroll 1
       for (int idx = lane; idx < 81; idx += 32) {
         const int i = idx / 27, j = (idx / 9) % 3, aa = (idx / 3) % 3, b = idx % 3;
         const size_t g = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[3 + aa] - a.nocc)) * a.nvir +
                          (ws.orb[3 + b] - a.nocc);
-        if (a.owner2[g] == sidx) a.t2_new[g] = a.t2_old[g] + 0.5 * (x2[idx] + x2[((j * 3 + i) * 3 + b) * 3 + aa]);
+        if (a.owner2[g] == sidx)
+          a.t2_new[g] = a.t2_old[g] + (double)(0.5f * (x2[idx] + x2[((j * 3 + i) * 3 + b) * 3 + aa]));
       }
     }
     if (lane == 0) {
-      a.energy[oidx] = ws.eshift + ws.theta;
+      a.energy[oidx] = ws.eshift + (double)ws.theta;
       a.status[oidx] = st;
       if (a.iters) a.iters[oidx] = ws.ctrl[3];
     }
@@ -799,7 +820,8 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
 
 }  // namespace
 
-cudaError_t launch_solve_warp33(const SolveArgs& a, const float* guess_in, float* guess_out, cudaStream_t st) {
+cudaError_t launch_solve_warp33(const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
+                                cudaStream_t st) {
   if (a.nspaces <= 0) return cudaSuccess;
   const size_t smem = sizeof(CtaSmem);
   cudaError_t e = cudaFuncSetAttribute(solve_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -813,7 +835,7 @@ cudaError_t launch_solve_warp33(const SolveArgs& a, const float* guess_in, float
   int64_t grid = (int64_t)sms * per_sm;
   const int64_t need = (a.nspaces + WARPS - 1) / WARPS;
   if (grid > need) grid = need;
-  solve_warp_kernel<<<(unsigned)grid, 32 * WARPS, smem, st>>>(a, guess_in, guess_out);
+  solve_warp_kernel<<<(unsigned)grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out);
   return cudaGetLastError();
 }
 

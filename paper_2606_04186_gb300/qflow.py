@@ -126,7 +126,7 @@ class Flow:
     """One flow on the current CUDA device (handle API of the library)."""
 
     def __init__(self, h, eri, nocc: int, spaces, precision: str = "fp64", max_iter: int | None = None,
-                 tol: float | None = None, guess: str = "phi"):
+                 tol: float | None = None, guess: str = "phi", diis: int = 0):
         h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
         self.n, self.nocc = h.shape[0], nocc
         self.nvir = self.n - nocc
@@ -137,6 +137,7 @@ class Flow:
         if tol is not None:
             opt.tol = tol
         opt.guess = {"phi": 0, "previous": 1}[guess]
+        opt.diis = diis
         self._h = C.c_void_p()
         code = lib().qflow_init(C.byref(self._h), _ptr(h), _ptr(eri), self.n, nocc, _ptr(sp), len(sp), C.byref(opt))
         self.init_status = _check(code, "qflow_init")

@@ -203,3 +203,22 @@ def test_previous_root_guess_same_result(qf, precision):
     assert np.abs(ta[1] - tb[1]).max() < tt
     a.close()
     b.close()
+
+
+def test_diis_flow_matches_oracle(qf):
+    eps, h, g, sp = synth.system_inputs("n10")
+    ref = flow.Flow(h, g, 3, sp, diis=True)
+    gpu = qf.Flow(h, g, 3, sp, precision="fp64", diis=8)
+    for sweep in range(6):
+        er, der, dtr, _ = ref.sweep()
+        de, dt, nf, code = gpu.sweep()
+        assert abs(gpu.energy() - er) < 1e-9
+        t1, t2 = gpu.amplitudes()
+        assert np.abs(t2 - ref.t2).max() < 1e-8 and np.abs(t1 - ref.t1).max() < 1e-8
+    e_cc, *_ = ccsd.ccsd(h, g, 3, tol=1e-13)
+    for _ in range(20):
+        de, dt, nf, code = gpu.sweep()
+        if abs(de) < 1e-11 and dt < 1e-10:
+            break
+    assert abs(gpu.energy() - e_cc) < 1e-9
+    gpu.close()
