@@ -58,8 +58,10 @@ typedef enum {
 
 typedef enum {
   QFLOW_PREC_FP64 = 0,   /* plain: every step in FP64                                        */
-  QFLOW_PREC_MIXED = 1   /* FP32 sigma-vectors and 400-length vector algebra, FP64 projected
-                            eigenproblem, FP64 dressing, energy and amplitude update          */
+  QFLOW_PREC_MIXED = 1   /* dressing: T1 transform, reference energy and Fock-like sums in FP64,
+                            T2 contractions in FP32 added to FP64 bases; solver: FP32 sigma,
+                            vectors and projected eigenproblem, FP64 diagonal/energy shift;
+                            FP64 energy and amplitude update                                  */
 } qflow_precision;
 
 typedef struct {

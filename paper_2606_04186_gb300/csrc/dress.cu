@@ -4,7 +4,9 @@
 // normal ordered with respect to the closed-shell reference and truncated to <= two-body:
 //   E0, F[p][q], W[p][q][r][s] (creators p, r; annihilators q, s; W[pqrs] = W[rspq]).
 //
-// Construction (plain FP64, one thread per output element in every kernel):
+// Construction (one thread per output element, or one block per element for the few long
+// sums; the T2 contractions run in FP64, or in FP32 on an FP32 copy of g~ and t2 for the
+// mixed-precision path, their FP64 base values being added in FP64):
 //   1. T1 exactly: orbital similarity transform of the integrals; creators by (1 - K),
 //      annihilators by (1 + K), K_ai = t_i^a (K^2 = 0) -> h~, g~ (four in-place passes).
 //   2. f~ = h~ + sum_k [2 g~_pqkk - g~_pkkq], E~ = <Phi|H~|Phi>.
@@ -128,80 +130,104 @@ __global__ void k_energy(const double* __restrict__ ht, const double* __restrict
   if (threadIdx.x == 0) *e0 = red[0];
 }
 
-// u = 2 t_ij^ab - t_ij^ba
-__device__ __forceinline__ double U(const double* t2, const Dims& d, int i, int j, int a, int b) {
-  return 2.0 * t2[ti(d, i, j, a, b)] - t2[ti(d, i, j, b, a)];
+// u = 2 t_ij^ab - t_ij^ba in the contraction precision T
+template <typename T>
+__device__ __forceinline__ T Ut(const T* t2, const Dims& d, int i, int j, int a, int b) {
+  return (T)2 * t2[ti(d, i, j, a, b)] - t2[ti(d, i, j, b, a)];
 }
 
-// Foo[m][i] = f~_mi + sum_nef g~_menf u_in^ef ;  Fvv[a][e] = f~_ae - sum_mnf g~_menf u_mn^af
-__global__ void k_foo_fvv(const double* __restrict__ F, const double* __restrict__ W, const double* __restrict__ t2,
-                          double* __restrict__ foo, double* __restrict__ fvv, Dims d) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < d.o * d.o) {
-    const int m = x / d.o, i = x % d.o;
-    double v = F[m * d.n + i];
-    for (int nn = 0; nn < d.o; ++nn)
-      for (int e = 0; e < d.v; ++e)
-        for (int f = 0; f < d.v; ++f) v += W[gi(d, m, d.o + e, nn, d.o + f)] * U(t2, d, i, nn, e, f);
-    foo[x] = v;
-  } else if (x < d.o * d.o + d.v * d.v) {
-    const int y = x - d.o * d.o, a = y / d.v, e = y % d.v;
-    double v = F[(d.o + a) * d.n + d.o + e];
-    for (int m = 0; m < d.o; ++m)
-      for (int nn = 0; nn < d.o; ++nn)
-        for (int f = 0; f < d.v; ++f) v -= W[gi(d, m, d.o + e, nn, d.o + f)] * U(t2, d, m, nn, a, f);
-    fvv[y] = v;
+// Fixed-order block sum (TPB threads) of a per-thread partial; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// One block per output element (FP64, these outputs are few and their sums long):
+//   Foo[m][i] = f~_mi + sum_nef g~_menf u_in^ef           (blocks 0 .. o^2-1)
+//   Fvv[a][e] = f~_ae - sum_mnf g~_menf u_mn^af           (next v^2 blocks)
+//   R1[a][i]  = f~_ai + sum_me f~_me u_im^ae + sum_mef g~_aemf u_im^ef - sum_mne g~_mine u_mn^ae
+//   Woooo[k][i][l][j] = g~_kilj + sum_ef g~_kelf t_ij^ef
+__global__ void k_small_blocks(const double* __restrict__ F, const double* __restrict__ W,
+                               const double* __restrict__ t2, double* __restrict__ foo, double* __restrict__ fvv,
+                               double* __restrict__ r1, double* __restrict__ wo, Dims d) {
+  __shared__ double red[TPB];
+  const int o = d.o, v = d.v;
+  const int x = blockIdx.x;
+  double acc = 0.0;
+  if (x < o * o) {
+    const int m = x / o, i = x % o;
+    for (int t = threadIdx.x; t < o * v * v; t += TPB) {
+      const int nn = t / (v * v), e = (t / v) % v, f = t % v;
+      acc += W[gi(d, m, o + e, nn, o + f)] * Ut(t2, d, i, nn, e, f);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) foo[x] = F[m * d.n + i] + acc;
+  } else if (x < o * o + v * v) {
+    const int y = x - o * o, a = y / v, e = y % v;
+    for (int t = threadIdx.x; t < o * o * v; t += TPB) {
+      const int m = t / (o * v), nn = (t / v) % o, f = t % v;
+      acc -= W[gi(d, m, o + e, nn, o + f)] * Ut(t2, d, m, nn, a, f);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) fvv[y] = F[(o + a) * d.n + o + e] + acc;
+  } else if (x < o * o + v * v + v * o) {
+    const int y = x - o * o - v * v, a = y / o, i = y % o;
+    for (int t = threadIdx.x; t < o * v * v; t += TPB) {
+      const int m = t / (v * v), e = (t / v) % v, f = t % v;
+      acc += W[gi(d, o + a, o + e, m, o + f)] * Ut(t2, d, i, m, e, f);
+    }
+    for (int t = threadIdx.x; t < o * o * v; t += TPB) {
+      const int m = t / (o * v), nn = (t / v) % o, e = t % v;
+      acc -= W[gi(d, m, i, nn, o + e)] * Ut(t2, d, m, nn, a, e);
+    }
+    for (int t = threadIdx.x; t < o * v; t += TPB) {
+      const int m = t / v, e = t % v;
+      acc += F[m * d.n + o + e] * Ut(t2, d, i, m, a, e);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) r1[y] = F[(o + a) * d.n + i] + acc;
+  } else {
+    const int y = x - o * o - v * v - v * o;
+    const int k = y / (o * o * o), i = (y / (o * o)) % o, l = (y / o) % o, j = y % o;
+    for (int t = threadIdx.x; t < v * v; t += TPB) {
+      const int e = t / v, f = t % v;
+      acc += W[gi(d, k, o + e, l, o + f)] * t2[ti(d, i, j, e, f)];
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) wo[y] = W[gi(d, k, i, l, j)] + acc;
   }
 }
 
-// Woooo[k][i][l][j] = g~_kilj + sum_ef g~_kelf t_ij^ef
-__global__ void k_woooo(const double* __restrict__ W, const double* __restrict__ t2, double* __restrict__ wo, Dims d) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= d.o * d.o * d.o * d.o) return;
-  const int k = x / (d.o * d.o * d.o), i = (x / (d.o * d.o)) % d.o, l = (x / d.o) % d.o, j = x % d.o;
-  double v = W[gi(d, k, i, l, j)];
-  for (int e = 0; e < d.v; ++e)
-    for (int f = 0; f < d.v; ++f) v += W[gi(d, k, d.o + e, l, d.o + f)] * t2[ti(d, i, j, e, f)];
-  wo[x] = v;
-}
-
-// R1[a][i] = f~_ai + sum_me f~_me u_im^ae + sum_mef g~_aemf u_im^ef - sum_mne g~_mine u_mn^ae
-__global__ void k_r1(const double* __restrict__ F, const double* __restrict__ W, const double* __restrict__ t2,
-                     double* __restrict__ r1, Dims d) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= d.v * d.o) return;
-  const int a = x / d.o, i = x % d.o;
-  double v = F[(d.o + a) * d.n + i];
-  for (int m = 0; m < d.o; ++m)
-    for (int e = 0; e < d.v; ++e) {
-      v += F[m * d.n + d.o + e] * U(t2, d, i, m, a, e);
-      for (int f = 0; f < d.v; ++f) v += W[gi(d, d.o + a, d.o + e, m, d.o + f)] * U(t2, d, i, m, e, f);
-      for (int nn = 0; nn < d.o; ++nn) v -= W[gi(d, m, i, nn, d.o + e)] * U(t2, d, m, nn, a, e);
-    }
-  r1[x] = v;
-}
-
-// Ring intermediates for the quadratic doubles terms, each [i][a][n][f] (o v o v):
+// Ring intermediates for the quadratic doubles terms, each [i][a][n][f] (o v o v), precision T:
 //   A = sum_me u_im^ae g~_menf,  B = sum_me u_im^ae g~_mfne,  Cq = sum_me t_im^ae g~_mfne,
 //   D[j][a][n][f] = sum_me t_jm^ea g~_mfne
-__global__ void k_rings(const double* __restrict__ W, const double* __restrict__ t2, double* __restrict__ A,
-                        double* __restrict__ B, double* __restrict__ Cq, double* __restrict__ D, Dims d) {
+template <typename T>
+__global__ void k_rings(const T* __restrict__ G, const T* __restrict__ t2, T* __restrict__ A, T* __restrict__ B,
+                        T* __restrict__ Cq, T* __restrict__ D, Dims d) {
   const size_t m_all = (size_t)d.o * d.v * d.o * d.v;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int i = (int)(x / ((size_t)d.v * d.o * d.v)), a = (int)((x / ((size_t)d.o * d.v)) % d.v);
   const int nn = (int)((x / d.v) % d.o), f = (int)(x % d.v);
-  double sa = 0, sb = 0, sc = 0, sd = 0;
+  T sa = 0, sb = 0, sc = 0, sd = 0;
   for (int m = 0; m < d.o; ++m)
     for (int e = 0; e < d.v; ++e) {
-      const double g1 = W[gi(d, m, d.o + e, nn, d.o + f)];
-      const double g2 = W[gi(d, m, d.o + f, nn, d.o + e)];
-      const double t = t2[ti(d, i, m, a, e)];
-      const double u = 2.0 * t - t2[ti(d, i, m, e, a)];
+      const T g1 = G[gi(d, m, d.o + e, nn, d.o + f)];
+      const T g2 = G[gi(d, m, d.o + f, nn, d.o + e)];
+      const T t = t2[ti(d, i, m, a, e)];
+      const T tx = t2[ti(d, i, m, e, a)];
+      const T u = (T)2 * t - tx;
       sa += u * g1;
       sb += u * g2;
       sc += t * g2;
-      sd += t2[ti(d, i, m, e, a)] * g2;
+      sd += tx * g2;
     }
   A[x] = sa;
   B[x] = sb;
@@ -209,38 +235,39 @@ __global__ void k_rings(const double* __restrict__ W, const double* __restrict__
   D[x] = sd;
 }
 
-// R2[i][j][a][b] = <Phi_{ij}^{ab}|H-bar|Phi> (alpha-beta), from bare g~ blocks and dressed
-// Foo, Fvv, Woooo.
-__global__ void k_r2(const double* __restrict__ W, const double* __restrict__ t2, const double* __restrict__ foo,
-                     const double* __restrict__ fvv, const double* __restrict__ wo, const double* __restrict__ A,
-                     const double* __restrict__ B, const double* __restrict__ Cq, const double* __restrict__ D,
-                     double* __restrict__ r2, Dims d) {
+// R2[i][j][a][b] = <Phi_{ij}^{ab}|H-bar|Phi> (alpha-beta): bare g~ vo|vo (FP64, from W) plus the
+// T2 terms in precision T (G: g~ in precision T; W is only read at untouched bare blocks).
+template <typename T>
+__global__ void k_r2(const double* __restrict__ W, const T* __restrict__ G, const T* __restrict__ t2,
+                     const double* __restrict__ foo, const double* __restrict__ fvv, const double* __restrict__ wo,
+                     const T* __restrict__ A, const T* __restrict__ B, const T* __restrict__ Cq,
+                     const T* __restrict__ D, double* __restrict__ r2, Dims d) {
   const size_t m_all = (size_t)d.o * d.o * d.v * d.v;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
   const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
   const int A_ = d.o + a, B_ = d.o + b;
-  double v = W[gi(d, A_, i, B_, j)];
+  T v = 0;
   for (int e = 0; e < d.v; ++e)
-    v += fvv[b * d.v + e] * t2[ti(d, i, j, a, e)] + fvv[a * d.v + e] * t2[ti(d, i, j, e, b)];
+    v += (T)fvv[b * d.v + e] * t2[ti(d, i, j, a, e)] + (T)fvv[a * d.v + e] * t2[ti(d, i, j, e, b)];
   for (int m = 0; m < d.o; ++m)
-    v -= foo[m * d.o + j] * t2[ti(d, i, m, a, b)] + foo[m * d.o + i] * t2[ti(d, m, j, a, b)];
+    v -= (T)foo[m * d.o + j] * t2[ti(d, i, m, a, b)] + (T)foo[m * d.o + i] * t2[ti(d, m, j, a, b)];
   for (int m = 0; m < d.o; ++m)
-    for (int nn = 0; nn < d.o; ++nn) v += wo[((m * d.o + i) * d.o + nn) * d.o + j] * t2[ti(d, m, nn, a, b)];
+    for (int nn = 0; nn < d.o; ++nn) v += (T)wo[((m * d.o + i) * d.o + nn) * d.o + j] * t2[ti(d, m, nn, a, b)];
   // particle-particle ladder
   for (int e = 0; e < d.v; ++e)
-    for (int f = 0; f < d.v; ++f) v += W[gi(d, A_, d.o + e, B_, d.o + f)] * t2[ti(d, i, j, e, f)];
+    for (int f = 0; f < d.v; ++f) v += G[gi(d, A_, d.o + e, B_, d.o + f)] * t2[ti(d, i, j, e, f)];
   // linear rings
   for (int m = 0; m < d.o; ++m)
     for (int e = 0; e < d.v; ++e) {
       const int E_ = d.o + e;
-      v += W[gi(d, m, E_, B_, j)] * U(t2, d, i, m, a, e);
-      v -= W[gi(d, m, j, B_, E_)] * t2[ti(d, i, m, a, e)];
-      v -= W[gi(d, m, i, B_, E_)] * t2[ti(d, j, m, e, a)];
-      v -= W[gi(d, m, j, A_, E_)] * t2[ti(d, i, m, e, b)];
-      v += W[gi(d, m, E_, A_, i)] * U(t2, d, j, m, b, e);
-      v -= W[gi(d, m, i, A_, E_)] * t2[ti(d, j, m, b, e)];
+      v += G[gi(d, m, E_, B_, j)] * Ut(t2, d, i, m, a, e);
+      v -= G[gi(d, m, j, B_, E_)] * t2[ti(d, i, m, a, e)];
+      v -= G[gi(d, m, i, B_, E_)] * t2[ti(d, j, m, e, a)];
+      v -= G[gi(d, m, j, A_, E_)] * t2[ti(d, i, m, e, b)];
+      v += G[gi(d, m, E_, A_, i)] * Ut(t2, d, j, m, b, e);
+      v -= G[gi(d, m, i, A_, E_)] * t2[ti(d, j, m, b, e)];
     }
   // quadratic rings through the intermediates
   const size_t ovov_i = (size_t)d.v * d.o * d.v, ovov_a = (size_t)d.o * d.v;
@@ -248,101 +275,112 @@ __global__ void k_r2(const double* __restrict__ W, const double* __restrict__ t2
     for (int f = 0; f < d.v; ++f) {
       const size_t ia = i * ovov_i + a * ovov_a + (size_t)nn * d.v + f;
       const size_t ja = j * ovov_i + a * ovov_a + (size_t)nn * d.v + f;
-      v += A[ia] * U(t2, d, j, nn, b, f) - B[ia] * t2[ti(d, j, nn, b, f)] + Cq[ia] * t2[ti(d, j, nn, f, b)] +
+      v += A[ia] * Ut(t2, d, j, nn, b, f) - B[ia] * t2[ti(d, j, nn, b, f)] + Cq[ia] * t2[ti(d, j, nn, f, b)] +
            D[ja] * t2[ti(d, i, nn, f, b)];
     }
-  r2[x] = v;
+  r2[x] = W[gi(d, A_, i, B_, j)] + (double)v;
 }
 
-// W[a,e,b,f] += sum_mn g~_menf t_mn^ab  (vvvv block, in place; reads only the ovov block)
-__global__ void k_vvvv(double* __restrict__ W, const double* __restrict__ t2, Dims d) {
+// W[a,e,b,f] += sum_mn g~_menf t_mn^ab  (vvvv block; G reads only the ovov block)
+template <typename T>
+__global__ void k_vvvv(double* __restrict__ W, const T* __restrict__ G, const T* __restrict__ t2, Dims d) {
   const size_t m_all = (size_t)d.v * d.v * d.v * d.v;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int a = (int)(x / ((size_t)d.v * d.v * d.v)), e = (int)((x / ((size_t)d.v * d.v)) % d.v);
   const int b = (int)((x / d.v) % d.v), f = (int)(x % d.v);
-  double v = 0.0;
+  T v = 0;
   for (int m = 0; m < d.o; ++m)
-    for (int nn = 0; nn < d.o; ++nn) v += W[gi(d, m, d.o + e, nn, d.o + f)] * t2[ti(d, m, nn, a, b)];
-  W[gi(d, d.o + a, d.o + e, d.o + b, d.o + f)] += v;
+    for (int nn = 0; nn < d.o; ++nn) v += G[gi(d, m, d.o + e, nn, d.o + f)] * t2[ti(d, m, nn, a, b)];
+  W[gi(d, d.o + a, d.o + e, d.o + b, d.o + f)] += (double)v;
 }
 
 // (ov|vo) and its pair partner (vo|ov):
 //   W[m,e,b,j] = g~_mebj + sum_nf g~_menf u_jn^bf - sum_nf g~_mfne t_jn^bf
-__global__ void k_ovvo(double* __restrict__ W, const double* __restrict__ t2, Dims d) {
+template <typename T>
+__global__ void k_ovvo(double* __restrict__ W, const T* __restrict__ G, const T* __restrict__ t2, Dims d) {
   const size_t m_all = (size_t)d.o * d.v * d.v * d.o;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int m = (int)(x / ((size_t)d.v * d.v * d.o)), e = (int)((x / ((size_t)d.v * d.o)) % d.v);
   const int b = (int)((x / d.o) % d.v), j = (int)(x % d.o);
-  double v = W[gi(d, m, d.o + e, d.o + b, j)];
+  T v = 0;
   for (int nn = 0; nn < d.o; ++nn)
     for (int f = 0; f < d.v; ++f)
-      v += W[gi(d, m, d.o + e, nn, d.o + f)] * U(t2, d, j, nn, b, f) -
-           W[gi(d, m, d.o + f, nn, d.o + e)] * t2[ti(d, j, nn, b, f)];
-  W[gi(d, m, d.o + e, d.o + b, j)] = v;
-  W[gi(d, d.o + b, j, m, d.o + e)] = v;
+      v += G[gi(d, m, d.o + e, nn, d.o + f)] * Ut(t2, d, j, nn, b, f) -
+           G[gi(d, m, d.o + f, nn, d.o + e)] * t2[ti(d, j, nn, b, f)];
+  const double w = W[gi(d, m, d.o + e, d.o + b, j)] + (double)v;
+  W[gi(d, m, d.o + e, d.o + b, j)] = w;
+  W[gi(d, d.o + b, j, m, d.o + e)] = w;
 }
 
 // (oo|vv) and (vv|oo):  W[i,j,a,b] = g~_ijab - sum_nf g~_ifnb t_jn^fa
-__global__ void k_oovv(double* __restrict__ W, const double* __restrict__ t2, Dims d) {
+template <typename T>
+__global__ void k_oovv(double* __restrict__ W, const T* __restrict__ G, const T* __restrict__ t2, Dims d) {
   const size_t m_all = (size_t)d.o * d.o * d.v * d.v;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
   const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
-  double v = W[gi(d, i, j, d.o + a, d.o + b)];
+  T v = 0;
   for (int nn = 0; nn < d.o; ++nn)
-    for (int f = 0; f < d.v; ++f) v -= W[gi(d, i, d.o + f, nn, d.o + b)] * t2[ti(d, j, nn, f, a)];
-  W[gi(d, i, j, d.o + a, d.o + b)] = v;
-  W[gi(d, d.o + a, d.o + b, i, j)] = v;
+    for (int f = 0; f < d.v; ++f) v -= G[gi(d, i, d.o + f, nn, d.o + b)] * t2[ti(d, j, nn, f, a)];
+  const double w = W[gi(d, i, j, d.o + a, d.o + b)] + (double)v;
+  W[gi(d, i, j, d.o + a, d.o + b)] = w;
+  W[gi(d, d.o + a, d.o + b, i, j)] = w;
 }
 
 // (oo|vo) and (vo|oo):
 //   W[m,i,b,j] = g~_mibj + sum_e f~_me t_ij^eb + sum_ef g~_mebf t_ij^ef
 //              + sum_ne [g~_mine u_jn^be - g~_meni t_jn^be - g~_menj t_in^eb]
-__global__ void k_oovo(double* __restrict__ W, const double* __restrict__ F, const double* __restrict__ t2, Dims d) {
+template <typename T>
+__global__ void k_oovo(double* __restrict__ W, const T* __restrict__ G, const double* __restrict__ F,
+                       const T* __restrict__ t2, Dims d) {
   const size_t m_all = (size_t)d.o * d.o * d.v * d.o;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int m = (int)(x / ((size_t)d.o * d.v * d.o)), i = (int)((x / ((size_t)d.v * d.o)) % d.o);
   const int b = (int)((x / d.o) % d.v), j = (int)(x % d.o);
   const int B_ = d.o + b;
-  double v = W[gi(d, m, i, B_, j)];
+  T v = 0;
   for (int e = 0; e < d.v; ++e) {
     const int E_ = d.o + e;
-    v += F[m * d.n + E_] * t2[ti(d, i, j, e, b)];
-    for (int f = 0; f < d.v; ++f) v += W[gi(d, m, E_, B_, d.o + f)] * t2[ti(d, i, j, e, f)];
+    v += (T)F[m * d.n + E_] * t2[ti(d, i, j, e, b)];
+    for (int f = 0; f < d.v; ++f) v += G[gi(d, m, E_, B_, d.o + f)] * t2[ti(d, i, j, e, f)];
     for (int nn = 0; nn < d.o; ++nn)
-      v += W[gi(d, m, i, nn, E_)] * U(t2, d, j, nn, b, e) - W[gi(d, m, E_, nn, i)] * t2[ti(d, j, nn, b, e)] -
-           W[gi(d, m, E_, nn, j)] * t2[ti(d, i, nn, e, b)];
+      v += G[gi(d, m, i, nn, E_)] * Ut(t2, d, j, nn, b, e) - G[gi(d, m, E_, nn, i)] * t2[ti(d, j, nn, b, e)] -
+           G[gi(d, m, E_, nn, j)] * t2[ti(d, i, nn, e, b)];
   }
-  W[gi(d, m, i, B_, j)] = v;
-  W[gi(d, B_, j, m, i)] = v;
+  const double w = W[gi(d, m, i, B_, j)] + (double)v;
+  W[gi(d, m, i, B_, j)] = w;
+  W[gi(d, B_, j, m, i)] = w;
 }
 
 // (vv|vo) and (vo|vv):
 //   W[a,e,b,i] = g~_aebi - sum_m f~_me t_mi^ab + sum_mn g~_meni t_mn^ab
 //              + sum_mf [g~_mfae u_mi^fb - g~_mebf t_mi^af - g~_meaf t_mi^fb]
-__global__ void k_vvvo(double* __restrict__ W, const double* __restrict__ F, const double* __restrict__ t2, Dims d) {
+template <typename T>
+__global__ void k_vvvo(double* __restrict__ W, const T* __restrict__ G, const double* __restrict__ F,
+                       const T* __restrict__ t2, Dims d) {
   const size_t m_all = (size_t)d.v * d.v * d.v * d.o;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int a = (int)(x / ((size_t)d.v * d.v * d.o)), e = (int)((x / ((size_t)d.v * d.o)) % d.v);
   const int b = (int)((x / d.o) % d.v), i = (int)(x % d.o);
   const int A_ = d.o + a, E_ = d.o + e, B_ = d.o + b;
-  double v = W[gi(d, A_, E_, B_, i)];
+  T v = 0;
   for (int m = 0; m < d.o; ++m) {
-    v -= F[m * d.n + E_] * t2[ti(d, m, i, a, b)];
-    for (int nn = 0; nn < d.o; ++nn) v += W[gi(d, m, E_, nn, i)] * t2[ti(d, m, nn, a, b)];
+    v -= (T)F[m * d.n + E_] * t2[ti(d, m, i, a, b)];
+    for (int nn = 0; nn < d.o; ++nn) v += G[gi(d, m, E_, nn, i)] * t2[ti(d, m, nn, a, b)];
     for (int f = 0; f < d.v; ++f) {
       const int F_ = d.o + f;
-      v += W[gi(d, m, F_, A_, E_)] * U(t2, d, m, i, f, b) - W[gi(d, m, E_, B_, F_)] * t2[ti(d, m, i, a, f)] -
-           W[gi(d, m, E_, A_, F_)] * t2[ti(d, m, i, f, b)];
+      v += G[gi(d, m, F_, A_, E_)] * Ut(t2, d, m, i, f, b) - G[gi(d, m, E_, B_, F_)] * t2[ti(d, m, i, a, f)] -
+           G[gi(d, m, E_, A_, F_)] * t2[ti(d, m, i, f, b)];
     }
   }
-  W[gi(d, A_, E_, B_, i)] = v;
-  W[gi(d, B_, i, A_, E_)] = v;
+  const double w = W[gi(d, A_, E_, B_, i)] + (double)v;
+  W[gi(d, A_, E_, B_, i)] = w;
+  W[gi(d, B_, i, A_, E_)] = w;
 }
 
 // Write the dressed oooo, vo|vo blocks and the oo / vv / vo Fock blocks.
@@ -373,17 +411,17 @@ __global__ void k_finalize(double* __restrict__ W, double* __restrict__ F, const
 }
 
 struct Work {
-  double *ht, *foo, *fvv, *wo, *r1, *r2, *A, *B, *Cq, *D;
+  double *ht, *foo, *fvv, *wo, *r1, *r2, *A, *B, *Cq, *D, *t2f;  // A..D, t2f hold T values
 };
 
 size_t carve(void* base, int n, int o, Work* w) {
   const int v = n - o;
   const size_t sizes[] = {(size_t)n * n, (size_t)o * o, (size_t)v * v, (size_t)o * o * o * o, (size_t)v * o,
                           (size_t)o * o * v * v, (size_t)o * v * o * v, (size_t)o * v * o * v, (size_t)o * v * o * v,
-                          (size_t)o * v * o * v};
-  double** ptrs[] = {&w->ht, &w->foo, &w->fvv, &w->wo, &w->r1, &w->r2, &w->A, &w->B, &w->Cq, &w->D};
+                          (size_t)o * v * o * v, (size_t)o * o * v * v};
+  double** ptrs[] = {&w->ht, &w->foo, &w->fvv, &w->wo, &w->r1, &w->r2, &w->A, &w->B, &w->Cq, &w->D, &w->t2f};
   size_t off = 0;
-  for (int k = 0; k < 10; ++k) {
+  for (int k = 0; k < 11; ++k) {
     if (base) *ptrs[k] = reinterpret_cast<double*>(static_cast<char*>(base) + off);
     off += ((sizes[k] * sizeof(double) + 255) / 256) * 256;
   }
@@ -408,17 +446,41 @@ size_t dress_workspace_bytes(int n, int nocc) {
   return carve(nullptr, n, nocc, &w);
 }
 
-int dress_launch_count(int n, int nocc) { return (n - nocc > 0 && nocc > 0) ? 19 : 4; }
+int dress_launch_count(int n, int nocc, bool mixed) {
+  return (n - nocc > 0 && nocc > 0) ? (mixed ? 19 : 17) : 4;
+}
+
+namespace {
+
+template <typename T>
+void t2_terms(const Dims& d, double* W, const T* G, const double* F, const T* t2, const Work& w, cudaStream_t st) {
+  const size_t o = d.o, v = d.v;
+  T* A = reinterpret_cast<T*>(w.A);
+  T* B = reinterpret_cast<T*>(w.B);
+  T* Cq = reinterpret_cast<T*>(w.Cq);
+  T* D = reinterpret_cast<T*>(w.D);
+  k_rings<T><<<blocks_for(o * v * o * v), TPB, 0, st>>>(G, t2, A, B, Cq, D, d);
+  k_r2<T><<<blocks_for(o * o * v * v), TPB, 0, st>>>(W, G, t2, w.foo, w.fvv, w.wo, A, B, Cq, D, w.r2, d);
+  // blocks that read only unmodified bare blocks (through G) may now be overwritten in W
+  k_vvvv<T><<<blocks_for(v * v * v * v), TPB, 0, st>>>(W, G, t2, d);
+  k_ovvo<T><<<blocks_for(o * v * v * o), TPB, 0, st>>>(W, G, t2, d);
+  k_oovv<T><<<blocks_for(o * o * v * v), TPB, 0, st>>>(W, G, t2, d);
+  k_oovo<T><<<blocks_for(o * o * v * o), TPB, 0, st>>>(W, G, F, t2, d);
+  k_vvvo<T><<<blocks_for(v * v * v * o), TPB, 0, st>>>(W, G, F, t2, d);
+}
+
+}  // namespace
 
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
-                         double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st) {
+                         double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st,
+                         float* g32) {
   Work w;
   if (work_bytes < carve(nullptr, n, nocc, &w)) return cudaErrorInvalidValue;
   carve(work, n, nocc, &w);
   Dims d{n, nocc, n - nocc};
   const size_t n4 = (size_t)n * n * n * n;
   const size_t o = nocc, v = n - nocc;
-  k_copy<<<blocks_for(n4) > 65535u * 8 ? 65535u * 8 : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
+  k_copy<<<blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
   if (v > 0 && o > 0) {
     const size_t mc = v * n * n * n, ma = o * n * n * n;
     k_t1_creator<<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
@@ -430,17 +492,17 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
   k_fock<<<blocks_for((size_t)n * n), TPB, 0, st>>>(w.ht, W, F, d);
   k_energy<<<1, TPB, 0, st>>>(w.ht, W, t2, e0, d);
   if (v > 0 && o > 0) {
-    k_foo_fvv<<<blocks_for(o * o + v * v), TPB, 0, st>>>(F, W, t2, w.foo, w.fvv, d);
-    k_woooo<<<blocks_for(o * o * o * o), TPB, 0, st>>>(W, t2, w.wo, d);
-    k_r1<<<blocks_for(v * o), TPB, 0, st>>>(F, W, t2, w.r1, d);
-    k_rings<<<blocks_for(o * v * o * v), TPB, 0, st>>>(W, t2, w.A, w.B, w.Cq, w.D, d);
-    k_r2<<<blocks_for(o * o * v * v), TPB, 0, st>>>(W, t2, w.foo, w.fvv, w.wo, w.A, w.B, w.Cq, w.D, w.r2, d);
-    // blocks that read only unmodified bare blocks may now be overwritten
-    k_vvvv<<<blocks_for(v * v * v * v), TPB, 0, st>>>(W, t2, d);
-    k_ovvo<<<blocks_for(o * v * v * o), TPB, 0, st>>>(W, t2, d);
-    k_oovv<<<blocks_for(o * o * v * v), TPB, 0, st>>>(W, t2, d);
-    k_oovo<<<blocks_for(o * o * v * o), TPB, 0, st>>>(W, F, t2, d);
-    k_vvvo<<<blocks_for(v * v * v * o), TPB, 0, st>>>(W, F, t2, d);
+    k_small_blocks<<<(unsigned)(o * o + v * v + v * o + o * o * o * o), TPB, 0, st>>>(F, W, t2, w.foo, w.fvv, w.r1,
+                                                                                     w.wo, d);
+    if (g32) {  // contractions of the T2 terms in FP32 (mixed precision), bases kept in FP64
+      float* t2f = reinterpret_cast<float*>(w.t2f);
+      const unsigned gg = blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4);
+      k_to_f32<<<gg, TPB, 0, st>>>(W, g32, n4);
+      k_to_f32<<<blocks_for(o * o * v * v), TPB, 0, st>>>(t2, t2f, o * o * v * v);
+      t2_terms<float>(d, W, g32, F, t2f, w, st);
+    } else {
+      t2_terms<double>(d, W, W, F, t2, w, st);
+    }
     const size_t nf = o * o * v * v + o * o * o * o + o * o + v * v + v * o;
     k_finalize<<<blocks_for(nf), TPB, 0, st>>>(W, F, w.foo, w.fvv, w.r1, w.wo, w.r2, d);
   }

@@ -345,8 +345,8 @@ int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
   cudaError_t e = cudaEventRecord(c->ev[0], c->stream);
   if (e == cudaSuccess)
     e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
-                         c->dwork_bytes, c->stream);
-  launches += qf::dress_launch_count(c->n, c->nocc);
+                         c->dwork_bytes, c->stream, c->W32);
+  launches += qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
   if (e == cudaSuccess && c->W32) {
     e = qf::launch_to_f32(c->W, c->W32, (size_t)c->n * c->n * c->n * c->n, c->stream);
     ++launches;
@@ -473,7 +473,7 @@ int qflow_dressed(qflow_handle c, double* e0, double* F, double* W) {
   if (!c) return QFLOW_ERR_ARG;
   const size_t n1 = c->n, n4 = n1 * n1 * n1 * n1;
   cudaError_t e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W,
-                                   c->dwork, c->dwork_bytes, c->stream);
+                                   c->dwork, c->dwork_bytes, c->stream, c->W32);
   if (e0 && e == cudaSuccess) e = cudaMemcpyAsync(e0, c->e0, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (F && e == cudaSuccess) e = cudaMemcpyAsync(F, c->F, sizeof(double) * n1 * n1, cudaMemcpyDeviceToHost, c->stream);
   if (W && e == cudaSuccess) e = cudaMemcpyAsync(W, c->W, sizeof(double) * n4, cudaMemcpyDeviceToHost, c->stream);

@@ -50,9 +50,12 @@ cudaError_t launch_to_f32(const double* W, float* W32, size_t count, cudaStream_
 
 // Dressing (step a) on caller-provided device buffers; returns a CUDA error code.
 size_t dress_workspace_bytes(int n, int nocc);
-int dress_launch_count(int n, int nocc);  // kernels one launch_dress issues
+int dress_launch_count(int n, int nocc, bool mixed);  // kernels one launch_dress issues
+// g32: NULL for FP64 contractions; else n^4 floats of scratch, and the T2 terms are contracted
+// in FP32 (mixed precision).
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
-                         double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st);
+                         double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st,
+                         float* g32 = nullptr);
 
 // Sweep reductions (step c): out4 = [mean E, max |t_new - t_old|, failed spaces, worst status].
 size_t mean_maxdiff_workspace(int64_t nspaces, int64_t nt);

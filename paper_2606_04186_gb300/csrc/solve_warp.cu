@@ -130,6 +130,11 @@ struct alignas(16) CtaSmem {
   int sg[NS * NSG];
   int mask[NS];
   unsigned short pair[NF * (NF + 1) / 2];  // (P, R) with P <= R, packed P | R << 8
+  int c0n[NS];          // number of replacements (pq) with <I| E_pq |Phi string> != 0
+  int c0pq[NS][3];      // their pq ...
+  int c0sg[NS][3];      // ... and signs
+  int xJ[9];            // a+_A a_i |Phi string> = xs * |xJ>, index i*3 + (A-3)
+  int xs[9];
   WarpSmem w[WARPS];
 };
 
@@ -138,24 +143,6 @@ static_assert(offsetof(WarpSmem, V) % 16 == 0 && offsetof(WarpSmem, S) % 16 == 0
                   offsetof(WarpSmem, Hs) % 16 == 0 && offsetof(WarpSmem, diag) % 16 == 0,
               "float4 rows");
 static_assert(offsetof(CtaSmem, w) % 16 == 0, "warp state alignment");
-
-// Index of the string with bit mask m (strings are numbered by increasing mask).
-__device__ __forceinline__ int str_index(const CtaSmem& cs, int m) {
-  int c = 0;
-  for (int t = 0; t < NS; ++t)
-    if (cs.mask[t] == m) c = t;
-  return c;
-}
-
-// a+_A a_i |Phi string> = sign |J>: returns J and the sign.
-__device__ __forceinline__ int phi_single(const CtaSmem& cs, int i, int A, double* sign) {
-  const int m0 = cs.mask[0];
-  int par = __popc(m0 & ((1 << i) - 1)) & 1;
-  const int m1 = m0 & ~(1 << i);
-  par ^= __popc(m1 & ((1 << A) - 1)) & 1;
-  *sign = par ? -1.0 : 1.0;
-  return str_index(cs, m1 | (1 << A));
-}
 
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
@@ -352,6 +339,27 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
     int t = 0;
     for (int P = 0; P < NF; ++P)
       for (int R = P; R < NF; ++R) cs.pair[t++] = (unsigned short)(P | (R << 8));
+    for (int I = 0; I < NS; ++I) {  // connections of each string to the Phi string
+      int c = 0;
+      for (int u = 0; u < NSG; ++u)
+        if (cs.J[I * NSG + u] == 0 && c < 3) {
+          cs.c0pq[I][c] = cs.pq[I * NSG + u];
+          cs.c0sg[I][c] = cs.sg[I * NSG + u];
+          ++c;
+        }
+      cs.c0n[I] = c;
+    }
+    for (int x = 0; x < 9; ++x) {  // single replacements i -> A of the Phi string
+      const int i = x / 3, A = 3 + x % 3, m0 = cs.mask[0];
+      int par = __popc(m0 & ((1 << i) - 1)) & 1;
+      const int m1 = m0 & ~(1 << i);
+      par ^= __popc(m1 & ((1 << A) - 1)) & 1;
+      int J = 0;
+      for (int q = 0; q < NS; ++q)
+        if (cs.mask[q] == (m1 | (1 << A))) J = q;
+      cs.xJ[x] = J;
+      cs.xs[x] = par ? -1 : 1;
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -499,11 +507,8 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
             const int pq = cs.pq[e], Kk = cs.J[e];
             const float s1 = (float)cs.sg[e];
             if (Kk == 0) hc = fmaf(s1, ws.hp[pq], hc);
-#pragma unroll 1
-            for (int v = 0; v < NSG; ++v) {
-              const int e2 = Kk * NSG + v;
-              if (cs.J[e2] == 0) hc = fmaf(0.5f * s1 * (float)cs.sg[e2], ws.Wt[pq * NF + cs.pq[e2]], hc);
-            }
+            for (int v = 0; v < cs.c0n[Kk]; ++v)
+              hc = fmaf(0.5f * s1 * (float)cs.c0sg[Kk][v], ws.Wt[pq * NF + cs.c0pq[Kk][v]], hc);
           }
         }
         ws.dh[I] = hc;
@@ -513,28 +518,22 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
         ws.V[d] = (d == 0) ? 1.f : 0.f;
       }
       __syncwarp();
-      if (lane < NS) {
-        const int Ia = lane;
-        if (Ia != 0) ws.S[Ia * NS] = ws.dh[Ia];
-        else
-          for (int b = 1; b < NS; ++b) ws.S[b] = ws.dh[b];
-        // alpha-beta: replacements (pq) into Ia from the Phi string times (rs) into Ib from it
+      // alpha-beta couplings: both strings are Phi or single replacements of it (10 x 10 pairs);
+      // same-spin couplings sit in row 0 and column 0 of the CI matrix
 #pragma unroll 1
-        for (int u = 0; u < NSG; ++u) {
-          const int e = Ia * NSG + u;
-          if (cs.J[e] != 0) continue;
-          const float su = (float)cs.sg[e];
-          const int pq = cs.pq[e];
-#pragma unroll 1
-          for (int b = 0; b < NS; ++b) {
-            float acc = 0.f;
-            for (int v = 0; v < NSG; ++v) {
-              const int e2 = b * NSG + v;
-              if (cs.J[e2] == 0) acc = fmaf((float)cs.sg[e2], ws.Wt[pq * NF + cs.pq[e2]], acc);
-            }
-            if (Ia * NS + b != 0) ws.S[Ia * NS + b] += su * acc;
-          }
-        }
+      for (int t = lane; t < 100; t += 32) {
+        const int x = t / 10, y = t % 10;
+        const int Ia = (x == 0) ? 0 : cs.xJ[x - 1], Ib = (y == 0) ? 0 : cs.xJ[y - 1];
+        float acc = 0.f;
+        for (int u = 0; u < cs.c0n[Ia]; ++u)
+          for (int v = 0; v < cs.c0n[Ib]; ++v)
+            acc = fmaf((float)(cs.c0sg[Ia][u] * cs.c0sg[Ib][v]), ws.Wt[cs.c0pq[Ia][u] * NF + cs.c0pq[Ib][v]], acc);
+        if (t != 0) ws.S[Ia * NS + Ib] = acc;
+      }
+      __syncwarp();
+      if (lane > 0 && lane < NS) {
+        ws.S[lane * NS] += ws.dh[lane];
+        ws.S[lane] += ws.dh[lane];
       }
       __syncwarp();
       float rr = 0.f;
@@ -777,21 +776,17 @@ __global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, con
     float* x1 = ws.V;  // V is free now: 9 + 81 floats of scratch
     float* x2 = x1 + 9;
     if (lane < 9) {
-      const int i = lane / 3, aa = lane % 3;
-      double sg;
-      const int J = phi_single(cs, i, 3 + aa, &sg);
-      const float f = (sg < 0.0) ? -inv0 : inv0;
+      const int J = cs.xJ[lane];
+      const float f = (cs.xs[lane] < 0) ? -inv0 : inv0;
       x1[lane] = 0.5f * f * (ws.S[J * NS] + ws.S[J]);
     }
     __syncwarp();
 #pragma unroll 1
     for (int idx = lane; idx < 81; idx += 32) {
       const int i = idx / 27, j = (idx / 9) % 3, aa = (idx / 3) % 3, b = idx % 3;
-      double sa, sb;
-      const int ja = phi_single(cs, i, 3 + aa, &sa);
-      const int jb = phi_single(cs, j, 3 + b, &sb);
-      const float f = ((sa < 0.0) != (sb < 0.0)) ? -inv0 : inv0;
-      x2[idx] = f * ws.S[ja * NS + jb] - x1[i * 3 + aa] * x1[j * 3 + b];
+      const int xa = i * 3 + aa, xb = j * 3 + b;
+      const float f = (cs.xs[xa] != cs.xs[xb]) ? -inv0 : inv0;
+      x2[idx] = f * ws.S[cs.xJ[xa] * NS + cs.xJ[xb]] - x1[xa] * x1[xb];
     }
     __syncwarp();
     if (st == kSpaceOk && a.owner1 && lane < 9) {

@@ -222,3 +222,19 @@ def test_diis_flow_matches_oracle(qf):
             break
     assert abs(gpu.energy() - e_cc) < 1e-9
     gpu.close()
+
+
+def test_mixed_dressing_close_to_oracle(qf):
+    """Mixed path: T2 contractions in FP32 on FP64 bases; E0 and the Fock blocks stay FP64."""
+    eps, h, g, sp = synth.system_inputs("n24")
+    s = synth.SYSTEMS["n24"]
+    no, nv = s.nocc, s.n - s.nocc
+    t1, t2 = _pool(no, nv, 13, 0.01, 0.02)
+    gpu = qf.Flow(h, g, no, sp, precision="mixed")
+    gpu.set_amplitudes(t1, t2)
+    e0, F, W = gpu.dressed()
+    e0r, Fr, Wr = hbar.hbar2(h, g, t1, t2, no)
+    assert abs(e0 - e0r) < 1e-11
+    assert np.abs(F - Fr).max() < 1e-11
+    assert np.abs(W - Wr).max() < 1e-6
+    gpu.close()
