@@ -135,8 +135,8 @@ class ClockSampler:
 def _oracle_worker(args):
     from oracle import cas
     out = []
-    for c, h, w in args:
-        out.append(cas.solve_problem(3, 3, c, h, w)[0])
+    for no, nv, c, h, w in args:
+        out.append(cas.solve_problem(no, nv, c, h, w)[0])
     return out
 
 
@@ -153,7 +153,7 @@ def oracle_sweep_sample(name: str, sample: int, pool, seed: int = 7):
     rng = np.random.default_rng(seed)
     pick = rng.choice(len(sp), size=min(sample, len(sp)), replace=False)
     t0 = time.perf_counter()
-    probs = [cas.space_problem(e0, F, W, *flow.space_orbitals(sp[k])) for k in pick]
+    probs = [(int(sp[k][0]), int(sp[k][1]), *cas.space_problem(e0, F, W, *flow.space_orbitals(sp[k]))) for k in pick]
     nproc = getattr(pool, "_processes", 1)
     chunks = [probs[i::nproc] for i in range(nproc)]
     pool.map(_oracle_worker, chunks)
@@ -177,7 +177,8 @@ def host_cores() -> int:
 
 def _warm_worker(_):
     from oracle import cas
-    cas.coupling(3, 3)  # build the determinant coupling maps once per worker
+    for k in (1, 2, 3):
+        cas.coupling(k, k)  # build the determinant coupling maps once per worker
     return 0
 
 

@@ -69,6 +69,14 @@ typedef struct {
   int32_t orb[6];
 } qflow_space;
 
+typedef enum {
+  QFLOW_SCHED_AUTO = 0,       /* mixed precision: the autotuner picks the launch schedule on the
+                                 first sweep (timed candidates on a calibration subset)       */
+  QFLOW_SCHED_PER_CLASS = 1,  /* one grid-stride launch per size class                        */
+  QFLOW_SCHED_PERSISTENT = 2  /* one persistent launch; warps take spaces of every class from a
+                                 single work queue, 6e6o first                                 */
+} qflow_schedule_kind;
+
 typedef struct {
   int32_t precision;          /* qflow_precision                                            */
   int32_t max_iter;           /* Davidson iteration limit per space (default 60)            */
@@ -82,7 +90,11 @@ typedef struct {
                                  space in mixed precision, x 8 B in FP64).  In a flow the pool
                                  absorbs each root's increment, so Phi is usually the closer
                                  start; 1 pays off when the pool is held fixed.             */
-  int32_t reserved[8];
+  int32_t schedule;           /* qflow_schedule_kind (mixed precision; FP64 uses per-class
+                                 launches)                                                   */
+  int32_t graph;              /* 1 = after the first sweep, capture the sweep's device work in
+                                 a CUDA graph and replay it (default 1)                      */
+  int32_t reserved[6];
 } qflow_options;
 
 /* Fill *opt with the defaults above for the given precision. */
@@ -142,6 +154,14 @@ int qflow_dressed(qflow_handle hnd, double* e0, double* F, double* W);
  * phase_ms[3] = dressing, per-space solve, merge reductions (milliseconds); and the number
  * of kernels the sweep launched.  Either output may be NULL. */
 int qflow_last_sweep_info(qflow_handle hnd, double* phase_ms, int64_t* kernel_launches);
+
+/* Launch schedule in use (after the first sweep): persistent queue or per-class launches,
+ * items per queue fetch, CTAs per SM (0 = occupancy limit), whether sweeps replay a CUDA
+ * graph, and the autotuner's calibration times (milliseconds per candidate, up to 8; the
+ * count is 0 when the schedule was fixed or came from the per-process cache).  Any output may
+ * be NULL. */
+int qflow_schedule(qflow_handle hnd, int32_t* persistent, int32_t* chunk, int32_t* ctas_per_sm, int32_t* graph,
+                   float* candidate_ms, int32_t* n_candidates);
 
 /* Stream the handle works on (a cudaStream_t). */
 void* qflow_stream(qflow_handle hnd);

@@ -6,6 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <limits>
 #include <new>
 #include <numeric>
@@ -144,6 +147,15 @@ struct qflow_ctx {
   void* guess[4] = {nullptr, nullptr, nullptr, nullptr};  // previous roots per size class (opt.guess == 1)
   void* diis = nullptr;                                   // DIIS ring (opt.diis > 0)
   float* W32 = nullptr;                                   // FP32 copy of W (mixed precision)
+  unsigned long long* queue = nullptr;                    // persistent-launch work counter
+  // launch schedule of the mixed-precision solver: persistent queue or one launch per class
+  int sched_persistent = 1, sched_chunk = 4, sched_ctas = 0;
+  bool tuned = false;
+  float tune_ms[8] = {0};
+  int tune_count = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase marks of the last sweep
   int64_t last_launches = 0;                                  // kernels launched by the last sweep
 };
@@ -165,6 +177,9 @@ void free_ctx(qflow_ctx* c) {
     if (p) cudaFree(p);
   if (c->diis) cudaFree(c->diis);
   if (c->W32) cudaFree(c->W32);
+  if (c->queue) cudaFree(c->queue);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
   if (c->red_host) cudaFreeHost(c->red_host);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -190,6 +205,8 @@ void qflow_default_options(qflow_options* opt, int32_t precision) {
   opt->tol = (precision == QFLOW_PREC_MIXED) ? 1e-6 : 1e-9;
   opt->diis = 0;
   opt->guess = 0;
+  opt->schedule = QFLOW_SCHED_AUTO;
+  opt->graph = 1;
 }
 
 int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
@@ -302,6 +319,14 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->red_host), 4 * sizeof(double));
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
   if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) e = dalloc(&c->W32, n4);
+  if (e == cudaSuccess) e = dalloc(&c->queue, 1);
+  if (c->opt.schedule == QFLOW_SCHED_PER_CLASS) {
+    c->sched_persistent = 0;
+    c->tuned = true;
+  } else if (c->opt.schedule == QFLOW_SCHED_PERSISTENT) {
+    c->sched_persistent = 1;
+    c->tuned = true;
+  }
   if (c->opt.diis > 0 && e == cudaSuccess) {
     e = cudaMalloc(&c->diis, qf::diis_workspace_bytes(c->opt.diis, (int64_t)npool));
     if (e == cudaSuccess) e = qf::diis_reset(c->diis, c->opt.diis, (int64_t)npool, c->stream);
@@ -338,68 +363,230 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   return (pl.uncovered > 0) ? QFLOW_WARN_UNCOVERED : QFLOW_OK;
 }
 
-int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
-  if (!c) return QFLOW_ERR_ARG;
-  const size_t npool = (size_t)(c->n_t1 + c->n_t2);
-  int64_t launches = 0;
-  cudaError_t e = cudaEventRecord(c->ev[0], c->stream);
+}  // extern "C"
+
+namespace {
+
+qf::SolveArgs solve_args(qflow_ctx* c, int k) {
+  SolveArgs a{};
+  a.n = c->n;
+  a.nocc = c->nocc;
+  a.nvir = c->nvir;
+  a.e0 = c->e0;
+  a.F = c->F;
+  a.W = c->W;
+  a.spaces = c->spaces + c->cls_off[k];
+  a.nspaces = c->cls_count[k];
+  a.space_base = 0;
+  a.sorted_index = c->sorted_index + c->cls_off[k];
+  a.owner1 = c->own1;
+  a.owner2 = c->own2;
+  a.t1_old = c->pool;
+  a.t2_old = c->pool + c->n_t1;
+  a.t1_new = c->pool_new;
+  a.t2_new = c->pool_new + c->n_t1;
+  a.energy = c->energy;
+  a.status = c->status;
+  a.iters = c->iters;
+  a.W32 = c->W32;
+  a.guess = c->guess[k];
+  a.save_root = c->guess[k] ? 1 : 0;
+  a.max_iter = c->opt.max_iter;
+  a.tol = c->opt.tol;
+  return a;
+}
+
+// Phase marker k.  Inside a stream capture the record becomes an event node of the graph, so
+// every replay records it again (a plain record would only take part in the capture).
+cudaError_t mark(qflow_ctx* c, int k) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecordWithFlags(c->ev[k], c->stream,
+                                  cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
+// Step (a): dressing (+ the FP32 copy of W for the mixed solver).
+cudaError_t enqueue_dress(qflow_ctx* c, int64_t* launches) {
+  cudaError_t e = mark(c, 0);
   if (e == cudaSuccess)
     e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
                          c->dwork_bytes, c->stream, c->W32);
-  launches += qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
+  *launches += qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
   if (e == cudaSuccess && c->W32) {
     e = qf::launch_to_f32(c->W, c->W32, (size_t)c->n * c->n * c->n * c->n, c->stream);
-    ++launches;
+    ++*launches;
   }
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev[1], c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->pool_new, c->pool, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
-  for (int k = 1; k <= 3 && e == cudaSuccess; ++k) {
-    if (c->cls_count[k] == 0) continue;
-    SolveArgs a{};
-    a.n = c->n;
-    a.nocc = c->nocc;
-    a.nvir = c->nvir;
-    a.e0 = c->e0;
-    a.F = c->F;
-    a.W = c->W;
-    a.spaces = c->spaces + c->cls_off[k];
-    a.nspaces = c->cls_count[k];
-    a.space_base = 0;
-    a.sorted_index = c->sorted_index + c->cls_off[k];
-    a.owner1 = c->own1;
-    a.owner2 = c->own2;
-    a.t1_old = c->pool;
-    a.t2_old = c->pool + c->n_t1;
-    a.t1_new = c->pool_new;
-    a.t2_new = c->pool_new + c->n_t1;
-    a.energy = c->energy;
-    a.status = c->status;
-    a.iters = c->iters;
-    a.W32 = c->W32;
-    a.guess = c->guess[k];
-    a.save_root = c->guess[k] ? 1 : 0;
-    a.max_iter = c->opt.max_iter;
-    a.tol = c->opt.tol;
-    e = qf::launch_solve(k, c->opt.precision, a, c->stream);
-    ++launches;
+  if (e == cudaSuccess) e = mark(c, 1);
+  return e;
+}
+
+// The per-space solves with a given schedule; `count` > 0 limits every class to its first
+// `count` spaces (autotuner calibration).
+cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int64_t count, int64_t* launches) {
+  SolveArgs cls[4];
+  for (int k = 1; k <= 3; ++k) {
+    cls[k] = solve_args(c, k);
+    if (count > 0) {  // calibration: a prefix of each class, no saved roots
+      if (cls[k].nspaces > count) cls[k].nspaces = count;
+      cls[k].guess = nullptr;
+      cls[k].save_root = 0;
+    }
   }
+  if (c->opt.precision != QFLOW_PREC_MIXED) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 1; k <= 3 && e == cudaSuccess; ++k) {
+      if (cls[k].nspaces == 0) continue;
+      e = qf::launch_solve(k, c->opt.precision, cls[k], c->stream);
+      ++*launches;
+    }
+    return e;
+  }
+  if (persistent) {
+    *launches += 2;  // queue reset + kernel
+    return qf::launch_solve_persistent(cls, c->W32, c->queue, chunk, ctas, c->stream);
+  }
+  cudaError_t e = cudaSuccess;
+  for (int k = 3; k >= 1 && e == cudaSuccess; --k) {
+    if (cls[k].nspaces == 0) continue;
+    e = qf::launch_solve_warp(k, cls[k], c->W32, static_cast<const float*>(cls[k].guess),
+                              cls[k].save_root ? static_cast<float*>(cls[k].guess) : nullptr, ctas, c->stream);
+    ++*launches;
+  }
+  return e;
+}
+
+// Steps (b)+(c): solves into pool_new, DIIS, reductions, pool_new -> pool, scalars to the host.
+cudaError_t enqueue_solve_merge(qflow_ctx* c, int64_t* launches) {
+  const size_t npool = (size_t)(c->n_t1 + c->n_t2);
+  cudaError_t e = cudaMemcpyAsync(c->pool_new, c->pool, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = enqueue_solve(c, c->sched_persistent, c->sched_chunk, c->sched_ctas, 0, launches);
   if (e == cudaSuccess && c->diis) {
     e = qf::launch_diis(c->diis, c->opt.diis, c->pool, c->pool_new, (int64_t)npool, c->stream);
-    launches += 4;
+    *launches += 4;
   }
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev[2], c->stream);
+  if (e == cudaSuccess) e = mark(c, 2);
   if (e == cudaSuccess)
     e = qf::launch_reduce(c->energy, c->status, c->nspaces, c->pool, c->pool_new, (int64_t)npool, c->red, c->rwork,
                           c->stream);
-  launches += 2;
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev[3], c->stream);
+  *launches += 2;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->pool, c->pool_new, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = mark(c, 3);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->red_host, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  return e;
+}
+
+// Autotuner: time candidate schedules on the first spaces of every class (the dressed integrals
+// of the current sweep are in place) and keep the fastest.  Results are cached per problem
+// shape for the process.
+struct TuneKey {
+  int n, nocc;
+  int64_t c1, c2, c3;
+  bool operator<(const TuneKey& o) const {
+    if (n != o.n) return n < o.n;
+    if (nocc != o.nocc) return nocc < o.nocc;
+    if (c1 != o.c1) return c1 < o.c1;
+    if (c2 != o.c2) return c2 < o.c2;
+    return c3 < o.c3;
+  }
+};
+std::map<TuneKey, std::array<int, 3>> g_tune_cache;
+std::mutex g_tune_mu;
+
+cudaError_t autotune(qflow_ctx* c) {
+  const TuneKey key{c->n, c->nocc, c->cls_count[1], c->cls_count[2], c->cls_count[3]};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c->sched_persistent = it->second[0];
+      c->sched_chunk = it->second[1];
+      c->sched_ctas = it->second[2];
+      c->tuned = true;
+      return cudaSuccess;
+    }
+  }
+  // candidates: (persistent, chunk, CTAs per SM)
+  const int cand[6][3] = {{0, 1, 0}, {1, 1, 0}, {1, 4, 0}, {1, 16, 0}, {0, 1, 1}, {1, 4, 1}};
+  const int64_t count = 16384;
+  cudaEvent_t t0, t1;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float best = 1e30f;
+  int bi = 0;
+  int64_t dummy = 0;
+  for (int ci = 0; ci < 6 && e == cudaSuccess; ++ci) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
+      e = cudaEventRecord(t0, c->stream);
+      if (e == cudaSuccess) e = enqueue_solve(c, cand[ci][0], cand[ci][1], cand[ci][2], count, &dummy);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    }
+    c->tune_ms[ci] = ms;
+    if (ms < best) {
+      best = ms;
+      bi = ci;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (e != cudaSuccess) return e;
+  c->tune_count = 6;
+  c->sched_persistent = cand[bi][0];
+  c->sched_chunk = cand[bi][1];
+  c->sched_ctas = cand[bi][2];
+  c->tuned = true;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = {c->sched_persistent, c->sched_chunk, c->sched_ctas};
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
+  if (!c) return QFLOW_ERR_ARG;
+  int64_t launches = 0;
+  cudaError_t e = cudaSuccess;
+  if (c->opt.graph && !c->graph_exec && c->tuned) {
+    // From the second sweep on: capture the sweep's device work once, then replay it.
+    int64_t l2 = 0;
+    e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = enqueue_dress(c, &l2);
+      if (e1 == cudaSuccess) e1 = enqueue_solve_merge(c, &l2);
+      e = cudaStreamEndCapture(c->stream, &c->graph);
+      if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, c->graph, 0);
+    if (e == cudaSuccess) {
+      c->graph_launches = l2;
+    } else {  // fall back to plain launches
+      if (c->graph) cudaGraphDestroy(c->graph);
+      c->graph = nullptr;
+      c->graph_exec = nullptr;
+      c->opt.graph = 0;
+      cudaGetLastError();
+      e = cudaSuccess;
+    }
+  }
+  if (c->graph_exec) {  // replay of the captured sweep
+    e = cudaGraphLaunch(c->graph_exec, c->stream);
+    launches = c->graph_launches;
+  } else {
+    e = enqueue_dress(c, &launches);
+    if (e == cudaSuccess && !c->tuned && c->opt.precision == QFLOW_PREC_MIXED) e = autotune(c);
+    if (e == cudaSuccess) e = enqueue_solve_merge(c, &launches);
+    c->tuned = true;  // FP64 needs no tuning; mixed has just been tuned
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_status(e);
   c->last_launches = launches;
-  std::swap(c->pool, c->pool_new);
   const double em = c->red_host[0];
   const double de = c->have_energy ? em - c->e_mean : std::numeric_limits<double>::infinity();
   c->e_mean = em;
@@ -482,6 +669,19 @@ int qflow_dressed(qflow_handle c, double* e0, double* F, double* W) {
 }
 
 void* qflow_stream(qflow_handle c) { return c ? (void*)c->stream : nullptr; }
+
+int qflow_schedule(qflow_handle c, int32_t* persistent, int32_t* chunk, int32_t* ctas_per_sm, int32_t* graph,
+                   float* candidate_ms, int32_t* n_candidates) {
+  if (!c) return QFLOW_ERR_ARG;
+  if (persistent) *persistent = c->sched_persistent;
+  if (chunk) *chunk = c->sched_chunk;
+  if (ctas_per_sm) *ctas_per_sm = c->sched_ctas;
+  if (graph) *graph = c->graph_exec ? 1 : 0;
+  if (candidate_ms)
+    for (int i = 0; i < c->tune_count; ++i) candidate_ms[i] = c->tune_ms[i];
+  if (n_candidates) *n_candidates = c->tune_count;
+  return QFLOW_OK;
+}
 
 int qflow_last_sweep_info(qflow_handle c, double* phase_ms, int64_t* kernel_launches) {
   if (!c) return QFLOW_ERR_ARG;

@@ -41,10 +41,14 @@ struct SolveArgs {
 
 // Launch the batched solver for spaces of size class k (1, 2 or 3) in the given precision.
 cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st);
-// Warp-per-space mixed-precision solver for (3,3) spaces (solve_warp.cu).
-// W32: optional FP32 copy of W (same layout); NULL reads and converts the FP64 W.
-cudaError_t launch_solve_warp33(const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
-                                cudaStream_t st);
+// Warp-per-space mixed-precision solvers (solve_warp.cu).  W32: optional FP32 copy of W (same
+// layout); NULL reads and converts the FP64 W.  ctas_per_sm: 0 = as many as fit.
+cudaError_t launch_solve_warp(int k, const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
+                              int ctas_per_sm, cudaStream_t st);
+// One persistent launch over every size class (cls[k], k = 1..3; guesses from cls[k].guess):
+// warps take `chunk` work items per atomic from `queue` (zeroed by the call), 6e6o first.
+cudaError_t launch_solve_persistent(const SolveArgs* cls, const float* W32, unsigned long long* queue, int chunk,
+                                    int ctas_per_sm, cudaStream_t st);
 // FP32 copy of the dressed two-body integrals for the mixed-precision solver.
 cudaError_t launch_to_f32(const double* W, float* W32, size_t count, cudaStream_t st);
 

@@ -609,15 +609,13 @@ cudaError_t launch_k(const SolveArgs& a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st) {
-  const bool mixed = (precision == QFLOW_PREC_MIXED);
+  if (precision == QFLOW_PREC_MIXED)
+    return launch_solve_warp(k, a, a.W32, static_cast<const float*>(a.guess),
+                             a.save_root ? static_cast<float*>(a.guess) : nullptr, 0, st);
   switch (k) {
-    case 1: return mixed ? launch_k<1, float>(a, st) : launch_k<1, double>(a, st);
-    case 2: return mixed ? launch_k<2, float>(a, st) : launch_k<2, double>(a, st);
-    case 3:
-      if (mixed)
-        return launch_solve_warp33(a, a.W32, static_cast<const float*>(a.guess),
-                                   a.save_root ? static_cast<float*>(a.guess) : nullptr, st);
-      return launch_k<3, double>(a, st);
+    case 1: return launch_k<1, double>(a, st);
+    case 2: return launch_k<2, double>(a, st);
+    case 3: return launch_k<3, double>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,21 +1,26 @@
-// Mixed-precision batched solver for 6e6o spaces (3 occupied + 3 virtual orbitals, 400
-// Sz = 0 determinants): one warp per space, sigma-vectors in FP32 from register tiles.
+// Mixed-precision batched solver, one warp per active space, for the three size classes
+// (k occupied + k virtual orbitals, k = 1, 2, 3: 4, 36 and 400 Sz = 0 determinants).
 //
 // What it computes is the same as solve.cu (gather + fold, Phi-dominant right eigenpair of the
 // space's determinant operator by Davidson, CI -> CC increment, owner-filtered merge), see that
-// file for the paper passages.  Differences are in the mapping onto the GB300:
+// file for the paper passages.  Mapping onto the GB300:
 //   * one warp owns one space (no block-wide barriers; all reductions are warp shuffles);
-//   * sigma: lane L < 20 owns alpha string I_alpha = L and the 20 determinants of that row.
-//     For each of the 12 single replacements (pq, J_alpha, s) into I_alpha it holds the W row
-//     W[pq][*] (36 values) and the CI row C[J_alpha][*] (20 values) in registers and applies the
-//     whole beta-side replacement table, which is a compile-time constant (same for every
-//     space), as 240 register-only FMAs; the same-spin parts are two 20 x 20 x 20 products
-//     from vectorised shared-memory rows;
+//   * 6e6o sigma: lane L < 20 owns alpha string I_alpha = L and the 20 determinants of that
+//     row.  For each of the 12 single replacements (pq, J_alpha, s) into I_alpha it holds the W
+//     row W[pq][*] (36 values) and the CI row C[J_alpha][*] (20 values) in registers and applies
+//     the whole beta-side replacement table, a compile-time constant (the same for every space),
+//     as 240 register-only FMAs; the same-spin parts are two 20 x 20 x 20 products from
+//     vectorised shared-memory rows.  The small classes use a determinant-per-lane sigma;
 //   * the operator diagonal is built in FP64 relative to E_Phi = <Phi|H|Phi> and removed from
 //     the sigma operands, so FP32 sums only off-diagonal couplings;
-//   * FP64 is kept for the fold, the diagonal, the projected k x k eigenproblem, the energy and
-//     the amplitude update; FP32 for the 400-length vectors and sigma.
-// Every loop is bounded; a warp never waits on another warp.
+//   * before anything else a space checks the residual of Phi from Phi's sparse column; spaces
+//     already at their root (most of a mid-flow sweep) stop there;
+//   * FP64 is kept for the fold, the diagonal, the energy and the amplitude update; FP32 for
+//     couplings, the determinant vectors, sigma and the small projected eigenproblem.
+// Kernels: one per size class (grid-stride over that class), and a persistent kernel whose
+// warps take work items from one queue holding every class (largest spaces first).
+// Every loop is bounded; a warp never waits on another warp (the queue is a single atomic
+// counter).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stddef.h>
@@ -28,17 +33,28 @@
 namespace qf {
 namespace {
 
-constexpr int NS = 20, NSG = 12, NDET = 400, NORB = 6, NF = 36, NW = 1296;
-constexpr int KM = 4;        // Davidson subspace limit (restart on the Ritz vector)
-constexpr int WARPS = 4;     // spaces (warps) per CTA
-constexpr int NPAIR = NF * (NF + 1) / 2;  // unique (pq, rs) pairs of the pair-symmetric W block
+constexpr int KM = 4;     // Davidson subspace limit (restart on the Ritz vector)
+constexpr int WARPS = 4;  // spaces (warps) per CTA
 
-struct Tab {
-  int mask[NS];
+template <int K>
+struct Dim {
+  static constexpr int NORB = 2 * K;
+  static constexpr int NS = (K == 1) ? 2 : (K == 2) ? 6 : 20;  // C(2k, k) strings per spin
+  static constexpr int NSG = K * (K + 1);                       // single replacements into a string
+  static constexpr int NDET = NS * NS;
+  static constexpr int NF = NORB * NORB;
+  static constexpr int NW = NF * NF;
+  static constexpr int NPAIR = NF * (NF + 1) / 2;  // unique (pq, rs) pairs of the pair-symmetric block
+};
+
+// ---- compile-time string tables (6e6o sigma) ------------------------------------------------
+
+struct Tab3 {
+  int mask[20];
   int idx[64];
-  int J[NS][NSG];    // single replacements into string I: <I| a+_p a_q |J> = sg
-  int pq[NS][NSG];
-  int sg[NS][NSG];
+  int J[20][12];  // single replacements into string I: <I| a+_p a_q |J> = sg
+  int pq[20][12];
+  int sg[20][12];
 };
 
 __host__ __device__ constexpr int popc6(int m) {
@@ -47,8 +63,8 @@ __host__ __device__ constexpr int popc6(int m) {
   return c;
 }
 
-__host__ __device__ constexpr Tab make_tab() {
-  Tab t{};
+__host__ __device__ constexpr Tab3 make_tab3() {
+  Tab3 t{};
   int c = 0;
   for (int m = 0; m < 64; ++m) {
     t.idx[m] = -1;
@@ -58,12 +74,12 @@ __host__ __device__ constexpr Tab make_tab() {
       ++c;
     }
   }
-  for (int I = 0; I < NS; ++I) {
+  for (int I = 0; I < 20; ++I) {
     const int mi = t.mask[I];
     int u = 0;
-    for (int p = 0; p < NORB; ++p) {
+    for (int p = 0; p < 6; ++p) {
       if (!((mi >> p) & 1)) continue;
-      for (int q = 0; q < NORB; ++q) {
+      for (int q = 0; q < 6; ++q) {
         if (q != p && ((mi >> q) & 1)) continue;
         const int mj = (mi & ~(1 << p)) | (1 << q);
         int s = 1;
@@ -74,7 +90,7 @@ __host__ __device__ constexpr Tab make_tab() {
           s = par ? -1 : 1;
         }
         t.J[I][u] = t.idx[mj];
-        t.pq[I][u] = p * NORB + q;
+        t.pq[I][u] = p * 6 + q;
         t.sg[I][u] = s;
         ++u;
       }
@@ -83,14 +99,14 @@ __host__ __device__ constexpr Tab make_tab() {
   return t;
 }
 
-// Compile-time copy of the tables: used only in constant expressions (template arguments), so
-// the beta-side replacement pattern becomes immediate register operands in sigma.
+// Used only in constant expressions (template arguments), so the beta-side replacement pattern
+// becomes immediate register operands in sigma.
 struct TabHolder {
-  static constexpr Tab value = make_tab();
+  static constexpr Tab3 value = make_tab3();
 };
 
 template <int B, int V>
-__device__ __forceinline__ void ab_term(float (&acc)[NS], const float (&wr)[NF], const float (&cr)[NS]) {
+__device__ __forceinline__ void ab_term(float (&acc)[20], const float (&wr)[36], const float (&cr)[20]) {
   constexpr int pq = TabHolder::value.pq[B][V];
   constexpr int J = TabHolder::value.J[B][V];
   constexpr int sg = TabHolder::value.sg[B][V];
@@ -99,50 +115,155 @@ __device__ __forceinline__ void ab_term(float (&acc)[NS], const float (&wr)[NF],
 }
 
 template <int... I>
-__device__ __forceinline__ void ab_terms(std::integer_sequence<int, I...>, float (&acc)[NS], const float (&wr)[NF],
-                                         const float (&cr)[NS]) {
-  (ab_term<I / NSG, I % NSG>(acc, wr, cr), ...);
+__device__ __forceinline__ void ab_terms(std::integer_sequence<int, I...>, float (&acc)[20], const float (&wr)[36],
+                                         const float (&cr)[20]) {
+  (ab_term<I / 12, I % 12>(acc, wr, cr), ...);
 }
 
-struct alignas(16) WarpSmem {  // 16-byte rows: sigma reads them as float4
-  float V[KM * NDET];
-  float S[KM * NDET];
-  float Wt[NW];        // FP32 W block without its [pp][rr] (diagonal-only) entries
-  float Hs[NS * NS];   // same-spin string operator, zero diagonal
-  float diag[NDET];    // operator diagonal minus E_Phi
-  float hp[NF];        // h' = h - 1/2 sum_r W_prrq (off-diagonal part used in FP32)
-  double F[NF], J[NF], K[NF];  // F block; J_pr = W_pprr, K_pr = W_prrp (FP64)
-  double hd[6];        // folded one-body diagonal h_pp (FP64)
-  double hsd[NS];      // same-spin string diagonal (FP64)
-  float dh[NS];        // hsd[I] - hsd[0] (FP64 difference, rounded); Hs[I][0] on the Phi path
-  float jb[6 * NS];    // jb[p][Ib] = sum_{r in Ib} J_pr
-  float G[KM * KM];    // projected matrix, G[i*KM+j] = V_i . S_j
-  float yf[KM];        // Ritz coefficients
-  float theta;         // Ritz value relative to eshift
+// ---- shared memory -------------------------------------------------------------------------
+
+template <int K>
+struct Tabs {  // run-time string tables of one size class
+  using D = Dim<K>;
+  int J[D::NS * D::NSG];
+  int pq[D::NS * D::NSG];
+  int sg[D::NS * D::NSG];
+  int mask[D::NS];
+  int c0n[D::NS];       // replacements (pq) with <I| E_pq |Phi string> != 0 (<= K of them)
+  int c0pq[D::NS][K];
+  int c0sg[D::NS][K];
+  int xJ[K * K];        // a+_A a_i |Phi string> = xs * |xJ>, index i*K + (A-K)
+  int xs[K * K];
+};
+
+template <int K>
+struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as float4
+  using D = Dim<K>;
+  float V[KM * D::NDET];
+  float S[KM * D::NDET];
+  float Wt[D::NW];        // FP32 W block without its [pp][rr] (diagonal-only) entries
+  float Hs[D::NS * D::NS];  // same-spin string operator, zero diagonal
+  float diag[D::NDET];    // operator diagonal minus E_Phi
+  float hp[D::NF];        // h' = h - 1/2 sum_r W_prrq (off-diagonal part, FP32)
+  double F[D::NF], J[D::NF], Kx[D::NF];  // F block; J_pr = W_pprr, K_pr = W_prrp (FP64)
+  double hd[D::NORB];     // folded one-body diagonal h_pp (FP64)
+  double hsd[D::NS];      // same-spin string diagonal (FP64)
+  float dh[D::NS];        // hsd[I] - hsd[0]; Hs[I][0] on the Phi path
+  float jb[D::NORB * D::NS];  // jb[p][Ib] = sum_{r in Ib} J_pr
+  float G[KM * KM];       // projected matrix, G[i*KM+j] = V_i . S_j
+  float yf[KM];           // Ritz coefficients
+  float theta;            // Ritz value relative to eshift
   double ecore, eshift;
-  int orb[6];
-  int ctrl[4];  // [0] subspace size, [1] valid, [2] status, [3] iterations
+  int orb[D::NORB];
+  int ctrl[4];            // [0] subspace size, [1] valid, [2] status, [3] iterations
+};
+
+union alignas(16) AnyWarpState {
+  WarpState<3> w3;
+  WarpState<2> w2;
+  WarpState<1> w1;
 };
 
 struct alignas(16) CtaSmem {
-  int J[NS * NSG];
-  int pq[NS * NSG];
-  int sg[NS * NSG];
-  int mask[NS];
-  unsigned short pair[NF * (NF + 1) / 2];  // (P, R) with P <= R, packed P | R << 8
-  int c0n[NS];          // number of replacements (pq) with <I| E_pq |Phi string> != 0
-  int c0pq[NS][3];      // their pq ...
-  int c0sg[NS][3];      // ... and signs
-  int xJ[9];            // a+_A a_i |Phi string> = xs * |xJ>, index i*3 + (A-3)
-  int xs[9];
-  WarpSmem w[WARPS];
+  Tabs<3> t3;
+  Tabs<2> t2;
+  Tabs<1> t1;
+  unsigned short pair3[Dim<3>::NPAIR];  // (P, R) with P <= R, packed P | R << 8
+  AnyWarpState w[WARPS];
 };
 
-static_assert(sizeof(WarpSmem) % 16 == 0, "per-warp state must keep 16-byte alignment");
-static_assert(offsetof(WarpSmem, V) % 16 == 0 && offsetof(WarpSmem, S) % 16 == 0 && offsetof(WarpSmem, Wt) % 16 == 0 &&
-                  offsetof(WarpSmem, Hs) % 16 == 0 && offsetof(WarpSmem, diag) % 16 == 0,
-              "float4 rows");
-static_assert(offsetof(CtaSmem, w) % 16 == 0, "warp state alignment");
+static_assert(sizeof(WarpState<3>) % 16 == 0 && offsetof(WarpState<3>, S) % 16 == 0 &&
+                  offsetof(WarpState<3>, Wt) % 16 == 0 && offsetof(WarpState<3>, Hs) % 16 == 0 &&
+                  offsetof(WarpState<3>, diag) % 16 == 0,
+              "float4 rows of the 6e6o state");
+static_assert(offsetof(CtaSmem, w) % 16 == 0 && sizeof(AnyWarpState) % 16 == 0, "warp state alignment");
+
+template <int K>
+__device__ Tabs<K>& tabs(CtaSmem& cs);
+template <>
+__device__ __forceinline__ Tabs<3>& tabs<3>(CtaSmem& cs) { return cs.t3; }
+template <>
+__device__ __forceinline__ Tabs<2>& tabs<2>(CtaSmem& cs) { return cs.t2; }
+template <>
+__device__ __forceinline__ Tabs<1>& tabs<1>(CtaSmem& cs) { return cs.t1; }
+
+template <int K>
+__device__ WarpState<K>& state(AnyWarpState& a);
+template <>
+__device__ __forceinline__ WarpState<3>& state<3>(AnyWarpState& a) { return a.w3; }
+template <>
+__device__ __forceinline__ WarpState<2>& state<2>(AnyWarpState& a) { return a.w2; }
+template <>
+__device__ __forceinline__ WarpState<1>& state<1>(AnyWarpState& a) { return a.w1; }
+
+// String tables of one class (single thread): strings by increasing bit mask (string 0 holds
+// the occupied orbitals), single replacements into each string, connections to the Phi string
+// and the single replacements i -> A of the Phi string.
+template <int K>
+__device__ void build_tabs(Tabs<K>& t) {
+  using D = Dim<K>;
+  int c = 0;
+  for (int m = 0; m < (1 << D::NORB); ++m)
+    if (__popc(m) == K) t.mask[c++] = m;
+  for (int I = 0; I < D::NS; ++I) {
+    const int mi = t.mask[I];
+    int u = 0;
+    for (int p = 0; p < D::NORB; ++p) {
+      if (!((mi >> p) & 1)) continue;
+      for (int q = 0; q < D::NORB; ++q) {
+        if (q != p && ((mi >> q) & 1)) continue;
+        const int mj = (mi & ~(1 << p)) | (1 << q);
+        int sgn = 1;
+        if (p != q) {
+          int par = __popc(mj & ((1 << q) - 1)) & 1;
+          const int m1 = mj & ~(1 << q);
+          par ^= __popc(m1 & ((1 << p) - 1)) & 1;
+          sgn = par ? -1 : 1;
+        }
+        int J = 0;
+        for (int x = 0; x < D::NS; ++x)
+          if (t.mask[x] == mj) J = x;
+        t.J[I * D::NSG + u] = J;
+        t.pq[I * D::NSG + u] = p * D::NORB + q;
+        t.sg[I * D::NSG + u] = sgn;
+        ++u;
+      }
+    }
+  }
+  for (int I = 0; I < D::NS; ++I) {
+    int n0 = 0;
+    for (int u = 0; u < D::NSG; ++u)
+      if (t.J[I * D::NSG + u] == 0 && n0 < K) {
+        t.c0pq[I][n0] = t.pq[I * D::NSG + u];
+        t.c0sg[I][n0] = t.sg[I * D::NSG + u];
+        ++n0;
+      }
+    t.c0n[I] = n0;
+  }
+  for (int x = 0; x < K * K; ++x) {
+    const int i = x / K, A = K + x % K, m0 = t.mask[0];
+    int par = __popc(m0 & ((1 << i) - 1)) & 1;
+    const int m1 = m0 & ~(1 << i);
+    par ^= __popc(m1 & ((1 << A) - 1)) & 1;
+    int J = 0;
+    for (int q = 0; q < D::NS; ++q)
+      if (t.mask[q] == (m1 | (1 << A))) J = q;
+    t.xJ[x] = J;
+    t.xs[x] = par ? -1 : 1;
+  }
+}
+
+__device__ void build_all_tabs(CtaSmem& cs) {
+  if (threadIdx.x == 0) build_tabs<3>(cs.t3);
+  if (threadIdx.x == 32) build_tabs<2>(cs.t2);
+  if (threadIdx.x == 64) build_tabs<1>(cs.t1);
+  if (threadIdx.x == 96) {
+    int t = 0;
+    for (int P = 0; P < Dim<3>::NF; ++P)
+      for (int R = P; R < Dim<3>::NF; ++R) cs.pair3[t++] = (unsigned short)(P | (R << 8));
+  }
+  __syncthreads();
+}
 
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
@@ -150,14 +271,16 @@ __device__ __forceinline__ float wsum(float v) {
   return v;
 }
 
-// sigma = H c restricted to off-diagonal couplings plus the shifted diagonal.
-__device__ __noinline__ void sigma_warp(const CtaSmem& cs, const WarpSmem& ws, const float* __restrict__ c,
-                                        float* __restrict__ out, int lane) {
+// ---- sigma ------------------------------------------------------------------------------------
+
+// 6e6o: sigma = H c restricted to off-diagonal couplings plus the shifted diagonal.
+__device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, const float* __restrict__ c,
+                                     float* __restrict__ out, int lane) {
+  constexpr int NS = 20, NSG = 12, NF = 36;
   if (lane < NS) {
     const int Ia = lane;
     float acc[NS];
-    // diagonal and alpha-alpha: acc[b] = diag * c + sum_J Hs[Ia][J] c[J][b]
-    {
+    {  // diagonal and alpha-alpha: acc[b] = diag * c + sum_J Hs[Ia][J] c[J][b]
       const float4* drow = reinterpret_cast<const float4*>(ws.diag + Ia * NS);
       const float4* crow = reinterpret_cast<const float4*>(c + Ia * NS);
 #pragma unroll
@@ -182,8 +305,7 @@ __device__ __noinline__ void sigma_warp(const CtaSmem& cs, const WarpSmem& ws, c
         acc[4 * q + 3] = fmaf(hj, cv.w, acc[4 * q + 3]);
       }
     }
-    // beta-beta: acc[b] += sum_J Hs[b][J] c[Ia][J]
-    {
+    {  // beta-beta: acc[b] += sum_J Hs[b][J] c[Ia][J]
       float ca[NS];
       const float4* crow = reinterpret_cast<const float4*>(c + Ia * NS);
 #pragma unroll
@@ -209,12 +331,12 @@ __device__ __noinline__ void sigma_warp(const CtaSmem& cs, const WarpSmem& ws, c
         acc[b] += s;
       }
     }
-    // alpha-beta: sum over the 12 replacements into Ia, register tiles of W and C rows
+    // alpha-beta: the 12 replacements into Ia, register tiles of W and C rows
 #pragma unroll 1
     for (int u = 0; u < NSG; ++u) {
       const int e = Ia * NSG + u;
-      const int pq = cs.pq[e], Ja = cs.J[e];
-      const float su = (float)cs.sg[e];
+      const int pq = tb.pq[e], Ja = tb.J[e];
+      const float su = (float)tb.sg[e];
       float wr[NF], cr[NS];
       const float4* wrow = reinterpret_cast<const float4*>(ws.Wt + pq * NF);
 #pragma unroll
@@ -241,6 +363,40 @@ __device__ __noinline__ void sigma_warp(const CtaSmem& cs, const WarpSmem& ws, c
     for (int q = 0; q < NS / 4; ++q) orow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
   }
   __syncwarp();
+}
+
+// 2e2o / 4e4o: one determinant per lane (at most 36 determinants).
+template <int K>
+__device__ __noinline__ void sigma_small(const Tabs<K>& tb, const WarpState<K>& ws, const float* __restrict__ c,
+                                         float* __restrict__ out, int lane) {
+  using D = Dim<K>;
+  for (int d = lane; d < D::NDET; d += 32) {
+    const int ia = d / D::NS, ib = d % D::NS;
+    float acc = ws.diag[d] * c[d];
+    for (int j = 0; j < D::NS; ++j) {
+      acc = fmaf(ws.Hs[ia * D::NS + j], c[j * D::NS + ib], acc);
+      acc = fmaf(ws.Hs[ib * D::NS + j], c[ia * D::NS + j], acc);
+    }
+    for (int u = 0; u < D::NSG; ++u) {
+      const int e = ia * D::NSG + u;
+      const float* wrow = ws.Wt + tb.pq[e] * D::NF;
+      const float* crow = c + tb.J[e] * D::NS;
+      float part = 0.f;
+      for (int v = 0; v < D::NSG; ++v) {
+        const int e2 = ib * D::NSG + v;
+        part = fmaf((float)tb.sg[e2] * wrow[tb.pq[e2]], crow[tb.J[e2]], part);
+      }
+      acc = fmaf((float)tb.sg[e], part, acc);
+    }
+    out[d] = acc;
+  }
+  __syncwarp();
+}
+
+template <int K>
+__device__ __forceinline__ void sigma(const Tabs<K>& tb, const WarpState<K>& ws, const float* c, float* out, int lane) {
+  if constexpr (K == 3) sigma33(tb, ws, c, out, lane);
+  else sigma_small<K>(tb, ws, c, out, lane);
 }
 
 // Phi-tracking eigenpair of the k x k projected matrix (lane 0): shifted inverse iteration
@@ -302,538 +458,580 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
   }
 }
 
-__global__ void __launch_bounds__(32 * WARPS) solve_warp_kernel(SolveArgs a, const float* __restrict__ W32,
-                                                                 const float* __restrict__ guess_in,
-                                                                 float* __restrict__ guess_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  CtaSmem& cs = *reinterpret_cast<CtaSmem*>(smem_raw);
-  if (threadIdx.x == 0) {  // string tables (same construction as make_tab, at run time)
-    int c = 0;
-    for (int m = 0; m < 64; ++m)
-      if (__popc(m) == 3) cs.mask[c++] = m;
-    for (int I = 0; I < NS; ++I) {
-      const int mi = cs.mask[I];
-      int u = 0;
-      for (int p = 0; p < NORB; ++p) {
-        if (!((mi >> p) & 1)) continue;
-        for (int q = 0; q < NORB; ++q) {
-          if (q != p && ((mi >> q) & 1)) continue;
-          const int mj = (mi & ~(1 << p)) | (1 << q);
-          int sgn = 1;
-          if (p != q) {
-            int par = __popc(mj & ((1 << q) - 1)) & 1;
-            const int m1 = mj & ~(1 << q);
-            par ^= __popc(m1 & ((1 << p) - 1)) & 1;
-            sgn = par ? -1 : 1;
-          }
-          int J = 0;
-          for (int t = 0; t < NS; ++t)
-            if (cs.mask[t] == mj) J = t;
-          cs.J[I * NSG + u] = J;
-          cs.pq[I * NSG + u] = p * NORB + q;
-          cs.sg[I * NSG + u] = sgn;
-          ++u;
-        }
-      }
-    }
-    int t = 0;
-    for (int P = 0; P < NF; ++P)
-      for (int R = P; R < NF; ++R) cs.pair[t++] = (unsigned short)(P | (R << 8));
-    for (int I = 0; I < NS; ++I) {  // connections of each string to the Phi string
-      int c = 0;
-      for (int u = 0; u < NSG; ++u)
-        if (cs.J[I * NSG + u] == 0 && c < 3) {
-          cs.c0pq[I][c] = cs.pq[I * NSG + u];
-          cs.c0sg[I][c] = cs.sg[I * NSG + u];
-          ++c;
-        }
-      cs.c0n[I] = c;
-    }
-    for (int x = 0; x < 9; ++x) {  // single replacements i -> A of the Phi string
-      const int i = x / 3, A = 3 + x % 3, m0 = cs.mask[0];
-      int par = __popc(m0 & ((1 << i) - 1)) & 1;
-      const int m1 = m0 & ~(1 << i);
-      par ^= __popc(m1 & ((1 << A) - 1)) & 1;
-      int J = 0;
-      for (int q = 0; q < NS; ++q)
-        if (cs.mask[q] == (m1 | (1 << A))) J = q;
-      cs.xJ[x] = J;
-      cs.xs[x] = par ? -1 : 1;
-    }
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpSmem& ws = cs.w[warp];
+// ---- one space -----------------------------------------------------------------------------------
+
+// Solve space s of the class list in `a` (s: index in that list) with the warp's state `ws`.
+template <int K>
+__device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ pair3, WarpState<K>& ws,
+                          const SolveArgs& a, const float* __restrict__ W32, const float* __restrict__ guess_in,
+                          float* __restrict__ guess_out, int64_t s, int lane) {
+  using D = Dim<K>;
+  constexpr int NS = D::NS, NSG = D::NSG, NDET = D::NDET, NORB = D::NORB, NF = D::NF;
   const int n = a.n;
   const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
   const float tol = (float)a.tol;
-
-#pragma unroll 1
-  for (int64_t s = (int64_t)blockIdx.x * WARPS + warp; s < a.nspaces; s += (int64_t)gridDim.x * WARPS) {
-    // ---- validate -------------------------------------------------------------------------
+  // ---- validate -------------------------------------------------------------------------
+  if (lane == 0) {
+    const qflow_space& q = a.spaces[s];
+    int ok = (q.no == K && q.nv == K);
+    for (int t = 0; t < NORB; ++t) {
+      const int o = q.orb[t];
+      ws.orb[t] = o;
+      if (t < K) ok &= (o >= 0 && o < a.nocc);
+      else ok &= (o >= a.nocc && o < a.n);
+    }
+    ws.ctrl[1] = ok;
+  }
+  __syncwarp();
+  const int64_t sidx = a.sorted_index ? a.sorted_index[s] : a.space_base + s;
+  const int64_t oidx = a.sorted_index ? sidx : s;
+  if (!ws.ctrl[1]) {
     if (lane == 0) {
-      const qflow_space& q = a.spaces[s];
-      int ok = (q.no == 3 && q.nv == 3);
-      for (int t = 0; t < 6; ++t) {
-        const int o = q.orb[t];
-        ws.orb[t] = o;
-        if (t < 3) ok &= (o >= 0 && o < a.nocc);
-        else ok &= (o >= a.nocc && o < a.n);
-      }
-      ws.ctrl[1] = ok;
+      a.energy[oidx] = 0.0;
+      a.status[oidx] = kSpaceInvalid;
+      if (a.iters) a.iters[oidx] = 0;
     }
     __syncwarp();
-    const int64_t sidx = a.sorted_index ? a.sorted_index[s] : a.space_base + s;
-    const int64_t oidx = a.sorted_index ? sidx : s;
-    if (!ws.ctrl[1]) {
-      if (lane == 0) {
-        a.energy[oidx] = 0.0;
-        a.status[oidx] = kSpaceInvalid;
-        if (a.iters) a.iters[oidx] = 0;
-      }
-      __syncwarp();
-      continue;
-    }
-    // ---- gather ------------------------------------------------------------------------------
-    // FP32 couplings: the 666 unique elements of the pair-symmetric W block (all loads in
-    // flight); FP64: J_pr = W_pprr, K_pr = W_prrp and the F block (energy-carrying parts).
-    {
-      size_t ro[6];
+    return;
+  }
+  // ---- gather ------------------------------------------------------------------------------
+  // FP32 couplings (all loads in flight); FP64: J_pr = W_pprr, K_pr = W_prrp and the F block.
+  {
+    size_t ro[NORB];
 #pragma unroll
-      for (int t = 0; t < 6; ++t) ro[t] = (size_t)ws.orb[t];
-      constexpr int PER = (NPAIR + 31) / 32;  // 21
+    for (int t = 0; t < NORB; ++t) ro[t] = (size_t)ws.orb[t];
+    if constexpr (K == 3) {  // the 666 unique elements of the pair-symmetric block
+      constexpr int PER = (D::NPAIR + 31) / 32;
       float wv[PER];
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
         const int t = lane + 32 * k;
         wv[k] = 0.f;
-        if (t < NPAIR) {
-          const int pr = cs.pair[t], P = pr & 255, R = pr >> 8;
-          const size_t g = ro[P / 6] * n3 + ro[P % 6] * n2 + ro[R / 6] * n1 + ro[R % 6];
+        if (t < D::NPAIR) {
+          const int pr = pair3[t], P = pr & 255, R = pr >> 8;
+          const size_t g = ro[P / NORB] * n3 + ro[P % NORB] * n2 + ro[R / NORB] * n1 + ro[R % NORB];
           wv[k] = W32 ? W32[g] : (float)a.W[g];
-        }
-      }
-      double jv[2], kv[2], fv[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int t = lane + 32 * k;
-        jv[k] = kv[k] = fv[k] = 0.0;
-        if (t < NF) {
-          const size_t p = ro[t / 6], r = ro[t % 6];
-          jv[k] = a.W[p * n3 + p * n2 + r * n1 + r];
-          kv[k] = a.W[p * n3 + r * n2 + r * n1 + p];
-          fv[k] = a.F[p * n1 + r];
         }
       }
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
         const int t = lane + 32 * k;
-        if (t < NPAIR) {
-          const int pr = cs.pair[t], P = pr & 255, R = pr >> 8;
-          const bool jj = (P / 6 == P % 6) && (R / 6 == R % 6);  // W_pprr: reaches only the diagonal
+        if (t < D::NPAIR) {
+          const int pr = pair3[t], P = pr & 255, R = pr >> 8;
+          const bool jj = (P / NORB == P % NORB) && (R / NORB == R % NORB);  // W_pprr: diagonal only
           const float wf = jj ? 0.f : wv[k];
           ws.Wt[P * NF + R] = wf;
           ws.Wt[R * NF + P] = wf;
         }
       }
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int t = lane + 32 * k;
-        if (t < NF) {
-          ws.J[t] = jv[k];
-          ws.K[t] = kv[k];
-          ws.F[t] = fv[k];
-        }
+    } else {
+      for (int t = lane; t < D::NW; t += 32) {
+        const int P = t / NF, R = t % NF;
+        const size_t g = ro[P / NORB] * n3 + ro[P % NORB] * n2 + ro[R / NORB] * n1 + ro[R % NORB];
+        const bool jj = (P / NORB == P % NORB) && (R / NORB == R % NORB);
+        ws.Wt[t] = jj ? 0.f : (W32 ? W32[g] : (float)a.W[g]);
       }
     }
-    __syncwarp();
-    // ---- fold (vacuum order over the active orbitals) -------------------------------------
-    // h_pp = F_pp - sum_k (2 J_pk - K_pk) in FP64; off-diagonal h' = h - 1/2 sum_r W_prrq in FP32
-    if (lane < 6) {
-      double v = ws.F[lane * 7];
-      for (int k = 0; k < 3; ++k) v -= 2.0 * ws.J[lane * 6 + k] - ws.K[lane * 6 + k];
-      ws.hd[lane] = v;
+    for (int t = lane; t < NF; t += 32) {
+      const size_t p = ro[t / NORB], r = ro[t % NORB];
+      ws.J[t] = a.W[p * n3 + p * n2 + r * n1 + r];
+      ws.Kx[t] = a.W[p * n3 + r * n2 + r * n1 + p];
+      ws.F[t] = a.F[p * n1 + r];
     }
-#pragma unroll 1
-    for (int idx = lane; idx < NF; idx += 32) {
-      const int p = idx / 6, q = idx % 6;
-      float v = (float)ws.F[idx];
-      for (int k = 0; k < 3; ++k) v -= 2.f * ws.Wt[idx * NF + k * 7] - ws.Wt[(p * 6 + k) * NF + k * 6 + q];
-      for (int r = 0; r < 6; ++r) v -= 0.5f * ws.Wt[(p * 6 + r) * NF + r * 6 + q];
-      ws.hp[idx] = (p == q) ? 0.f : v;
+  }
+  __syncwarp();
+  // ---- fold (vacuum order over the active orbitals) -------------------------------------
+  // h_pp = F_pp - sum_k (2 J_pk - K_pk) in FP64; off-diagonal h' = h - 1/2 sum_r W_prrq in FP32
+  if (lane < NORB) {
+    double v = ws.F[lane * (NORB + 1)];
+    for (int k = 0; k < K; ++k) v -= 2.0 * ws.J[lane * NORB + k] - ws.Kx[lane * NORB + k];
+    ws.hd[lane] = v;
+  }
+  for (int idx = lane; idx < NF; idx += 32) {
+    const int p = idx / NORB, q = idx % NORB;
+    float v = (float)ws.F[idx];
+    for (int k = 0; k < K; ++k)
+      v -= 2.f * ws.Wt[idx * NF + k * (NORB + 1)] - ws.Wt[(p * NORB + k) * NF + k * NORB + q];
+    for (int r = 0; r < NORB; ++r) v -= 0.5f * ws.Wt[(p * NORB + r) * NF + r * NORB + q];
+    ws.hp[idx] = (p == q) ? 0.f : v;
+  }
+  __syncwarp();
+  if (lane < NS) {  // same-spin string diagonal: sum_{p in I} h_pp + 1/2 sum_{p,r in I} (J_pr - K_pr)
+    const int m = tb.mask[lane];
+    double v = 0.0;
+    for (int p = 0; p < NORB; ++p) {
+      if (!((m >> p) & 1)) continue;
+      v += ws.hd[p];
+      for (int r = 0; r < NORB; ++r)
+        if ((m >> r) & 1) v += 0.5 * (ws.J[p * NORB + r] - ws.Kx[p * NORB + r]);
     }
-    __syncwarp();
-    if (lane < NS) {  // same-spin string diagonal: sum_{p in I} h_pp + 1/2 sum_{p,r in I} (J_pr - K_pr)
-      const int m = cs.mask[lane];
-      double v = 0.0;
-      for (int p = 0; p < 6; ++p) {
-        if (!((m >> p) & 1)) continue;
-        v += ws.hd[p];
-        for (int r = 0; r < 6; ++r)
-          if ((m >> r) & 1) v += 0.5 * (ws.J[p * 6 + r] - ws.K[p * 6 + r]);
-      }
-      ws.hsd[lane] = v;
-    }
-    __syncwarp();
-    if (lane == 0) {
-      double ec = *a.e0;
-      for (int k = 0; k < 3; ++k) ec -= ws.hd[k] + ws.F[k * 7];
-      ws.ecore = ec;
-      double v = ec + 2.0 * ws.hsd[0];
-      for (int p = 0; p < 3; ++p)
-        for (int r = 0; r < 3; ++r) v += ws.J[p * 6 + r];
-      ws.eshift = v;  // <Phi|H|Phi>
-      ws.ctrl[0] = 1;
-      ws.ctrl[2] = kSpaceNoConv;
-      ws.ctrl[3] = 0;
-      ws.theta = 0.f;
-      ws.G[0] = 0.f;
-      ws.yf[0] = 1.f;
-    }
-    __syncwarp();
-    // ---- Phi fast path: sigma(Phi) = column 0 of H (0 at Phi after the shift) --------------
-    // Only determinants connected to Phi by single or double replacements are nonzero.  If the
-    // residual of Phi is already below the tolerance the root is Phi, the increment is zero and
-    // the space is done without building the full string operator or the diagonal.
-    const bool phi_start = (guess_in == nullptr);
-    if (phi_start) {
-      if (lane < NS) {  // dh[I] <- Hs[I][0]: same-spin coupling of string I to the Phi string
-        const int I = lane;
-        float hc = 0.f;
-        if (I != 0) {
-#pragma unroll 1
-          for (int u = 0; u < NSG; ++u) {
-            const int e = I * NSG + u;
-            const int pq = cs.pq[e], Kk = cs.J[e];
-            const float s1 = (float)cs.sg[e];
-            if (Kk == 0) hc = fmaf(s1, ws.hp[pq], hc);
-            for (int v = 0; v < cs.c0n[Kk]; ++v)
-              hc = fmaf(0.5f * s1 * (float)cs.c0sg[Kk][v], ws.Wt[pq * NF + cs.c0pq[Kk][v]], hc);
-          }
-        }
-        ws.dh[I] = hc;
-      }
-      for (int d = lane; d < NDET; d += 32) {
-        ws.S[d] = 0.f;
-        ws.V[d] = (d == 0) ? 1.f : 0.f;
-      }
-      __syncwarp();
-      // alpha-beta couplings: both strings are Phi or single replacements of it (10 x 10 pairs);
-      // same-spin couplings sit in row 0 and column 0 of the CI matrix
-#pragma unroll 1
-      for (int t = lane; t < 100; t += 32) {
-        const int x = t / 10, y = t % 10;
-        const int Ia = (x == 0) ? 0 : cs.xJ[x - 1], Ib = (y == 0) ? 0 : cs.xJ[y - 1];
-        float acc = 0.f;
-        for (int u = 0; u < cs.c0n[Ia]; ++u)
-          for (int v = 0; v < cs.c0n[Ib]; ++v)
-            acc = fmaf((float)(cs.c0sg[Ia][u] * cs.c0sg[Ib][v]), ws.Wt[cs.c0pq[Ia][u] * NF + cs.c0pq[Ib][v]], acc);
-        if (t != 0) ws.S[Ia * NS + Ib] = acc;
-      }
-      __syncwarp();
-      if (lane > 0 && lane < NS) {
-        ws.S[lane * NS] += ws.dh[lane];
-        ws.S[lane] += ws.dh[lane];
-      }
-      __syncwarp();
-      float rr = 0.f;
-      for (int d = lane; d < NDET; d += 32) rr = fmaf(ws.S[d], ws.S[d], rr);
-      const float rphi = sqrtf(wsum(rr));
-      if (rphi < tol) {  // converged at Phi: E = <Phi|H|Phi>, X = 0
-        if (lane == 0) {
-          a.energy[oidx] = ws.eshift;
-          a.status[oidx] = kSpaceOk;
-          if (a.iters) a.iters[oidx] = 0;
-        }
-        if (guess_out)
-          for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (d == 0) ? 1.f : 0.f;
-        __syncwarp();
-        continue;
-      }
-    }
-    // ---- same-spin string operator, off-diagonal (row I owned by lane I) ---------------------
-    if (lane < NS) {
+    ws.hsd[lane] = v;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double ec = *a.e0;
+    for (int k = 0; k < K; ++k) ec -= ws.hd[k] + ws.F[k * (NORB + 1)];
+    ws.ecore = ec;
+    double v = ec + 2.0 * ws.hsd[0];
+    for (int p = 0; p < K; ++p)
+      for (int r = 0; r < K; ++r) v += ws.J[p * NORB + r];
+    ws.eshift = v;  // <Phi|H|Phi>
+    ws.ctrl[0] = 1;
+    ws.ctrl[2] = kSpaceNoConv;
+    ws.ctrl[3] = 0;
+    ws.theta = 0.f;
+    ws.G[0] = 0.f;
+    ws.yf[0] = 1.f;
+  }
+  __syncwarp();
+  // ---- Phi fast path: sigma(Phi) = column 0 of H (0 at Phi after the shift) ----------------
+  // Only determinants connected to Phi by single or double replacements are nonzero.  If the
+  // residual of Phi is below the tolerance, the root is Phi, the increment is zero and the
+  // space is done without building the full string operator or the diagonal.
+  const bool phi_start = (guess_in == nullptr);
+  if (phi_start) {
+    if (lane < NS) {  // dh[I] <- Hs[I][0]: same-spin coupling of string I to the Phi string
       const int I = lane;
+      float hc = 0.f;
+      if (I != 0) {
 #pragma unroll 1
-      for (int j = 0; j < NS; ++j) ws.Hs[I * NS + j] = 0.f;
-#pragma unroll 1
-      for (int u = 0; u < NSG; ++u) {
-        const int e = I * NSG + u;
-        const int pq = cs.pq[e], Kk = cs.J[e];
-        const float s1 = (float)cs.sg[e];
-        if (Kk != I) ws.Hs[I * NS + Kk] += s1 * ws.hp[pq];
-#pragma unroll 1
-        for (int v = 0; v < NSG; ++v) {
-          const int e2 = Kk * NSG + v;
-          const int J2 = cs.J[e2];
-          if (J2 == I) continue;  // the diagonal is kept in FP64
-          ws.Hs[I * NS + J2] += 0.5f * s1 * (float)cs.sg[e2] * ws.Wt[pq * NF + cs.pq[e2]];
+        for (int u = 0; u < NSG; ++u) {
+          const int e = I * NSG + u;
+          const int pq = tb.pq[e], Kk = tb.J[e];
+          const float s1 = (float)tb.sg[e];
+          if (Kk == 0) hc = fmaf(s1, ws.hp[pq], hc);
+          for (int v = 0; v < tb.c0n[Kk]; ++v)
+            hc = fmaf(0.5f * s1 * (float)tb.c0sg[Kk][v], ws.Wt[pq * NF + tb.c0pq[Kk][v]], hc);
         }
       }
+      ws.dh[I] = hc;
     }
-    // the diagonal relative to <Phi|H|Phi>: string parts as FP64 differences, the alpha-beta
-    // Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
-    if (lane < NS) ws.dh[lane] = (float)(ws.hsd[lane] - ws.hsd[0]);
-#pragma unroll 1
-    for (int t = lane; t < 6 * NS; t += 32) {
-      const int p = t / NS, b = t % NS, mb = cs.mask[b];
-      float v = 0.f;
-      for (int r = 0; r < 6; ++r)
-        if ((mb >> r) & 1) v += (float)ws.J[p * 6 + r];
-      ws.jb[t] = v;
-    }
-    __syncwarp();
-#pragma unroll 1
     for (int d = lane; d < NDET; d += 32) {
-      const int ia = d / NS, ib = d % NS;
-      const int ma = cs.mask[ia];
-      float jj = 0.f, j0 = 0.f;
-      for (int p = 0; p < 6; ++p) {
-        if ((ma >> p) & 1) jj += ws.jb[p * NS + ib];
-        if (p < 3) j0 += ws.jb[p * NS + 0];
-      }
-      ws.diag[d] = (d == 0) ? 0.f : ws.dh[ia] + ws.dh[ib] + (jj - j0);
-      if (!phi_start) ws.V[d] = guess_in[(size_t)s * NDET + d];
+      ws.S[d] = 0.f;
+      ws.V[d] = (d == 0) ? 1.f : 0.f;
     }
     __syncwarp();
-    if (!phi_start) {
-      float p = 0.f;
-      for (int d = lane; d < NDET; d += 32) p = fmaf(ws.V[d], ws.V[d], p);
-      const float nr = sqrtf(wsum(p));
-      const float inv = (nr > 0.f) ? 1.f / nr : 0.f;
-      for (int d = lane; d < NDET; d += 32) ws.V[d] = (nr > 0.f) ? ws.V[d] * inv : ((d == 0) ? 1.f : 0.f);
-      __syncwarp();
-      sigma_warp(cs, ws, ws.V, ws.S, lane);
-      float g = 0.f;
-      for (int d = lane; d < NDET; d += 32) g = fmaf(ws.V[d], ws.S[d], g);
-      g = wsum(g);
-      if (lane == 0) {
-        ws.G[0] = g;
-        ws.theta = g;
-      }
-      __syncwarp();
-    }
-    // ---- Davidson ----------------------------------------------------------------------------
+    // alpha-beta couplings: both strings are Phi or single replacements of it; same-spin
+    // couplings sit in row 0 and column 0 of the CI matrix
+    constexpr int NC = 1 + K * K;
 #pragma unroll 1
-    for (int it = 0; it < a.max_iter; ++it) {
-      int k = ws.ctrl[0];
-      if (k == KM) {  // restart on the Ritz vector
-        float pv = 0.f, ps = 0.f;
-        for (int d = lane; d < NDET; d += 32) {
-          float xv = 0.f, sv = 0.f;
-          for (int j = 0; j < k; ++j) {
-            xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
-            sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
-          }
-          ws.V[d] = xv;
-          ws.S[d] = sv;
-          pv = fmaf(xv, xv, pv);
-          ps = fmaf(xv, sv, ps);
-        }
-        pv = wsum(pv);
-        ps = wsum(ps);
-        const float inv = 1.f / sqrtf(pv);
-        for (int d = lane; d < NDET; d += 32) {
-          ws.V[d] *= inv;
-          ws.S[d] *= inv;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          ws.G[0] = ps / pv;
-          ws.theta = ws.G[0];
-          ws.yf[0] = 1.f;
-          ws.ctrl[0] = 1;
-        }
-        __syncwarp();
-        k = 1;
+    for (int t = lane; t < NC * NC; t += 32) {
+      const int x = t / NC, y = t % NC;
+      const int Ia = (x == 0) ? 0 : tb.xJ[x - 1], Ib = (y == 0) ? 0 : tb.xJ[y - 1];
+      float acc = 0.f;
+      for (int u = 0; u < tb.c0n[Ia]; ++u)
+        for (int v = 0; v < tb.c0n[Ib]; ++v)
+          acc = fmaf((float)(tb.c0sg[Ia][u] * tb.c0sg[Ib][v]), ws.Wt[tb.c0pq[Ia][u] * NF + tb.c0pq[Ib][v]], acc);
+      if (t != 0) ws.S[Ia * NS + Ib] = acc;
+    }
+    __syncwarp();
+    if (lane > 0 && lane < NS) {
+      ws.S[lane * NS] += ws.dh[lane];
+      ws.S[lane] += ws.dh[lane];
+    }
+    __syncwarp();
+    float rr = 0.f;
+    for (int d = lane; d < NDET; d += 32) rr = fmaf(ws.S[d], ws.S[d], rr);
+    const float rphi = sqrtf(wsum(rr));
+    if (rphi < tol) {  // converged at Phi: E = <Phi|H|Phi>, X = 0
+      if (lane == 0) {
+        a.energy[oidx] = ws.eshift;
+        a.status[oidx] = kSpaceOk;
+        if (a.iters) a.iters[oidx] = 0;
       }
-      const float th = ws.theta;
-      float rr = 0.f;
-      float* vk = ws.V + k * NDET;
+      if (guess_out)
+        for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (d == 0) ? 1.f : 0.f;
+      __syncwarp();
+      return;
+    }
+  }
+  // ---- same-spin string operator, off-diagonal (row I owned by lane I) ---------------------
+  if (lane < NS) {
+    const int I = lane;
+#pragma unroll 1
+    for (int j = 0; j < NS; ++j) ws.Hs[I * NS + j] = 0.f;
+#pragma unroll 1
+    for (int u = 0; u < NSG; ++u) {
+      const int e = I * NSG + u;
+      const int pq = tb.pq[e], Kk = tb.J[e];
+      const float s1 = (float)tb.sg[e];
+      if (Kk != I) ws.Hs[I * NS + Kk] += s1 * ws.hp[pq];
+#pragma unroll 1
+      for (int v = 0; v < NSG; ++v) {
+        const int e2 = Kk * NSG + v;
+        const int J2 = tb.J[e2];
+        if (J2 == I) continue;  // the diagonal is kept in FP64
+        ws.Hs[I * NS + J2] += 0.5f * s1 * (float)tb.sg[e2] * ws.Wt[pq * NF + tb.pq[e2]];
+      }
+    }
+  }
+  // the diagonal relative to <Phi|H|Phi>: string parts as FP64 differences, the alpha-beta
+  // Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
+  if (lane < NS) ws.dh[lane] = (float)(ws.hsd[lane] - ws.hsd[0]);
+#pragma unroll 1
+  for (int t = lane; t < NORB * NS; t += 32) {
+    const int p = t / NS, b = t % NS, mb = tb.mask[b];
+    float v = 0.f;
+    for (int r = 0; r < NORB; ++r)
+      if ((mb >> r) & 1) v += (float)ws.J[p * NORB + r];
+    ws.jb[t] = v;
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int d = lane; d < NDET; d += 32) {
+    const int ia = d / NS, ib = d % NS;
+    const int ma = tb.mask[ia];
+    float jj = 0.f, j0 = 0.f;
+    for (int p = 0; p < NORB; ++p) {
+      if ((ma >> p) & 1) jj += ws.jb[p * NS + ib];
+      if (p < K) j0 += ws.jb[p * NS + 0];
+    }
+    ws.diag[d] = (d == 0) ? 0.f : ws.dh[ia] + ws.dh[ib] + (jj - j0);
+    if (!phi_start) ws.V[d] = guess_in[(size_t)s * NDET + d];
+  }
+  __syncwarp();
+  if (!phi_start) {
+    float p = 0.f;
+    for (int d = lane; d < NDET; d += 32) p = fmaf(ws.V[d], ws.V[d], p);
+    const float nr = sqrtf(wsum(p));
+    const float inv = (nr > 0.f) ? 1.f / nr : 0.f;
+    for (int d = lane; d < NDET; d += 32) ws.V[d] = (nr > 0.f) ? ws.V[d] * inv : ((d == 0) ? 1.f : 0.f);
+    __syncwarp();
+    sigma<K>(tb, ws, ws.V, ws.S, lane);
+    float g = 0.f;
+    for (int d = lane; d < NDET; d += 32) g = fmaf(ws.V[d], ws.S[d], g);
+    g = wsum(g);
+    if (lane == 0) {
+      ws.G[0] = g;
+      ws.theta = g;
+    }
+    __syncwarp();
+  }
+  // ---- Davidson ----------------------------------------------------------------------------
+  constexpr int KMX = (NDET < KM) ? NDET : KM;  // the 2e2o space has only 4 determinants
+#pragma unroll 1
+  for (int it = 0; it < a.max_iter; ++it) {
+    int k = ws.ctrl[0];
+    if (k == KMX) {  // restart on the Ritz vector
+      float pv = 0.f, ps = 0.f;
       for (int d = lane; d < NDET; d += 32) {
         float xv = 0.f, sv = 0.f;
         for (int j = 0; j < k; ++j) {
           xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
           sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
         }
-        const float r = sv - th * xv;
-        rr = fmaf(r, r, rr);
-        float den = th - ws.diag[d];
-        if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
-        vk[d] = r / den;
+        ws.V[d] = xv;
+        ws.S[d] = sv;
+        pv = fmaf(xv, xv, pv);
+        ps = fmaf(xv, sv, ps);
       }
-      const float rnorm = sqrtf(wsum(rr));
-      if (!isfinite(rnorm) || !isfinite(th)) {
-        if (lane == 0) ws.ctrl[2] = kSpaceNonFinite;
-        __syncwarp();
-        break;
-      }
-      if (rnorm < tol) {
-        if (lane == 0) {
-          ws.ctrl[2] = kSpaceOk;
-          ws.ctrl[3] = it;
-        }
-        __syncwarp();
-        break;
-      }
-      __syncwarp();
-      for (int pass = 0; pass < 2; ++pass) {
-        float cf[KM];
-#pragma unroll
-        for (int j = 0; j < KM; ++j) cf[j] = 0.f;
-        for (int d = lane; d < NDET; d += 32) {
-          const float v = vk[d];
-#pragma unroll
-          for (int j = 0; j < KM; ++j)
-            if (j < k) cf[j] = fmaf(ws.V[j * NDET + d], v, cf[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < k) cf[j] = wsum(cf[j]);
-        for (int d = lane; d < NDET; d += 32) {
-          float v = vk[d];
-#pragma unroll
-          for (int j = 0; j < KM; ++j)
-            if (j < k) v = fmaf(-cf[j], ws.V[j * NDET + d], v);
-          vk[d] = v;
-        }
-        __syncwarp();
-      }
-      float nn = 0.f;
-      for (int d = lane; d < NDET; d += 32) nn = fmaf(vk[d], vk[d], nn);
-      const float vn = sqrtf(wsum(nn));
-      if (!(vn > 1e-6f)) {
-        if (lane == 0) {
-          ws.ctrl[2] = (rnorm < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
-          ws.ctrl[3] = it;
-        }
-        __syncwarp();
-        break;
-      }
-      const float inv = 1.f / vn;
-      for (int d = lane; d < NDET; d += 32) vk[d] *= inv;
-      __syncwarp();
-      float* sk = ws.S + k * NDET;
-      sigma_warp(cs, ws, vk, sk, lane);
-      float gc[KM], gr[KM];
-#pragma unroll
-      for (int j = 0; j < KM; ++j) gc[j] = gr[j] = 0.f;
-      float gkk = 0.f;
+      pv = wsum(pv);
+      ps = wsum(ps);
+      const float inv = 1.f / sqrtf(pv);
       for (int d = lane; d < NDET; d += 32) {
-        const float vkd = vk[d], skd = sk[d];
-        gkk = fmaf(vkd, skd, gkk);
+        ws.V[d] *= inv;
+        ws.S[d] *= inv;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        ws.G[0] = ps / pv;
+        ws.theta = ws.G[0];
+        ws.yf[0] = 1.f;
+        ws.ctrl[0] = 1;
+      }
+      __syncwarp();
+      k = 1;
+    }
+    const float th = ws.theta;
+    float rr = 0.f;
+    float* vk = ws.V + k * NDET;
+    for (int d = lane; d < NDET; d += 32) {
+      float xv = 0.f, sv = 0.f;
+      for (int j = 0; j < k; ++j) {
+        xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+        sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
+      }
+      const float r = sv - th * xv;
+      rr = fmaf(r, r, rr);
+      float den = th - ws.diag[d];
+      if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
+      vk[d] = r / den;
+    }
+    const float rnorm = sqrtf(wsum(rr));
+    if (!isfinite(rnorm) || !isfinite(th)) {
+      if (lane == 0) ws.ctrl[2] = kSpaceNonFinite;
+      __syncwarp();
+      break;
+    }
+    if (rnorm < tol) {
+      if (lane == 0) {
+        ws.ctrl[2] = kSpaceOk;
+        ws.ctrl[3] = it;
+      }
+      __syncwarp();
+      break;
+    }
+    __syncwarp();
+    for (int pass = 0; pass < 2; ++pass) {
+      float cf[KM];
+#pragma unroll
+      for (int j = 0; j < KM; ++j) cf[j] = 0.f;
+      for (int d = lane; d < NDET; d += 32) {
+        const float v = vk[d];
 #pragma unroll
         for (int j = 0; j < KM; ++j)
-          if (j < k) {
-            gc[j] = fmaf(ws.V[j * NDET + d], skd, gc[j]);
-            gr[j] = fmaf(vkd, ws.S[j * NDET + d], gr[j]);
-          }
+          if (j < k) cf[j] = fmaf(ws.V[j * NDET + d], v, cf[j]);
       }
-      gkk = wsum(gkk);
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (j < k) cf[j] = wsum(cf[j]);
+      for (int d = lane; d < NDET; d += 32) {
+        float v = vk[d];
+#pragma unroll
+        for (int j = 0; j < KM; ++j)
+          if (j < k) v = fmaf(-cf[j], ws.V[j * NDET + d], v);
+        vk[d] = v;
+      }
+      __syncwarp();
+    }
+    float nn = 0.f;
+    for (int d = lane; d < NDET; d += 32) nn = fmaf(vk[d], vk[d], nn);
+    const float vn = sqrtf(wsum(nn));
+    if (!(vn > 1e-6f)) {  // the subspace cannot grow (complete or stagnated)
+      if (lane == 0) {
+        ws.ctrl[2] = (rnorm < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
+        ws.ctrl[3] = it;
+      }
+      __syncwarp();
+      break;
+    }
+    const float inv = 1.f / vn;
+    for (int d = lane; d < NDET; d += 32) vk[d] *= inv;
+    __syncwarp();
+    float* sk = ws.S + k * NDET;
+    sigma<K>(tb, ws, vk, sk, lane);
+    float gc[KM], gr[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) gc[j] = gr[j] = 0.f;
+    float gkk = 0.f;
+    for (int d = lane; d < NDET; d += 32) {
+      const float vkd = vk[d], skd = sk[d];
+      gkk = fmaf(vkd, skd, gkk);
 #pragma unroll
       for (int j = 0; j < KM; ++j)
         if (j < k) {
-          gc[j] = wsum(gc[j]);
-          gr[j] = wsum(gr[j]);
+          gc[j] = fmaf(ws.V[j * NDET + d], skd, gc[j]);
+          gr[j] = fmaf(vkd, ws.S[j * NDET + d], gr[j]);
         }
-      if (lane == 0) {
-        for (int j = 0; j < k; ++j) {
-          ws.G[j * KM + k] = gc[j];
-          ws.G[k * KM + j] = gr[j];
-        }
-        ws.G[k * KM + k] = gkk;
-        const int kk = k + 1;
-        float yn[KM];
-        for (int j = 0; j < kk; ++j) yn[j] = (j < k) ? ws.yf[j] : 0.f;
-        float thn = ws.theta;
-        small_eig(ws.G, kk, ws.theta - 1e-2f, yn, &thn);
-        for (int j = 0; j < kk; ++j) ws.yf[j] = yn[j];
-        ws.theta = thn;
-        ws.ctrl[0] = kk;
-        ws.ctrl[3] = it + 1;
+    }
+    gkk = wsum(gkk);
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) {
+        gc[j] = wsum(gc[j]);
+        gr[j] = wsum(gr[j]);
       }
-      __syncwarp();
-    }
-    // ---- root, increment, merge ------------------------------------------------------------
-    const int k = ws.ctrl[0];
-    float xx = 0.f;
-    for (int d = lane; d < NDET; d += 32) {
-      float xv = 0.f;
-      for (int j = 0; j < k; ++j) xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
-      ws.S[d] = xv;
-      xx = fmaf(xv, xv, xx);
-    }
-    xx = wsum(xx);
-    __syncwarp();
-    const float xn = sqrtf(xx);
-    const float c0 = ws.S[0];
-    int st = ws.ctrl[2];
-    if (st == kSpaceOk && !(fabsf(c0) >= 1e-3f * xn)) st = kSpaceRoot;
-    if (!isfinite(c0) || !isfinite(ws.theta)) st = kSpaceNonFinite;
-    const float inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.f / c0 : 0.f;
-    if (guess_out && st == kSpaceOk)
-      for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = ws.S[d] * inv0;
-    float* x1 = ws.V;  // V is free now: 9 + 81 floats of scratch
-    float* x2 = x1 + 9;
-    if (lane < 9) {
-      const int J = cs.xJ[lane];
-      const float f = (cs.xs[lane] < 0) ? -inv0 : inv0;
-      x1[lane] = 0.5f * f * (ws.S[J * NS] + ws.S[J]);
-    }
-    __syncwarp();
-#pragma unroll 1
-    for (int idx = lane; idx < 81; idx += 32) {
-      const int i = idx / 27, j = (idx / 9) % 3, aa = (idx / 3) % 3, b = idx % 3;
-      const int xa = i * 3 + aa, xb = j * 3 + b;
-      const float f = (cs.xs[xa] != cs.xs[xb]) ? -inv0 : inv0;
-      x2[idx] = f * ws.S[cs.xJ[xa] * NS + cs.xJ[xb]] - x1[xa] * x1[xb];
-    }
-    __syncwarp();
-    if (st == kSpaceOk && a.owner1 && lane < 9) {
-      const int i = lane / 3, aa = lane % 3;
-      const size_t g = (size_t)ws.orb[i] * a.nvir + (ws.orb[3 + aa] - a.nocc);
-      if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + (double)x1[lane];
-    }
-    if (st == kSpaceOk && a.owner2) {
-#pragma unroll 1
-      for (int idx = lane; idx < 81; idx += 32) {
-        const int i = idx / 27, j = (idx / 9) % 3, aa = (idx / 3) % 3, b = idx % 3;
-        const size_t g = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[3 + aa] - a.nocc)) * a.nvir +
-                         (ws.orb[3 + b] - a.nocc);
-        if (a.owner2[g] == sidx)
-          a.t2_new[g] = a.t2_old[g] + (double)(0.5f * (x2[idx] + x2[((j * 3 + i) * 3 + b) * 3 + aa]));
-      }
-    }
     if (lane == 0) {
-      a.energy[oidx] = ws.eshift + (double)ws.theta;
-      a.status[oidx] = st;
-      if (a.iters) a.iters[oidx] = ws.ctrl[3];
+      for (int j = 0; j < k; ++j) {
+        ws.G[j * KM + k] = gc[j];
+        ws.G[k * KM + j] = gr[j];
+      }
+      ws.G[k * KM + k] = gkk;
+      const int kk = k + 1;
+      float yn[KM];
+      for (int j = 0; j < kk; ++j) yn[j] = (j < k) ? ws.yf[j] : 0.f;
+      float thn = ws.theta;
+      small_eig(ws.G, kk, ws.theta - 1e-2f, yn, &thn);
+      for (int j = 0; j < kk; ++j) ws.yf[j] = yn[j];
+      ws.theta = thn;
+      ws.ctrl[0] = kk;
+      ws.ctrl[3] = it + 1;
     }
     __syncwarp();
   }
+  // ---- root, increment, merge ------------------------------------------------------------
+  const int k = ws.ctrl[0];
+  float xx = 0.f;
+  for (int d = lane; d < NDET; d += 32) {
+    float xv = 0.f;
+    for (int j = 0; j < k; ++j) xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+    ws.S[d] = xv;
+    xx = fmaf(xv, xv, xx);
+  }
+  xx = wsum(xx);
+  __syncwarp();
+  const float xn = sqrtf(xx);
+  const float c0 = ws.S[0];
+  int st = ws.ctrl[2];
+  if (st == kSpaceOk && !(fabsf(c0) >= 1e-3f * xn)) st = kSpaceRoot;
+  if (!isfinite(c0) || !isfinite(ws.theta)) st = kSpaceNonFinite;
+  const float inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.f / c0 : 0.f;
+  if (guess_out && st == kSpaceOk)
+    for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = ws.S[d] * inv0;
+  float* x1 = ws.V;  // V is free now: K^2 + K^4 floats of scratch
+  float* x2 = x1 + K * K;
+  if (lane < K * K) {
+    const int J = tb.xJ[lane];
+    const float f = (tb.xs[lane] < 0) ? -inv0 : inv0;
+    x1[lane] = 0.5f * f * (ws.S[J * NS] + ws.S[J]);
+  }
+  __syncwarp();
+  constexpr int K4 = K * K * K * K;
+#pragma unroll 1
+  for (int idx = lane; idx < K4; idx += 32) {
+    const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
+    const int xa = i * K + aa, xb = j * K + b;
+    const float f = (tb.xs[xa] != tb.xs[xb]) ? -inv0 : inv0;
+    x2[idx] = f * ws.S[tb.xJ[xa] * NS + tb.xJ[xb]] - x1[xa] * x1[xb];
+  }
+  __syncwarp();
+  if (st == kSpaceOk && a.owner1 && lane < K * K) {
+    const int i = lane / K, aa = lane % K;
+    const size_t g = (size_t)ws.orb[i] * a.nvir + (ws.orb[K + aa] - a.nocc);
+    if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + (double)x1[lane];
+  }
+  if (st == kSpaceOk && a.owner2) {
+#pragma unroll 1
+    for (int idx = lane; idx < K4; idx += 32) {
+      const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
+      const size_t g = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[K + aa] - a.nocc)) * a.nvir +
+                       (ws.orb[K + b] - a.nocc);
+      if (a.owner2[g] == sidx)
+        a.t2_new[g] = a.t2_old[g] + (double)(0.5f * (x2[idx] + x2[((j * K + i) * K + b) * K + aa]));
+    }
+  }
+  if (lane == 0) {
+    a.energy[oidx] = ws.eshift + (double)ws.theta;
+    a.status[oidx] = st;
+    if (a.iters) a.iters[oidx] = ws.ctrl[3];
+  }
+  __syncwarp();
+}
+
+// ---- kernels --------------------------------------------------------------------------------------
+
+template <int K>
+__global__ void __launch_bounds__(32 * WARPS) solve_class_kernel(SolveArgs a, const float* __restrict__ W32,
+                                                                  const float* __restrict__ guess_in,
+                                                                  float* __restrict__ guess_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CtaSmem& cs = *reinterpret_cast<CtaSmem*>(smem_raw);
+  build_all_tabs(cs);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpState<K>& ws = state<K>(cs.w[warp]);
+#pragma unroll 1
+  for (int64_t s = (int64_t)blockIdx.x * WARPS + warp; s < a.nspaces; s += (int64_t)gridDim.x * WARPS)
+    solve_one<K>(tabs<K>(cs), cs.pair3, ws, a, W32, guess_in, guess_out, s, lane);
+}
+
+struct PersistentArgs {
+  SolveArgs cls[4];           // [k] for k = 1..3 (cls[0] unused)
+  const float* W32;
+  unsigned long long* queue;  // work counter, zero at launch
+  int chunk;                  // work items taken per atomic
+};
+
+// One queue over every size class: items [0, n3) are 6e6o spaces, then 4e4o, then 2e2o.
+__global__ void __launch_bounds__(32 * WARPS) solve_persistent_kernel(PersistentArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CtaSmem& cs = *reinterpret_cast<CtaSmem*>(smem_raw);
+  build_all_tabs(cs);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n3 = p.cls[3].nspaces, n2 = p.cls[2].nspaces, n1 = p.cls[1].nspaces;
+  const unsigned long long total = (unsigned long long)(n3 + n2 + n1);
+  // each pass takes `chunk` new items, so the loop ends after at most total / chunk + 1 passes
+#pragma unroll 1
+  for (unsigned long long pass = 0; pass <= total; ++pass) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)p.chunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= total) break;
+#pragma unroll 1
+    for (int c = 0; c < p.chunk; ++c) {
+      const unsigned long long item = base + (unsigned long long)c;
+      if (item >= total) break;
+      const int64_t it = (int64_t)item;
+      if (it < n3) {
+        const SolveArgs& a = p.cls[3];
+        solve_one<3>(cs.t3, cs.pair3, state<3>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+                     a.save_root ? static_cast<float*>(a.guess) : nullptr, it, lane);
+      } else if (it < n3 + n2) {
+        const SolveArgs& a = p.cls[2];
+        solve_one<2>(cs.t2, cs.pair3, state<2>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+                     a.save_root ? static_cast<float*>(a.guess) : nullptr, it - n3, lane);
+      } else {
+        const SolveArgs& a = p.cls[1];
+        solve_one<1>(cs.t1, cs.pair3, state<1>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+                     a.save_root ? static_cast<float*>(a.guess) : nullptr, it - n3 - n2, lane);
+      }
+    }
+  }
+}
+
+template <typename Kern>
+cudaError_t grid_for(Kern kern, int ctas_per_sm, int* grid) {
+  const size_t smem = sizeof(CtaSmem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WARPS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  *grid = sms * per_sm;
+  return cudaSuccess;
 }
 
 }  // namespace
 
-cudaError_t launch_solve_warp33(const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
-                                cudaStream_t st) {
+cudaError_t launch_solve_warp(int k, const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
+                              int ctas_per_sm, cudaStream_t st) {
   if (a.nspaces <= 0) return cudaSuccess;
-  const size_t smem = sizeof(CtaSmem);
-  cudaError_t e = cudaFuncSetAttribute(solve_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_warp_kernel, 32 * WARPS, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)sms * per_sm;
+  int grid = 0;
+  cudaError_t e;
   const int64_t need = (a.nspaces + WARPS - 1) / WARPS;
-  if (grid > need) grid = need;
-  solve_warp_kernel<<<(unsigned)grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out);
+  switch (k) {
+    case 1: e = grid_for(solve_class_kernel<1>, ctas_per_sm, &grid); break;
+    case 2: e = grid_for(solve_class_kernel<2>, ctas_per_sm, &grid); break;
+    case 3: e = grid_for(solve_class_kernel<3>, ctas_per_sm, &grid); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  if (grid > need) grid = (int)need;
+  const size_t smem = sizeof(CtaSmem);
+  switch (k) {
+    case 1: solve_class_kernel<1><<<grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out); break;
+    case 2: solve_class_kernel<2><<<grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out); break;
+    default: solve_class_kernel<3><<<grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out); break;
+  }
   return cudaGetLastError();
 }
 
-size_t solve_warp33_smem() { return sizeof(CtaSmem); }
+cudaError_t launch_solve_persistent(const SolveArgs* cls, const float* W32, unsigned long long* queue, int chunk,
+                                    int ctas_per_sm, cudaStream_t st) {
+  PersistentArgs p{};
+  int64_t total = 0;
+  for (int k = 1; k <= 3; ++k) {
+    p.cls[k] = cls[k];
+    total += cls[k].nspaces;
+  }
+  if (total <= 0) return cudaSuccess;
+  p.W32 = W32;
+  p.queue = queue;
+  p.chunk = chunk < 1 ? 1 : chunk;
+  int grid = 0;
+  cudaError_t e = grid_for(solve_persistent_kernel, ctas_per_sm, &grid);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (total + WARPS - 1) / WARPS;
+  if (grid > need) grid = (int)need;
+  e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  solve_persistent_kernel<<<grid, 32 * WARPS, sizeof(CtaSmem), st>>>(p);
+  return cudaGetLastError();
+}
 
 }  // namespace qf

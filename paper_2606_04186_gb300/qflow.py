@@ -32,7 +32,8 @@ class QFlowError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
-                ("diis", C.c_int32), ("guess", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("diis", C.c_int32), ("guess", C.c_int32), ("schedule", C.c_int32), ("graph", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 _lib = None
@@ -60,6 +61,7 @@ def lib() -> C.CDLL:
         "qflow_dressed": (I32, [P, P, P, P]),
         "qflow_stream": (V, [P]),
         "qflow_last_sweep_info": (I32, [P, P, P]),
+        "qflow_schedule": (I32, [P, P, P, P, P, P, P]),
         "qflow_destroy": (None, [P]),
         "qflow_strerror": (C.c_char_p, [C.c_int]),
         "qflow_dress_workspace": (C.c_size_t, [I32, I32]),
@@ -126,7 +128,8 @@ class Flow:
     """One flow on the current CUDA device (handle API of the library)."""
 
     def __init__(self, h, eri, nocc: int, spaces, precision: str = "fp64", max_iter: int | None = None,
-                 tol: float | None = None, guess: str = "phi", diis: int = 0):
+                 tol: float | None = None, guess: str = "phi", diis: int = 0, schedule: str = "auto",
+                 graph: bool = True):
         h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
         self.n, self.nocc = h.shape[0], nocc
         self.nvir = self.n - nocc
@@ -138,6 +141,8 @@ class Flow:
             opt.tol = tol
         opt.guess = {"phi": 0, "previous": 1}[guess]
         opt.diis = diis
+        opt.schedule = {"auto": 0, "per_class": 1, "persistent": 2}[schedule]
+        opt.graph = int(graph)
         self._h = C.c_void_p()
         code = lib().qflow_init(C.byref(self._h), _ptr(h), _ptr(eri), self.n, nocc, _ptr(sp), len(sp), C.byref(opt))
         self.init_status = _check(code, "qflow_init")
@@ -199,6 +204,14 @@ class Flow:
         nl = C.c_int64()
         _check(lib().qflow_last_sweep_info(self._h, _ptr(ph), C.byref(nl)), "qflow_last_sweep_info")
         return ph, nl.value
+
+    def schedule(self) -> dict:
+        p, ch, ct, gr, nc = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        ms = (C.c_float * 8)()
+        _check(lib().qflow_schedule(self._h, C.byref(p), C.byref(ch), C.byref(ct), C.byref(gr), ms, C.byref(nc)),
+               "qflow_schedule")
+        return {"persistent": bool(p.value), "chunk": ch.value, "ctas_per_sm": ct.value, "graph": bool(gr.value),
+                "candidate_ms": [float(ms[i]) for i in range(nc.value)]}
 
     def stream(self) -> int:
         return lib().qflow_stream(self._h) or 0

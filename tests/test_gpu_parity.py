@@ -146,7 +146,7 @@ def test_ccsd_fixed_point_n24(qf):
     gpu.close()
 
 
-@pytest.mark.parametrize("name,precision", [("n24", "fp64"), ("n24", "mixed"), ("n40", "fp64")])
+@pytest.mark.parametrize("name,precision", [("n24", "fp64"), ("n24", "mixed"), ("n40", "fp64"), ("n40", "mixed")])
 def test_sampled_spaces_full_list(qf, name, precision):
     """Full space lists on the GPU; a seeded sample of spaces recomputed by the oracle."""
     eps, h, g, sp = synth.system_inputs(name)
@@ -238,3 +238,36 @@ def test_mixed_dressing_close_to_oracle(qf):
     assert np.abs(F - Fr).max() < 1e-11
     assert np.abs(W - Wr).max() < 1e-6
     gpu.close()
+
+
+def test_schedules_and_graph_replay_agree(qf):
+    """Per-class launches, the persistent queue and CUDA-graph replay compute the same sweep."""
+    eps, h, g, sp = synth.system_inputs("n40")
+    runs = {}
+    for name, kw in [("per_class", dict(schedule="per_class", graph=False)),
+                     ("persistent", dict(schedule="persistent", graph=False)),
+                     ("graph", dict(schedule="persistent", graph=True))]:
+        f = qf.Flow(h, g, 6, sp, precision="mixed", **kw)
+        per = []
+        for _ in range(3):
+            f.sweep()
+            per.append(f.energy(per_space=True)[1])
+            phases, launches = f.last_sweep_info()   # phase timers also work on a replayed sweep
+            assert (np.asarray(phases) >= 0).all() and launches > 0
+        runs[name] = (np.array(per), f.amplitudes(), f.schedule())
+        f.close()
+    ref = runs["per_class"]
+    for name in ("persistent", "graph"):
+        assert np.array_equal(runs[name][0], ref[0])
+        assert np.array_equal(runs[name][1][1], ref[1][1])
+    assert runs["graph"][2]["graph"] and runs["graph"][2]["persistent"]
+
+
+def test_autotuner_times_candidates(qf):
+    eps, h, g, sp = synth.system_inputs("n40")
+    sp = sp[::3]   # a space list of its own, so the per-process cache is cold
+    f = qf.Flow(h, g, 6, sp, precision="mixed", schedule="auto")
+    f.sweep()
+    sch = f.schedule()
+    assert len(sch["candidate_ms"]) == 6 and min(sch["candidate_ms"]) > 0
+    f.close()
