@@ -204,3 +204,24 @@ def random_amplitudes(nocc: int, nvir: int, seed: int, scale1: float = 0.02, sca
     t2 = scale2 * rng.standard_normal((nocc, nocc, nvir, nvir))
     t2 = 0.5 * (t2 + t2.transpose(1, 0, 3, 2))
     return t1, t2
+
+
+# ---- warm-start network inputs -----------------------------------------------------------------
+
+def mlp_init_params(n_in: int, hidden: int, n_out: int, seed: int) -> np.ndarray:
+    """Seeded Glorot-uniform weights and zero biases, packed W1, b1, W2, b2, W3, b3 with every W
+    stored [fan_in][fan_out] row-major (float64; callers cast)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fi, fo in ((n_in, hidden), (hidden, hidden), (hidden, n_out)):
+        lim = math.sqrt(6.0 / (fi + fo))
+        parts.append(rng.uniform(-lim, lim, size=fi * fo))
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts)
+
+
+def mlp_init_model(hidden: int, seed: int, n_in: int = 708, n_out: int = 54) -> np.ndarray:
+    """Initial model of the 6e6o warm-start network: parameters followed by placeholder
+    standardisation (mean 0, scale 1) that training replaces (float32)."""
+    p = mlp_init_params(n_in, hidden, n_out, seed)
+    return np.concatenate([p, np.zeros(n_in), np.ones(n_in), np.zeros(n_out), np.ones(n_out)]).astype(np.float32)
