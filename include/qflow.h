@@ -70,8 +70,9 @@ typedef struct {
 } qflow_space;
 
 typedef enum {
-  QFLOW_SCHED_AUTO = 0,       /* mixed precision: the autotuner picks the launch schedule on the
-                                 first sweep (timed candidates on a calibration subset)       */
+  QFLOW_SCHED_AUTO = 0,       /* mixed precision: the first sweep runs the persistent queue;
+                                 at the second sweep the autotuner times the candidates on a
+                                 calibration subset and keeps the fastest                     */
   QFLOW_SCHED_PER_CLASS = 1,  /* one grid-stride launch per size class                        */
   QFLOW_SCHED_PERSISTENT = 2  /* one persistent launch; warps take spaces of every class from a
                                  single work queue, 6e6o first                                 */
@@ -89,11 +90,16 @@ typedef struct {
                                  one CI vector per space on the device: 400 x 4 B per 6e6o
                                  space in mixed precision, x 8 B in FP64).  In a flow the pool
                                  absorbs each root's increment, so Phi is usually the closer
-                                 start; 1 pays off when the pool is held fixed.             */
+                                 start; 1 pays off when the pool is held fixed.
+                                 2 = warm-start network (QFLOW_GUESS_NETWORK below): 6e6o
+                                 roots are kept like 1, but sweeps start from Phi except the
+                                 first sweep after a model is set or trained, which starts the
+                                 6e6o spaces from the network's guess.                       */
   int32_t schedule;           /* qflow_schedule_kind (mixed precision; FP64 uses per-class
                                  launches)                                                   */
-  int32_t graph;              /* 1 = after the first sweep, capture the sweep's device work in
-                                 a CUDA graph and replay it (default 1)                      */
+  int32_t graph;              /* 1 = once the schedule is fixed (mixed: from the third sweep,
+                                 FP64: from the second), capture the sweep's device work in a
+                                 CUDA graph and replay it (default 1)                        */
   int32_t reserved[6];
 } qflow_options;
 
@@ -155,7 +161,7 @@ int qflow_dressed(qflow_handle hnd, double* e0, double* F, double* W);
  * of kernels the sweep launched.  Either output may be NULL. */
 int qflow_last_sweep_info(qflow_handle hnd, double* phase_ms, int64_t* kernel_launches);
 
-/* Launch schedule in use (after the first sweep): persistent queue or per-class launches,
+/* Launch schedule in use (tuned at the second sweep): persistent queue or per-class launches,
  * items per queue fetch, CTAs per SM (0 = occupancy limit), whether sweeps replay a CUDA
  * graph, and the autotuner's calibration times (milliseconds per candidate, up to 8; the
  * count is 0 when the schedule was fixed or came from the per-process cache).  Any output may
@@ -196,9 +202,11 @@ int qflow_dress_device(const double* h, const double* eri, const double* t1, con
  *             amplitudes (the caller initialises them, e.g. with a copy of the old pool)
  *   energy[nspaces], status[nspaces], iters[nspaces]: outputs (iters may be NULL)
  *   guess     NULL or device [nspaces][C(2k,k)^2] start vectors in the path's working
- *             precision (double for QFLOW_PREC_FP64, float for QFLOW_PREC_MIXED), any scale
- *             (an all-zero vector means Phi); receives the converged root (Phi coefficient 1)
- *             when save_root != 0
+ *             precision (double for QFLOW_PREC_FP64, float for QFLOW_PREC_MIXED), any scale.
+ *             FP64: the solver starts from the guess (an all-zero vector means Phi).  Mixed:
+ *             the solver first tests Phi (converged there: done), else starts from the span
+ *             of Phi and the guess, whose sigma counts as one iteration.  Receives the
+ *             converged root (Phi coefficient 1) when save_root != 0
  *   precision qflow_precision; max_iter, tol as in qflow_options. */
 int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* F, const double* W,
                        int32_t size_class, const qflow_space* spaces, int64_t nspaces, int64_t space_base, const int32_t* owner1,
@@ -231,6 +239,95 @@ int qflow_dress_device_static(const double* h, const double* eri, const double* 
                               int32_t nocc, double* e0, double* F, double* W, void* stream);
 /* Size of that static scratch array in bytes. */
 size_t qflow_static_scratch_bytes(void);
+
+/* ---- warm-start network (not in the paper) -----------------------------------------------
+ * The paper mentions learning only for choosing active spaces.  This optional network
+ * predicts the CI -> CC increment of a 6e6o space from its folded integrals, and the first
+ * sweep after a model is loaded starts those spaces' Davidson solvers from the prediction
+ * instead of Phi.  The solver still converges every space to its own tolerance, so energies
+ * and amplitudes do not depend on the network; only the iteration count does.
+ *
+ * Features of a (3,3) space (QFLOW_MLP_NIN = 708 floats): the vacuum-ordered one-body block
+ * h[p][q] = F[p][q] - sum_{k occupied} (2 W[p][q][k][k] - W[p][k][k][q]) over the six local
+ * orbitals (occupied first; 36, row-major), W[p][q][r][s] once per index-pair pair
+ * P = 6p+q <= R = 6r+s (666, row-major over (P, R)), F[p][p] of the six orbitals (6).
+ * Targets (QFLOW_MLP_NOUT = 54): X1[i][a] (9, row-major) and X2[i][j][a][b] once per
+ * P = 3i+a <= R = 3j+b (45, row-major over (P, R)), local indices.
+ * Start vector (400 determinants, the solver's layout: alpha string * 20 + beta string,
+ * strings by increasing bit mask over the local orbitals): Phi + X1 Phi + (X2 + X1^2/2) Phi.
+ * Network: H1 = tanh(x W1 + b1), H2 = tanh(H1 W2 + b2), y = H2 W3 + b3, FP32, W stored
+ * [fan_in][fan_out] row-major; parameters packed as W1, b1, W2, b2, W3, b3
+ * (qflow_mlp_param_count).  Loss: 1/(2 rows) sum (y - t)^2 over rows whose mask is set.
+ * Adam: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2, p -= lr (m/(1-b1^k)) / (sqrt(v/(1-b2^k)) + eps).
+ * A model (qflow_mlp_model_size floats) is the parameters followed by the standardisation
+ * mu_x[708], s_x[708] (network input = (x - mu_x) * s_x) and mu_y[54], sd_y[54]
+ * (increment = mu_y + sd_y * network output). */
+#define QFLOW_MLP_NIN 708
+#define QFLOW_MLP_NOUT 54
+#define QFLOW_GUESS_NETWORK 2
+
+int64_t qflow_mlp_param_count(int32_t n_in, int32_t hidden, int32_t n_out);
+int64_t qflow_mlp_model_size(int32_t hidden);
+
+/* Load a model for the handle (host floats, qflow_mlp_model_size(hidden)); hidden in 1..1024.
+ * has_stats = 0: the standardisation is computed from the training set at the next
+ * qflow_mlp_train (the stored one is ignored).  Resets the Adam state.  In guess mode 2 the
+ * next sweep starts 6e6o spaces from the model's prediction (an increment model). */
+int qflow_mlp_set_model(qflow_handle hnd, int32_t hidden, const float* model, int32_t has_stats);
+/* Copy the handle's model to a host buffer of qflow_mlp_model_size(hidden) floats. */
+int qflow_mlp_get_model(qflow_handle hnd, float* model);
+
+/* Append training pairs for every 6e6o space at class position p = k * stride (the class
+ * position of a 6e6o space is its rank in lexicographic order of orb[0..5], ties by Delta-eps
+ * position).  Two kinds of pair, one kind per handle:
+ *   QFLOW_MLP_TARGET_INCREMENT: features from the last sweep's dressed integrals, target the
+ *     increment of the space's converged root (guess mode 2, right after a sweep; spaces whose
+ *     solve failed enter with a cleared mask).  A model trained on these gives Davidson guesses.
+ *   QFLOW_MLP_TARGET_POOL: features from the bare integrals (the dressing of the zero pool),
+ *     target the space's internal amplitudes in the current pool, e.g. after the flow has
+ *     converged.  A model trained on these initialises a new flow's pool (qflow_mlp_warm_pool).
+ * The call re-dresses for POOL pairs (the next sweep dresses again).  The first call fixes the
+ * capacity (max_pairs rows); later calls append until it is full.  n_pairs (nullable) receives
+ * the number of stored pairs. */
+#define QFLOW_MLP_TARGET_INCREMENT 0
+#define QFLOW_MLP_TARGET_POOL 1
+int qflow_mlp_collect(qflow_handle hnd, int32_t target, int64_t stride, int64_t max_pairs, int64_t* n_pairs);
+
+/* Warm start of the flow: the pool is set to the model's prediction, from the bare integrals,
+ * of every 6e6o space's internal amplitudes, each amplitude taken from its owner space (the
+ * owner rule of the merge); amplitudes no 6e6o space owns start at zero.  Needs a model with
+ * standardisation (trained on QFLOW_MLP_TARGET_POOL pairs).  The sweeps that follow are the
+ * plain flow, so its fixed point does not depend on the model; only the number of sweeps to
+ * reach it does.  Resets the DIIS history. */
+int qflow_mlp_warm_pool(qflow_handle hnd);
+
+/* Train the loaded model on the stored pairs: `epochs` passes of mini-batches of `batch` rows
+ * in the order given by order[n_pairs] (host, nullable = stored order), one Adam step
+ * (b1 0.9, b2 0.999, eps 1e-8, learning rate lr) per batch.  loss (host, nullable,
+ * `epochs` floats) receives each epoch's mean batch loss on standardised targets. */
+int qflow_mlp_train(qflow_handle hnd, int32_t epochs, int32_t batch, float lr, const int64_t* order,
+                    float* loss);
+
+/* Device-level network steps (device pointers, stream-ordered, see the device-level section).
+ * Workspace: qflow_mlp_workspace(n_in, hidden, n_out, rows) bytes. */
+size_t qflow_mlp_workspace(int32_t n_in, int32_t hidden, int32_t n_out, int64_t rows);
+/* y[rows][n_out] = network(x[rows][n_in]). */
+int qflow_mlp_forward_device(int32_t n_in, int32_t hidden, int32_t n_out, const float* params, const float* x,
+                             int64_t rows, float* y, void* work, void* stream);
+/* loss[1] and grad[param_count] of the loss above; mask[rows] nullable (all rows count). */
+int qflow_mlp_grad_device(int32_t n_in, int32_t hidden, int32_t n_out, const float* params, const float* x,
+                          const float* target, const uint8_t* mask, int64_t rows, float* grad, float* loss,
+                          void* work, void* stream);
+/* One Adam step on n parameters; step counts from 1. */
+int qflow_mlp_adam_device(int64_t n, float* params, const float* grad, float* m, float* v, int32_t step, float lr,
+                          float beta1, float beta2, float eps, void* stream);
+/* features[nspaces][708] of (3,3) spaces (device list) from dressed F, W (no standardisation). */
+int qflow_mlp_features_device(int32_t n, const double* F, const double* W, const qflow_space* spaces,
+                              int64_t nspaces, float* features, void* stream);
+/* targets[rows][54] from CI vectors roots[rows][400] (Phi coefficient 1, float). */
+int qflow_mlp_targets_device(const float* roots, int64_t rows, float* targets, void* stream);
+/* Start vectors guess[rows][400] (float) from increments y[rows][54]. */
+int qflow_mlp_guess_device(const float* y, int64_t rows, float* guess, void* stream);
 
 #ifdef __cplusplus
 }

@@ -151,6 +151,7 @@ struct qflow_ctx {
   // launch schedule of the mixed-precision solver: persistent queue or one launch per class
   int sched_persistent = 1, sched_chunk = 4, sched_ctas = 0;
   bool tuned = false;
+  int64_t sweeps = 0;  // sweeps run so far
   float tune_ms[8] = {0};
   int tune_count = 0;
   cudaGraph_t graph = nullptr;
@@ -158,6 +159,20 @@ struct qflow_ctx {
   int64_t graph_launches = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase marks of the last sweep
   int64_t last_launches = 0;                                  // kernels launched by the last sweep
+  // warm-start network (opt.guess == 2): model = parameters + standardisation (device)
+  int mlp_hidden = 0;
+  int64_t mlp_nparam = 0;
+  float* mlp_model = nullptr;
+  float *mlp_grad = nullptr, *mlp_m = nullptr, *mlp_v = nullptr;  // Adam state
+  int mlp_step = 0;
+  bool mlp_has_stats = false;
+  bool mlp_pending = false;    // the next sweep starts 6e6o spaces from the network
+  bool mlp_guess_now = false;  // set while such a sweep is enqueued
+  bool fw_of_last_sweep = false;  // F, W still hold the dressing of the last sweep
+  int64_t mlp_cap = 0, mlp_n = 0;  // training pairs: capacity, stored
+  int mlp_target = 0;              // kind of the stored pairs (QFLOW_MLP_TARGET_*)
+  float *mlp_X = nullptr, *mlp_T = nullptr;
+  uint8_t* mlp_mask = nullptr;
 };
 
 namespace {
@@ -178,6 +193,9 @@ void free_ctx(qflow_ctx* c) {
   if (c->diis) cudaFree(c->diis);
   if (c->W32) cudaFree(c->W32);
   if (c->queue) cudaFree(c->queue);
+  void* mptrs[] = {c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v, c->mlp_X, c->mlp_T, c->mlp_mask};
+  for (void* p : mptrs)
+    if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -241,7 +259,8 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     return QFLOW_ERR_ARG;
   }
   if (c->opt.max_iter <= 0) c->opt.max_iter = 60;
-  if (c->opt.diis < 0 || c->opt.diis > QFLOW_DIIS_MAX || c->opt.diis == 1) {
+  if (c->opt.diis < 0 || c->opt.diis > QFLOW_DIIS_MAX || c->opt.diis == 1 || c->opt.guess < 0 ||
+      c->opt.guess > QFLOW_GUESS_NETWORK) {
     delete c;
     return QFLOW_ERR_ARG;
   }
@@ -331,10 +350,10 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     e = cudaMalloc(&c->diis, qf::diis_workspace_bytes(c->opt.diis, (int64_t)npool));
     if (e == cudaSuccess) e = qf::diis_reset(c->diis, c->opt.diis, (int64_t)npool, c->stream);
   }
-  if (c->opt.guess == 1) {
+  if (c->opt.guess == 1 || c->opt.guess == QFLOW_GUESS_NETWORK) {  // roots of every class (1) or 6e6o (2)
     const size_t ndet[4] = {0, 4, 36, 400};
     const size_t esz = (c->opt.precision == QFLOW_PREC_MIXED) ? sizeof(float) : sizeof(double);
-    for (int k = 1; k <= 3 && e == cudaSuccess; ++k) {
+    for (int k = (c->opt.guess == 1 ? 1 : 3); k <= 3 && e == cudaSuccess; ++k) {
       if (c->cls_count[k] == 0) continue;
       const size_t bytes = (size_t)c->cls_count[k] * ndet[k] * esz;
       e = cudaMalloc(&c->guess[k], bytes);
@@ -389,8 +408,10 @@ qf::SolveArgs solve_args(qflow_ctx* c, int k) {
   a.status = c->status;
   a.iters = c->iters;
   a.W32 = c->W32;
-  a.guess = c->guess[k];
-  a.save_root = c->guess[k] ? 1 : 0;
+  // guess mode 1: start from and keep the previous roots; mode 2: keep 6e6o roots, start from
+  // them only on a warm-start sweep (where the network has just written them)
+  a.guess = (c->opt.guess == 1 || c->mlp_guess_now) ? c->guess[k] : nullptr;
+  a.root_out = c->guess[k];
   a.max_iter = c->opt.max_iter;
   a.tol = c->opt.tol;
   return a;
@@ -430,7 +451,7 @@ cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int
     if (count > 0) {  // calibration: a prefix of each class, no saved roots
       if (cls[k].nspaces > count) cls[k].nspaces = count;
       cls[k].guess = nullptr;
-      cls[k].save_root = 0;
+      cls[k].root_out = nullptr;
     }
   }
   if (c->opt.precision != QFLOW_PREC_MIXED) {
@@ -450,7 +471,7 @@ cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int
   for (int k = 3; k >= 1 && e == cudaSuccess; --k) {
     if (cls[k].nspaces == 0) continue;
     e = qf::launch_solve_warp(k, cls[k], c->W32, static_cast<const float*>(cls[k].guess),
-                              cls[k].save_root ? static_cast<float*>(cls[k].guess) : nullptr, ctas, c->stream);
+                              static_cast<float*>(cls[k].root_out), ctas, c->stream);
     ++*launches;
   }
   return e;
@@ -495,6 +516,55 @@ struct TuneKey {
 std::map<TuneKey, std::array<int, 3>> g_tune_cache;
 std::mutex g_tune_mu;
 
+// Model layout: parameters, then mu_x[708], s_x[708], mu_y[54], sd_y[54].
+float* mlp_stats(qflow_ctx* c, int which) {
+  float* p = c->mlp_model + c->mlp_nparam;
+  const int64_t off[4] = {0, QFLOW_MLP_NIN, 2 * QFLOW_MLP_NIN, 2 * QFLOW_MLP_NIN + QFLOW_MLP_NOUT};
+  return p + off[which];
+}
+
+// Dressing of the zero pool (bare Fock matrix and integrals) into F, W; pool_new is scratch.
+cudaError_t dress_bare(qflow_ctx* c) {
+  cudaError_t e = cudaMemsetAsync(c->pool_new, 0, sizeof(double) * (size_t)(c->n_t1 + c->n_t2), c->stream);
+  if (e == cudaSuccess)
+    e = qf::launch_dress(c->h, c->eri, c->pool_new, c->pool_new + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
+                         c->dwork_bytes, c->stream, c->W32);
+  c->fw_of_last_sweep = false;
+  return e;
+}
+
+// Warm start: the network's start vectors for every 6e6o space, written where the solver reads
+// its guesses (the 6e6o root buffer), in chunks of rows.
+cudaError_t enqueue_mlp_guess(qflow_ctx* c, int64_t* launches) {
+  const int64_t n3 = c->cls_count[3];
+  const int64_t CH = 131072;
+  const int64_t rows = n3 < CH ? n3 : CH;
+  const int H = c->mlp_hidden;
+  const size_t fx = (size_t)rows * QFLOW_MLP_NIN * sizeof(float), fy = (size_t)rows * QFLOW_MLP_NOUT * sizeof(float);
+  const size_t bytes = fx + fy + qf::mlp_workspace_bytes(QFLOW_MLP_NIN, H, QFLOW_MLP_NOUT, rows) + 512;
+  void* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, bytes, c->stream);
+  if (e != cudaSuccess) return e;
+  float* X = static_cast<float*>(buf);
+  float* Y = reinterpret_cast<float*>(static_cast<char*>(buf) + ((fx + 255) / 256) * 256);
+  void* work = static_cast<char*>(buf) + ((fx + 255) / 256) * 256 + ((fy + 255) / 256) * 256;
+  const bool fp64 = c->opt.precision != QFLOW_PREC_MIXED;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  for (int64_t off = 0; off < n3 && e == cudaSuccess; off += CH) {
+    const int64_t r = (n3 - off < CH) ? n3 - off : CH;
+    e = qf::mlp_features(c->n, c->F, c->W, c->spaces + c->cls_off[3] + off, r, 1, mlp_stats(c, 0), mlp_stats(c, 1), X,
+                         c->stream);
+    if (e == cudaSuccess)
+      e = qf::mlp_forward(QFLOW_MLP_NIN, H, QFLOW_MLP_NOUT, c->mlp_model, X, r, Y, work, c->stream);
+    if (e == cudaSuccess)
+      e = qf::mlp_guess(Y, r, mlp_stats(c, 2), mlp_stats(c, 3), static_cast<char*>(c->guess[3]) + (size_t)off * 400 * esz,
+                        fp64, c->stream);
+    *launches += 5;
+  }
+  cudaError_t e2 = cudaFreeAsync(buf, c->stream);
+  return e != cudaSuccess ? e : e2;
+}
+
 cudaError_t autotune(qflow_ctx* c) {
   const TuneKey key{c->n, c->nocc, c->cls_count[1], c->cls_count[2], c->cls_count[3]};
   {
@@ -510,7 +580,9 @@ cudaError_t autotune(qflow_ctx* c) {
   }
   // candidates: (persistent, chunk, CTAs per SM)
   const int cand[6][3] = {{0, 1, 0}, {1, 1, 0}, {1, 4, 0}, {1, 16, 0}, {0, 1, 1}, {1, 4, 1}};
-  const int64_t count = 16384;
+  // calibration prefix of every class: large enough that the warps' drift through the list
+  // (which decides L2 reuse of the W blocks) shows, small next to a full solve
+  const int64_t count = 262144;
   cudaEvent_t t0, t1;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -553,7 +625,9 @@ int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
   if (!c) return QFLOW_ERR_ARG;
   int64_t launches = 0;
   cudaError_t e = cudaSuccess;
-  if (c->opt.graph && !c->graph_exec && c->tuned) {
+  // a warm-start sweep (network guesses for the 6e6o spaces) runs outside the captured graph
+  const bool warm = c->opt.guess == QFLOW_GUESS_NETWORK && c->mlp_pending && c->cls_count[3] > 0;
+  if (c->opt.graph && !c->graph_exec && c->tuned && !warm) {
     // From the second sweep on: capture the sweep's device work once, then replay it.
     int64_t l2 = 0;
     e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
@@ -575,17 +649,28 @@ int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
       e = cudaSuccess;
     }
   }
-  if (c->graph_exec) {  // replay of the captured sweep
+  if (c->graph_exec && !warm) {  // replay of the captured sweep
     e = cudaGraphLaunch(c->graph_exec, c->stream);
     launches = c->graph_launches;
   } else {
     e = enqueue_dress(c, &launches);
-    if (e == cudaSuccess && !c->tuned && c->opt.precision == QFLOW_PREC_MIXED) e = autotune(c);
+    if (e == cudaSuccess && warm) {
+      e = enqueue_mlp_guess(c, &launches);
+      c->mlp_guess_now = true;
+    }
+    // The mixed-precision schedule is calibrated at the second sweep, whose work mix (most
+    // spaces near their root) is that of the rest of a flow; the first sweep runs the default.
+    const bool mixed = c->opt.precision == QFLOW_PREC_MIXED;
+    if (e == cudaSuccess && !c->tuned && mixed && c->sweeps >= 1) e = autotune(c);
     if (e == cudaSuccess) e = enqueue_solve_merge(c, &launches);
-    c->tuned = true;  // FP64 needs no tuning; mixed has just been tuned
+    c->mlp_guess_now = false;
+    if (!mixed) c->tuned = true;  // FP64 runs per-class launches and needs no tuning
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_status(e);
+  if (warm) c->mlp_pending = false;
+  c->fw_of_last_sweep = true;
+  ++c->sweeps;
   c->last_launches = launches;
   const double em = c->red_host[0];
   const double de = c->have_energy ? em - c->e_mean : std::numeric_limits<double>::infinity();
@@ -661,6 +746,7 @@ int qflow_dressed(qflow_handle c, double* e0, double* F, double* W) {
   const size_t n1 = c->n, n4 = n1 * n1 * n1 * n1;
   cudaError_t e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W,
                                    c->dwork, c->dwork_bytes, c->stream, c->W32);
+  c->fw_of_last_sweep = false;
   if (e0 && e == cudaSuccess) e = cudaMemcpyAsync(e0, c->e0, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (F && e == cudaSuccess) e = cudaMemcpyAsync(F, c->F, sizeof(double) * n1 * n1, cudaMemcpyDeviceToHost, c->stream);
   if (W && e == cudaSuccess) e = cudaMemcpyAsync(W, c->W, sizeof(double) * n4, cudaMemcpyDeviceToHost, c->stream);
@@ -767,10 +853,280 @@ int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* 
   a.status = status;
   a.iters = iters;
   a.guess = guess;
-  a.save_root = save_root;
+  a.root_out = save_root ? guess : nullptr;
   a.max_iter = max_iter;
   a.tol = tol;
   return cuda_status(qf::launch_solve(size_class, precision, a, (cudaStream_t)stream));
+}
+
+}  // extern "C"
+
+// ---- warm-start network ---------------------------------------------------------------------
+
+namespace {
+
+bool mlp_sizes_ok(int32_t I, int32_t H, int32_t O) {
+  return I >= 1 && I <= 65536 && H >= 1 && H <= 4096 && O >= 1 && O <= 65536;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t qflow_mlp_param_count(int32_t n_in, int32_t hidden, int32_t n_out) {
+  if (!mlp_sizes_ok(n_in, hidden, n_out)) return 0;
+  return qf::mlp_param_count(n_in, hidden, n_out);
+}
+
+int64_t qflow_mlp_model_size(int32_t hidden) {
+  if (hidden < 1 || hidden > 1024) return 0;
+  return qf::mlp_param_count(QFLOW_MLP_NIN, hidden, QFLOW_MLP_NOUT) + 2 * QFLOW_MLP_NIN + 2 * QFLOW_MLP_NOUT;
+}
+
+int qflow_mlp_set_model(qflow_handle c, int32_t hidden, const float* model, int32_t has_stats) {
+  if (!c || !model || hidden < 1 || hidden > 1024) return QFLOW_ERR_ARG;
+  const int64_t np = qf::mlp_param_count(QFLOW_MLP_NIN, hidden, QFLOW_MLP_NOUT);
+  const int64_t total = qflow_mlp_model_size(hidden);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  float* ptrs[4] = {c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v};
+  for (float* p : ptrs)
+    if (p) cudaFree(p);
+  c->mlp_model = c->mlp_grad = c->mlp_m = c->mlp_v = nullptr;
+  c->mlp_hidden = 0;
+  e = dalloc(&c->mlp_model, (size_t)total);
+  if (e == cudaSuccess) e = dalloc(&c->mlp_grad, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&c->mlp_m, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&c->mlp_v, (size_t)np);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->mlp_model, model, sizeof(float) * total, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->mlp_m, 0, sizeof(float) * np, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->mlp_v, 0, sizeof(float) * np, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  c->mlp_hidden = hidden;
+  c->mlp_nparam = np;
+  c->mlp_step = 0;
+  c->mlp_has_stats = has_stats != 0;
+  c->mlp_pending = c->mlp_has_stats;
+  return QFLOW_OK;
+}
+
+int qflow_mlp_get_model(qflow_handle c, float* model) {
+  if (!c || !model) return QFLOW_ERR_ARG;
+  if (!c->mlp_model) return QFLOW_ERR_STATE;
+  const int64_t total = qflow_mlp_model_size(c->mlp_hidden);
+  cudaError_t e = cudaMemcpyAsync(model, c->mlp_model, sizeof(float) * total, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+int qflow_mlp_collect(qflow_handle c, int32_t target, int64_t stride, int64_t max_pairs, int64_t* n_pairs) {
+  if (!c || stride < 1 || max_pairs < 1) return QFLOW_ERR_ARG;
+  if (target != QFLOW_MLP_TARGET_INCREMENT && target != QFLOW_MLP_TARGET_POOL) return QFLOW_ERR_ARG;
+  if (target == QFLOW_MLP_TARGET_INCREMENT &&
+      (c->opt.guess != QFLOW_GUESS_NETWORK || !c->have_energy || !c->fw_of_last_sweep || !c->guess[3]))
+    return QFLOW_ERR_STATE;
+  if (c->mlp_cap > 0 && c->mlp_target != target) return QFLOW_ERR_STATE;  // one kind of pair per set
+  cudaError_t e = cudaSuccess;
+  if (c->mlp_cap == 0) {
+    e = dalloc(&c->mlp_X, (size_t)max_pairs * QFLOW_MLP_NIN);
+    if (e == cudaSuccess) e = dalloc(&c->mlp_T, (size_t)max_pairs * QFLOW_MLP_NOUT);
+    if (e == cudaSuccess) e = dalloc(&c->mlp_mask, (size_t)max_pairs);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->mlp_cap = max_pairs;
+    c->mlp_target = target;
+  }
+  const int64_t n3 = c->cls_count[3];
+  int64_t rows = (n3 + stride - 1) / stride;
+  if (rows > c->mlp_cap - c->mlp_n) rows = c->mlp_cap - c->mlp_n;
+  if (rows > 0) {
+    const bool fp64 = c->opt.precision != QFLOW_PREC_MIXED;
+    float* X = c->mlp_X + (size_t)c->mlp_n * QFLOW_MLP_NIN;
+    float* T = c->mlp_T + (size_t)c->mlp_n * QFLOW_MLP_NOUT;
+    if (target == QFLOW_MLP_TARGET_POOL) {  // bare features, the pool's internal amplitudes
+      e = dress_bare(c);
+      if (e == cudaSuccess)
+        e = qf::mlp_features(c->n, c->F, c->W, c->spaces + c->cls_off[3], rows, stride, nullptr, nullptr, X, c->stream);
+      if (e == cudaSuccess)
+        e = qf::mlp_pool_targets(c->pool, c->spaces + c->cls_off[3], rows, stride, c->nocc, c->nvir, T,
+                                 c->mlp_mask + c->mlp_n, c->stream);
+    } else {  // the last sweep's features, its roots' increments
+      e = qf::mlp_features(c->n, c->F, c->W, c->spaces + c->cls_off[3], rows, stride, nullptr, nullptr, X, c->stream);
+      if (e == cudaSuccess)
+        e = qf::mlp_targets(c->guess[3], fp64, rows, stride, c->sorted_index + c->cls_off[3], c->status, T,
+                            c->mlp_mask + c->mlp_n, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->mlp_n += rows;
+  }
+  if (n_pairs) *n_pairs = c->mlp_n;
+  return QFLOW_OK;
+}
+
+int qflow_mlp_train(qflow_handle c, int32_t epochs, int32_t batch, float lr, const int64_t* order, float* loss) {
+  if (!c || epochs < 0 || batch < 1 || !(lr > 0.f)) return QFLOW_ERR_ARG;
+  if (!c->mlp_model || c->mlp_n == 0) return QFLOW_ERR_STATE;
+  const int64_t n = c->mlp_n;
+  if (order)
+    for (int64_t i = 0; i < n; ++i)
+      if (order[i] < 0 || order[i] >= n) return QFLOW_ERR_ARG;
+  std::vector<uint8_t> mask((size_t)n);
+  cudaError_t e = cudaMemcpyAsync(mask.data(), c->mlp_mask, (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int64_t count = 0;
+  for (uint8_t m : mask) count += m ? 1 : 0;
+  if (count == 0) return QFLOW_ERR_STATE;
+  const int I = QFLOW_MLP_NIN, O = QFLOW_MLP_NOUT, H = c->mlp_hidden;
+  const int64_t B = batch < n ? batch : n;
+  const int64_t nb = (n + B - 1) / B;
+  // scratch: batch rows, masks, order, per-batch losses, inverse target scales, workspaces
+  const size_t sz[7] = {(size_t)B * I * sizeof(float), (size_t)B * O * sizeof(float), (size_t)B,
+                        (size_t)n * sizeof(int64_t), (size_t)(epochs > 0 ? epochs : 1) * nb * sizeof(float),
+                        (size_t)O * sizeof(float),
+                        std::max(qf::mlp_workspace_bytes(I, H, O, B), qf::mlp_stats_workspace_bytes(n, I))};
+  size_t off[8] = {0};
+  for (int i = 0; i < 7; ++i) off[i + 1] = off[i] + ((sz[i] + 255) / 256) * 256;
+  char* buf = nullptr;
+  e = cudaMalloc(reinterpret_cast<void**>(&buf), off[7]);
+  if (e != cudaSuccess) return cuda_status(e);
+  float* Xb = reinterpret_cast<float*>(buf + off[0]);
+  float* Tb = reinterpret_cast<float*>(buf + off[1]);
+  uint8_t* Mb = reinterpret_cast<uint8_t*>(buf + off[2]);
+  int64_t* ord = reinterpret_cast<int64_t*>(buf + off[3]);
+  float* lossd = reinterpret_cast<float*>(buf + off[4]);
+  float* inv_sd = reinterpret_cast<float*>(buf + off[5]);
+  void* work = buf + off[6];
+  std::vector<int64_t> ident;
+  if (!order) {
+    ident.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) ident[(size_t)i] = i;
+  }
+  e = cudaMemcpyAsync(ord, order ? order : ident.data(), sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice,
+                      c->stream);
+  if (e == cudaSuccess && !c->mlp_has_stats) {
+    e = qf::mlp_col_stats(c->mlp_X, n, I, c->mlp_mask, count, 1, mlp_stats(c, 0), mlp_stats(c, 1), work, c->stream);
+    if (e == cudaSuccess)
+      e = qf::mlp_col_stats(c->mlp_T, n, O, c->mlp_mask, count, 0, mlp_stats(c, 2), mlp_stats(c, 3), work, c->stream);
+  }
+  if (e == cudaSuccess) e = qf::mlp_invert(mlp_stats(c, 3), O, inv_sd, c->stream);
+  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    for (int64_t b = 0; b < nb && e == cudaSuccess; ++b) {
+      const int64_t r = (n - b * B < B) ? n - b * B : B;
+      e = qf::mlp_rows(c->mlp_X, r, I, ord + b * B, mlp_stats(c, 0), mlp_stats(c, 1), Xb, c->mlp_mask, Mb, c->stream);
+      if (e == cudaSuccess)
+        e = qf::mlp_rows(c->mlp_T, r, O, ord + b * B, mlp_stats(c, 2), inv_sd, Tb, nullptr, nullptr, c->stream);
+      if (e == cudaSuccess)
+        e = qf::mlp_loss_grad(I, H, O, c->mlp_model, Xb, Tb, Mb, r, c->mlp_grad, lossd + (size_t)ep * nb + b, work,
+                              c->stream);
+      if (e == cudaSuccess)
+        e = qf::mlp_adam(c->mlp_nparam, c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v, ++c->mlp_step, lr, 0.9f,
+                         0.999f, 1e-8f, c->stream);
+    }
+  }
+  std::vector<float> lh((size_t)(epochs > 0 ? epochs : 0) * nb);
+  if (e == cudaSuccess && !lh.empty())
+    e = cudaMemcpyAsync(lh.data(), lossd, sizeof(float) * lh.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_status(e);
+  c->mlp_has_stats = true;
+  c->mlp_pending = c->mlp_target == QFLOW_MLP_TARGET_INCREMENT;  // a guess model: next sweep uses it
+  if (loss)
+    for (int ep = 0; ep < epochs; ++ep) {
+      double s = 0.0;
+      for (int64_t b = 0; b < nb; ++b) s += lh[(size_t)ep * nb + b];
+      loss[ep] = (float)(s / (double)nb);
+    }
+  return QFLOW_OK;
+}
+
+int qflow_mlp_warm_pool(qflow_handle c) {
+  if (!c) return QFLOW_ERR_ARG;
+  if (!c->mlp_model || !c->mlp_has_stats) return QFLOW_ERR_STATE;
+  const int64_t n3 = c->cls_count[3];
+  const int64_t CH = 131072;
+  const int64_t rows = n3 < CH ? n3 : CH;
+  const int H = c->mlp_hidden;
+  cudaError_t e = dress_bare(c);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->pool, 0, sizeof(double) * (size_t)(c->n_t1 + c->n_t2), c->stream);
+  char* buf = nullptr;
+  const size_t fx = ((size_t)rows * QFLOW_MLP_NIN * sizeof(float) + 255) / 256 * 256;
+  const size_t fy = ((size_t)rows * QFLOW_MLP_NOUT * sizeof(float) + 255) / 256 * 256;
+  if (e == cudaSuccess && rows > 0)
+    e = cudaMalloc(reinterpret_cast<void**>(&buf), fx + fy + qf::mlp_workspace_bytes(QFLOW_MLP_NIN, H, QFLOW_MLP_NOUT, rows));
+  for (int64_t off = 0; off < n3 && e == cudaSuccess; off += CH) {
+    const int64_t r = (n3 - off < CH) ? n3 - off : CH;
+    float* X = reinterpret_cast<float*>(buf);
+    float* Y = reinterpret_cast<float*>(buf + fx);
+    e = qf::mlp_features(c->n, c->F, c->W, c->spaces + c->cls_off[3] + off, r, 1, mlp_stats(c, 0), mlp_stats(c, 1), X,
+                         c->stream);
+    if (e == cudaSuccess)
+      e = qf::mlp_forward(QFLOW_MLP_NIN, H, QFLOW_MLP_NOUT, c->mlp_model, X, r, Y, buf + fx + fy, c->stream);
+    if (e == cudaSuccess)
+      e = qf::mlp_pool_from_pred(Y, mlp_stats(c, 2), mlp_stats(c, 3), c->spaces + c->cls_off[3] + off,
+                                 c->sorted_index + c->cls_off[3] + off, r, c->nocc, c->nvir, c->own1, c->own2, c->pool,
+                                 c->stream);
+  }
+  if (e == cudaSuccess && c->diis) e = qf::diis_reset(c->diis, c->opt.diis, c->n_t1 + c->n_t2, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (buf) cudaFree(buf);
+  return cuda_status(e);
+}
+
+size_t qflow_mlp_workspace(int32_t n_in, int32_t hidden, int32_t n_out, int64_t rows) {
+  if (!mlp_sizes_ok(n_in, hidden, n_out) || rows < 0) return 0;
+  return qf::mlp_workspace_bytes(n_in, hidden, n_out, rows);
+}
+
+int qflow_mlp_forward_device(int32_t n_in, int32_t hidden, int32_t n_out, const float* params, const float* x,
+                             int64_t rows, float* y, void* work, void* stream) {
+  if (!mlp_sizes_ok(n_in, hidden, n_out) || rows < 0 || rows > (1 << 30)) return QFLOW_ERR_ARG;
+  if (rows == 0) return QFLOW_OK;
+  if (!params || !x || !y || !work) return QFLOW_ERR_ARG;
+  return cuda_status(qf::mlp_forward(n_in, hidden, n_out, params, x, rows, y, work, (cudaStream_t)stream));
+}
+
+int qflow_mlp_grad_device(int32_t n_in, int32_t hidden, int32_t n_out, const float* params, const float* x,
+                          const float* target, const uint8_t* mask, int64_t rows, float* grad, float* loss,
+                          void* work, void* stream) {
+  if (!mlp_sizes_ok(n_in, hidden, n_out) || rows < 1 || rows > (1 << 30)) return QFLOW_ERR_ARG;
+  if (!params || !x || !target || !grad || !loss || !work) return QFLOW_ERR_ARG;
+  return cuda_status(qf::mlp_loss_grad(n_in, hidden, n_out, params, x, target, mask, rows, grad, loss, work,
+                                       (cudaStream_t)stream));
+}
+
+int qflow_mlp_adam_device(int64_t n, float* params, const float* grad, float* m, float* v, int32_t step, float lr,
+                          float beta1, float beta2, float eps, void* stream) {
+  if (n < 0 || step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f)) return QFLOW_ERR_ARG;
+  if (n == 0) return QFLOW_OK;
+  if (!params || !grad || !m || !v) return QFLOW_ERR_ARG;
+  return cuda_status(qf::mlp_adam(n, params, grad, m, v, step, lr, beta1, beta2, eps, (cudaStream_t)stream));
+}
+
+int qflow_mlp_features_device(int32_t n, const double* F, const double* W, const qflow_space* spaces,
+                              int64_t nspaces, float* features, void* stream) {
+  if (n < 6 || n > 128 || nspaces < 0) return QFLOW_ERR_ARG;
+  if (nspaces == 0) return QFLOW_OK;
+  if (!F || !W || !spaces || !features) return QFLOW_ERR_ARG;
+  return cuda_status(
+      qf::mlp_features(n, F, W, spaces, nspaces, 1, nullptr, nullptr, features, (cudaStream_t)stream));
+}
+
+int qflow_mlp_targets_device(const float* roots, int64_t rows, float* targets, void* stream) {
+  if (rows < 0) return QFLOW_ERR_ARG;
+  if (rows == 0) return QFLOW_OK;
+  if (!roots || !targets) return QFLOW_ERR_ARG;
+  return cuda_status(qf::mlp_targets(roots, false, rows, 1, nullptr, nullptr, targets, nullptr, (cudaStream_t)stream));
+}
+
+int qflow_mlp_guess_device(const float* y, int64_t rows, float* guess, void* stream) {
+  if (rows < 0) return QFLOW_ERR_ARG;
+  if (rows == 0) return QFLOW_OK;
+  if (!y || !guess) return QFLOW_ERR_ARG;
+  return cuda_status(qf::mlp_guess(y, rows, nullptr, nullptr, guess, false, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -33,8 +33,8 @@ struct SolveArgs {
   int32_t* status;
   int32_t* iters;
   const float* W32;  // nullable FP32 copy of W (mixed path)
-  void* guess;  // start vectors / saved roots: double (FP64 path) or float (mixed path)
-  int32_t save_root;
+  const void* guess;  // nullable start vectors: double (FP64 path) or float (mixed path)
+  void* root_out;     // nullable: receives converged roots (Phi coefficient 1), same type/layout
   int32_t max_iter;
   double tol;
 };
@@ -71,5 +71,44 @@ cudaError_t launch_reduce(const double* energy, const int32_t* status, int64_t n
 size_t diis_workspace_bytes(int m, int64_t N);
 cudaError_t launch_diis(void* work, int m, const double* t_old, double* t_new, int64_t N, cudaStream_t st);
 cudaError_t diis_reset(void* work, int m, int64_t N, cudaStream_t st);
+
+// Warm-start network (mlp.cu).  Parameters packed W1, b1, W2, b2, W3, b3 (W [fan_in][fan_out]).
+int64_t mlp_param_count(int I, int H, int O);
+size_t mlp_workspace_bytes(int I, int H, int O, int64_t rows);
+cudaError_t mlp_forward(int I, int H, int O, const float* params, const float* x, int64_t rows, float* y, void* work,
+                        cudaStream_t st);
+cudaError_t mlp_loss_grad(int I, int H, int O, const float* params, const float* x, const float* t,
+                          const uint8_t* mask, int64_t rows, float* grad, float* loss, void* work, cudaStream_t st);
+cudaError_t mlp_adam(int64_t n, float* p, const float* g, float* m, float* v, int step, float lr, float b1, float b2,
+                     float eps, cudaStream_t st);
+// features[s][708] of (3,3) spaces spaces[s * stride]; standardised as (x - mu) * sc when mu
+// is given
+cudaError_t mlp_features(int n, const double* F, const double* W, const qflow_space* spaces, int64_t nspaces,
+                         int64_t stride, const float* mu, const float* sc, float* out, cudaStream_t st);
+// targets[r][54] (+ mask[r]) from roots (double when fp64, else float) of class positions
+// r * stride; status/sorted_index/mask nullable (then every row counts)
+cudaError_t mlp_targets(const void* roots, bool fp64, int64_t rows, int64_t stride, const int64_t* sorted_index,
+                        const int32_t* status, float* targets, uint8_t* mask, cudaStream_t st);
+// targets[r][54] = the pool's internal amplitudes of spaces[r * stride] (mask set to 1)
+cudaError_t mlp_pool_targets(const double* pool, const qflow_space* spaces, int64_t rows, int64_t stride, int nocc,
+                             int nvir, float* targets, uint8_t* mask, cudaStream_t st);
+// pool <- mu + sd * pred for the amplitudes each space (class position r, sorted index
+// sorted_index[r]) owns
+cudaError_t mlp_pool_from_pred(const float* pred, const float* mu, const float* sd, const qflow_space* spaces,
+                               const int64_t* sorted_index, int64_t rows, int nocc, int nvir, const int32_t* owner1,
+                               const int32_t* owner2, double* pool, cudaStream_t st);
+// out[i] = 1 / sd[i] (0 where sd[i] <= 0)
+cudaError_t mlp_invert(const float* sd, int n, float* out, cudaStream_t st);
+// start vectors guess[r][400] (double when fp64, else float) from outputs pred[r][54];
+// increment = mu + sd * pred when mu is given
+cudaError_t mlp_guess(const float* pred, int64_t rows, const float* mu, const float* sd, void* guess, bool fp64,
+                      cudaStream_t st);
+size_t mlp_stats_workspace_bytes(int64_t rows, int cols);
+// column mean (mu) and 1/sd (inverse) or sd of X over rows with mask set (count of them)
+cudaError_t mlp_col_stats(const float* X, int64_t rows, int cols, const uint8_t* mask, int64_t count, int inverse,
+                          float* mu, float* scale, void* work, cudaStream_t st);
+// out[r] = (X[order[r]] - mu) * sc (order, mu nullable); copies masks when mask_out is given
+cudaError_t mlp_rows(const float* X, int64_t rows, int cols, const int64_t* order, const float* mu, const float* sc,
+                     float* out, const uint8_t* mask_in, uint8_t* mask_out, cudaStream_t st);
 
 }  // namespace qf

@@ -533,9 +533,9 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
     if (st == kSpaceOk && !(fabs(c0) >= 1e-3 * xn)) st = kSpaceRoot;
     if (!isfinite(c0) || !isfinite(sm.theta)) st = kSpaceNonFinite;
     const double inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.0 / c0 : 0.0;
-    if (a.guess && a.save_root && st == kSpaceOk)
+    if (a.root_out && st == kSpaceOk)
       for (int d = tid; d < C::NDET; d += C::NT)
-        static_cast<T*>(a.guess)[(size_t)s * C::NDET + d] = (T)((double)sm.S[d] * inv0);
+        static_cast<T*>(a.root_out)[(size_t)s * C::NDET + d] = (T)((double)sm.S[d] * inv0);
     if (tid < K * K) {
       const int i = tid / K, aa = tid % K;
       int sg;
@@ -610,8 +610,8 @@ cudaError_t launch_k(const SolveArgs& a, cudaStream_t st) {
 
 cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st) {
   if (precision == QFLOW_PREC_MIXED)
-    return launch_solve_warp(k, a, a.W32, static_cast<const float*>(a.guess),
-                             a.save_root ? static_cast<float*>(a.guess) : nullptr, 0, st);
+    return launch_solve_warp(k, a, a.W32, static_cast<const float*>(a.guess), static_cast<float*>(a.root_out), 0,
+                             st);
   switch (k) {
     case 1: return launch_k<1, double>(a, st);
     case 2: return launch_k<2, double>(a, st);

@@ -587,9 +587,9 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   // ---- Phi fast path: sigma(Phi) = column 0 of H (0 at Phi after the shift) ----------------
   // Only determinants connected to Phi by single or double replacements are nonzero.  If the
   // residual of Phi is below the tolerance, the root is Phi, the increment is zero and the
-  // space is done without building the full string operator or the diagonal.
-  const bool phi_start = (guess_in == nullptr);
-  if (phi_start) {
+  // space is done without building the full string operator or the diagonal.  This check runs
+  // with or without a caller's guess; a guess then enters as a second subspace vector.
+  {
     if (lane < NS) {  // dh[I] <- Hs[I][0]: same-spin coupling of string I to the Phi string
       const int I = lane;
       float hc = 0.f;
@@ -687,25 +687,49 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       if (p < K) j0 += ws.jb[p * NS + 0];
     }
     ws.diag[d] = (d == 0) ? 0.f : ws.dh[ia] + ws.dh[ib] + (jj - j0);
-    if (!phi_start) ws.V[d] = guess_in[(size_t)s * NDET + d];
   }
   __syncwarp();
-  if (!phi_start) {
+  // ---- caller's guess: subspace {Phi, g - g_Phi Phi}; its sigma counts as one iteration -------
+  int it0 = 0;
+  if (guess_in && KM >= 2) {
+    float* v1 = ws.V + NDET;
     float p = 0.f;
-    for (int d = lane; d < NDET; d += 32) p = fmaf(ws.V[d], ws.V[d], p);
-    const float nr = sqrtf(wsum(p));
-    const float inv = (nr > 0.f) ? 1.f / nr : 0.f;
-    for (int d = lane; d < NDET; d += 32) ws.V[d] = (nr > 0.f) ? ws.V[d] * inv : ((d == 0) ? 1.f : 0.f);
-    __syncwarp();
-    sigma<K>(tb, ws, ws.V, ws.S, lane);
-    float g = 0.f;
-    for (int d = lane; d < NDET; d += 32) g = fmaf(ws.V[d], ws.S[d], g);
-    g = wsum(g);
-    if (lane == 0) {
-      ws.G[0] = g;
-      ws.theta = g;
+    for (int d = lane; d < NDET; d += 32) {
+      const float gv = (d == 0) ? 0.f : guess_in[(size_t)s * NDET + d];
+      v1[d] = gv;
+      p = fmaf(gv, gv, p);
     }
-    __syncwarp();
+    const float nr = sqrtf(wsum(p));
+    if (nr > 1e-6f) {  // an all-Phi (or zero) guess adds nothing
+      const float inv = 1.f / nr;
+      for (int d = lane; d < NDET; d += 32) v1[d] *= inv;
+      __syncwarp();
+      float* s1 = ws.S + NDET;
+      sigma<K>(tb, ws, v1, s1, lane);
+      float g01 = 0.f, g10 = 0.f, g11 = 0.f;
+      for (int d = lane; d < NDET; d += 32) {
+        g10 = fmaf(v1[d], ws.S[d], g10);
+        g11 = fmaf(v1[d], s1[d], g11);
+      }
+      g10 = wsum(g10);
+      g11 = wsum(g11);
+      g01 = s1[0];  // Phi . sigma(v1)
+      if (lane == 0) {
+        ws.G[0] = 0.f;  // Phi . sigma(Phi) relative to <Phi|H|Phi>
+        ws.G[1] = g01;
+        ws.G[KM] = g10;
+        ws.G[KM + 1] = g11;
+        float yn[KM];
+        for (int j = 0; j < KM; ++j) yn[j] = (j == 0) ? 1.f : 0.f;
+        float thn = 0.f;
+        small_eig(ws.G, 2, -1e-2f, yn, &thn);
+        for (int j = 0; j < KM; ++j) ws.yf[j] = yn[j];
+        ws.theta = thn;
+        ws.ctrl[0] = 2;
+      }
+      it0 = 1;
+      __syncwarp();
+    }
   }
   // ---- Davidson ----------------------------------------------------------------------------
   constexpr int KMX = (NDET < KM) ? NDET : KM;  // the 2e2o space has only 4 determinants
@@ -766,7 +790,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     if (rnorm < tol) {
       if (lane == 0) {
         ws.ctrl[2] = kSpaceOk;
-        ws.ctrl[3] = it;
+        ws.ctrl[3] = it + it0;
       }
       __syncwarp();
       break;
@@ -800,7 +824,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     if (!(vn > 1e-6f)) {  // the subspace cannot grow (complete or stagnated)
       if (lane == 0) {
         ws.ctrl[2] = (rnorm < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
-        ws.ctrl[3] = it;
+        ws.ctrl[3] = it + it0;
       }
       __syncwarp();
       break;
@@ -845,7 +869,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       for (int j = 0; j < kk; ++j) ws.yf[j] = yn[j];
       ws.theta = thn;
       ws.ctrl[0] = kk;
-      ws.ctrl[3] = it + 1;
+      ws.ctrl[3] = it + 1 + it0;
     }
     __syncwarp();
   }
@@ -954,15 +978,15 @@ __global__ void __launch_bounds__(32 * WARPS) solve_persistent_kernel(Persistent
       if (it < n3) {
         const SolveArgs& a = p.cls[3];
         solve_one<3>(cs.t3, cs.pair3, state<3>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
-                     a.save_root ? static_cast<float*>(a.guess) : nullptr, it, lane);
+                     static_cast<float*>(a.root_out), it, lane);
       } else if (it < n3 + n2) {
         const SolveArgs& a = p.cls[2];
         solve_one<2>(cs.t2, cs.pair3, state<2>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
-                     a.save_root ? static_cast<float*>(a.guess) : nullptr, it - n3, lane);
+                     static_cast<float*>(a.root_out), it - n3, lane);
       } else {
         const SolveArgs& a = p.cls[1];
         solve_one<1>(cs.t1, cs.pair3, state<1>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
-                     a.save_root ? static_cast<float*>(a.guess) : nullptr, it - n3 - n2, lane);
+                     static_cast<float*>(a.root_out), it - n3 - n2, lane);
       }
     }
   }

@@ -70,6 +70,20 @@ def lib() -> C.CDLL:
         "qflow_dress_device": (I32, [P, P, P, P, I32, I32, P, P, P, P, C.c_size_t, P]),
         "qflow_solve_device": (I32, [I32, I32, P, P, P, I32, P, I64, I64, P, P, P, P, P, P, P, P, P, P, I32, I32,
                                      I32, D, P]),
+        "qflow_mlp_param_count": (I64, [I32, I32, I32]),
+        "qflow_mlp_model_size": (I64, [I32]),
+        "qflow_mlp_set_model": (I32, [P, I32, P, I32]),
+        "qflow_mlp_get_model": (I32, [P, P]),
+        "qflow_mlp_collect": (I32, [P, I32, I64, I64, P]),
+        "qflow_mlp_warm_pool": (I32, [P]),
+        "qflow_mlp_train": (I32, [P, I32, I32, C.c_float, P, P]),
+        "qflow_mlp_workspace": (C.c_size_t, [I32, I32, I32, I64]),
+        "qflow_mlp_forward_device": (I32, [I32, I32, I32, P, P, I64, P, P, P]),
+        "qflow_mlp_grad_device": (I32, [I32, I32, I32, P, P, P, P, I64, P, P, P, P]),
+        "qflow_mlp_adam_device": (I32, [I64, P, P, P, P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P]),
+        "qflow_mlp_features_device": (I32, [I32, P, P, P, I64, P, P]),
+        "qflow_mlp_targets_device": (I32, [P, I64, P, P]),
+        "qflow_mlp_guess_device": (I32, [P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -139,7 +153,7 @@ class Flow:
             opt.max_iter = max_iter
         if tol is not None:
             opt.tol = tol
-        opt.guess = {"phi": 0, "previous": 1}[guess]
+        opt.guess = {"phi": 0, "previous": 1, "network": 2}[guess]
         opt.diis = diis
         opt.schedule = {"auto": 0, "per_class": 1, "persistent": 2}[schedule]
         opt.graph = int(graph)
@@ -216,6 +230,37 @@ class Flow:
     def stream(self) -> int:
         return lib().qflow_stream(self._h) or 0
 
+    # ---- warm-start network (guess="network") ----
+    def mlp_set_model(self, model, hidden: int, has_stats: bool):
+        model = np.ascontiguousarray(model, dtype=np.float32)
+        if model.size != mlp_model_size(hidden):
+            raise ValueError("model size does not match the hidden width")
+        _check(lib().qflow_mlp_set_model(self._h, hidden, _ptr(model), int(has_stats)), "qflow_mlp_set_model")
+        self._mlp_hidden = hidden
+
+    def mlp_get_model(self) -> np.ndarray:
+        out = np.empty(mlp_model_size(self._mlp_hidden), dtype=np.float32)
+        _check(lib().qflow_mlp_get_model(self._h, _ptr(out)), "qflow_mlp_get_model")
+        return out
+
+    def mlp_collect(self, stride: int = 1, max_pairs: int = 1 << 20, target: str = "increment") -> int:
+        """Store training pairs; target "increment" (Davidson guesses) or "pool" (flow warm start)."""
+        n = C.c_int64()
+        _check(lib().qflow_mlp_collect(self._h, {"increment": 0, "pool": 1}[target], stride, max_pairs,
+                                       C.byref(n)), "qflow_mlp_collect")
+        return n.value
+
+    def mlp_warm_pool(self):
+        """Set the pool to the model's prediction of every space's converged internal amplitudes."""
+        _check(lib().qflow_mlp_warm_pool(self._h), "qflow_mlp_warm_pool")
+
+    def mlp_train(self, epochs: int, batch: int, lr: float, order=None) -> np.ndarray:
+        loss = np.empty(max(epochs, 0), dtype=np.float32)
+        o = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+        _check(lib().qflow_mlp_train(self._h, epochs, batch, lr, None if o is None else _ptr(o),
+                                     _ptr(loss) if epochs > 0 else None), "qflow_mlp_train")
+        return loss
+
 
 # ---- device-level steps on torch CUDA tensors ------------------------------------------------
 
@@ -262,3 +307,52 @@ def solve_device(n: int, nocc: int, e0, F, W, size_class: int, spaces, energy, s
                                     opt(t2_old), opt(t1_new), opt(t2_new), _dptr(energy), _dptr(status),
                                     opt(iters), opt(guess), int(save_root), PREC[precision], max_iter, tol,
                                     stream or None), "qflow_solve_device")
+
+
+# ---- warm-start network: sizes and device-level steps -----------------------------------------
+
+MLP_NIN, MLP_NOUT = 708, 54
+
+
+def mlp_param_count(n_in: int, hidden: int, n_out: int) -> int:
+    return int(lib().qflow_mlp_param_count(n_in, hidden, n_out))
+
+
+def mlp_model_size(hidden: int) -> int:
+    return int(lib().qflow_mlp_model_size(hidden))
+
+
+def mlp_workspace(n_in: int, hidden: int, n_out: int, rows: int) -> int:
+    return int(lib().qflow_mlp_workspace(n_in, hidden, n_out, rows))
+
+
+def mlp_forward_device(n_in, hidden, n_out, params, x, y, work, stream: int = 0):
+    _check(lib().qflow_mlp_forward_device(n_in, hidden, n_out, _dptr(params), _dptr(x), x.shape[0], _dptr(y),
+                                          _dptr(work), stream or None), "qflow_mlp_forward_device")
+
+
+def mlp_grad_device(n_in, hidden, n_out, params, x, target, grad, loss, work, mask=None, stream: int = 0):
+    _check(lib().qflow_mlp_grad_device(n_in, hidden, n_out, _dptr(params), _dptr(x), _dptr(target),
+                                       None if mask is None else _dptr(mask), x.shape[0], _dptr(grad), _dptr(loss),
+                                       _dptr(work), stream or None), "qflow_mlp_grad_device")
+
+
+def mlp_adam_device(params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                    eps: float = 1e-8, stream: int = 0):
+    _check(lib().qflow_mlp_adam_device(params.numel(), _dptr(params), _dptr(grad), _dptr(m), _dptr(v), step, lr,
+                                       beta1, beta2, eps, stream or None), "qflow_mlp_adam_device")
+
+
+def mlp_features_device(n: int, F, W, spaces, features, stream: int = 0):
+    _check(lib().qflow_mlp_features_device(n, _dptr(F), _dptr(W), _dptr(spaces), spaces.shape[0],
+                                           _dptr(features), stream or None), "qflow_mlp_features_device")
+
+
+def mlp_targets_device(roots, targets, stream: int = 0):
+    _check(lib().qflow_mlp_targets_device(_dptr(roots), roots.shape[0], _dptr(targets), stream or None),
+           "qflow_mlp_targets_device")
+
+
+def mlp_guess_device(y, guess, stream: int = 0):
+    _check(lib().qflow_mlp_guess_device(_dptr(y), y.shape[0], _dptr(guess), stream or None),
+           "qflow_mlp_guess_device")

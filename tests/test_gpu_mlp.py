@@ -1,0 +1,276 @@
+"""Warm-start network on the GPU vs the FP64 oracle, through the C ABI.
+
+Kernels (forward, gradient, Adam, features, targets, start vectors) are compared element by
+element with oracle/mlp.py on the same seeded inputs; FP32 tolerances are relative to the
+largest reference value.  The handle-level test trains on half of a Phi-started first sweep,
+checks the network's increments on the other half against the oracle, and checks that a fresh
+flow started from the network's guesses reproduces the Phi-started energies and amplitudes
+(the solver remains the judge); it reports the Davidson iteration counts of both starts.
+"""
+import numpy as np
+import pytest
+
+from oracle import cas, flow, hbar, mlp
+from paper_2606_04186_gb300 import synth
+
+from gpu_util import dev, library
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return library()
+
+
+def _f32(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def _close(got, ref, rtol):
+    scale = max(1.0, float(np.abs(ref).max()))
+    err = float(np.abs(np.asarray(got, dtype=np.float64) - ref).max())
+    assert err <= rtol * scale, (err, scale)
+
+
+@pytest.mark.parametrize("sizes,rows", [((708, 256, 54), 37), ((13, 7, 5), 70), ((708, 64, 54), 1)])
+def test_forward_and_gradient_match_oracle(qf, sizes, rows):
+    import torch
+    I, H, O = sizes
+    rng = np.random.default_rng(11)
+    p = synth.mlp_init_params(I, H, O, 5) + 0.05 * rng.standard_normal(mlp.param_count(I, H, O))
+    p = p.astype(np.float32).astype(np.float64)   # both sides see the same FP32 values
+    x = rng.standard_normal((rows, I)).astype(np.float32).astype(np.float64)
+    t = rng.standard_normal((rows, O)).astype(np.float32).astype(np.float64)
+    work = torch.zeros(qf.mlp_workspace(I, H, O, rows), dtype=torch.uint8, device="cuda")
+    y = torch.zeros((rows, O), dtype=torch.float32, device="cuda")
+    qf.mlp_forward_device(I, H, O, _f32(p), _f32(x), y, work)
+    grad = torch.zeros(p.size, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    qf.mlp_grad_device(I, H, O, _f32(p), _f32(x), _f32(t), grad, loss, work)
+    torch.cuda.synchronize()
+    y_ref, _ = mlp.forward(p, x, I, H, O)
+    l_ref, g_ref = mlp.loss_and_grad(p, x, t, I, H, O)
+    _close(y.cpu().numpy(), y_ref, 2e-5)
+    _close(grad.cpu().numpy(), g_ref, 2e-5)
+    assert abs(loss.item() - l_ref) <= 2e-5 * max(1.0, l_ref)
+
+
+def test_masked_rows_do_not_contribute(qf):
+    import torch
+    I, H, O, rows = 20, 16, 6, 48
+    rng = np.random.default_rng(12)
+    p = synth.mlp_init_params(I, H, O, 6).astype(np.float32).astype(np.float64)
+    x = rng.standard_normal((rows, I)).astype(np.float32).astype(np.float64)
+    t = rng.standard_normal((rows, O)).astype(np.float32).astype(np.float64)
+    keep = rng.random(rows) < 0.6
+    work = torch.zeros(qf.mlp_workspace(I, H, O, rows), dtype=torch.uint8, device="cuda")
+    grad = torch.zeros(p.size, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    mask = torch.as_tensor(keep.astype(np.uint8), device="cuda")
+    qf.mlp_grad_device(I, H, O, _f32(p), _f32(x), _f32(t), grad, loss, work, mask=mask)
+    torch.cuda.synchronize()
+    # the masked loss is the subset's loss rescaled by (subset rows / all rows)
+    l_sub, g_sub = mlp.loss_and_grad(p, x[keep], t[keep], I, H, O)
+    f = keep.sum() / rows
+    _close(grad.cpu().numpy(), f * g_sub, 2e-5)
+    assert abs(loss.item() - f * l_sub) <= 2e-5
+
+
+def test_adam_matches_oracle(qf):
+    import torch
+    rng = np.random.default_rng(13)
+    n = 3001
+    p = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    pd, md, vd = _f32(p), _f32(m), _f32(v)
+    for step in range(1, 4):
+        g = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+        qf.mlp_adam_device(pd, _f32(g), md, vd, step, 1e-2)
+        p, m, v = mlp.adam_step(p, g, m, v, step, 1e-2)
+    torch.cuda.synchronize()
+    _close(pd.cpu().numpy(), p, 1e-6)
+    _close(md.cpu().numpy(), m, 1e-6)
+    _close(vd.cpu().numpy(), v, 1e-6)
+
+
+def test_features_match_oracle(qf):
+    import torch
+    eps, h, g, sp = synth.system_inputs("n24")
+    t1, t2 = synth.random_amplitudes(5, 19, 9, 0.01, 0.02)
+    e0, F, W = hbar.hbar2(h, g, t1, t2, 5)
+    rows = sp[(sp[:, 0] == 3)][::97][:64]          # 64 spaces spread over the list
+    out = torch.zeros((len(rows), qf.MLP_NIN), dtype=torch.float32, device="cuda")
+    qf.mlp_features_device(24, dev(F), dev(W), dev(rows), out)
+    torch.cuda.synchronize()
+    ref = np.array([mlp.features(e0, F, W, *flow.space_orbitals(r)) for r in rows])
+    got = out.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+
+
+def _to_solver_layout(v):
+    """Oracle CAS basis (states a | b << 6 ascending: beta string major) -> the solver's layout
+    (alpha string * 20 + beta string)."""
+    return v.reshape(20, 20).T.ravel()
+
+
+def test_guess_vectors_match_oracle(qf):
+    import torch
+    rng = np.random.default_rng(14)
+    y = 0.05 * rng.standard_normal((19, mlp.N_TARGETS))
+    out = torch.zeros((19, 400), dtype=torch.float32, device="cuda")
+    qf.mlp_guess_device(_f32(y), out)
+    torch.cuda.synchronize()
+    ref = np.array([_to_solver_layout(mlp.guess_vector(r)) for r in y.astype(np.float32).astype(np.float64)])
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-6
+
+
+def test_targets_match_oracle(qf):
+    import torch
+    eps, h, g, sp = synth.system_inputs("n10")
+    t1, t2 = synth.random_amplitudes(3, 7, 2, 0.01, 0.02)
+    e0, F, W = hbar.hbar2(h, g, t1, t2, 3)
+    rows = sp[sp[:, 0] == 3][::7][:12]
+    vecs, ref = [], []
+    for r in rows:
+        c, hh, w = cas.space_problem(e0, F, W, *flow.space_orbitals(r))
+        mat = cas.cas_matrix(3, 3, c, hh, w)
+        _, vec, st = cas.phi_root(mat, cas.coupling(3, 3)[3])
+        assert st == 0
+        vecs.append(_to_solver_layout(vec))
+        ref.append(mlp.targets(vec.astype(np.float32).astype(np.float64)))
+    out = torch.zeros((len(rows), mlp.N_TARGETS), dtype=torch.float32, device="cuda")
+    qf.mlp_targets_device(_f32(np.array(vecs)), out)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - np.array(ref)).max() <= 1e-6
+
+
+def test_network_api_order_errors(qf):
+    eps, h, g, sp = synth.system_inputs("n10")
+    f = qf.Flow(h, g, 3, sp, precision="mixed")
+    f.sweep()
+    with pytest.raises(qf.QFlowError):      # increment pairs need the roots of guess mode "network"
+        f.mlp_collect(1, 100)
+    with pytest.raises(qf.QFlowError):      # warm pool needs a model with standardisation
+        f.mlp_warm_pool()
+    f.mlp_set_model(synth.mlp_init_model(32, 0), 32, False)
+    with pytest.raises(qf.QFlowError):
+        f.mlp_warm_pool()
+    f.close()
+    f = qf.Flow(h, g, 3, sp, precision="mixed", guess="network")
+    with pytest.raises(qf.QFlowError):      # nothing to collect before a sweep
+        f.mlp_collect(1, 100)
+    with pytest.raises(qf.QFlowError):      # no model, no pairs
+        f.mlp_train(1, 8, 1e-3)
+    f.close()
+
+
+def _class_positions(sp):
+    """Class position of each space of a one-class list: rank in lexicographic order of its
+    orbital tuple (the order the library keeps a size class in)."""
+    order = np.lexsort(tuple(sp[:, c] for c in range(7, 1, -1)))
+    pos = np.empty(len(sp), dtype=np.int64)
+    pos[order] = np.arange(len(sp))
+    return pos
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_warm_start_network(qf, precision):
+    """Train on every second space of a Phi-started first sweep, check the network on the other
+    half, then start a fresh flow from its guesses: energies and amplitudes must be those of the
+    Phi-started sweep (the solver is the judge); the iteration counts are reported."""
+    import torch
+    eps, h, g, sp = synth.system_inputs("n24")
+    hidden = 256
+    fa = qf.Flow(h, g, 5, sp, precision=precision, guess="network")
+    fa.sweep()
+    e_phi, per_phi = fa.energy(per_space=True)
+    it_phi, _ = fa.stats()
+    t_phi = fa.amplitudes()
+    npairs = fa.mlp_collect(stride=2, max_pairs=len(sp))
+    assert npairs == (len(sp) + 1) // 2
+    fa.mlp_set_model(synth.mlp_init_model(hidden, 1), hidden, has_stats=False)
+    loss = fa.mlp_train(epochs=40, batch=128, lr=2e-3, order=np.random.default_rng(3).permutation(npairs))
+    assert np.isfinite(loss).all() and loss[-1] < 0.3 * loss[0], loss
+    model = fa.mlp_get_model()
+    fa.close()
+    # held-out spaces (odd class positions): network increment vs the oracle's exact increment
+    held = sp[_class_positions(sp) % 2 == 1][::120][:40]
+    e0, F, W = hbar.hbar2(h, g, np.zeros((5, 19)), np.zeros((5, 5, 19, 19)), 5)
+    x = np.array([mlp.features(e0, F, W, *flow.space_orbitals(r)) for r in held])
+    ref = np.array([mlp.pack_increment(*cas.solve_space(e0, F, W, *flow.space_orbitals(r))[1:3]) for r in held])
+    P = qf.mlp_param_count(qf.MLP_NIN, hidden, qf.MLP_NOUT)
+    mu_x, s_x = model[P:P + 708], model[P + 708:P + 1416]
+    mu_y, sd_y = model[P + 1416:P + 1470], model[P + 1470:P + 1524]
+    out = torch.zeros((len(held), 54), dtype=torch.float32, device="cuda")
+    work = torch.zeros(qf.mlp_workspace(708, hidden, 54, len(held)), dtype=torch.uint8, device="cuda")
+    qf.mlp_forward_device(708, hidden, 54, _f32(model[:P]), _f32((x - mu_x) * s_x), out, work)
+    torch.cuda.synchronize()
+    pred = mu_y + sd_y * out.cpu().numpy()
+    rel = np.linalg.norm(pred - ref) / np.linalg.norm(ref)
+    assert rel < 0.5, rel             # a zero increment (the Phi start) has relative error 1
+    # flow B: a fresh flow whose first sweep starts its 6e6o spaces from the network's guesses
+    fb = qf.Flow(h, g, 5, sp, precision=precision, guess="network")
+    fb.mlp_set_model(model, hidden, has_stats=True)
+    de, dt, nf, code = fb.sweep()
+    assert nf == 0 and code == 0
+    e_net, per_net = fb.energy(per_space=True)
+    it_net, _ = fb.stats()
+    t_net = fb.amplitudes()
+    tol_e, tol_t = (1e-6, 1e-5) if precision == "mixed" else (1e-8, 1e-7)
+    assert np.abs(per_net - per_phi).max() < tol_e
+    assert np.abs(t_net[1] - t_phi[1]).max() < tol_t and np.abs(t_net[0] - t_phi[0]).max() < tol_t
+    print(f"{precision}: held-out relative error {rel:.3f}; mean Davidson iterations "
+          f"Phi start {it_phi.mean():.3f}, network start {it_net.mean():.3f}")
+    assert it_net.mean() < 2.0 * it_phi.mean()
+    fb.sweep()      # later sweeps start from Phi again
+    fb.close()
+
+
+def _sweeps_to_converge(f, tol_e, tol_t, max_sweeps=80):
+    for k in range(1, max_sweeps + 1):
+        de, dt, nf, code = f.sweep()
+        assert nf == 0 and code == 0
+        if abs(de) < tol_e and dt < tol_t:
+            return k
+    return max_sweeps + 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pool_warm_start_saves_sweeps(qf, precision):
+    """Train on a converged flow of one 24-orbital system (bare integrals -> converged internal
+    amplitudes of every space), warm-start the pool of a different system of the same family
+    (another seed) and count the sweeps to convergence against the empty-pool start; both reach
+    the same fixed point."""
+    tol_e, tol_t = (1e-8, 1e-7) if precision == "fp64" else (1e-7, 1e-5)
+    hidden = 256
+    eps, h, g, sp = synth.system_inputs("n24")
+    fa = qf.Flow(h, g, 5, sp, precision=precision)
+    _sweeps_to_converge(fa, tol_e, tol_t)
+    n = fa.mlp_collect(stride=1, max_pairs=len(sp), target="pool")
+    assert n == len(sp)
+    fa.mlp_set_model(synth.mlp_init_model(hidden, 2), hidden, has_stats=False)
+    loss = fa.mlp_train(epochs=60, batch=128, lr=2e-3, order=np.random.default_rng(4).permutation(n))
+    assert loss[-1] < 0.2 * loss[0], loss
+    model = fa.mlp_get_model()
+    fa.close()
+    eps2, h2, g2 = synth.make_system(24, 5, 4.0, 11)
+    sp2 = synth.all_spaces(24, 5)
+    cold = qf.Flow(h2, g2, 5, sp2, precision=precision)
+    k_cold = _sweeps_to_converge(cold, tol_e, tol_t)
+    e_cold = cold.energy()
+    cold.close()
+    warm = qf.Flow(h2, g2, 5, sp2, precision=precision)
+    warm.mlp_set_model(model, hidden, has_stats=True)
+    warm.mlp_warm_pool()
+    k_warm = _sweeps_to_converge(warm, tol_e, tol_t)
+    e_warm = warm.energy()
+    warm.close()
+    print(f"{precision}: sweeps to convergence, empty pool {k_cold}, network pool {k_warm}; "
+          f"E {e_cold:.10f} / {e_warm:.10f}")
+    assert abs(e_warm - e_cold) < (1e-8 if precision == "fp64" else 1e-6)
+    assert k_warm < k_cold

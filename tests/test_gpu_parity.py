@@ -268,6 +268,8 @@ def test_autotuner_times_candidates(qf):
     sp = sp[::3]   # a space list of its own, so the per-process cache is cold
     f = qf.Flow(h, g, 6, sp, precision="mixed", schedule="auto")
     f.sweep()
+    assert f.schedule()["candidate_ms"] == []     # calibration happens at the second sweep
+    f.sweep()
     sch = f.schedule()
     assert len(sch["candidate_ms"]) == 6 and min(sch["candidate_ms"]) > 0
     f.close()
