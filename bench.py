@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=800, help="spaces solved by the oracle for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "persistent", "per_class"])
+    ap.add_argument("--spaces-limit", type=int, default=0,
+                    help="keep an evenly strided subset of at most this many spaces (small profiling case)")
     return ap.parse_args()
 
 
@@ -248,10 +251,12 @@ def run_ours(args):
     name = args.workload
     s = synth.SYSTEMS[name]
     eps, h, g, sp = synth.system_inputs(name)
+    if args.spaces_limit and len(sp) > args.spaces_limit:
+        sp = np.ascontiguousarray(sp[::-(-len(sp) // args.spaces_limit)])
     no, nv = s.nocc, s.n - s.nocc
     log(f"inputs ready: {name}, {len(sp)} spaces")
     t_init = time.perf_counter()
-    fl = qflow.Flow(h, g, no, sp, precision=args.precision)
+    fl = qflow.Flow(h, g, no, sp, precision=args.precision, schedule=args.schedule)
     t_init = time.perf_counter() - t_init
     stream = torch.cuda.ExternalStream(fl.stream())
     log(f"init {t_init:.1f} s")
@@ -293,6 +298,7 @@ def run_ours(args):
     log(f"timed {args.steps} sweeps: {elapsed_ms:.1f} ms")
     it, st = fl.stats()
     e_mean = fl.energy()
+    sched = fl.schedule()
     if dist is not None:
         tt = torch.tensor([elapsed_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -372,18 +378,23 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": sweep_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} (3,3) spaces",
+        "config": {"workload": f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} spaces "
+                               f"({', '.join(f'{int((sp[:, 0] == k).sum())} ({k},{k})' for k in (3, 2, 1) if (sp[:, 0] == k).any())})",
                    "precision": args.precision, "sweep_s": sweep_ms / 1e3, "l2": "inputs larger than L2 (W = "
                    f"{8 * s.n ** 4 / 1e6:.0f} MB)", "replicas": world, "e_sweep3": e_mean,
                    "step": "third sweep of the flow (pool after two sweeps restored before each step)",
                    "init_s": t_init},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": f"solve_kernel<3,{'float' if args.precision == 'mixed' else 'double'}>",
+                     "frac": achieved / peak, "traffic": None, "kernel": ("solve_persistent_kernel" if sched["persistent"] else "solve_class_kernel<K>")
+                     if args.precision == "mixed" else "solve_kernel<K,double>",
                      "flops_per_launch": flops, "launch_ms": solve_ms,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "mixed"
                      else "GB300 FP64 nominal"},
+        "schedule": sched,
         "phase_ms": {"dress": float(ph[:, 0].mean()), "solve": solve_ms, "merge": float(ph[:, 2].mean())},
-        "davidson_iters_mean": float(it.mean()), "failed_spaces": int((st != 0).sum()),
+        "davidson_iters_mean": float(it.mean()),
+        "davidson_iters_hist": np.bincount(np.minimum(it.astype(np.int64), 12), minlength=13).tolist(),
+        "failed_spaces": int((st != 0).sum()),
         "sweep_codes": sorted(set(int(c) for c in codes)),
         "fp64_form": fp64,
         "speedup_vs_fp64": (fp64["sweep_s"] / (sweep_ms / 1e3)) if fp64 else None,
