@@ -33,7 +33,7 @@
 namespace qf {
 namespace {
 
-constexpr int KM = 4;     // Davidson subspace limit (restart on the Ritz vector)
+constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
 constexpr int WARPS = 4;  // spaces (warps) per CTA
 
 template <int K>
@@ -123,17 +123,28 @@ __device__ __forceinline__ void ab_terms(std::integer_sequence<int, I...>, float
 // ---- shared memory -------------------------------------------------------------------------
 
 template <int K>
-struct Tabs {  // run-time string tables of one size class
+struct Tabs {  // run-time string tables of one size class (bytes: they share the SM with warps)
   using D = Dim<K>;
-  int J[D::NS * D::NSG];
-  int pq[D::NS * D::NSG];
-  int sg[D::NS * D::NSG];
-  int mask[D::NS];
-  int c0n[D::NS];       // replacements (pq) with <I| E_pq |Phi string> != 0 (<= K of them)
-  int c0pq[D::NS][K];
-  int c0sg[D::NS][K];
-  int xJ[K * K];        // a+_A a_i |Phi string> = xs * |xJ>, index i*K + (A-K)
-  int xs[K * K];
+  signed char J[D::NS * D::NSG];
+  signed char pq[D::NS * D::NSG];
+  signed char sg[D::NS * D::NSG];
+  signed char mask[D::NS];
+  signed char occ[D::NS][K];   // orbitals of each string, ascending
+  signed char c0n[D::NS];      // replacements (pq) with <I| E_pq |Phi string> != 0 (<= K of them)
+  signed char c0pq[D::NS][K];
+  signed char c0sg[D::NS][K];
+  signed char xJ[K * K];       // a+_A a_i |Phi string> = xs * |xJ>, index i*K + (A-K)
+  signed char xs[K * K];
+};
+
+// FP64 set-up data of one space (gather, fold, string diagonal); dead once the Davidson loop
+// has more than two vectors, so the 6e6o state keeps it in its third vector slot.
+template <int K>
+struct SetupF64 {
+  using D = Dim<K>;
+  double F[D::NF], J[D::NF], Kx[D::NF];  // F block; J_pr = W_pprr, K_pr = W_prrp
+  double hd[D::NORB];                    // folded one-body diagonal h_pp
+  double hsd[D::NS];                     // same-spin string diagonal
 };
 
 template <int K>
@@ -141,22 +152,37 @@ struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as fl
   using D = Dim<K>;
   float V[KM * D::NDET];
   float S[KM * D::NDET];
-  float Wt[D::NW];        // FP32 W block without its [pp][rr] (diagonal-only) entries
+  float Wt[D::NW];          // FP32 W block without its [pp][rr] (diagonal-only) entries
   float Hs[D::NS * D::NS];  // same-spin string operator, zero diagonal
-  float diag[D::NDET];    // operator diagonal minus E_Phi
-  float hp[D::NF];        // h' = h - 1/2 sum_r W_prrq (off-diagonal part, FP32)
-  double F[D::NF], J[D::NF], Kx[D::NF];  // F block; J_pr = W_pprr, K_pr = W_prrp (FP64)
-  double hd[D::NORB];     // folded one-body diagonal h_pp (FP64)
-  double hsd[D::NS];      // same-spin string diagonal (FP64)
-  float dh[D::NS];        // hsd[I] - hsd[0]; Hs[I][0] on the Phi path
+  float dh[(D::NS + 3) / 4 * 4];  // hsd[I] - hsd[0]; Hs[I][0] on the Phi path
   float jb[D::NORB * D::NS];  // jb[p][Ib] = sum_{r in Ib} J_pr
-  float G[KM * KM];       // projected matrix, G[i*KM+j] = V_i . S_j
-  float yf[KM];           // Ritz coefficients
-  float theta;            // Ritz value relative to eshift
+  float hp[D::NF];          // h' = h - 1/2 sum_r W_prrq (off-diagonal part, FP32)
+  float G[KM * KM];         // projected matrix, G[i*KM+j] = V_i . S_j
+  float yf[KM];             // Ritz coefficients
+  float theta;              // Ritz value relative to eshift
+  float j0;                 // sum_{p, r in Phi string} J_pr (FP32, diagonal reference)
   double ecore, eshift;
   int orb[D::NORB];
-  int ctrl[4];            // [0] subspace size, [1] valid, [2] status, [3] iterations
+  int ctrl[4];              // [0] subspace size, [1] valid, [2] status, [3] iterations
+  // the small classes keep set-up data and gather offsets here (the 6e6o state reuses the
+  // third V slot and the second S slot, which are free until the Davidson loop needs them)
+  alignas(16) unsigned char extra[K == 3 ? 16 : sizeof(SetupF64<K>) + 2 * D::NF * sizeof(long long)];
 };
+
+template <int K>
+__device__ __forceinline__ SetupF64<K>& setup(WarpState<K>& ws) {
+  if constexpr (K == 3) return *reinterpret_cast<SetupF64<K>*>(ws.V + 2 * Dim<K>::NDET);
+  else return *reinterpret_cast<SetupF64<K>*>(ws.extra);
+}
+// gather offsets: element (P, R) of the W block sits at off[P] + off[NF + R]
+template <int K>
+__device__ __forceinline__ long long* gather_off(WarpState<K>& ws) {
+  if constexpr (K == 3) return reinterpret_cast<long long*>(ws.S + Dim<K>::NDET);
+  else return reinterpret_cast<long long*>(ws.extra + sizeof(SetupF64<K>));
+}
+static_assert(KM == 3 && sizeof(SetupF64<3>) <= Dim<3>::NDET * sizeof(float) &&
+                  2 * Dim<3>::NF * sizeof(long long) <= Dim<3>::NDET * sizeof(float),
+              "set-up data must fit the reused 6e6o vector slots");
 
 union alignas(16) AnyWarpState {
   WarpState<3> w3;
@@ -174,7 +200,8 @@ struct alignas(16) CtaSmem {
 
 static_assert(sizeof(WarpState<3>) % 16 == 0 && offsetof(WarpState<3>, S) % 16 == 0 &&
                   offsetof(WarpState<3>, Wt) % 16 == 0 && offsetof(WarpState<3>, Hs) % 16 == 0 &&
-                  offsetof(WarpState<3>, diag) % 16 == 0,
+                  offsetof(WarpState<3>, dh) % 16 == 0 && offsetof(WarpState<3>, jb) % 16 == 0 &&
+                  (2 * Dim<3>::NDET * sizeof(float)) % 16 == 0,
               "float4 rows of the 6e6o state");
 static_assert(offsetof(CtaSmem, w) % 16 == 0 && sizeof(AnyWarpState) % 16 == 0, "warp state alignment");
 
@@ -196,6 +223,16 @@ __device__ __forceinline__ WarpState<2>& state<2>(AnyWarpState& a) { return a.w2
 template <>
 __device__ __forceinline__ WarpState<1>& state<1>(AnyWarpState& a) { return a.w1; }
 
+// Operator diagonal at determinant (ia, ib) relative to <Phi|H|Phi> (exactly 0 at Phi).
+template <int K>
+__device__ __forceinline__ float diag_at(const Tabs<K>& tb, const WarpState<K>& ws, int ia, int ib) {
+  constexpr int NS = Dim<K>::NS;
+  float jj = 0.f;
+#pragma unroll
+  for (int l = 0; l < K; ++l) jj += ws.jb[tb.occ[ia][l] * NS + ib];
+  return ws.dh[ia] + ws.dh[ib] + (jj - ws.j0);
+}
+
 // String tables of one class (single thread): strings by increasing bit mask (string 0 holds
 // the occupied orbitals), single replacements into each string, connections to the Phi string
 // and the single replacements i -> A of the Phi string.
@@ -205,6 +242,11 @@ __device__ void build_tabs(Tabs<K>& t) {
   int c = 0;
   for (int m = 0; m < (1 << D::NORB); ++m)
     if (__popc(m) == K) t.mask[c++] = m;
+  for (int I = 0; I < D::NS; ++I) {
+    int j = 0;
+    for (int p = 0; p < D::NORB; ++p)
+      if ((t.mask[I] >> p) & 1) t.occ[I][j++] = (signed char)p;
+  }
   for (int I = 0; I < D::NS; ++I) {
     const int mi = t.mask[I];
     int u = 0;
@@ -281,15 +323,20 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
     const int Ia = lane;
     float acc[NS];
     {  // diagonal and alpha-alpha: acc[b] = diag * c + sum_J Hs[Ia][J] c[J][b]
-      const float4* drow = reinterpret_cast<const float4*>(ws.diag + Ia * NS);
+      // diag(Ia, b) = dh[Ia] + dh[b] + (sum_{p in Ia} jb[p][b] - j0), as diag_at
+      const float4* j0r = reinterpret_cast<const float4*>(ws.jb + tb.occ[Ia][0] * NS);
+      const float4* j1r = reinterpret_cast<const float4*>(ws.jb + tb.occ[Ia][1] * NS);
+      const float4* j2r = reinterpret_cast<const float4*>(ws.jb + tb.occ[Ia][2] * NS);
+      const float4* dhr = reinterpret_cast<const float4*>(ws.dh);
       const float4* crow = reinterpret_cast<const float4*>(c + Ia * NS);
+      const float dha = ws.dh[Ia], jz = ws.j0;
 #pragma unroll
       for (int q = 0; q < NS / 4; ++q) {
-        const float4 dv = drow[q], cv = crow[q];
-        acc[4 * q + 0] = dv.x * cv.x;
-        acc[4 * q + 1] = dv.y * cv.y;
-        acc[4 * q + 2] = dv.z * cv.z;
-        acc[4 * q + 3] = dv.w * cv.w;
+        const float4 a0 = j0r[q], a1 = j1r[q], a2 = j2r[q], dv = dhr[q], cv = crow[q];
+        acc[4 * q + 0] = (dha + dv.x + (a0.x + a1.x + a2.x - jz)) * cv.x;
+        acc[4 * q + 1] = (dha + dv.y + (a0.y + a1.y + a2.y - jz)) * cv.y;
+        acc[4 * q + 2] = (dha + dv.z + (a0.z + a1.z + a2.z - jz)) * cv.z;
+        acc[4 * q + 3] = (dha + dv.w + (a0.w + a1.w + a2.w - jz)) * cv.w;
       }
     }
 #pragma unroll 2
@@ -372,7 +419,7 @@ __device__ __noinline__ void sigma_small(const Tabs<K>& tb, const WarpState<K>& 
   using D = Dim<K>;
   for (int d = lane; d < D::NDET; d += 32) {
     const int ia = d / D::NS, ib = d % D::NS;
-    float acc = ws.diag[d] * c[d];
+    float acc = diag_at<K>(tb, ws, ia, ib) * c[d];
     for (int j = 0; j < D::NS; ++j) {
       acc = fmaf(ws.Hs[ia * D::NS + j], c[j * D::NS + ib], acc);
       acc = fmaf(ws.Hs[ib * D::NS + j], c[ia * D::NS + j], acc);
@@ -403,6 +450,33 @@ __device__ __forceinline__ void sigma(const Tabs<K>& tb, const WarpState<K>& ws,
 // from the previous Ritz value, then Rayleigh-quotient refinement.  The projected matrix is
 // built from FP32 vectors, so it is solved in FP32 too.
 __device__ __noinline__ void small_eig(const float* G, int k, float shift, float* y, float* theta) {
+  if (k == 2) {  // closed form: the eigenvalue nearest the shift and its eigenvector
+    const float g00 = G[0], g01 = G[1], g10 = G[KM], g11 = G[KM + 1];
+    const float tr = 0.5f * (g00 + g11), df = 0.5f * (g00 - g11);
+    const float disc = df * df + g01 * g10;
+    if (disc >= 0.f && isfinite(disc)) {
+      const float sq = sqrtf(disc);
+      const float l1 = tr + sq, l2 = tr - sq;
+      const float lam = (fabsf(l1 - shift) <= fabsf(l2 - shift)) ? l1 : l2;
+      // (G - lam) y = 0: take the better conditioned of the two rows
+      float y0, y1;
+      if (fabsf(g01) + fabsf(lam - g00) >= fabsf(g10) + fabsf(lam - g11)) {
+        y0 = g01;
+        y1 = lam - g00;
+      } else {
+        y0 = lam - g11;
+        y1 = g10;
+      }
+      const float nrm = sqrtf(y0 * y0 + y1 * y1);
+      if (nrm > 0.f && isfinite(nrm)) {
+        const float sc = ((y0 < 0.f) ? -1.f : 1.f) / nrm;
+        y[0] = sc * y0;
+        y[1] = sc * y1;
+        *theta = lam;
+        return;
+      }
+    }
+  }
   float a[KM * KM], z[KM];
   for (int phase = 0; phase < 5; ++phase) {
     const float sg = (phase < 2) ? shift : *theta;
@@ -496,10 +570,16 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   }
   // ---- gather ------------------------------------------------------------------------------
   // FP32 couplings (all loads in flight); FP64: J_pr = W_pprr, K_pr = W_prrp and the F block.
+  // Element (P, R) of the block is at off[P] + off[NF + R] (pair offsets built first).
+  SetupF64<K>& su = setup(ws);
   {
-    size_t ro[NORB];
-#pragma unroll
-    for (int t = 0; t < NORB; ++t) ro[t] = (size_t)ws.orb[t];
+    long long* off = gather_off(ws);
+    for (int t = lane; t < 2 * NF; t += 32) {
+      const int P = t % NF;
+      const long long o0 = ws.orb[P / NORB], o1 = ws.orb[P % NORB];
+      off[t] = (t < NF) ? o0 * (long long)n3 + o1 * (long long)n2 : o0 * (long long)n1 + o1;
+    }
+    __syncwarp();
     if constexpr (K == 3) {  // the 666 unique elements of the pair-symmetric block
       constexpr int PER = (D::NPAIR + 31) / 32;
       float wv[PER];
@@ -509,7 +589,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
         wv[k] = 0.f;
         if (t < D::NPAIR) {
           const int pr = pair3[t], P = pr & 255, R = pr >> 8;
-          const size_t g = ro[P / NORB] * n3 + ro[P % NORB] * n2 + ro[R / NORB] * n1 + ro[R % NORB];
+          const size_t g = (size_t)(off[P] + off[NF + R]);
           wv[k] = W32 ? W32[g] : (float)a.W[g];
         }
       }
@@ -527,29 +607,29 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     } else {
       for (int t = lane; t < D::NW; t += 32) {
         const int P = t / NF, R = t % NF;
-        const size_t g = ro[P / NORB] * n3 + ro[P % NORB] * n2 + ro[R / NORB] * n1 + ro[R % NORB];
+        const size_t g = (size_t)(off[P] + off[NF + R]);
         const bool jj = (P / NORB == P % NORB) && (R / NORB == R % NORB);
         ws.Wt[t] = jj ? 0.f : (W32 ? W32[g] : (float)a.W[g]);
       }
     }
     for (int t = lane; t < NF; t += 32) {
-      const size_t p = ro[t / NORB], r = ro[t % NORB];
-      ws.J[t] = a.W[p * n3 + p * n2 + r * n1 + r];
-      ws.Kx[t] = a.W[p * n3 + r * n2 + r * n1 + p];
-      ws.F[t] = a.F[p * n1 + r];
+      const int p = t / NORB, r = t % NORB;
+      su.J[t] = a.W[off[p * (NORB + 1)] + off[NF + r * (NORB + 1)]];
+      su.Kx[t] = a.W[off[p * NORB + r] + off[NF + r * NORB + p]];
+      su.F[t] = a.F[(size_t)ws.orb[p] * n1 + ws.orb[r]];
     }
   }
   __syncwarp();
   // ---- fold (vacuum order over the active orbitals) -------------------------------------
   // h_pp = F_pp - sum_k (2 J_pk - K_pk) in FP64; off-diagonal h' = h - 1/2 sum_r W_prrq in FP32
   if (lane < NORB) {
-    double v = ws.F[lane * (NORB + 1)];
-    for (int k = 0; k < K; ++k) v -= 2.0 * ws.J[lane * NORB + k] - ws.Kx[lane * NORB + k];
-    ws.hd[lane] = v;
+    double v = su.F[lane * (NORB + 1)];
+    for (int k = 0; k < K; ++k) v -= 2.0 * su.J[lane * NORB + k] - su.Kx[lane * NORB + k];
+    su.hd[lane] = v;
   }
   for (int idx = lane; idx < NF; idx += 32) {
     const int p = idx / NORB, q = idx % NORB;
-    float v = (float)ws.F[idx];
+    float v = (float)su.F[idx];
     for (int k = 0; k < K; ++k)
       v -= 2.f * ws.Wt[idx * NF + k * (NORB + 1)] - ws.Wt[(p * NORB + k) * NF + k * NORB + q];
     for (int r = 0; r < NORB; ++r) v -= 0.5f * ws.Wt[(p * NORB + r) * NF + r * NORB + q];
@@ -557,24 +637,27 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   }
   __syncwarp();
   if (lane < NS) {  // same-spin string diagonal: sum_{p in I} h_pp + 1/2 sum_{p,r in I} (J_pr - K_pr)
-    const int m = tb.mask[lane];
     double v = 0.0;
-    for (int p = 0; p < NORB; ++p) {
-      if (!((m >> p) & 1)) continue;
-      v += ws.hd[p];
-      for (int r = 0; r < NORB; ++r)
-        if ((m >> r) & 1) v += 0.5 * (ws.J[p * NORB + r] - ws.Kx[p * NORB + r]);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int p = tb.occ[lane][j];
+      v += su.hd[p];
+#pragma unroll
+      for (int l = 0; l < K; ++l) {
+        const int r = tb.occ[lane][l];
+        v += 0.5 * (su.J[p * NORB + r] - su.Kx[p * NORB + r]);
+      }
     }
-    ws.hsd[lane] = v;
+    su.hsd[lane] = v;
   }
   __syncwarp();
   if (lane == 0) {
     double ec = *a.e0;
-    for (int k = 0; k < K; ++k) ec -= ws.hd[k] + ws.F[k * (NORB + 1)];
+    for (int k = 0; k < K; ++k) ec -= su.hd[k] + su.F[k * (NORB + 1)];
     ws.ecore = ec;
-    double v = ec + 2.0 * ws.hsd[0];
+    double v = ec + 2.0 * su.hsd[0];
     for (int p = 0; p < K; ++p)
-      for (int r = 0; r < K; ++r) v += ws.J[p * NORB + r];
+      for (int r = 0; r < K; ++r) v += su.J[p * NORB + r];
     ws.eshift = v;  // <Phi|H|Phi>
     ws.ctrl[0] = 1;
     ws.ctrl[2] = kSpaceNoConv;
@@ -665,28 +748,22 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       }
     }
   }
-  // the diagonal relative to <Phi|H|Phi>: string parts as FP64 differences, the alpha-beta
-  // Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
-  if (lane < NS) ws.dh[lane] = (float)(ws.hsd[lane] - ws.hsd[0]);
+  // the diagonal relative to <Phi|H|Phi> (diag_at): string parts as FP64 differences, the
+  // alpha-beta Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
+  if (lane < NS) ws.dh[lane] = (float)(su.hsd[lane] - su.hsd[0]);
 #pragma unroll 1
   for (int t = lane; t < NORB * NS; t += 32) {
-    const int p = t / NS, b = t % NS, mb = tb.mask[b];
+    const int p = t / NS, b = t % NS;
     float v = 0.f;
-    for (int r = 0; r < NORB; ++r)
-      if ((mb >> r) & 1) v += (float)ws.J[p * NORB + r];
+#pragma unroll
+    for (int l = 0; l < K; ++l) v += (float)su.J[p * NORB + tb.occ[b][l]];
     ws.jb[t] = v;
   }
   __syncwarp();
-#pragma unroll 1
-  for (int d = lane; d < NDET; d += 32) {
-    const int ia = d / NS, ib = d % NS;
-    const int ma = tb.mask[ia];
-    float jj = 0.f, j0 = 0.f;
-    for (int p = 0; p < NORB; ++p) {
-      if ((ma >> p) & 1) jj += ws.jb[p * NS + ib];
-      if (p < K) j0 += ws.jb[p * NS + 0];
-    }
-    ws.diag[d] = (d == 0) ? 0.f : ws.dh[ia] + ws.dh[ib] + (jj - j0);
+  if (lane == 0) {
+    float j0 = 0.f;
+    for (int l = 0; l < K; ++l) j0 += ws.jb[tb.occ[0][l] * NS + 0];
+    ws.j0 = j0;
   }
   __syncwarp();
   // ---- caller's guess: subspace {Phi, g - g_Phi Phi}; its sigma counts as one iteration -------
@@ -777,7 +854,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       }
       const float r = sv - th * xv;
       rr = fmaf(r, r, rr);
-      float den = th - ws.diag[d];
+      float den = th - diag_at<K>(tb, ws, d / NS, d % NS);
       if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
       vk[d] = r / den;
     }
@@ -956,7 +1033,7 @@ struct PersistentArgs {
 };
 
 // One queue over every size class: items [0, n3) are 6e6o spaces, then 4e4o, then 2e2o.
-__global__ void __launch_bounds__(32 * WARPS) solve_persistent_kernel(PersistentArgs p) {
+__global__ void __maxnreg__(128) solve_persistent_kernel(PersistentArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CtaSmem& cs = *reinterpret_cast<CtaSmem*>(smem_raw);
   build_all_tabs(cs);
