@@ -58,10 +58,11 @@ typedef enum {
 
 typedef enum {
   QFLOW_PREC_FP64 = 0,   /* plain: every step in FP64                                        */
-  QFLOW_PREC_MIXED = 1   /* dressing: T1 transform, reference energy and Fock-like sums in FP64,
-                            T2 contractions in FP32 added to FP64 bases; solver: FP32 sigma,
-                            vectors and projected eigenproblem, FP64 diagonal/energy shift;
-                            FP64 energy and amplitude update                                  */
+  QFLOW_PREC_MIXED = 1   /* dressing: FP64 integrals with FP32 T1 correction sums, reference
+                            energy and Fock-like sums in FP64, T2 contractions as tensor-core
+                            GEMMs (three-term TF32, FP32 accumulation) added to FP64 bases;
+                            solver: FP32 sigma, vectors and projected eigenproblem, FP64
+                            diagonal/energy shift; FP64 energy and amplitude update          */
 } qflow_precision;
 
 typedef struct {
@@ -213,6 +214,15 @@ int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* 
                        const int32_t* owner2, const double* t1_old, const double* t2_old, double* t1_new,
                        double* t2_new, double* energy, int32_t* status, int32_t* iters, void* guess,
                        int32_t save_root, int32_t precision, int32_t max_iter, double tol, void* stream);
+
+/* Tensor-core GEMM engine of the dressing contractions (tcgen05, kind::tf32 with three-term
+ * hi/lo operand splits, FP32 accumulation in tensor memory): C[m][n] = sum_k A[m][k] B[n][k]
+ * for row-major FP32 device arrays (leading dimensions lda >= K, ldb >= K, ldc >= N).  Each
+ * product is accurate to about 2^-21 relative; accumulation is FP32.  err: device int, set to 1 when a tile gave up
+ * waiting for its tensor-core work (it then leaves its C block unwritten); the caller zeroes
+ * it.  Asynchronous on `stream`. */
+int qflow_gemm_tf32x3_device(int32_t M, int32_t N, int32_t K, const float* A, int32_t lda, const float* B,
+                             int32_t ldb, float* C, int32_t ldc, int32_t* err, void* stream);
 
 /* ---- allocation-free dressing ---------------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot call

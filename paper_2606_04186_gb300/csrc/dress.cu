@@ -5,8 +5,9 @@
 //   E0, F[p][q], W[p][q][r][s] (creators p, r; annihilators q, s; W[pqrs] = W[rspq]).
 //
 // Construction (one thread per output element, or one block per element for the few long
-// sums; the T2 contractions run in FP64, or in FP32 on an FP32 copy of g~ and t2 for the
-// mixed-precision path, their FP64 base values being added in FP64):
+// sums; the T2 contractions run in FP64, or for the mixed-precision path on the tensor cores
+// (tcgen05 GEMMs with three-term TF32 operands and FP32 accumulation, tc_gemm.cuh) on an FP32
+// copy of g~ and t2, their FP64 base values being added in FP64):
 //   1. T1 exactly: orbital similarity transform of the integrals; creators by (1 - K),
 //      annihilators by (1 + K), K_ai = t_i^a (K^2 = 0) -> h~, g~ (four in-place passes).
 //   2. f~ = h~ + sum_k [2 g~_pqkk - g~_pkkq], E~ = <Phi|H~|Phi>.
@@ -14,9 +15,11 @@
 //      the quadratic term 1/2 [[H~,T2],T2] only reaches the doubly excited (vo|vo) block).
 // Index names: occupied i j k l m n, virtual a b e f (absolute index nocc + a).
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "qflow_internal.h"
+#include "tc_gemm.cuh"
 
 namespace qf {
 namespace {
@@ -41,37 +44,41 @@ __global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst,
 }
 
 // Creator index `pos` (0 or 2): rows p >= nocc get  - sum_i t1[i][p-nocc] * row_i.
+// The correction sum runs in precision A (FP64, or FP32 for the mixed path) and is added to
+// the FP64 element.
+template <typename A>
 __global__ void k_t1_creator(double* __restrict__ W, const double* __restrict__ t1, Dims d, int pos) {
   const size_t m = (size_t)d.v * d.n * d.n * d.n;
   for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m; x += (size_t)gridDim.x * blockDim.x) {
     const int a = (int)(x / ((size_t)d.n * d.n * d.n));
     const size_t rest = x % ((size_t)d.n * d.n * d.n);
     const int u = (int)(rest / ((size_t)d.n * d.n)), w = (int)((rest / d.n) % d.n), z = (int)(rest % d.n);
-    double acc = 0.0;
+    A acc = 0;
     if (pos == 0) {
-      for (int i = 0; i < d.o; ++i) acc += t1[i * d.v + a] * W[gi(d, i, u, w, z)];
-      W[gi(d, d.o + a, u, w, z)] -= acc;
+      for (int i = 0; i < d.o; ++i) acc += (A)t1[i * d.v + a] * (A)W[gi(d, i, u, w, z)];
+      W[gi(d, d.o + a, u, w, z)] -= (double)acc;
     } else {
-      for (int i = 0; i < d.o; ++i) acc += t1[i * d.v + a] * W[gi(d, u, w, i, z)];
-      W[gi(d, u, w, d.o + a, z)] -= acc;
+      for (int i = 0; i < d.o; ++i) acc += (A)t1[i * d.v + a] * (A)W[gi(d, u, w, i, z)];
+      W[gi(d, u, w, d.o + a, z)] -= (double)acc;
     }
   }
 }
 
 // Annihilator index `pos` (1 or 3): rows q < nocc get  + sum_a t1[q][a] * row_(nocc+a).
+template <typename A>
 __global__ void k_t1_annihilator(double* __restrict__ W, const double* __restrict__ t1, Dims d, int pos) {
   const size_t m = (size_t)d.o * d.n * d.n * d.n;
   for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m; x += (size_t)gridDim.x * blockDim.x) {
     const int q = (int)(x / ((size_t)d.n * d.n * d.n));
     const size_t rest = x % ((size_t)d.n * d.n * d.n);
     const int u = (int)(rest / ((size_t)d.n * d.n)), w = (int)((rest / d.n) % d.n), z = (int)(rest % d.n);
-    double acc = 0.0;
+    A acc = 0;
     if (pos == 1) {
-      for (int a = 0; a < d.v; ++a) acc += t1[q * d.v + a] * W[gi(d, u, d.o + a, w, z)];
-      W[gi(d, u, q, w, z)] += acc;
+      for (int a = 0; a < d.v; ++a) acc += (A)t1[q * d.v + a] * (A)W[gi(d, u, d.o + a, w, z)];
+      W[gi(d, u, q, w, z)] += (double)acc;
     } else {
-      for (int a = 0; a < d.v; ++a) acc += t1[q * d.v + a] * W[gi(d, u, w, z, d.o + a)];
-      W[gi(d, u, w, z, q)] += acc;
+      for (int a = 0; a < d.v; ++a) acc += (A)t1[q * d.v + a] * (A)W[gi(d, u, w, z, d.o + a)];
+      W[gi(d, u, w, z, q)] += (double)acc;
     }
   }
 }
@@ -105,25 +112,39 @@ __global__ void k_fock(const double* __restrict__ ht, const double* __restrict__
 }
 
 // E0 = sum_k 2 h~_kk + sum_kl [2 g~_kkll - g~_kllk] + sum_ijab g~_iajb (2 t_ij^ab - t_ij^ba).
-// One block; fixed-order reduction.
-__global__ void k_energy(const double* __restrict__ ht, const double* __restrict__ W, const double* __restrict__ t2,
-                         double* __restrict__ e0, Dims d) {
+// Fixed-order reduction: EGRID block partials (grid-stride), then one block sums them in order.
+constexpr int EGRID = 256;
+__global__ void k_energy_part(const double* __restrict__ ht, const double* __restrict__ W,
+                              const double* __restrict__ t2, double* __restrict__ part, Dims d) {
   __shared__ double red[TPB];
   double acc = 0.0;
   const size_t m = (size_t)d.o * d.o * d.v * d.v;
-  for (size_t x = threadIdx.x; x < m; x += blockDim.x) {
+  for (size_t x = blockIdx.x * (size_t)TPB + threadIdx.x; x < m; x += (size_t)EGRID * TPB) {
     const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
     const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
     acc += W[gi(d, i, d.o + a, j, d.o + b)] * (2.0 * t2[x] - t2[ti(d, i, j, b, a)]);
   }
-  for (int x = threadIdx.x; x < d.o * d.o; x += blockDim.x) {
-    const int k = x / d.o, l = x % d.o;
-    acc += 2.0 * W[gi(d, k, k, l, l)] - W[gi(d, k, l, l, k)];
+  if (blockIdx.x == 0) {
+    for (int x = threadIdx.x; x < d.o * d.o; x += TPB) {
+      const int k = x / d.o, l = x % d.o;
+      acc += 2.0 * W[gi(d, k, k, l, l)] - W[gi(d, k, l, l, k)];
+    }
+    for (int k = threadIdx.x; k < d.o; k += TPB) acc += 2.0 * ht[k * d.n + k];
   }
-  for (int k = threadIdx.x; k < d.o; k += blockDim.x) acc += 2.0 * ht[k * d.n + k];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int s = TPB / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_energy_sum(const double* __restrict__ part, double* __restrict__ e0) {
+  __shared__ double red[EGRID];
+  red[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int s = EGRID / 2; s > 0; s >>= 1) {
     if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
@@ -412,18 +433,31 @@ __global__ void k_finalize(double* __restrict__ W, double* __restrict__ F, const
 
 struct Work {
   double *ht, *foo, *fvv, *wo, *r1, *r2, *A, *B, *Cq, *D, *t2f;  // A..D, t2f hold T values
+  double* epart;  // energy partials
+  float* acc;     // mixed path: FP32 GEMM accumulation (v^3 o floats)
+  int* err;       // mixed path: set by a GEMM tile that gave up waiting
 };
 
-size_t carve(void* base, int n, int o, Work* w) {
+size_t carve(void* base, int n, int o, Work* w, bool mixed = false) {
   const int v = n - o;
   const size_t sizes[] = {(size_t)n * n, (size_t)o * o, (size_t)v * v, (size_t)o * o * o * o, (size_t)v * o,
                           (size_t)o * o * v * v, (size_t)o * v * o * v, (size_t)o * v * o * v, (size_t)o * v * o * v,
-                          (size_t)o * v * o * v, (size_t)o * o * v * v};
-  double** ptrs[] = {&w->ht, &w->foo, &w->fvv, &w->wo, &w->r1, &w->r2, &w->A, &w->B, &w->Cq, &w->D, &w->t2f};
+                          (size_t)o * v * o * v, (size_t)o * o * v * v, (size_t)EGRID};
+  double** ptrs[] = {&w->ht, &w->foo, &w->fvv, &w->wo, &w->r1, &w->r2, &w->A, &w->B, &w->Cq, &w->D, &w->t2f,
+                     &w->epart};
   size_t off = 0;
-  for (int k = 0; k < 11; ++k) {
+  for (int k = 0; k < 12; ++k) {
     if (base) *ptrs[k] = reinterpret_cast<double*>(static_cast<char*>(base) + off);
     off += ((sizes[k] * sizeof(double) + 255) / 256) * 256;
+  }
+  w->acc = nullptr;
+  w->err = nullptr;
+  if (mixed) {
+    const size_t na = (size_t)v * v * v * o > (size_t)o * o * v * v ? (size_t)v * v * v * o : (size_t)o * o * v * v;
+    if (base) w->acc = reinterpret_cast<float*>(static_cast<char*>(base) + off);
+    off += ((na * sizeof(float) + 255) / 256) * 256;
+    if (base) w->err = reinterpret_cast<int*>(static_cast<char*>(base) + off);
+    off += 256;
   }
   return off;
 }
@@ -446,8 +480,15 @@ size_t dress_workspace_bytes(int n, int nocc) {
   return carve(nullptr, n, nocc, &w);
 }
 
+size_t dress_workspace_bytes_mixed(int n, int nocc) {
+  Work w;
+  return carve(nullptr, n, nocc, &w, true);
+}
+
 int dress_launch_count(int n, int nocc, bool mixed) {
-  return (n - nocc > 0 && nocc > 0) ? (mixed ? 19 : 17) : 4;
+  // copy, 4 T1 passes, h~, f~, 2 energy, small blocks, finalize; T2 terms: 7 SIMT kernels
+  // (FP64) or 2 FP32 copies + 16 GEMMs + 3 SIMT kernels + error check (mixed)
+  return (n - nocc > 0 && nocc > 0) ? (mixed ? 11 + 22 : 11 + 7) : 5;
 }
 
 namespace {
@@ -469,28 +510,433 @@ void t2_terms(const Dims& d, double* W, const T* G, const double* F, const T* t2
   k_vvvo<T><<<blocks_for(v * v * v * o), TPB, 0, st>>>(W, G, F, t2, d);
 }
 
+
+// ---- mixed precision: the T2 contractions as tensor-core GEMMs ----------------------------
+// Every contraction below is a GEMM over index pairs, D[(r1 r2)][(c1 c2)] = sum_k A(r, k) B(c, k),
+// with several terms of one output map concatenated along k (segments of o*v or v^2).  Loaders
+// read the FP32 copy g of g~ (after the T1 transform, before any T2 term) and the FP32 t2; the
+// stores add into FP32 scratch or, for blocks with a single GEMM, directly onto the FP64 base.
+struct TcCtx {
+  const float* g;   // g~ [n^4]
+  const float* t;   // t2 [o o v v]
+  const float* ra;  // ring intermediates [i a][n f] (A, B, Cq, D)
+  const float* rb;
+  const float* rc;
+  const float* rd;
+  const double* wo;  // dressed oooo block [k i l j] (FP64)
+  int n, o, v;
+  __device__ __forceinline__ float G(int p, int q, int r, int s) const {
+    return g[(((size_t)p * n + q) * n + r) * n + s];
+  }
+  __device__ __forceinline__ float T(int i, int j, int a, int b) const {
+    return t[(((size_t)i * o + j) * v + a) * v + b];
+  }
+  __device__ __forceinline__ float U(int i, int j, int a, int b) const { return 2.f * T(i, j, a, b) - T(i, j, b, a); }
+};
+
+// rings: rows (i, a), cols (n, f), k = (m, e)
+struct LRingA {  // sel 0: u[i m a e], 1: t[i m a e], 2: t[i m e a]
+  TcCtx c;
+  int sel;
+  __device__ float operator()(int r, int k) const {
+    const int i = r / c.v, a = r % c.v, m = k / c.v, e = k % c.v;
+    return sel == 0 ? c.U(i, m, a, e) : (sel == 1 ? c.T(i, m, a, e) : c.T(i, m, e, a));
+  }
+};
+struct LRingB {  // swap 0: g[m E n F], 1: g[m F n E]
+  TcCtx c;
+  int swap;
+  __device__ float operator()(int col, int k) const {
+    const int nn = col / c.v, f = col % c.v, m = k / c.v, e = k % c.v;
+    return swap ? c.G(m, c.o + f, nn, c.o + e) : c.G(m, c.o + e, nn, c.o + f);
+  }
+};
+struct StoreRows {
+  float* p;
+  int ld;
+  __device__ void operator()(int m, int n, float v) const { p[(size_t)m * ld + n] = v; }
+};
+
+// r2, ladder + oooo: rows (i, j), cols (a, b), k = (e, f) then (m, n)
+struct LR2G1A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    const int i = r / c.o, j = r % c.o, vv = c.v * c.v;
+    if (k < vv) return c.T(i, j, k / c.v, k % c.v);
+    k -= vv;
+    const int m = k / c.o, nn = k % c.o;
+    return (float)c.wo[(((size_t)m * c.o + i) * c.o + nn) * c.o + j];
+  }
+};
+struct LR2G1B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    const int a = col / c.v, b = col % c.v, vv = c.v * c.v;
+    if (k < vv) return c.G(c.o + a, c.o + k / c.v, c.o + b, c.o + k % c.v);
+    k -= vv;
+    return c.T(k / c.o, k % c.o, a, b);
+  }
+};
+// r2 accumulation at (i, j, a, b) from a GEMM whose rows / cols are pairs of (i|j, a|b)
+struct StoreR2 {
+  float* acc;
+  int o, v, mode;  // 0: (i a)(j b)  1: (j a)(i b)  2: (i b)(j a)  3: (j b)(i a)  4: (i j)(a b), set
+  __device__ void operator()(int r, int col, float val) const {
+    int i, j, a, b;
+    if (mode == 4) {
+      acc[(size_t)r * v * v + col] = val;
+      return;
+    }
+    const int r1 = r / v, r2 = r % v, c1 = col / v, c2 = col % v;
+    if (mode == 0) { i = r1; a = r2; j = c1; b = c2; }
+    else if (mode == 1) { j = r1; a = r2; i = c1; b = c2; }
+    else if (mode == 2) { i = r1; b = r2; j = c1; a = c2; }
+    else { j = r1; b = r2; i = c1; a = c2; }
+    acc[(((size_t)i * o + j) * v + a) * v + b] += val;
+  }
+};
+// rows (i, a), cols (j, b): linear rings through (m, e) and quadratic rings through (n, f)
+struct LR2G3A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    const int ov = c.o * c.v, seg = k / ov, kk = k % ov, i = r / c.v, a = r % c.v, m = kk / c.v, e = kk % c.v;
+    switch (seg) {
+      case 0: return c.U(i, m, a, e);
+      case 1: return c.T(i, m, a, e);
+      case 2: return c.ra[(size_t)r * ov + kk];
+      case 3: return c.rb[(size_t)r * ov + kk];
+      default: return c.rc[(size_t)r * ov + kk];
+    }
+  }
+};
+struct LR2G3B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    const int ov = c.o * c.v, seg = k / ov, kk = k % ov, j = col / c.v, b = col % c.v, m = kk / c.v, e = kk % c.v;
+    switch (seg) {
+      case 0: return c.G(m, c.o + e, c.o + b, j);
+      case 1: return -c.G(m, j, c.o + b, c.o + e);
+      case 2: return c.U(j, m, b, e);
+      case 3: return -c.T(j, m, b, e);
+      default: return c.T(j, m, e, b);
+    }
+  }
+};
+// rows (j, a), cols (i, b)
+struct LR2G4A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, j = r / c.v, a = r % c.v;
+    return (k < ov) ? c.T(j, kk / c.v, kk % c.v, a) : c.rd[(size_t)r * ov + kk];
+  }
+};
+struct LR2G4B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, i = col / c.v, b = col % c.v, m = kk / c.v, e = kk % c.v;
+    return (k < ov) ? -c.G(m, i, c.o + b, c.o + e) : c.T(i, m, e, b);
+  }
+};
+// rows (i, b), cols (j, a)
+struct LR2G5A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const { return c.T(r / c.v, k / c.v, k % c.v, r % c.v); }
+};
+struct LR2G5B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    return -c.G(k / c.v, col / c.v, c.o + col % c.v, c.o + k % c.v);
+  }
+};
+// rows (j, b), cols (i, a)
+struct LR2G6A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, j = r / c.v, b = r % c.v, m = kk / c.v, e = kk % c.v;
+    return (k < ov) ? c.U(j, m, b, e) : c.T(j, m, b, e);
+  }
+};
+struct LR2G6B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, i = col / c.v, a = col % c.v, m = kk / c.v, e = kk % c.v;
+    return (k < ov) ? c.G(m, c.o + e, c.o + a, i) : -c.G(m, i, c.o + a, c.o + e);
+  }
+};
+
+// vvvv: rows (a, b), cols (e, f), k = (m, n); W[a e b f] += D
+struct LV4A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const { return c.T(k / c.o, k % c.o, r / c.v, r % c.v); }
+};
+struct LV4B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    return c.G(k / c.o, c.o + col / c.v, k % c.o, c.o + col % c.v);
+  }
+};
+struct StoreV4 {
+  double* W;
+  int n, o, v;
+  __device__ void operator()(int r, int col, float val) const {
+    const size_t x = (((size_t)(o + r / v) * n + (o + col / v)) * n + (o + r % v)) * n + (o + col % v);
+    W[x] += (double)val;
+  }
+};
+
+// ovvo: rows (m, e), cols (j, b), k = (n, f) twice; W[m E B j] = W[B j m E] = base + D
+struct LOVA {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, m = r / c.v, e = r % c.v, nn = kk / c.v, f = kk % c.v;
+    return (k < ov) ? c.G(m, c.o + e, nn, c.o + f) : -c.G(m, c.o + f, nn, c.o + e);
+  }
+};
+struct LOVB {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, j = col / c.v, b = col % c.v, nn = kk / c.v, f = kk % c.v;
+    return (k < ov) ? c.U(j, nn, b, f) : c.T(j, nn, b, f);
+  }
+};
+struct StoreOV {
+  double* W;
+  int n, o, v;
+  __device__ void operator()(int r, int col, float val) const {
+    const int m = r / v, E = o + r % v, j = col / v, B = o + col % v;
+    const size_t x = (((size_t)m * n + E) * n + B) * n + j, y = (((size_t)B * n + j) * n + m) * n + E;
+    const double w = W[x] + (double)val;
+    W[x] = w;
+    W[y] = w;
+  }
+};
+
+// oovv: rows (i, b), cols (j, a), k = (n, f); W[i j A B] = W[A B i j] = base + D
+struct LOOA {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    return c.G(r / c.v, c.o + k % c.v, k / c.v, c.o + r % c.v);
+  }
+};
+struct LOOB {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const { return -c.T(col / c.v, k / c.v, k % c.v, col % c.v); }
+};
+struct StoreOO {
+  double* W;
+  int n, o, v;
+  __device__ void operator()(int r, int col, float val) const {
+    const int i = r / v, B = o + r % v, j = col / v, A = o + col % v;
+    const size_t x = (((size_t)i * n + j) * n + A) * n + B, y = (((size_t)A * n + B) * n + i) * n + j;
+    const double w = W[x] + (double)val;
+    W[x] = w;
+    W[y] = w;
+  }
+};
+
+// oovo, the v^2 term: rows (m, b), cols (i, j), k = (e, f) -> acc[m i b j]
+struct LOVOA {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    return c.G(r / c.v, c.o + k / c.v, c.o + r % c.v, c.o + k % c.v);
+  }
+};
+struct LOVOB {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const { return c.T(col / c.o, col % c.o, k / c.v, k % c.v); }
+};
+struct StoreOVO {
+  float* acc;
+  int o, v;
+  __device__ void operator()(int r, int col, float val) const {
+    const int m = r / v, b = r % v, i = col / o, j = col % o;
+    acc[(((size_t)m * o + i) * v + b) * o + j] = val;
+  }
+};
+
+// vvvo: acc[a e b i] from three GEMMs
+struct LVV1A {  // rows (a, e), k = (m, f) twice: g[m F A E], -g[m E A F]
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, a = r / c.v, e = r % c.v, m = kk / c.v, f = kk % c.v;
+    return (k < ov) ? c.G(m, c.o + f, c.o + a, c.o + e) : -c.G(m, c.o + e, c.o + a, c.o + f);
+  }
+};
+struct LVV1B {  // cols (b, i): u[m i f b], t[m i f b]
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    const int ov = c.o * c.v, kk = k % ov, b = col / c.o, i = col % c.o, m = kk / c.v, f = kk % c.v;
+    return (k < ov) ? c.U(m, i, f, b) : c.T(m, i, f, b);
+  }
+};
+struct LVV2A {  // rows (a, b), k = (m, n): t[m n a b]
+  TcCtx c;
+  __device__ float operator()(int r, int k) const { return c.T(k / c.o, k % c.o, r / c.v, r % c.v); }
+};
+struct LVV2B {  // cols (e, i): g[m E n i]
+  TcCtx c;
+  __device__ float operator()(int col, int k) const { return c.G(k / c.o, c.o + col / c.o, k % c.o, col % c.o); }
+};
+struct LVV3A {  // rows (e, b), k = (m, f): -g[m E B F]
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    return -c.G(k / c.v, c.o + r / c.v, c.o + r % c.v, c.o + k % c.v);
+  }
+};
+struct LVV3B {  // cols (a, i): t[m i a f]
+  TcCtx c;
+  __device__ float operator()(int col, int k) const { return c.T(k / c.v, col % c.o, col / c.o, k % c.v); }
+};
+struct StoreVV {
+  float* acc;
+  int o, v, mode;  // 0: (a e)(b i) set  1: (a b)(e i) add  2: (e b)(a i) add
+  __device__ void operator()(int r, int col, float val) const {
+    int a, e, b, i;
+    if (mode == 0) { a = r / v; e = r % v; b = col / o; i = col % o; }
+    else if (mode == 1) { a = r / v; b = r % v; e = col / o; i = col % o; }
+    else { e = r / v; b = r % v; a = col / o; i = col % o; }
+    const size_t x = (((size_t)a * v + e) * v + b) * o + i;
+    if (mode == 0) acc[x] = val;
+    else acc[x] += val;
+  }
+};
+
+// r2 = bare vo|vo + GEMM part + the O(v) Fock terms (FP32), added in FP64
+__global__ void k_r2_fin(const double* __restrict__ W, const float* __restrict__ t2, const double* __restrict__ foo,
+                         const double* __restrict__ fvv, const float* __restrict__ acc, double* __restrict__ r2,
+                         Dims d) {
+  const size_t m_all = (size_t)d.o * d.o * d.v * d.v;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
+  const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
+  float v = acc[x];
+  for (int e = 0; e < d.v; ++e)
+    v += (float)fvv[b * d.v + e] * t2[ti(d, i, j, a, e)] + (float)fvv[a * d.v + e] * t2[ti(d, i, j, e, b)];
+  for (int m = 0; m < d.o; ++m)
+    v -= (float)foo[m * d.o + j] * t2[ti(d, i, m, a, b)] + (float)foo[m * d.o + i] * t2[ti(d, m, j, a, b)];
+  r2[x] = W[gi(d, d.o + a, i, d.o + b, j)] + (double)v;
+}
+
+// oovo: the GEMM's v^2 term plus the O(v) and O(ov) terms, onto the FP64 base and its mirror
+__global__ void k_oovo_fin(double* __restrict__ W, const float* __restrict__ G, const double* __restrict__ F,
+                           const float* __restrict__ t2, const float* __restrict__ acc, Dims d) {
+  const size_t m_all = (size_t)d.o * d.o * d.v * d.o;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int m = (int)(x / ((size_t)d.o * d.v * d.o)), i = (int)((x / ((size_t)d.v * d.o)) % d.o);
+  const int b = (int)((x / d.o) % d.v), j = (int)(x % d.o);
+  const int B_ = d.o + b;
+  float v = acc[x];
+  for (int e = 0; e < d.v; ++e) {
+    const int E_ = d.o + e;
+    v += (float)F[m * d.n + E_] * t2[ti(d, i, j, e, b)];
+    for (int nn = 0; nn < d.o; ++nn)
+      v += G[gi(d, m, i, nn, E_)] * Ut(t2, d, j, nn, b, e) - G[gi(d, m, E_, nn, i)] * t2[ti(d, j, nn, b, e)] -
+           G[gi(d, m, E_, nn, j)] * t2[ti(d, i, nn, e, b)];
+  }
+  const double w = W[gi(d, m, i, B_, j)] + (double)v;
+  W[gi(d, m, i, B_, j)] = w;
+  W[gi(d, B_, j, m, i)] = w;
+}
+
+// vvvo: GEMM part minus the f~ term, onto the FP64 base and its mirror
+__global__ void k_vvvo_fin(double* __restrict__ W, const double* __restrict__ F, const float* __restrict__ t2,
+                           const float* __restrict__ acc, Dims d) {
+  const size_t m_all = (size_t)d.v * d.v * d.v * d.o;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= m_all) return;
+  const int a = (int)(x / ((size_t)d.v * d.v * d.o)), e = (int)((x / ((size_t)d.v * d.o)) % d.v);
+  const int b = (int)((x / d.o) % d.v), i = (int)(x % d.o);
+  const int A_ = d.o + a, E_ = d.o + e, B_ = d.o + b;
+  float v = acc[x];
+  for (int m = 0; m < d.o; ++m) v -= (float)F[m * d.n + E_] * t2[ti(d, m, i, a, b)];
+  const double w = W[gi(d, A_, E_, B_, i)] + (double)v;
+  W[gi(d, A_, E_, B_, i)] = w;
+  W[gi(d, B_, i, A_, E_)] = w;
+}
+
+// A tensor-core tile that gave up waiting poisons E0, so the sweep reports a non-finite energy.
+__global__ void k_gemm_check(const int* __restrict__ err, double* __restrict__ e0) {
+  if (threadIdx.x == 0 && *err) *e0 = nan("");
+}
+
+template <int BN, class LA, class LB, class ST>
+cudaError_t run_gemm(int M, int N, int K, LA la, LB lb, ST st, int* err, cudaStream_t s) {
+  return tc::gemm_tf32x3<BN>(M, N, K, la, lb, st, err, s);
+}
+
+cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* F, const float* t2, const Work& w,
+                        double* e0, cudaStream_t st) {
+  const int o = d.o, v = d.v, ov = o * v, vv = v * v, oo = o * o;
+  float* A = reinterpret_cast<float*>(w.A);
+  float* B = reinterpret_cast<float*>(w.B);
+  float* Cq = reinterpret_cast<float*>(w.Cq);
+  float* D = reinterpret_cast<float*>(w.D);
+  TcCtx c{G, t2, A, B, Cq, D, w.wo, d.n, o, v};
+  int* err = w.err;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  // ring intermediates
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 0}, LRingB{c, 0}, StoreRows{A, ov}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 0}, LRingB{c, 1}, StoreRows{B, ov}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 1}, LRingB{c, 1}, StoreRows{Cq, ov}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 2}, LRingB{c, 1}, StoreRows{D, ov}, err, st);
+  // r2
+  float* acc = w.acc;
+  if (e == cudaSuccess) e = run_gemm<64>(oo, vv, vv + oo, LR2G1A{c}, LR2G1B{c}, StoreR2{acc, o, v, 4}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 5 * ov, LR2G3A{c}, LR2G3B{c}, StoreR2{acc, o, v, 0}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 2 * ov, LR2G4A{c}, LR2G4B{c}, StoreR2{acc, o, v, 1}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LR2G5A{c}, LR2G5B{c}, StoreR2{acc, o, v, 2}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 2 * ov, LR2G6A{c}, LR2G6B{c}, StoreR2{acc, o, v, 3}, err, st);
+  if (e != cudaSuccess) return e;
+  k_r2_fin<<<blocks_for((size_t)oo * vv), TPB, 0, st>>>(W, t2, w.foo, w.fvv, acc, w.r2, d);
+  // blocks written in place (their bases are read from W by the store of their single GEMM)
+  e = run_gemm<128>(vv, vv, oo, LV4A{c}, LV4B{c}, StoreV4{W, d.n, o, v}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 2 * ov, LOVA{c}, LOVB{c}, StoreOV{W, d.n, o, v}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LOOA{c}, LOOB{c}, StoreOO{W, d.n, o, v}, err, st);
+  if (e == cudaSuccess) e = run_gemm<32>(ov, oo, vv, LOVOA{c}, LOVOB{c}, StoreOVO{acc, o, v}, err, st);
+  if (e != cudaSuccess) return e;
+  k_oovo_fin<<<blocks_for((size_t)oo * v * o), TPB, 0, st>>>(W, G, F, t2, acc, d);
+  e = run_gemm<128>(vv, v * o, 2 * ov, LVV1A{c}, LVV1B{c}, StoreVV{acc, o, v, 0}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(vv, v * o, oo, LVV2A{c}, LVV2B{c}, StoreVV{acc, o, v, 1}, err, st);
+  if (e == cudaSuccess) e = run_gemm<128>(vv, v * o, ov, LVV3A{c}, LVV3B{c}, StoreVV{acc, o, v, 2}, err, st);
+  if (e != cudaSuccess) return e;
+  k_vvvo_fin<<<blocks_for((size_t)vv * v * o), TPB, 0, st>>>(W, F, t2, acc, d);
+  k_gemm_check<<<1, 32, 0, st>>>(err, e0);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
                          double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st,
                          float* g32) {
   Work w;
-  if (work_bytes < carve(nullptr, n, nocc, &w)) return cudaErrorInvalidValue;
-  carve(work, n, nocc, &w);
+  const bool mixed = g32 != nullptr;
+  if (work_bytes < carve(nullptr, n, nocc, &w, mixed)) return cudaErrorInvalidValue;
+  carve(work, n, nocc, &w, mixed);
   Dims d{n, nocc, n - nocc};
   const size_t n4 = (size_t)n * n * n * n;
   const size_t o = nocc, v = n - nocc;
   k_copy<<<blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
   if (v > 0 && o > 0) {
     const size_t mc = v * n * n * n, ma = o * n * n * n;
-    k_t1_creator<<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
-    k_t1_creator<<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
-    k_t1_annihilator<<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
-    k_t1_annihilator<<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 3);
+    if (mixed) {  // FP32 correction sums onto the FP64 elements
+      k_t1_creator<float><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
+      k_t1_creator<float><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
+      k_t1_annihilator<float><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
+      k_t1_annihilator<float><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 3);
+    } else {
+      k_t1_creator<double><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
+      k_t1_creator<double><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
+      k_t1_annihilator<double><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
+      k_t1_annihilator<double><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 3);
+    }
   }
   k_h_tilde<<<blocks_for((size_t)n * n), TPB, 0, st>>>(h, t1, w.ht, d);
   k_fock<<<blocks_for((size_t)n * n), TPB, 0, st>>>(w.ht, W, F, d);
-  k_energy<<<1, TPB, 0, st>>>(w.ht, W, t2, e0, d);
+  k_energy_part<<<EGRID, TPB, 0, st>>>(w.ht, W, t2, w.epart, d);
+  k_energy_sum<<<1, EGRID, 0, st>>>(w.epart, e0);
   if (v > 0 && o > 0) {
     k_small_blocks<<<(unsigned)(o * o + v * v + v * o + o * o * o * o), TPB, 0, st>>>(F, W, t2, w.foo, w.fvv, w.r1,
                                                                                      w.wo, d);
@@ -499,7 +945,8 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
       const unsigned gg = blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4);
       k_to_f32<<<gg, TPB, 0, st>>>(W, g32, n4);
       k_to_f32<<<blocks_for(o * o * v * v), TPB, 0, st>>>(t2, t2f, o * o * v * v);
-      t2_terms<float>(d, W, g32, F, t2f, w, st);
+      cudaError_t e = t2_terms_tc(d, W, g32, F, t2f, w, e0, st);
+      if (e != cudaSuccess) return e;
     } else {
       t2_terms<double>(d, W, W, F, t2, w, st);
     }

@@ -316,7 +316,8 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   }
   const size_t n1 = n, n4 = n1 * n1 * n1 * n1;
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-  c->dwork_bytes = qf::dress_workspace_bytes(n, nocc);
+  c->dwork_bytes = (c->opt.precision == QFLOW_PREC_MIXED) ? qf::dress_workspace_bytes_mixed(n, nocc)
+                                                          : qf::dress_workspace_bytes(n, nocc);
   const size_t npool = (size_t)(c->n_t1 + c->n_t2);
   if (e == cudaSuccess) e = dalloc(&c->h, n1 * n1);
   if (e == cudaSuccess) e = dalloc(&c->eri, n4);

@@ -54,6 +54,7 @@ cudaError_t launch_to_f32(const double* W, float* W32, size_t count, cudaStream_
 
 // Dressing (step a) on caller-provided device buffers; returns a CUDA error code.
 size_t dress_workspace_bytes(int n, int nocc);
+size_t dress_workspace_bytes_mixed(int n, int nocc);  // + FP32 GEMM scratch of the mixed path
 int dress_launch_count(int n, int nocc, bool mixed);  // kernels one launch_dress issues
 // g32: NULL for FP64 contractions; else n^4 floats of scratch, and the T2 terms are contracted
 // in FP32 (mixed precision).

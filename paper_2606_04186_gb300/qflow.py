@@ -84,6 +84,7 @@ def lib() -> C.CDLL:
         "qflow_mlp_features_device": (I32, [I32, P, P, P, I64, P, P]),
         "qflow_mlp_targets_device": (I32, [P, I64, P, P]),
         "qflow_mlp_guess_device": (I32, [P, I64, P, P]),
+        "qflow_gemm_tf32x3_device": (I32, [I32, I32, I32, P, I32, P, I32, P, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -356,3 +357,11 @@ def mlp_targets_device(roots, targets, stream: int = 0):
 def mlp_guess_device(y, guess, stream: int = 0):
     _check(lib().qflow_mlp_guess_device(_dptr(y), y.shape[0], _dptr(guess), stream or None),
            "qflow_mlp_guess_device")
+
+
+def gemm_tf32x3_device(A, B, C, err, stream: int = 0):
+    """C = A @ B.T on the tensor cores (row-major float32 CUDA tensors; err: int32[1])."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().qflow_gemm_tf32x3_device(M, N, K, _dptr(A), A.stride(0), _dptr(B), B.stride(0), _dptr(C),
+                                          C.stride(0), _dptr(err), stream or None), "qflow_gemm_tf32x3_device")

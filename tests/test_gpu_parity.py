@@ -225,7 +225,8 @@ def test_diis_flow_matches_oracle(qf):
 
 
 def test_mixed_dressing_close_to_oracle(qf):
-    """Mixed path: T2 contractions in FP32 on FP64 bases; E0 and the Fock blocks stay FP64."""
+    """Mixed path: FP64 integrals with FP32 T1 correction sums (E0 and the Fock blocks follow
+    them to ~1e-10), T2 contractions on the tensor cores onto FP64 bases."""
     eps, h, g, sp = synth.system_inputs("n24")
     s = synth.SYSTEMS["n24"]
     no, nv = s.nocc, s.n - s.nocc
@@ -234,8 +235,8 @@ def test_mixed_dressing_close_to_oracle(qf):
     gpu.set_amplitudes(t1, t2)
     e0, F, W = gpu.dressed()
     e0r, Fr, Wr = hbar.hbar2(h, g, t1, t2, no)
-    assert abs(e0 - e0r) < 1e-11
-    assert np.abs(F - Fr).max() < 1e-11
+    assert abs(e0 - e0r) < 1e-9
+    assert np.abs(F - Fr).max() < 1e-9
     assert np.abs(W - Wr).max() < 1e-6
     gpu.close()
 
