@@ -105,6 +105,69 @@ struct TabHolder {
   static constexpr Tab3 value = make_tab3();
 };
 
+// Same-spin string operator of the 6e6o class as a list of coupling paths per string I:
+//   Hs[I][J] = sum_u [J_u = J] s_u h'[pq_u] + 1/2 sum_{u,v} [J(J_u, v) = J] s_u s_v W[pq_u][pq_v],
+// J != I, u over the replacements into I and v over those into J_u.  Entry k of string I is
+// e[k][I]: bits 0-10 source (W index pq_u * 36 + pq_v, or 1296 + pq_u for h'), bit 11 sign,
+// bits 12-16 target J, bit 17 last entry of its target (grouped by target, so a row is summed
+// in registers and each entry stored once).  The same for every space: built at compile time.
+constexpr int kHsPaths = 9 + 126;  // one-body and two-body paths per string
+struct HsPaths {
+  unsigned e[kHsPaths * 20];
+};
+__host__ __device__ constexpr HsPaths make_hs_paths() {
+  HsPaths h{};
+  constexpr Tab3 t = make_tab3();
+  for (int I = 0; I < 20; ++I) {
+    unsigned src[kHsPaths] = {}, tgt[kHsPaths] = {};
+    int n = 0;
+    for (int u = 0; u < 12; ++u) {
+      const int Ku = t.J[I][u];
+      if (Ku != I && n < kHsPaths) {
+        src[n] = (unsigned)(1296 + t.pq[I][u]) | (t.sg[I][u] < 0 ? 2048u : 0u);
+        tgt[n] = (unsigned)Ku;
+        ++n;
+      }
+      for (int v = 0; v < 12; ++v) {
+        const int J2 = t.J[Ku][v];
+        if (J2 == I || n >= kHsPaths) continue;
+        const int sgn = t.sg[I][u] * t.sg[Ku][v];
+        src[n] = (unsigned)(t.pq[I][u] * 36 + t.pq[Ku][v]) | (sgn < 0 ? 2048u : 0u);
+        tgt[n] = (unsigned)J2;
+        ++n;
+      }
+    }
+    // stable grouping by target
+    int k = 0;
+    for (int J = 0; J < 20; ++J) {
+      int last = -1;
+      for (int x = 0; x < n; ++x)
+        if ((int)tgt[x] == J) {
+          h.e[k * 20 + I] = src[x] | (tgt[x] << 12);
+          last = k;
+          ++k;
+        }
+      if (last >= 0) h.e[last * 20 + I] |= 1u << 17;
+    }
+  }
+  return h;
+}
+__host__ __device__ constexpr bool hs_paths_complete() {  // every string has exactly kHsPaths
+  constexpr Tab3 t = make_tab3();
+  for (int I = 0; I < 20; ++I) {
+    int n = 0;
+    for (int u = 0; u < 12; ++u) {
+      if (t.J[I][u] != I) ++n;
+      for (int v = 0; v < 12; ++v)
+        if (t.J[t.J[I][u]][v] != I) ++n;
+    }
+    if (n != kHsPaths) return false;
+  }
+  return true;
+}
+static_assert(hs_paths_complete(), "uniform path count per 6e6o string");
+__device__ const HsPaths g_hs_paths = make_hs_paths();
+
 template <int B, int V>
 __device__ __forceinline__ void ab_term(float (&acc)[20], const float (&wr)[36], const float (&cr)[20]) {
   constexpr int pq = TabHolder::value.pq[B][V];
@@ -727,9 +790,77 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       __syncwarp();
       return;
     }
+    // the diagonal relative to <Phi|H|Phi> (diag_at): string parts as FP64 differences, the
+    // alpha-beta Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
+    if (lane < NS) ws.dh[lane] = (float)(su.hsd[lane] - su.hsd[0]);
+#pragma unroll 1
+    for (int t = lane; t < NORB * NS; t += 32) {
+      const int p = t / NS, b = t % NS;
+      float v = 0.f;
+#pragma unroll
+      for (int l = 0; l < K; ++l) v += (float)su.J[p * NORB + tb.occ[b][l]];
+      ws.jb[t] = v;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      float j0 = 0.f;
+      for (int l = 0; l < K; ++l) j0 += ws.jb[tb.occ[0][l] * NS + 0];
+      ws.j0 = j0;
+    }
+    __syncwarp();
+    // Without a guess, the first-order correction from Phi is r / (0 - diag); when its norm is
+    // below what FP32 vectors resolve (1e-6) the space stays at Phi (energy error below
+    // |r| * 1e-6), decided here before the string operator is built.
+    if (!guess_in) {
+      float nn = 0.f;
+      for (int d = lane; d < NDET; d += 32) {
+        float den = -diag_at<K>(tb, ws, d / NS, d % NS);
+        if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
+        const float v = ws.S[d] / den;
+        nn = fmaf(v, v, nn);
+      }
+      const float vn = sqrtf(wsum(nn));
+      if (!(vn > 1e-6f)) {
+        const int st = (rphi < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
+        if (lane == 0) {
+          a.energy[oidx] = ws.eshift;
+          a.status[oidx] = st;
+          if (a.iters) a.iters[oidx] = 0;
+        }
+        if (guess_out && st == kSpaceOk)
+          for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (d == 0) ? 1.f : 0.f;
+        __syncwarp();
+        return;
+      }
+    }
   }
   // ---- same-spin string operator, off-diagonal (row I owned by lane I) ---------------------
-  if (lane < NS) {
+  if constexpr (K == 3) {
+    if (lane < NS) {
+      const int I = lane;
+#pragma unroll 1
+      for (int j = 0; j < NS; ++j) ws.Hs[I * NS + j] = 0.f;
+      float acc1 = 0.f, acc2 = 0.f;  // one-body and (doubled) two-body parts of the current target
+#pragma unroll 5
+      for (int k = 0; k < kHsPaths; ++k) {
+        const unsigned e = __ldg(&g_hs_paths.e[k * 20 + I]);
+        const int src = (int)(e & 2047u);
+        const bool neg = (e & 2048u) != 0;
+        if (src >= 1296) {
+          const float h = ws.hp[src - 1296];
+          acc1 += neg ? -h : h;
+        } else {
+          const float w = ws.Wt[src];
+          acc2 += neg ? -w : w;
+        }
+        if (e & (1u << 17)) {
+          ws.Hs[I * NS + ((e >> 12) & 31u)] = acc1 + 0.5f * acc2;
+          acc1 = 0.f;
+          acc2 = 0.f;
+        }
+      }
+    }
+  } else if (lane < NS) {
     const int I = lane;
 #pragma unroll 1
     for (int j = 0; j < NS; ++j) ws.Hs[I * NS + j] = 0.f;
@@ -748,24 +879,6 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       }
     }
   }
-  // the diagonal relative to <Phi|H|Phi> (diag_at): string parts as FP64 differences, the
-  // alpha-beta Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
-  if (lane < NS) ws.dh[lane] = (float)(su.hsd[lane] - su.hsd[0]);
-#pragma unroll 1
-  for (int t = lane; t < NORB * NS; t += 32) {
-    const int p = t / NS, b = t % NS;
-    float v = 0.f;
-#pragma unroll
-    for (int l = 0; l < K; ++l) v += (float)su.J[p * NORB + tb.occ[b][l]];
-    ws.jb[t] = v;
-  }
-  __syncwarp();
-  if (lane == 0) {
-    float j0 = 0.f;
-    for (int l = 0; l < K; ++l) j0 += ws.jb[tb.occ[0][l] * NS + 0];
-    ws.j0 = j0;
-  }
-  __syncwarp();
   // ---- caller's guess: subspace {Phi, g - g_Phi Phi}; its sigma counts as one iteration -------
   int it0 = 0;
   if (guess_in && KM >= 2) {
@@ -873,31 +986,51 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       break;
     }
     __syncwarp();
-    for (int pass = 0; pass < 2; ++pass) {
-      float cf[KM];
+    // expansion vector: the preconditioned residual, orthogonalised against the subspace.  When
+    // that leaves (almost) nothing while the residual is still above 100 x tol, the residual
+    // itself (orthogonal to the subspace at a Ritz pair) is used instead, so the loop does not
+    // stall on a correction that lies in the subspace
+    float vn = 0.f;
+#pragma unroll 1
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (attempt == 1) {
+        for (int d = lane; d < NDET; d += 32) {
+          float xv = 0.f, sv = 0.f;
+          for (int j = 0; j < k; ++j) {
+            xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+            sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
+          }
+          vk[d] = sv - th * xv;
+        }
+        __syncwarp();
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        float cf[KM];
 #pragma unroll
-      for (int j = 0; j < KM; ++j) cf[j] = 0.f;
-      for (int d = lane; d < NDET; d += 32) {
-        const float v = vk[d];
+        for (int j = 0; j < KM; ++j) cf[j] = 0.f;
+        for (int d = lane; d < NDET; d += 32) {
+          const float v = vk[d];
+#pragma unroll
+          for (int j = 0; j < KM; ++j)
+            if (j < k) cf[j] = fmaf(ws.V[j * NDET + d], v, cf[j]);
+        }
 #pragma unroll
         for (int j = 0; j < KM; ++j)
-          if (j < k) cf[j] = fmaf(ws.V[j * NDET + d], v, cf[j]);
-      }
+          if (j < k) cf[j] = wsum(cf[j]);
+        for (int d = lane; d < NDET; d += 32) {
+          float v = vk[d];
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
-        if (j < k) cf[j] = wsum(cf[j]);
-      for (int d = lane; d < NDET; d += 32) {
-        float v = vk[d];
-#pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < k) v = fmaf(-cf[j], ws.V[j * NDET + d], v);
-        vk[d] = v;
+          for (int j = 0; j < KM; ++j)
+            if (j < k) v = fmaf(-cf[j], ws.V[j * NDET + d], v);
+          vk[d] = v;
+        }
+        __syncwarp();
       }
-      __syncwarp();
+      float nn = 0.f;
+      for (int d = lane; d < NDET; d += 32) nn = fmaf(vk[d], vk[d], nn);
+      vn = sqrtf(wsum(nn));
+      if (vn > 1e-6f || rnorm < 100.f * tol) break;
     }
-    float nn = 0.f;
-    for (int d = lane; d < NDET; d += 32) nn = fmaf(vk[d], vk[d], nn);
-    const float vn = sqrtf(wsum(nn));
     if (!(vn > 1e-6f)) {  // the subspace cannot grow (complete or stagnated)
       if (lane == 0) {
         ws.ctrl[2] = (rnorm < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
