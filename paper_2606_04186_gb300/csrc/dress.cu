@@ -43,6 +43,36 @@ __global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst,
     dst[x] = src[x];
 }
 
+// IEEE-754 conversions between binary64 and binary32 by field arithmetic on the integer pipe
+// (GB300 converts floating types on its slow FP64 pipe).  double -> float truncates the
+// significand (error below one float ulp) and flushes values below the normal float range to
+// zero; float -> double is exact for normal floats (subnormals flush to zero).  Used only for
+// the mixed path's FP32 correction sums, whose operands are normal and far from overflow.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int ef = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)ef << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f), sign = u & 0x80000000u, e = (u >> 23) & 0xFFu;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  const unsigned hi = sign | ((e - 127u + 1023u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 7u) << 29));
+}
+template <typename A>
+__device__ __forceinline__ A to_acc(double x) {
+  if constexpr (sizeof(A) == 4) return d2f_bits(x);
+  else return x;
+}
+template <typename A>
+__device__ __forceinline__ double from_acc(A x) {
+  if constexpr (sizeof(A) == 4) return f2d_bits(x);
+  else return x;
+}
+
 // Creator index `pos` (0 or 2): rows p >= nocc get  - sum_i t1[i][p-nocc] * row_i.
 // The correction sum runs in precision A (FP64, or FP32 for the mixed path) and is added to
 // the FP64 element.
@@ -55,11 +85,11 @@ __global__ void k_t1_creator(double* __restrict__ W, const double* __restrict__ 
     const int u = (int)(rest / ((size_t)d.n * d.n)), w = (int)((rest / d.n) % d.n), z = (int)(rest % d.n);
     A acc = 0;
     if (pos == 0) {
-      for (int i = 0; i < d.o; ++i) acc += (A)t1[i * d.v + a] * (A)W[gi(d, i, u, w, z)];
-      W[gi(d, d.o + a, u, w, z)] -= (double)acc;
+      for (int i = 0; i < d.o; ++i) acc += to_acc<A>(t1[i * d.v + a]) * to_acc<A>(W[gi(d, i, u, w, z)]);
+      W[gi(d, d.o + a, u, w, z)] -= from_acc<A>(acc);
     } else {
-      for (int i = 0; i < d.o; ++i) acc += (A)t1[i * d.v + a] * (A)W[gi(d, u, w, i, z)];
-      W[gi(d, u, w, d.o + a, z)] -= (double)acc;
+      for (int i = 0; i < d.o; ++i) acc += to_acc<A>(t1[i * d.v + a]) * to_acc<A>(W[gi(d, u, w, i, z)]);
+      W[gi(d, u, w, d.o + a, z)] -= from_acc<A>(acc);
     }
   }
 }
@@ -74,12 +104,88 @@ __global__ void k_t1_annihilator(double* __restrict__ W, const double* __restric
     const int u = (int)(rest / ((size_t)d.n * d.n)), w = (int)((rest / d.n) % d.n), z = (int)(rest % d.n);
     A acc = 0;
     if (pos == 1) {
-      for (int a = 0; a < d.v; ++a) acc += (A)t1[q * d.v + a] * (A)W[gi(d, u, d.o + a, w, z)];
-      W[gi(d, u, q, w, z)] += (double)acc;
+      for (int a = 0; a < d.v; ++a) acc += to_acc<A>(t1[q * d.v + a]) * to_acc<A>(W[gi(d, u, d.o + a, w, z)]);
+      W[gi(d, u, q, w, z)] += from_acc<A>(acc);
     } else {
-      for (int a = 0; a < d.v; ++a) acc += (A)t1[q * d.v + a] * (A)W[gi(d, u, w, z, d.o + a)];
-      W[gi(d, u, w, z, q)] += (double)acc;
+      for (int a = 0; a < d.v; ++a) acc += to_acc<A>(t1[q * d.v + a]) * to_acc<A>(W[gi(d, u, w, z, d.o + a)]);
+      W[gi(d, u, w, z, q)] += from_acc<A>(acc);
     }
+  }
+}
+
+// The same four passes with each element read once per pass: thread per index triple (the
+// three positions other than the transformed one), t1 in shared memory, the occupied-index
+// values (creator) or the o accumulators (annihilator) in registers.  Used when o <= kT1Omax.
+constexpr int kT1Omax = 16;
+
+template <typename A, int POS>
+__device__ __forceinline__ size_t t1_index(const Dims& d, int p, size_t rest) {
+  const size_t n1 = d.n, n2 = n1 * n1;
+  const size_t u = rest / n2, w = (rest / n1) % n1, z = rest % n1;
+  // the transformed index p sits at position POS; (u, w, z) fill the other three in order
+  if constexpr (POS == 0) return ((size_t)p * n1 + u) * n2 + w * n1 + z;
+  else if constexpr (POS == 1) return ((u * n1 + p) * n1 + w) * n1 + z;
+  else if constexpr (POS == 2) return ((u * n1 + w) * n1 + p) * n1 + z;
+  else return ((u * n1 + w) * n1 + z) * n1 + p;
+}
+
+template <typename A, int POS>
+__global__ void k_t1_creator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
+  extern __shared__ double t1s[];  // [o][v]
+  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = t1[x];
+  __syncthreads();
+  const size_t m = (size_t)d.n * d.n * d.n;
+  for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
+    A wi[kT1Omax];
+#pragma unroll
+    for (int i = 0; i < kT1Omax; ++i) wi[i] = (i < d.o) ? to_acc<A>(W[t1_index<A, POS>(d, i, rest)]) : (A)0;
+    for (int a = 0; a < d.v; ++a) {
+      A acc = 0;
+#pragma unroll
+      for (int i = 0; i < kT1Omax; ++i)
+        if (i < d.o) acc += to_acc<A>(t1s[i * d.v + a]) * wi[i];
+      W[t1_index<A, POS>(d, d.o + a, rest)] -= from_acc<A>(acc);
+    }
+  }
+}
+
+template <typename A, int POS>
+__global__ void k_t1_annihilator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
+  extern __shared__ double t1s[];
+  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = t1[x];
+  __syncthreads();
+  const size_t m = (size_t)d.n * d.n * d.n;
+  for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
+    A acc[kT1Omax];
+#pragma unroll
+    for (int q = 0; q < kT1Omax; ++q) acc[q] = 0;
+    for (int a = 0; a < d.v; ++a) {
+      const A wa = to_acc<A>(W[t1_index<A, POS>(d, d.o + a, rest)]);
+#pragma unroll
+      for (int q = 0; q < kT1Omax; ++q)
+        if (q < d.o) acc[q] += to_acc<A>(t1s[q * d.v + a]) * wa;
+    }
+#pragma unroll
+    for (int q = 0; q < kT1Omax; ++q)
+      if (q < d.o) W[t1_index<A, POS>(d, q, rest)] += from_acc<A>(acc[q]);
+  }
+}
+
+template <typename A>
+void t1_passes(double* W, const double* t1, const Dims& d, cudaStream_t st) {
+  const size_t mc = (size_t)d.v * d.n * d.n * d.n, ma = (size_t)d.o * d.n * d.n * d.n;
+  if (d.o <= kT1Omax) {
+    const size_t n3 = (size_t)d.n * d.n * d.n, sm = sizeof(double) * d.o * d.v;
+    const unsigned g = blocks_for(n3) > 152u * 16u ? 152u * 16u : blocks_for(n3);
+    k_t1_creator_fast<A, 0><<<g, TPB, sm, st>>>(W, t1, d);
+    k_t1_creator_fast<A, 2><<<g, TPB, sm, st>>>(W, t1, d);
+    k_t1_annihilator_fast<A, 1><<<g, TPB, sm, st>>>(W, t1, d);
+    k_t1_annihilator_fast<A, 3><<<g, TPB, sm, st>>>(W, t1, d);
+  } else {
+    k_t1_creator<A><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
+    k_t1_creator<A><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
+    k_t1_annihilator<A><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
+    k_t1_annihilator<A><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 3);
   }
 }
 
@@ -434,9 +540,12 @@ __global__ void k_finalize(double* __restrict__ W, double* __restrict__ F, const
 struct Work {
   double *ht, *foo, *fvv, *wo, *r1, *r2, *A, *B, *Cq, *D, *t2f;  // A..D, t2f hold T values
   double* epart;  // energy partials
-  float* acc;     // mixed path: FP32 GEMM accumulation (v^3 o floats)
+  float* acc;     // mixed path: FP32 GEMM results (v^3 o floats)
   int* err;       // mixed path: set by a GEMM tile that gave up waiting
+  float* arena;   // mixed path: packed GEMM operands and partial products
 };
+
+size_t tc_arena_floats(int n, int nocc);
 
 size_t carve(void* base, int n, int o, Work* w, bool mixed = false) {
   const int v = n - o;
@@ -452,12 +561,15 @@ size_t carve(void* base, int n, int o, Work* w, bool mixed = false) {
   }
   w->acc = nullptr;
   w->err = nullptr;
-  if (mixed) {
+  w->arena = nullptr;
+  if (mixed && v > 0 && o > 0) {
     const size_t na = (size_t)v * v * v * o > (size_t)o * o * v * v ? (size_t)v * v * v * o : (size_t)o * o * v * v;
     if (base) w->acc = reinterpret_cast<float*>(static_cast<char*>(base) + off);
     off += ((na * sizeof(float) + 255) / 256) * 256;
     if (base) w->err = reinterpret_cast<int*>(static_cast<char*>(base) + off);
     off += 256;
+    if (base) w->arena = reinterpret_cast<float*>(static_cast<char*>(base) + off);
+    off += ((tc_arena_floats(n, o) * sizeof(float) + 255) / 256) * 256;
   }
   return off;
 }
@@ -487,8 +599,9 @@ size_t dress_workspace_bytes_mixed(int n, int nocc) {
 
 int dress_launch_count(int n, int nocc, bool mixed) {
   // copy, 4 T1 passes, h~, f~, 2 energy, small blocks, finalize; T2 terms: 7 SIMT kernels
-  // (FP64) or 2 FP32 copies + 16 GEMMs + 3 SIMT kernels + error check (mixed)
-  return (n - nocc > 0 && nocc > 0) ? (mixed ? 11 + 22 : 11 + 7) : 5;
+  // (FP64) or 2 FP32 copies + 29 operand packs + 8 GEMM launches + 3 finalize kernels + error
+  // check (mixed)
+  return (n - nocc > 0 && nocc > 0) ? (mixed ? 11 + 43 : 11 + 7) : 5;
 }
 
 namespace {
@@ -577,10 +690,11 @@ struct LR2G1B {
     return c.T(k / c.o, k % c.o, a, b);
   }
 };
-// r2 accumulation at (i, j, a, b) from a GEMM whose rows / cols are pairs of (i|j, a|b)
+// r2 part at (i, j, a, b) from a GEMM whose rows / cols are pairs of (i|j, a|b); every job of
+// a launch writes its own buffer (jobs run concurrently)
 struct StoreR2 {
   float* acc;
-  int o, v, mode;  // 0: (i a)(j b)  1: (j a)(i b)  2: (i b)(j a)  3: (j b)(i a)  4: (i j)(a b), set
+  int o, v, mode;  // 0: (i a)(j b)  1: (j a)(i b)  2: (i b)(j a)  3: (j b)(i a)  4: (i j)(a b)
   __device__ void operator()(int r, int col, float val) const {
     int i, j, a, b;
     if (mode == 4) {
@@ -592,7 +706,7 @@ struct StoreR2 {
     else if (mode == 1) { j = r1; a = r2; i = c1; b = c2; }
     else if (mode == 2) { i = r1; b = r2; j = c1; a = c2; }
     else { j = r1; b = r2; i = c1; a = c2; }
-    acc[(((size_t)i * o + j) * v + a) * v + b] += val;
+    acc[(((size_t)i * o + j) * v + a) * v + b] = val;
   }
 };
 // rows (i, a), cols (j, b): linear rings through (m, e) and quadratic rings through (n, f)
@@ -675,11 +789,11 @@ struct LV4B {
     return c.G(k / c.o, c.o + col / c.v, k % c.o, c.o + col % c.v);
   }
 };
-struct StoreV4 {
+struct StoreV4 {  // rows (e, f), cols (a, b): consecutive lanes write consecutive f
   double* W;
   int n, o, v;
   __device__ void operator()(int r, int col, float val) const {
-    const size_t x = (((size_t)(o + r / v) * n + (o + col / v)) * n + (o + r % v)) * n + (o + col % v);
+    const size_t x = (((size_t)(o + col / v) * n + (o + r / v)) * n + (o + col % v)) * n + (o + r % v);
     W[x] += (double)val;
   }
 };
@@ -787,30 +901,29 @@ struct LVV3B {  // cols (a, i): t[m i a f]
   TcCtx c;
   __device__ float operator()(int col, int k) const { return c.T(k / c.v, col % c.o, col / c.o, k % c.v); }
 };
-struct StoreVV {
+struct StoreVV {  // each job its own buffer
   float* acc;
-  int o, v, mode;  // 0: (a e)(b i) set  1: (a b)(e i) add  2: (e b)(a i) add
+  int o, v, mode;  // 0: (a e)(b i)  1: (a b)(e i)  2: (e b)(a i)
   __device__ void operator()(int r, int col, float val) const {
     int a, e, b, i;
     if (mode == 0) { a = r / v; e = r % v; b = col / o; i = col % o; }
     else if (mode == 1) { a = r / v; b = r % v; e = col / o; i = col % o; }
     else { e = r / v; b = r % v; a = col / o; i = col % o; }
-    const size_t x = (((size_t)a * v + e) * v + b) * o + i;
-    if (mode == 0) acc[x] = val;
-    else acc[x] += val;
+    acc[(((size_t)a * v + e) * v + b) * o + i] = val;
   }
 };
 
-// r2 = bare vo|vo + GEMM part + the O(v) Fock terms (FP32), added in FP64
+// r2 = bare vo|vo + GEMM parts (ladder/oooo in acc, four ring maps in part[0..3]) + the O(v)
+// Fock terms (FP32), added in FP64
 __global__ void k_r2_fin(const double* __restrict__ W, const float* __restrict__ t2, const double* __restrict__ foo,
-                         const double* __restrict__ fvv, const float* __restrict__ acc, double* __restrict__ r2,
-                         Dims d) {
+                         const double* __restrict__ fvv, const float* __restrict__ acc, const float* __restrict__ part,
+                         double* __restrict__ r2, Dims d) {
   const size_t m_all = (size_t)d.o * d.o * d.v * d.v;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int i = (int)(x / ((size_t)d.o * d.v * d.v)), j = (int)((x / ((size_t)d.v * d.v)) % d.o);
   const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
-  float v = acc[x];
+  float v = acc[x] + part[x] + part[m_all + x] + part[2 * m_all + x] + part[3 * m_all + x];
   for (int e = 0; e < d.v; ++e)
     v += (float)fvv[b * d.v + e] * t2[ti(d, i, j, a, e)] + (float)fvv[a * d.v + e] * t2[ti(d, i, j, e, b)];
   for (int m = 0; m < d.o; ++m)
@@ -820,14 +933,15 @@ __global__ void k_r2_fin(const double* __restrict__ W, const float* __restrict__
 
 // oovo: the GEMM's v^2 term plus the O(v) and O(ov) terms, onto the FP64 base and its mirror
 __global__ void k_oovo_fin(double* __restrict__ W, const float* __restrict__ G, const double* __restrict__ F,
-                           const float* __restrict__ t2, const float* __restrict__ acc, Dims d) {
+                           const float* __restrict__ t2, const float* __restrict__ part, int nsplit, Dims d) {
   const size_t m_all = (size_t)d.o * d.o * d.v * d.o;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int m = (int)(x / ((size_t)d.o * d.v * d.o)), i = (int)((x / ((size_t)d.v * d.o)) % d.o);
   const int b = (int)((x / d.o) % d.v), j = (int)(x % d.o);
   const int B_ = d.o + b;
-  float v = acc[x];
+  float v = 0.f;
+  for (int z = 0; z < nsplit; ++z) v += part[(size_t)z * m_all + x];  // split-K partials, in order
   for (int e = 0; e < d.v; ++e) {
     const int E_ = d.o + e;
     v += (float)F[m * d.n + E_] * t2[ti(d, i, j, e, b)];
@@ -842,14 +956,15 @@ __global__ void k_oovo_fin(double* __restrict__ W, const float* __restrict__ G, 
 
 // vvvo: GEMM part minus the f~ term, onto the FP64 base and its mirror
 __global__ void k_vvvo_fin(double* __restrict__ W, const double* __restrict__ F, const float* __restrict__ t2,
-                           const float* __restrict__ acc, Dims d) {
+                           const float* __restrict__ acc, const float* __restrict__ p1, const float* __restrict__ p2,
+                           Dims d) {
   const size_t m_all = (size_t)d.v * d.v * d.v * d.o;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
   const int a = (int)(x / ((size_t)d.v * d.v * d.o)), e = (int)((x / ((size_t)d.v * d.o)) % d.v);
   const int b = (int)((x / d.o) % d.v), i = (int)(x % d.o);
   const int A_ = d.o + a, E_ = d.o + e, B_ = d.o + b;
-  float v = acc[x];
+  float v = acc[x] + p1[x] + p2[x];
   for (int m = 0; m < d.o; ++m) v -= (float)F[m * d.n + E_] * t2[ti(d, m, i, a, b)];
   const double w = W[gi(d, A_, E_, B_, i)] + (double)v;
   W[gi(d, A_, E_, B_, i)] = w;
@@ -861,51 +976,224 @@ __global__ void k_gemm_check(const int* __restrict__ err, double* __restrict__ e
   if (threadIdx.x == 0 && *err) *e0 = nan("");
 }
 
-template <int BN, class LA, class LB, class ST>
-cudaError_t run_gemm(int M, int N, int K, LA la, LB lb, ST st, int* err, cudaStream_t s) {
-  return tc::gemm_tf32x3<BN>(M, N, K, la, lb, st, err, s);
+// Scratch for packed operands: a bump allocator over one region, reset between phases; a dry
+// run (base == nullptr) only records the peak, which sizes the workspace.
+struct Arena {
+  float* base;
+  size_t used = 0, peak = 0;
+  float* take(size_t n) {
+    float* p = base ? base + used : nullptr;
+    used += (n + 63) / 64 * 64;
+    if (used > peak) peak = used;
+    return p;
+  }
+  void reset() { used = 0; }
+};
+
+struct Op {  // a packed operand: hi / lo parts, rows padded to the tile, K padded to 32
+  float *hi, *lo;
+  int rows, K, ld;
+};
+
+template <class L>
+cudaError_t pack_op(L ld, int rows, int K, int tile, Arena& ar, Op* out, cudaStream_t st) {
+  const int rows_p = tc::pad_to(rows, tile), Kp = tc::pad_to(K, tc::BK);
+  out->rows = rows;
+  out->K = K;
+  out->ld = Kp;
+  out->hi = ar.take((size_t)rows_p * Kp);
+  out->lo = ar.take((size_t)rows_p * Kp);
+  if (!ar.base) return cudaSuccess;
+  return tc::pack(ld, rows, K, rows_p, Kp, out->hi, out->lo, st);
 }
 
+// operand tiles: A rows pad to 128; B rows pad to the launch's BN
+constexpr int kTileM = tc::BM;
+
+template <class Store>
+tc::PackedJob<Store> job(const Op& a, const Op& b, Store st, int split = 0, int nsplit = 1) {
+  tc::PackedJob<Store> j{};
+  j.ahi = a.hi;
+  j.alo = a.lo;
+  j.bhi = b.hi;
+  j.blo = b.lo;
+  j.M = a.rows;
+  j.N = b.rows;
+  j.ld = a.ld;
+  const int slabs = a.ld / tc::BK, per = (slabs + nsplit - 1) / nsplit;
+  j.k_begin = split * per * tc::BK;
+  j.k_slabs = (split * per >= slabs) ? 0 : ((split + 1) * per > slabs ? slabs - split * per : per);
+  j.st = st;
+  return j;
+}
+
+template <int BN, class Store>
+cudaError_t run_jobs(tc::PackedJobs<Store>& jobs, const Arena& ar, int* err, cudaStream_t st) {
+  if (!ar.base) return cudaSuccess;
+  return tc::gemm_packed<BN>(jobs, err, st);
+}
+
+constexpr int kOvoSplit = 6;  // split K of the oovo v^2 product (720 x 100 x v^2)
+
+// The T2 terms of the mixed path; with ar.base == nullptr only sizes the packed scratch.
 cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* F, const float* t2, const Work& w,
-                        double* e0, cudaStream_t st) {
+                        double* e0, Arena& ar, cudaStream_t st) {
   const int o = d.o, v = d.v, ov = o * v, vv = v * v, oo = o * o;
-  float* A = reinterpret_cast<float*>(w.A);
-  float* B = reinterpret_cast<float*>(w.B);
-  float* Cq = reinterpret_cast<float*>(w.Cq);
-  float* D = reinterpret_cast<float*>(w.D);
+  const bool run = ar.base != nullptr;
+  float* A = run ? reinterpret_cast<float*>(w.A) : nullptr;
+  float* B = run ? reinterpret_cast<float*>(w.B) : nullptr;
+  float* Cq = run ? reinterpret_cast<float*>(w.Cq) : nullptr;
+  float* D = run ? reinterpret_cast<float*>(w.D) : nullptr;
   TcCtx c{G, t2, A, B, Cq, D, w.wo, d.n, o, v};
   int* err = w.err;
-  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
-  // ring intermediates
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 0}, LRingB{c, 0}, StoreRows{A, ov}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 0}, LRingB{c, 1}, StoreRows{B, ov}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 1}, LRingB{c, 1}, StoreRows{Cq, ov}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LRingA{c, 2}, LRingB{c, 1}, StoreRows{D, ov}, err, st);
-  // r2
   float* acc = w.acc;
-  if (e == cudaSuccess) e = run_gemm<64>(oo, vv, vv + oo, LR2G1A{c}, LR2G1B{c}, StoreR2{acc, o, v, 4}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 5 * ov, LR2G3A{c}, LR2G3B{c}, StoreR2{acc, o, v, 0}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 2 * ov, LR2G4A{c}, LR2G4B{c}, StoreR2{acc, o, v, 1}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LR2G5A{c}, LR2G5B{c}, StoreR2{acc, o, v, 2}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 2 * ov, LR2G6A{c}, LR2G6B{c}, StoreR2{acc, o, v, 3}, err, st);
-  if (e != cudaSuccess) return e;
-  k_r2_fin<<<blocks_for((size_t)oo * vv), TPB, 0, st>>>(W, t2, w.foo, w.fvv, acc, w.r2, d);
-  // blocks written in place (their bases are read from W by the store of their single GEMM)
-  e = run_gemm<128>(vv, vv, oo, LV4A{c}, LV4B{c}, StoreV4{W, d.n, o, v}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, 2 * ov, LOVA{c}, LOVB{c}, StoreOV{W, d.n, o, v}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(ov, ov, ov, LOOA{c}, LOOB{c}, StoreOO{W, d.n, o, v}, err, st);
-  if (e == cudaSuccess) e = run_gemm<32>(ov, oo, vv, LOVOA{c}, LOVOB{c}, StoreOVO{acc, o, v}, err, st);
-  if (e != cudaSuccess) return e;
-  k_oovo_fin<<<blocks_for((size_t)oo * v * o), TPB, 0, st>>>(W, G, F, t2, acc, d);
-  e = run_gemm<128>(vv, v * o, 2 * ov, LVV1A{c}, LVV1B{c}, StoreVV{acc, o, v, 0}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(vv, v * o, oo, LVV2A{c}, LVV2B{c}, StoreVV{acc, o, v, 1}, err, st);
-  if (e == cudaSuccess) e = run_gemm<128>(vv, v * o, ov, LVV3A{c}, LVV3B{c}, StoreVV{acc, o, v, 2}, err, st);
-  if (e != cudaSuccess) return e;
-  k_vvvo_fin<<<blocks_for((size_t)vv * v * o), TPB, 0, st>>>(W, F, t2, acc, d);
-  k_gemm_check<<<1, 32, 0, st>>>(err, e0);
-  return cudaGetLastError();
+  cudaError_t e = run ? cudaMemsetAsync(err, 0, sizeof(int), st) : cudaSuccess;
+#define QF_TRY(x)                       \
+  do {                                  \
+    if (e == cudaSuccess) e = (x);      \
+  } while (0)
+  // ring intermediates: one launch of four jobs sharing packed operands
+  {
+    ar.reset();
+    Op au, at, atx, b0, b1;
+    QF_TRY(pack_op(LRingA{c, 0}, ov, ov, kTileM, ar, &au, st));
+    QF_TRY(pack_op(LRingA{c, 1}, ov, ov, kTileM, ar, &at, st));
+    QF_TRY(pack_op(LRingA{c, 2}, ov, ov, kTileM, ar, &atx, st));
+    QF_TRY(pack_op(LRingB{c, 0}, ov, ov, 64, ar, &b0, st));
+    QF_TRY(pack_op(LRingB{c, 1}, ov, ov, 64, ar, &b1, st));
+    tc::PackedJobs<StoreRows> js{};
+    js.j[0] = job(au, b0, StoreRows{A, ov});
+    js.j[1] = job(au, b1, StoreRows{B, ov});
+    js.j[2] = job(at, b1, StoreRows{Cq, ov});
+    js.j[3] = job(atx, b1, StoreRows{D, ov});
+    js.count = 4;
+    QF_TRY((run_jobs<64>(js, ar, err, st)));
+  }
+  // r2: ladder + oooo term
+  {
+    ar.reset();
+    Op a1, b1;
+    QF_TRY(pack_op(LR2G1A{c}, oo, vv + oo, kTileM, ar, &a1, st));
+    QF_TRY(pack_op(LR2G1B{c}, vv, vv + oo, 32, ar, &b1, st));
+    tc::PackedJobs<StoreR2> js{};
+    js.j[0] = job(a1, b1, StoreR2{acc, o, v, 4});
+    js.count = 1;
+    QF_TRY((run_jobs<32>(js, ar, err, st)));
+  }
+  // r2: rings (four output maps, one launch)
+  {
+    ar.reset();
+    Op a3, b3, a4, b4, a5, b5, a6, b6;
+    QF_TRY(pack_op(LR2G3A{c}, ov, 5 * ov, kTileM, ar, &a3, st));
+    QF_TRY(pack_op(LR2G3B{c}, ov, 5 * ov, 64, ar, &b3, st));
+    QF_TRY(pack_op(LR2G4A{c}, ov, 2 * ov, kTileM, ar, &a4, st));
+    QF_TRY(pack_op(LR2G4B{c}, ov, 2 * ov, 64, ar, &b4, st));
+    QF_TRY(pack_op(LR2G5A{c}, ov, ov, kTileM, ar, &a5, st));
+    QF_TRY(pack_op(LR2G5B{c}, ov, ov, 64, ar, &b5, st));
+    QF_TRY(pack_op(LR2G6A{c}, ov, 2 * ov, kTileM, ar, &a6, st));
+    QF_TRY(pack_op(LR2G6B{c}, ov, 2 * ov, 64, ar, &b6, st));
+    const size_t n_r2 = (size_t)oo * vv;
+    float* part = ar.take(4 * n_r2);
+    tc::PackedJobs<StoreR2> js{};
+    js.j[0] = job(a3, b3, StoreR2{part, o, v, 0});
+    js.j[1] = job(a4, b4, StoreR2{run ? part + n_r2 : nullptr, o, v, 1});
+    js.j[2] = job(a5, b5, StoreR2{run ? part + 2 * n_r2 : nullptr, o, v, 2});
+    js.j[3] = job(a6, b6, StoreR2{run ? part + 3 * n_r2 : nullptr, o, v, 3});
+    js.count = 4;
+    QF_TRY((run_jobs<64>(js, ar, err, st)));
+    if (run && e == cudaSuccess) {
+      k_r2_fin<<<blocks_for(n_r2), TPB, 0, st>>>(W, t2, w.foo, w.fvv, acc, part, w.r2, d);
+      e = cudaGetLastError();
+    }
+  }
+  // blocks written in place (their bases are read from W by the store of their single job)
+  {
+    ar.reset();
+    Op a, b;
+    QF_TRY(pack_op(LV4B{c}, vv, oo, kTileM, ar, &a, st));
+    QF_TRY(pack_op(LV4A{c}, vv, oo, 128, ar, &b, st));
+    tc::PackedJobs<StoreV4> js{};
+    js.j[0] = job(a, b, StoreV4{W, d.n, o, v});
+    js.count = 1;
+    QF_TRY((run_jobs<128>(js, ar, err, st)));
+  }
+  {
+    ar.reset();
+    Op a, b;
+    QF_TRY(pack_op(LOVA{c}, ov, 2 * ov, kTileM, ar, &a, st));
+    QF_TRY(pack_op(LOVB{c}, ov, 2 * ov, 32, ar, &b, st));
+    tc::PackedJobs<StoreOV> js{};
+    js.j[0] = job(a, b, StoreOV{W, d.n, o, v});
+    js.count = 1;
+    QF_TRY((run_jobs<32>(js, ar, err, st)));
+  }
+  {
+    ar.reset();
+    Op a, b;
+    QF_TRY(pack_op(LOOA{c}, ov, ov, kTileM, ar, &a, st));
+    QF_TRY(pack_op(LOOB{c}, ov, ov, 32, ar, &b, st));
+    tc::PackedJobs<StoreOO> js{};
+    js.j[0] = job(a, b, StoreOO{W, d.n, o, v});
+    js.count = 1;
+    QF_TRY((run_jobs<32>(js, ar, err, st)));
+  }
+  // oovo v^2 term, split K into partial outputs summed in order by k_oovo_fin
+  float* part = nullptr;
+  {
+    ar.reset();
+    Op a, b;
+    QF_TRY(pack_op(LOVOA{c}, ov, vv, kTileM, ar, &a, st));
+    QF_TRY(pack_op(LOVOB{c}, oo, vv, 32, ar, &b, st));
+    const size_t n_ovo = (size_t)oo * v * o;
+    part = ar.take(n_ovo * kOvoSplit);
+    tc::PackedJobs<StoreOVO> js{};
+    for (int z = 0; z < kOvoSplit; ++z) js.j[z] = job(a, b, StoreOVO{part + (run ? n_ovo * z : 0), o, v}, z, kOvoSplit);
+    js.count = kOvoSplit;
+    QF_TRY((run_jobs<32>(js, ar, err, st)));
+  }
+  if (run && e == cudaSuccess) {
+    k_oovo_fin<<<blocks_for((size_t)oo * v * o), TPB, 0, st>>>(W, G, F, t2, part, kOvoSplit, d);
+    e = cudaGetLastError();
+  }
+  // vvvo: three output maps, one launch; each job its own buffer, summed by k_vvvo_fin
+  {
+    ar.reset();
+    Op a1, b1, a2, b2, a3, b3;
+    QF_TRY(pack_op(LVV1A{c}, vv, 2 * ov, kTileM, ar, &a1, st));
+    QF_TRY(pack_op(LVV1B{c}, v * o, 2 * ov, 64, ar, &b1, st));
+    QF_TRY(pack_op(LVV2A{c}, vv, oo, kTileM, ar, &a2, st));
+    QF_TRY(pack_op(LVV2B{c}, v * o, oo, 64, ar, &b2, st));
+    QF_TRY(pack_op(LVV3A{c}, vv, ov, kTileM, ar, &a3, st));
+    QF_TRY(pack_op(LVV3B{c}, v * o, ov, 64, ar, &b3, st));
+    const size_t n_vvvo = (size_t)vv * v * o;
+    float* p1 = ar.take(n_vvvo);
+    float* p2 = ar.take(n_vvvo);
+    tc::PackedJobs<StoreVV> js{};
+    js.j[0] = job(a1, b1, StoreVV{acc, o, v, 0});
+    js.j[1] = job(a2, b2, StoreVV{p1, o, v, 1});
+    js.j[2] = job(a3, b3, StoreVV{p2, o, v, 2});
+    js.count = 3;
+    QF_TRY((run_jobs<64>(js, ar, err, st)));
+    if (run && e == cudaSuccess) {
+      k_vvvo_fin<<<blocks_for(n_vvvo), TPB, 0, st>>>(W, F, t2, acc, p1, p2, d);
+      e = cudaGetLastError();
+    }
+  }
+#undef QF_TRY
+  if (run && e == cudaSuccess) {
+    k_gemm_check<<<1, 32, 0, st>>>(err, e0);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
+size_t tc_arena_floats(int n, int nocc) {
+  Dims d{n, nocc, n - nocc};
+  Work w{};
+  Arena ar{nullptr};
+  t2_terms_tc(d, nullptr, nullptr, nullptr, nullptr, w, nullptr, ar, nullptr);
+  return ar.peak;
+}
 }  // namespace
 
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
@@ -920,18 +1208,8 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
   const size_t o = nocc, v = n - nocc;
   k_copy<<<blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
   if (v > 0 && o > 0) {
-    const size_t mc = v * n * n * n, ma = o * n * n * n;
-    if (mixed) {  // FP32 correction sums onto the FP64 elements
-      k_t1_creator<float><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
-      k_t1_creator<float><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
-      k_t1_annihilator<float><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
-      k_t1_annihilator<float><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 3);
-    } else {
-      k_t1_creator<double><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
-      k_t1_creator<double><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
-      k_t1_annihilator<double><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
-      k_t1_annihilator<double><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 3);
-    }
+    if (mixed) t1_passes<float>(W, t1, d, st);  // FP32 correction sums onto the FP64 elements
+    else t1_passes<double>(W, t1, d, st);
   }
   k_h_tilde<<<blocks_for((size_t)n * n), TPB, 0, st>>>(h, t1, w.ht, d);
   k_fock<<<blocks_for((size_t)n * n), TPB, 0, st>>>(w.ht, W, F, d);
@@ -945,7 +1223,8 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
       const unsigned gg = blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4);
       k_to_f32<<<gg, TPB, 0, st>>>(W, g32, n4);
       k_to_f32<<<blocks_for(o * o * v * v), TPB, 0, st>>>(t2, t2f, o * o * v * v);
-      cudaError_t e = t2_terms_tc(d, W, g32, F, t2f, w, e0, st);
+      Arena ar{w.arena};
+      cudaError_t e = t2_terms_tc(d, W, g32, F, t2f, w, e0, ar, st);
       if (e != cudaSuccess) return e;
     } else {
       t2_terms<double>(d, W, W, F, t2, w, st);

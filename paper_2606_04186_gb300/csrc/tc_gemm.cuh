@@ -283,3 +283,191 @@ cudaError_t gemm_tf32x3(int M, int N, int K, LoadA la, LoadB lb, Store st, int* 
 
 }  // namespace tc
 }  // namespace qf
+
+// ---- packed operands --------------------------------------------------------------------------
+// A second engine for operands prepared by k_pack: hi and lo TF32 parts as row-major FP32
+// matrices with K padded to a multiple of 32 and rows padded to the tile, so a slab is copied
+// into the canonical layout with 16-byte cp.async (no index arithmetic, no registers) while the
+// tensor cores work on the previous slab.  Up to kMaxJobs independent jobs of one store type
+// share a launch (blockIdx.z selects the job); jobs may also be K-ranges of one product
+// (split K) writing separate partial outputs.
+namespace qf {
+namespace tc {
+
+// out_hi/out_lo[r][k] = split(L(r, k)) for r < rows, k < K; zero in the padding.
+template <class L>
+__global__ void k_pack(L ld, int rows, int K, int rows_p, int Kp, float* __restrict__ hi, float* __restrict__ lo) {
+  const size_t total = (size_t)rows_p * Kp;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(x / Kp), k = (int)(x % Kp);
+    const float v = (r < rows && k < K) ? ld(r, k) : 0.f;
+    const float h = tf32_round(v);
+    hi[x] = h;
+    lo[x] = tf32_round(v - h);
+  }
+}
+
+template <class L>
+cudaError_t pack(L ld, int rows, int K, int rows_p, int Kp, float* hi, float* lo, cudaStream_t st) {
+  const size_t total = (size_t)rows_p * Kp;
+  size_t g = (total + 255) / 256;
+  if (g > 152 * 64) g = 152 * 64;
+  if (g < 1) g = 1;
+  k_pack<L><<<(unsigned)g, 256, 0, st>>>(ld, rows, K, rows_p, Kp, hi, lo);
+  return cudaGetLastError();
+}
+
+__host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+template <class Store>
+struct PackedJob {
+  const float *ahi, *alo, *bhi, *blo;  // [M_p][ld], [N_p][ld]
+  int M, N, ld;                        // ld = padded K of the packed arrays
+  int k_begin, k_slabs;                // slabs [k_begin / 32, k_begin / 32 + k_slabs)
+  Store st;
+};
+
+constexpr int kMaxJobs = 8;
+template <class Store>
+struct PackedJobs {
+  PackedJob<Store> j[kMaxJobs];
+  int count;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copy slab s of rows [r0, r0 + nrows) of a packed pair into a stage (canonical layout).
+__device__ __forceinline__ void slab_copy(const float* hi, const float* lo, int ld, int r0, int nrows, int s,
+                                          float* shi, float* slo, int tid) {
+  const int chunks = nrows * 8;  // 16-byte chunks per array
+  for (int c = tid; c < chunks; c += THREADS) {
+    const int row = c >> 3, k4 = (c & 7) * 4;
+    const size_t g = (size_t)(r0 + row) * ld + (size_t)s * BK + k4;
+    const uint32_t o = slab_off(row, k4);
+    cp_async16(smem_u32(shi) + o, hi + g);
+    cp_async16(smem_u32(slo) + o, lo + g);
+  }
+}
+
+template <int BN, class Store>
+__global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs, int* __restrict__ err) {
+  if ((int)blockIdx.z >= jobs.count) return;
+  const PackedJob<Store> jb = jobs.j[blockIdx.z];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (m0 >= jb.M || n0 >= jb.N) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem<BN>& sm = *reinterpret_cast<Smem<BN>*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    sm.abort = 0;
+  }
+  if (warp == 0) tmem_alloc(&sm.tmem, 2 * BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+  constexpr uint32_t idesc = idesc_tf32(BN);
+  const int nslab = jb.k_slabs, s0 = jb.k_begin / BK;
+  uint32_t phase[2] = {0u, 0u};
+  int issued[2] = {0, 0};
+  if (nslab > 0) {
+    slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0, sm.a_hi[0], sm.a_lo[0], tid);
+    slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0, sm.b_hi[0], sm.b_lo[0], tid);
+  }
+  cp_async_commit();
+  for (int s = 0; s < nslab; ++s) {
+    const int buf = s & 1, nb = buf ^ 1;
+    // prefetch slab s+1 into the other stage once the MMAs that read it (slab s-1) are done
+    if (s + 1 < nslab) {
+      if (issued[nb]) {
+        if (!mbar_wait(&sm.bar[nb], phase[nb])) sm.abort = 1;
+        phase[nb] ^= 1u;
+        issued[nb] = 0;
+      }
+      slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0 + s + 1, sm.a_hi[nb], sm.a_lo[nb], tid);
+      slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0 + s + 1, sm.b_hi[nb], sm.b_lo[nb], tid);
+    }
+    cp_async_commit();
+    cp_async_wait_1();  // slab s has landed (slab s+1 may still be in flight)
+    fence_async_smem();
+    __syncthreads();
+    if (sm.abort) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ah = smem_u32(sm.a_hi[buf]), al = smem_u32(sm.a_lo[buf]);
+      const uint32_t bh = smem_u32(sm.b_hi[buf]), bl = smem_u32(sm.b_lo[buf]);
+#pragma unroll
+      for (int ks = 0; ks < BK / 8; ++ks) {
+        const uint32_t koff = (uint32_t)ks * 256;
+        const uint64_t dah = smem_desc(ah + koff, 128, 1024), dal = smem_desc(al + koff, 128, 1024);
+        const uint64_t dbh = smem_desc(bh + koff, 128, 1024), dbl = smem_desc(bl + koff, 128, 1024);
+        const uint32_t acc0 = (s > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem, dah, dbh, idesc, acc0);
+        mma_tf32(tmem + BN, dah, dbl, idesc, acc0);
+        mma_tf32(tmem + BN, dal, dbh, idesc, 1u);
+      }
+      mma_commit(&sm.bar[buf]);
+    }
+    issued[buf] = 1;
+  }
+  cp_async_wait_0();
+  for (int b = 0; b < 2; ++b)
+    if (issued[b]) {
+      if (!mbar_wait(&sm.bar[b], phase[b])) sm.abort = 1;
+      phase[b] ^= 1u;
+    }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const bool ok = (sm.abort == 0);
+  if (ok && nslab > 0) {
+    const int m = m0 + warp * 32 + (tid & 31);
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      float v[32], w[32];
+      const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+      tmem_ld32(tmem + lane_base + (uint32_t)c, v);
+      tmem_ld32(tmem + lane_base + (uint32_t)(BN + c), w);
+      if (m < jb.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c + j;
+          if (n < jb.N) jb.st(m, n, v[j] + w[j]);
+        }
+      }
+    }
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tmem_dealloc(tmem, 2 * BN);
+    tmem_relinquish();
+  }
+}
+
+template <int BN, class Store>
+cudaError_t gemm_packed(const PackedJobs<Store>& jobs, int* err, cudaStream_t stream) {
+  int gx = 1, gy = 1;
+  for (int i = 0; i < jobs.count; ++i) {
+    const int x = (jobs.j[i].N + BN - 1) / BN, y = (jobs.j[i].M + BM - 1) / BM;
+    gx = x > gx ? x : gx;
+    gy = y > gy ? y : gy;
+  }
+  const size_t smem = sizeof(Smem<BN>) + 1024;
+  auto kern = k_gemm_packed<BN, Store>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)jobs.count), THREADS, smem, stream>>>(jobs, err);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace qf
