@@ -57,29 +57,44 @@ def parse():
 
 # ---- per-space flop accounting of the solve kernel (6e6o, 400 determinants) ------------------
 
-def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12, kmax: int = 8) -> float:
+def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12, k: int = 3, kmax: int = 3) -> float:
     """Algorithmic flops of the batched Davidson for spaces that ran `iters` iterations.
 
-    sigma: per determinant 2 * (NSG*NSG) for the alpha-beta double sum + 2 * 2 * NS for the
-    same-spin string products + 2 for the diagonal  -> 400 * (288 + 80 + 2) = 148,000 flop.
-    Setup: same-spin string operator NS*NSG*(1+NSG)*2, start sigma, 2 dot products.
-    Iteration with subspace k: residual 400*(4k+4), Gram-Schmidt 2 passes 400*(4k),
-    norm+scale 400*3, sigma, projected row/column 400*2*(2k+1).  k runs 1..kmax-1 then restarts.
+    Every space: sigma(Phi) from Phi's sparse column (alpha-beta couplings of the (1+k^2)^2
+    Phi/single string pairs, k^2 terms each, and the same-spin column, NS*NSG*(1+k) terms) and the
+    residual norm.  Spaces that iterate: the same-spin string operator (135 coupling paths per
+    string) and the first-order correction test.  Iteration with subspace size j: residual
+    400*(4j+4), Gram-Schmidt 2 passes 400*(4j), norm+scale 400*3, one sigma = 400 * (2*NSG^2 +
+    4*NS + 2) = 148,000 flop, projected row/column 400*2*(2j+1); the subspace restarts at kmax.
     """
     sig = ndet * (2 * nsg * nsg + 4 * ns + 2)
-    setup = ns * nsg * (1 + nsg) * 2 + sig + 4 * ndet
-    # flops of m iterations: follow the subspace size sequence of the kernel
+    phi = 2 * ((1 + k * k) ** 2 * k * k + ns * nsg * (1 + k)) + 2 * ndet
+    hs = 2 * ns * 135 + 4 * ndet
     m_max = int(iters.max()) if iters.size else 0
     cum = np.zeros(m_max + 1)
-    k, tot = 1, 0.0
+    j, tot = 1, 0.0
     for m in range(1, m_max + 1):
-        if k == kmax:
+        if j == kmax:
             tot += ndet * (4 * kmax + 6)          # restart: Ritz vector + its sigma combination + norms
-            k = 1
-        tot += ndet * (4 * k + 4) + ndet * 8 * k + ndet * 3 + sig + ndet * 2 * (2 * k + 1)
-        k += 1
+            j = 1
+        tot += ndet * (4 * j + 4) + ndet * 8 * j + ndet * 3 + sig + ndet * 2 * (2 * j + 1)
+        j += 1
         cum[m] = tot
-    return float(setup * iters.size + cum[np.clip(iters, 0, m_max)].sum())
+    return float(phi * iters.size + hs * np.count_nonzero(iters > 0) + cum[np.clip(iters, 0, m_max)].sum())
+
+
+def dress_gemm_flops(o: int, v: int) -> float:
+    """Algorithmic flops (2 M N K, one term) of the T2 contractions the mixed dressing runs as
+    tensor-core GEMMs: ring intermediates, ladder + oooo, the residual's rings, vvvv, ovvo, oovv,
+    the oovo v^2 term and the three vvvo maps."""
+    ov, vv, oo = o * v, v * v, o * o
+    mnk = (4 * ov * ov * ov + oo * vv * (vv + oo) + ov * ov * (5 + 2 + 1 + 2) * ov + vv * vv * oo
+           + ov * ov * 2 * ov + ov * ov * ov + ov * oo * vv + vv * (v * o) * (2 * ov + oo + ov))
+    return 2.0 * mnk
+
+
+# solve-kernel DRAM traffic per space, sweep 3 (ncu capture of the 500,000-space n82 subset)
+TRAFFIC_PER_SPACE = {"n82": 148.9}
 
 
 # ---- clocks ------------------------------------------------------------------------------------
@@ -385,12 +400,20 @@ def run_ours(args):
                    "step": "third sweep of the flow (pool after two sweeps restored before each step)",
                    "init_s": t_init},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": ("solve_persistent_kernel" if sched["persistent"] else "solve_class_kernel<K>")
+                     "frac": achieved / peak,
+                     "traffic": (TRAFFIC_PER_SPACE[name] * len(sp)
+                                 if name in TRAFFIC_PER_SPACE and args.precision == "mixed" and not args.spaces_limit
+                                 else None),
+                     "kernel": ("solve_persistent_kernel" if sched["persistent"] else "solve_class_kernel<K>")
                      if args.precision == "mixed" else "solve_kernel<K,double>",
                      "flops_per_launch": flops, "launch_ms": solve_ms,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "mixed"
                      else "GB300 FP64 nominal"},
         "schedule": sched,
+        "dress_tensor": ({"gemm_flops": dress_gemm_flops(no, nv), "phase_ms": float(ph[:, 0].mean()),
+                          "tflops_over_phase": dress_gemm_flops(no, nv) / (float(ph[:, 0].mean()) / 1e3) / 1e12,
+                          "note": "algorithmic one-term flops of the tcgen05 GEMMs / whole dressing phase"}
+                         if args.precision == "mixed" else None),
         "phase_ms": {"dress": float(ph[:, 0].mean()), "solve": solve_ms, "merge": float(ph[:, 2].mean())},
         "davidson_iters_mean": float(it.mean()),
         "davidson_iters_hist": np.bincount(np.minimum(it.astype(np.int64), 12), minlength=13).tolist(),
