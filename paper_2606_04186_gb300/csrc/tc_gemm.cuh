@@ -338,8 +338,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Copy slab s of rows [r0, r0 + nrows) of a packed pair into a stage (canonical layout).
 __device__ __forceinline__ void slab_copy(const float* hi, const float* lo, int ld, int r0, int nrows, int s,
@@ -354,18 +352,34 @@ __device__ __forceinline__ void slab_copy(const float* hi, const float* lo, int 
   }
 }
 
-template <int BN, class Store>
+template <int BN, int S>
+struct SmemP {  // S-stage buffers of the packed engine
+  float a_hi[S][BM * BK], a_lo[S][BM * BK];
+  float b_hi[S][BN * BK], b_lo[S][BN * BK];
+  uint64_t bar[S];
+  uint32_t tmem;
+  int abort;
+};
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// S-stage pipeline: slabs s+1 .. s+S-2 are in flight while the tensor cores work on slab s; the
+// stage of slab s-1 is refilled (with slab s+S-1) once its MMAs have completed.
+template <int BN, int S, class Store>
 __global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs, int* __restrict__ err) {
+  static_assert(S >= 2 && S <= 4, "stages");
   if ((int)blockIdx.z >= jobs.count) return;
-  const PackedJob<Store> jb = jobs.j[blockIdx.z];
+  const PackedJob<Store>& jb = jobs.j[blockIdx.z];
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (m0 >= jb.M || n0 >= jb.N) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  Smem<BN>& sm = *reinterpret_cast<Smem<BN>*>(smem_raw);
+  SmemP<BN, S>& sm = *reinterpret_cast<SmemP<BN, S>*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
-    mbar_init(&sm.bar[0], 1);
-    mbar_init(&sm.bar[1], 1);
+    for (int i = 0; i < S; ++i) mbar_init(&sm.bar[i], 1);
     sm.abort = 0;
   }
   if (warp == 0) tmem_alloc(&sm.tmem, 2 * BN);
@@ -375,34 +389,26 @@ __global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs,
   const uint32_t tmem = sm.tmem;
   constexpr uint32_t idesc = idesc_tf32(BN);
   const int nslab = jb.k_slabs, s0 = jb.k_begin / BK;
-  uint32_t phase[2] = {0u, 0u};
-  int issued[2] = {0, 0};
-  if (nslab > 0) {
-    slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0, sm.a_hi[0], sm.a_lo[0], tid);
-    slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0, sm.b_hi[0], sm.b_lo[0], tid);
-  }
-  cp_async_commit();
-  for (int s = 0; s < nslab; ++s) {
-    const int buf = s & 1, nb = buf ^ 1;
-    // prefetch slab s+1 into the other stage once the MMAs that read it (slab s-1) are done
-    if (s + 1 < nslab) {
-      if (issued[nb]) {
-        if (!mbar_wait(&sm.bar[nb], phase[nb])) sm.abort = 1;
-        phase[nb] ^= 1u;
-        issued[nb] = 0;
-      }
-      slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0 + s + 1, sm.a_hi[nb], sm.a_lo[nb], tid);
-      slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0 + s + 1, sm.b_hi[nb], sm.b_lo[nb], tid);
+  uint32_t phase = 0u;  // bit i: parity to wait for on bar[i]
+  uint32_t issued = 0u;  // bit i: bar[i] has a commit not yet waited for
+#pragma unroll
+  for (int p = 0; p < S - 1; ++p) {
+    if (p < nslab) {
+      slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0 + p, sm.a_hi[p], sm.a_lo[p], tid);
+      slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0 + p, sm.b_hi[p], sm.b_lo[p], tid);
     }
     cp_async_commit();
-    cp_async_wait_1();  // slab s has landed (slab s+1 may still be in flight)
+  }
+  for (int s = 0; s < nslab; ++s) {
+    const int st = s % S;
+    cp_async_wait<S - 2>();  // slab s has landed
     fence_async_smem();
     __syncthreads();
     if (sm.abort) break;
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t ah = smem_u32(sm.a_hi[buf]), al = smem_u32(sm.a_lo[buf]);
-      const uint32_t bh = smem_u32(sm.b_hi[buf]), bl = smem_u32(sm.b_lo[buf]);
+      const uint32_t ah = smem_u32(sm.a_hi[st]), al = smem_u32(sm.a_lo[st]);
+      const uint32_t bh = smem_u32(sm.b_hi[st]), bl = smem_u32(sm.b_lo[st]);
 #pragma unroll
       for (int ks = 0; ks < BK / 8; ++ks) {
         const uint32_t koff = (uint32_t)ks * 256;
@@ -413,15 +419,28 @@ __global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs,
         mma_tf32(tmem + BN, dah, dbl, idesc, acc0);
         mma_tf32(tmem + BN, dal, dbh, idesc, 1u);
       }
-      mma_commit(&sm.bar[buf]);
+      mma_commit(&sm.bar[st]);
     }
-    issued[buf] = 1;
+    issued |= 1u << st;
+    // refill the stage of slab s-1 with slab s+S-1 once its MMAs are done
+    const int nxt = s + S - 1;
+    if (nxt < nslab) {
+      const int ps = nxt % S;
+      if (issued & (1u << ps)) {
+        if (!mbar_wait(&sm.bar[ps], (phase >> ps) & 1u)) sm.abort = 1;
+        phase ^= 1u << ps;
+        issued &= ~(1u << ps);
+      }
+      slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0 + nxt, sm.a_hi[ps], sm.a_lo[ps], tid);
+      slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0 + nxt, sm.b_hi[ps], sm.b_lo[ps], tid);
+    }
+    cp_async_commit();
   }
-  cp_async_wait_0();
-  for (int b = 0; b < 2; ++b)
-    if (issued[b]) {
-      if (!mbar_wait(&sm.bar[b], phase[b])) sm.abort = 1;
-      phase[b] ^= 1u;
+  cp_async_wait<0>();
+  for (int b = 0; b < S; ++b)
+    if (issued & (1u << b)) {
+      if (!mbar_wait(&sm.bar[b], (phase >> b) & 1u)) sm.abort = 1;
+      phase ^= 1u << b;
     }
   tc_fence_before();
   __syncthreads();
@@ -455,14 +474,15 @@ __global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs,
 
 template <int BN, class Store>
 cudaError_t gemm_packed(const PackedJobs<Store>& jobs, int* err, cudaStream_t stream) {
+  constexpr int S = (BN <= 32) ? 4 : (BN <= 64 ? 3 : 2);
   int gx = 1, gy = 1;
   for (int i = 0; i < jobs.count; ++i) {
     const int x = (jobs.j[i].N + BN - 1) / BN, y = (jobs.j[i].M + BM - 1) / BM;
     gx = x > gx ? x : gx;
     gy = y > gy ? y : gy;
   }
-  const size_t smem = sizeof(Smem<BN>) + 1024;
-  auto kern = k_gemm_packed<BN, Store>;
+  const size_t smem = sizeof(SmemP<BN, S>) + 1024;
+  auto kern = k_gemm_packed<BN, S, Store>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)jobs.count), THREADS, smem, stream>>>(jobs, err);
