@@ -540,6 +540,59 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
       }
     }
   }
+  if (k == 3) {  // real roots of the characteristic cubic; eigenvector from a cross product
+    const float* g = G;
+    const float g00 = g[0], g01 = g[1], g02 = g[2], g10 = g[KM], g11 = g[KM + 1], g12 = g[KM + 2];
+    const float g20 = g[2 * KM], g21 = g[2 * KM + 1], g22 = g[2 * KM + 2];
+    // det(lambda I - G) = lambda^3 + a2 lambda^2 + a1 lambda + a0
+    const float a2 = -(g00 + g11 + g22);
+    const float a1 = g00 * g11 - g01 * g10 + g00 * g22 - g02 * g20 + g11 * g22 - g12 * g21;
+    const float a0 = -(g00 * (g11 * g22 - g12 * g21) - g01 * (g10 * g22 - g12 * g20) + g02 * (g10 * g21 - g11 * g20));
+    // lambda = mu - a2 / 3:  mu^3 + p mu + q = 0
+    const float p = a1 - a2 * a2 / 3.f, q = 2.f * a2 * a2 * a2 / 27.f - a2 * a1 / 3.f + a0;
+    float root[3];
+    int nr = 0;
+    const float disc = q * q / 4.f + p * p * p / 27.f;
+    if (disc < 0.f && p < 0.f) {  // three real roots (trigonometric form)
+      const float m = 2.f * sqrtf(-p / 3.f);
+      float c = 3.f * q / (p * m);
+      c = fminf(1.f, fmaxf(-1.f, c));
+      const float phi = acosf(c) / 3.f;
+      for (int j = 0; j < 3; ++j) root[nr++] = m * cosf(phi - 2.0943951f * (float)j) - a2 / 3.f;
+    } else {  // one real root
+      const float sq = sqrtf(fmaxf(disc, 0.f));
+      root[nr++] = cbrtf(-q / 2.f + sq) + cbrtf(-q / 2.f - sq) - a2 / 3.f;
+    }
+    float lam = root[0];
+    for (int j = 1; j < nr; ++j)
+      if (fabsf(root[j] - shift) < fabsf(lam - shift)) lam = root[j];
+    // null vector of G - lam I: the largest cross product of two of its rows
+    const float r0[3] = {g00 - lam, g01, g02}, r1[3] = {g10, g11 - lam, g12}, r2[3] = {g20, g21, g22 - lam};
+    auto cross = [](const float* u, const float* w, float* o) {
+      o[0] = u[1] * w[2] - u[2] * w[1];
+      o[1] = u[2] * w[0] - u[0] * w[2];
+      o[2] = u[0] * w[1] - u[1] * w[0];
+    };
+    float c01[3], c02[3], c12[3];
+    cross(r0, r1, c01);
+    cross(r0, r2, c02);
+    cross(r1, r2, c12);
+    const float n01 = c01[0] * c01[0] + c01[1] * c01[1] + c01[2] * c01[2];
+    const float n02 = c02[0] * c02[0] + c02[1] * c02[1] + c02[2] * c02[2];
+    const float n12 = c12[0] * c12[0] + c12[1] * c12[1] + c12[2] * c12[2];
+    const float* vb = c01;
+    float nb = n01;
+    if (n02 > nb) { vb = c02; nb = n02; }
+    if (n12 > nb) { vb = c12; nb = n12; }
+    if (nb > 0.f && isfinite(nb) && isfinite(lam)) {
+      const float sc = ((vb[0] < 0.f) ? -1.f : 1.f) / sqrtf(nb);
+      y[0] = sc * vb[0];
+      y[1] = sc * vb[1];
+      y[2] = sc * vb[2];
+      *theta = lam;
+      return;
+    }
+  }
   float a[KM * KM], z[KM];
   for (int phase = 0; phase < 5; ++phase) {
     const float sg = (phase < 2) ? shift : *theta;
@@ -967,9 +1020,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       }
       const float r = sv - th * xv;
       rr = fmaf(r, r, rr);
-      float den = th - diag_at<K>(tb, ws, d / NS, d % NS);
-      if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
-      vk[d] = r / den;
+      vk[d] = r;  // the residual; preconditioned below once the space is known not to be done
     }
     const float rnorm = sqrtf(wsum(rr));
     if (!isfinite(rnorm) || !isfinite(th)) {
@@ -984,6 +1035,11 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       }
       __syncwarp();
       break;
+    }
+    for (int d = lane; d < NDET; d += 32) {  // diagonal preconditioner r / (theta - D)
+      float den = th - diag_at<K>(tb, ws, d / NS, d % NS);
+      if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
+      vk[d] = __fdividef(vk[d], den);
     }
     __syncwarp();
     // expansion vector: the preconditioned residual, orthogonalised against the subspace.  When
@@ -1004,7 +1060,12 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
         }
         __syncwarp();
       }
-      for (int pass = 0; pass < 2; ++pass) {
+      const bool from_phi = (it == 0 && k == 1 && !guess_in);  // V0 is exactly Phi
+      if (from_phi) {
+        if (lane == 0) vk[0] = 0.f;
+        __syncwarp();
+      }
+      for (int pass = 0; pass < (from_phi ? 0 : 2); ++pass) {
         float cf[KM];
 #pragma unroll
         for (int j = 0; j < KM; ++j) cf[j] = 0.f;
@@ -1119,19 +1180,25 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     x2[idx] = f * ws.S[tb.xJ[xa] * NS + tb.xJ[xb]] - x1[xa] * x1[xb];
   }
   __syncwarp();
+  // owner and old value are loaded together (independent loads, one latency)
   if (st == kSpaceOk && a.owner1 && lane < K * K) {
     const int i = lane / K, aa = lane % K;
     const size_t g = (size_t)ws.orb[i] * a.nvir + (ws.orb[K + aa] - a.nocc);
-    if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + (double)x1[lane];
+    const int32_t own = a.owner1[g];
+    const double old = a.t1_old[g];
+    if (own == sidx) a.t1_new[g] = old + (double)x1[lane];
   }
   if (st == kSpaceOk && a.owner2) {
-#pragma unroll 1
-    for (int idx = lane; idx < K4; idx += 32) {
+#pragma unroll
+    for (int r = 0; r < (K4 + 31) / 32; ++r) {
+      const int idx = lane + 32 * r;
+      if (idx >= K4) break;
       const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
       const size_t g = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[K + aa] - a.nocc)) * a.nvir +
                        (ws.orb[K + b] - a.nocc);
-      if (a.owner2[g] == sidx)
-        a.t2_new[g] = a.t2_old[g] + (double)(0.5f * (x2[idx] + x2[((j * K + i) * K + b) * K + aa]));
+      const int32_t own = a.owner2[g];
+      const double old = a.t2_old[g];
+      if (own == sidx) a.t2_new[g] = old + (double)(0.5f * (x2[idx] + x2[((j * K + i) * K + b) * K + aa]));
     }
   }
   if (lane == 0) {
