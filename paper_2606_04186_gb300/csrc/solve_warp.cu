@@ -696,6 +696,24 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       off[t] = (t < NF) ? o0 * (long long)n3 + o1 * (long long)n2 : o0 * (long long)n1 + o1;
     }
     __syncwarp();
+    // FP64 loads first, so their latency overlaps the FP32 gather: J and K are symmetric (pair
+    // symmetry of W), one lane per unordered pair p <= r; F (not symmetric) in two rounds
+    constexpr int NU = NORB * (NORB + 1) / 2;
+    static_assert(NU <= 32 && NF <= 64, "one round of pairs, two of F");
+    int up = 0, ur = 0;
+    double jv = 0.0, kv = 0.0, f0 = 0.0, f1 = 0.0;
+    if (lane < NU) {
+      int rem = lane;
+      while (rem >= NORB - up) {
+        rem -= NORB - up;
+        ++up;
+      }
+      ur = up + rem;
+      jv = a.W[off[up * (NORB + 1)] + off[NF + ur * (NORB + 1)]];
+      kv = a.W[off[up * NORB + ur] + off[NF + ur * NORB + up]];
+    }
+    if (lane < NF) f0 = a.F[(size_t)ws.orb[lane / NORB] * n1 + ws.orb[lane % NORB]];
+    if (lane + 32 < NF) f1 = a.F[(size_t)ws.orb[(lane + 32) / NORB] * n1 + ws.orb[(lane + 32) % NORB]];
     if constexpr (K == 3) {  // the 666 unique elements of the pair-symmetric block
       constexpr int PER = (D::NPAIR + 31) / 32;
       float wv[PER];
@@ -728,12 +746,14 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
         ws.Wt[t] = jj ? 0.f : (W32 ? W32[g] : (float)a.W[g]);
       }
     }
-    for (int t = lane; t < NF; t += 32) {
-      const int p = t / NORB, r = t % NORB;
-      su.J[t] = a.W[off[p * (NORB + 1)] + off[NF + r * (NORB + 1)]];
-      su.Kx[t] = a.W[off[p * NORB + r] + off[NF + r * NORB + p]];
-      su.F[t] = a.F[(size_t)ws.orb[p] * n1 + ws.orb[r]];
+    if (lane < NU) {
+      su.J[up * NORB + ur] = jv;
+      su.J[ur * NORB + up] = jv;
+      su.Kx[up * NORB + ur] = kv;
+      su.Kx[ur * NORB + up] = kv;
     }
+    if (lane < NF) su.F[lane] = f0;
+    if (lane + 32 < NF) su.F[lane + 32] = f1;
   }
   __syncwarp();
   // ---- fold (vacuum order over the active orbitals) -------------------------------------
