@@ -11,6 +11,11 @@ same sweep is timed beside it, and the FP64 oracle is timed on the host cores on
 sample (cpu_baseline).  The inputs (W: 362 MB) are larger than the 126 MB L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload n82]
+
+With N > 1 (torchrun, one process per GPU) the sweep is sharded: every rank holds the whole
+problem, dresses the same pool, solves its block of every size class, and the ranks sum their
+exchange vectors with one NCCL allreduce per sweep before the merge (strong scaling: the value is
+the spaces of the one problem per second).  --sharded runs the same three-call path at N = 1.
 """
 from __future__ import annotations
 
@@ -50,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=800, help="spaces solved by the oracle for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "persistent", "per_class"])
+    ap.add_argument("--sharded", action="store_true",
+                    help="sharded sweep path (begin / exchange / end) also at N = 1")
     ap.add_argument("--spaces-limit", type=int, default=0,
                     help="keep an evenly strided subset of at most this many spaces (small profiling case)")
     return ap.parse_args()
@@ -64,7 +71,8 @@ def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12
     Phi/single string pairs, k^2 terms each, and the same-spin column, NS*NSG*(1+k) terms) and the
     residual norm.  Spaces that iterate: the same-spin string operator (135 coupling paths per
     string) and the first-order correction test.  Iteration with subspace size j: residual
-    400*(4j+4), Gram-Schmidt 2 passes 400*(4j), norm+scale 400*3, one sigma = 400 * (2*NSG^2 +
+    400*(4j+4), Gram-Schmidt 2 passes 400*(4j) (none on the first step from Phi, whose new
+    direction only drops its Phi component), norm+scale 400*3, one sigma = 400 * (2*NSG^2 +
     4*NS + 2) = 148,000 flop, projected row/column 400*2*(2j+1); the subspace restarts at kmax.
     """
     sig = ndet * (2 * nsg * nsg + 4 * ns + 2)
@@ -77,7 +85,8 @@ def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12
         if j == kmax:
             tot += ndet * (4 * kmax + 6)          # restart: Ritz vector + its sigma combination + norms
             j = 1
-        tot += ndet * (4 * j + 4) + ndet * 8 * j + ndet * 3 + sig + ndet * 2 * (2 * j + 1)
+        gs = 0 if m == 1 else ndet * 8 * j
+        tot += ndet * (4 * j + 4) + gs + ndet * 3 + sig + ndet * 2 * (2 * j + 1)
         j += 1
         cum[m] = tot
     return float(phi * iters.size + hs * np.count_nonzero(iters > 0) + cum[np.clip(iters, 0, m_max)].sum())
@@ -275,17 +284,29 @@ def run_ours(args):
     t_init = time.perf_counter() - t_init
     stream = torch.cuda.ExternalStream(fl.stream())
     log(f"init {t_init:.1f} s")
+    sharded = world > 1 or args.sharded
+    if sharded:
+        fl.set_shard(rank, world)
+        xbuf = torch.empty(fl.exchange_size(), dtype=torch.float64, device="cuda")
+
+    def sweep():
+        if not sharded:
+            return fl.sweep(raise_on_fail=False)
+        if world > 1:
+            return fl.sweep_sharded(xbuf, raise_on_fail=False)
+        fl.sweep_shard_begin(xbuf)   # one rank: the exchange vector is already the sum
+        return fl.sweep_shard_end(xbuf, raise_on_fail=False)
     # every timed step is the third sweep of the flow: the pool after two sweeps from empty is
     # restored before each step (outside the timed events)
     e_hist = []
     for _ in range(2):
-        fl.sweep(raise_on_fail=False)
+        sweep()
         e_hist.append(fl.energy())
         log(f"sweep {len(e_hist)}: E = {e_hist[-1]:.10f}, phases {fl.last_sweep_info()[0]}")
     p2 = fl.amplitudes()
     for _ in range(max(3, args.warmup)):
         fl.set_amplitudes(*p2)
-        fl.sweep(raise_on_fail=False)
+        sweep()
     e3 = fl.energy()
     log(f"warm-up done: sweep-3 E = {e3:.10f}, phases {fl.last_sweep_info()[0]}")
 
@@ -302,7 +323,7 @@ def run_ours(args):
         for k in range(args.steps):
             fl.set_amplitudes(*p2)
             starts[k].record(stream)
-            de, dt, nf, code = fl.sweep(raise_on_fail=False)
+            de, dt, nf, code = sweep()
             ends[k].record(stream)
             codes.append(code)
             ph, nl = fl.last_sweep_info()
@@ -319,10 +340,15 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed_ms = float(tt.item())
     sweep_ms = elapsed_ms / args.steps
-    value = world * len(sp) / (sweep_ms / 1e3)
+    # sharded: the ranks share one problem (strong scaling); replicas are not run
+    value = len(sp) / (sweep_ms / 1e3)
     ph = np.array(phases)
     solve_ms = float(ph[:, 1].mean())
-    flops = solver_flops(it.astype(np.int64))
+    if world > 1:  # this rank's solve phase covers its own shard only
+        own = qflow.shard_plan(h, g, no, sp, rank, world)[0].astype(bool)
+        flops = solver_flops(it[own].astype(np.int64))
+    else:
+        flops = solver_flops(it.astype(np.int64))
     achieved = flops / (solve_ms / 1e3) / 1e12
     peak = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
 
@@ -337,7 +363,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         qflow.lib().qflow_set_amplitudes(fl._h, t1h.data_ptr(), t2h.data_ptr())
-        fl.sweep(raise_on_fail=False)
+        sweep()
         ec = qflow.C.c_double()
         qflow.lib().qflow_energy(fl._h, qflow.C.byref(ec), ebuf.data_ptr())
         qflow.lib().qflow_amplitudes(fl._h, t1h.data_ptr(), t2h.data_ptr())
@@ -347,12 +373,13 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
     log(f"e2e {e2e_s:.3f} s per step")
     pool_bytes = 8 * (t1h.numel() + t2h.numel())
+    fl_xsize = fl.exchange_size()
     fl.close()
 
     # plain FP64 GPU form of the same sweep (pool after the same number of sweeps as the first
     # warm-up of the mixed run: compare energies after sweep 2)
     fp64 = None
-    if args.fp64_steps > 0 and args.precision == "mixed":
+    if args.fp64_steps > 0 and args.precision == "mixed" and world == 1:
         f64 = qflow.Flow(h, g, no, sp, precision="fp64")
         s64 = torch.cuda.ExternalStream(f64.stream())
         ms = []
@@ -391,12 +418,15 @@ def run_ours(args):
                          f"extrapolated ({r['sweep_s_extrapolated']:.1f} s)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": sweep_ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": max(3, args.warmup), "ms_per_step": sweep_ms, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} spaces "
                                f"({', '.join(f'{int((sp[:, 0] == k).sum())} ({k},{k})' for k in (3, 2, 1) if (sp[:, 0] == k).any())})",
                    "precision": args.precision, "sweep_s": sweep_ms / 1e3, "l2": "inputs larger than L2 (W = "
-                   f"{8 * s.n ** 4 / 1e6:.0f} MB)", "replicas": world, "e_sweep3": e_mean,
+                   f"{8 * s.n ** 4 / 1e6:.0f} MB)", "e_sweep3": e_mean,
+                   "parallelism": (f"sharded over {world} GPUs: per-class blocks, one allreduce of "
+                                   f"{8 * fl_xsize / 1e6:.0f} MB per sweep") if sharded else "one GPU",
                    "step": "third sweep of the flow (pool after two sweeps restored before each step)",
                    "init_s": t_init},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -422,7 +452,7 @@ def run_ours(args):
         "fp64_form": fp64,
         "speedup_vs_fp64": (fp64["sweep_s"] / (sweep_ms / 1e3)) if fp64 else None,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * len(sp) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": pool_bytes,
+        "e2e": {"value": len(sp) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": pool_bytes,
                 "d2h_bytes_per_step": pool_bytes + 8 * len(sp), "sweep_s": e2e_s},
         "clocks": clk.summary(),
         "gpu_launches": int(launches),

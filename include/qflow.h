@@ -121,6 +121,19 @@ void qflow_default_options(qflow_options* opt, int32_t precision);
 int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
                int64_t nspaces, int64_t* perm, int32_t* owner1, int32_t* owner2, int64_t* n_uncovered);
 
+/* Shard `rank` of `nranks` of a space list, for sweeps split over several processes (one GPU
+ * each; the paper's cycles run in process groups that meet at a barrier after every cycle,
+ * Numerical Implementation).  The device order of the list is grouped by size class and, within
+ * a class, in orbital-tuple order (occupied tuple, then virtual tuple); rank r takes positions
+ * [floor(r c_k / R), floor((r+1) c_k / R)) of every class k (c_k spaces, R ranks).
+ *   space_mask[nspaces]   out (nullable): 1 for the sorted positions the shard solves, else 0
+ *   pool_mask[nocc*nvir + nocc^2*nvir^2]  out (nullable): 1 for the amplitudes (t1 then t2)
+ *                          whose owner space the shard solves, else 0
+ * Over all ranks the space masks partition the list and the pool masks the owned amplitudes.
+ * Errors: QFLOW_ERR_ARG (bad rank / nranks or invalid problem), QFLOW_ERR_OOM. */
+int qflow_shard_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
+                     int64_t nspaces, int32_t rank, int32_t nranks, uint8_t* space_mask, uint8_t* pool_mask);
+
 /* ---- handle API: one flow on one GPU ---------------------------------------------------- */
 
 typedef struct qflow_ctx* qflow_handle;
@@ -135,6 +148,35 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
  * solver did not finish with status 0.  Returns QFLOW_ERR_NOCONV / ROOT / NONFINITE when some
  * space failed (its owned amplitudes then keep their old value). */
 int qflow_sweep(qflow_handle hnd, double* d_e, double* max_dt, int32_t* nfailed);
+
+/* ---- sharded sweeps: every rank holds a handle of the whole problem ----------------------
+ * After qflow_set_shard(h, rank, nranks) a sweep is three calls: qflow_sweep_shard_begin
+ * dresses (replicated: every rank dresses the same pool), solves the shard's spaces (see
+ * qflow_shard_plan) and writes the exchange vector; the caller sums the exchange vectors of all
+ * ranks element-wise (an allreduce with sum, e.g. NCCL on the device buffers) into each rank's
+ * buffer; qflow_sweep_shard_end merges it and runs DIIS and the reductions.  Every rank then
+ * holds the same pool, per-space energies and statistics, bitwise equal to an unsharded sweep:
+ * each owned amplitude (owner rule: one owner space) and each per-space value is produced by
+ * exactly one rank, and the other ranks contribute -0.0, which leaves any value unchanged under
+ * addition.  qflow_sweep returns QFLOW_ERR_STATE on a sharded handle; sharded sweeps run plain
+ * launches (no graph replay).  nranks = 1 makes the three-call form cover the whole list. */
+int qflow_set_shard(qflow_handle hnd, int32_t rank, int32_t nranks);
+
+/* Length (FP64 elements) of the exchange vector: pool (nocc*nvir + nocc^2*nvir^2), then
+ * energy, status and Davidson iterations per space (3 * nspaces, sorted order). */
+int64_t qflow_exchange_size(qflow_handle hnd);
+
+/* Dressing + this shard's solves; fills exchange[qflow_exchange_size] (device pointer, caller
+ * owned, 8-byte aligned) and synchronises the handle's stream before returning.  Errors:
+ * QFLOW_ERR_STATE without qflow_set_shard or while a sharded sweep is open. */
+int qflow_sweep_shard_begin(qflow_handle hnd, double* exchange);
+
+/* Merge of the summed exchange vector (device pointer; must be complete on the device when the
+ * call is made), DIIS, reductions.  Outputs and return codes as qflow_sweep.  Errors:
+ * QFLOW_ERR_STATE without a preceding qflow_sweep_shard_begin.  Between begin and end the
+ * handle refuses qflow_set_amplitudes, qflow_dressed and the network's pool calls. */
+int qflow_sweep_shard_end(qflow_handle hnd, const double* exchange, double* d_e, double* max_dt,
+                          int32_t* nfailed);
 
 /* E_QFlow of the last sweep and (nullable) the per-space energies in sorted order. */
 int qflow_energy(qflow_handle hnd, double* e_mean, double* e_per_space);

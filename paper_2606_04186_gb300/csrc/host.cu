@@ -115,6 +115,72 @@ void make_plan(const double* h, const double* eri, int n, int nocc, const qflow_
   for (int32_t o : pl->own2) pl->uncovered += (o < 0);
 }
 
+// Device order of a planned list: grouped by size class (k = 1, 2, 3), and within a class in
+// orbital-tuple order (occupied tuple, then virtual tuple) so that warps running at the same time
+// gather overlapping rows of W from L2.  gidx[d] = Delta-eps (sorted) position of device slot d.
+void group_spaces(const qflow_space* spaces, int64_t ns, const Plan& pl, std::vector<qflow_space>* grouped,
+                  std::vector<int64_t>* gidx, int64_t cls_count[4], int64_t cls_off[4]) {
+  grouped->assign((size_t)ns, qflow_space{});
+  gidx->assign((size_t)ns, 0);
+  for (int k = 0; k < 4; ++k) cls_count[k] = 0;
+  for (int64_t s = 0; s < ns; ++s) cls_count[spaces[pl.perm[s]].no]++;
+  cls_off[0] = 0;
+  cls_off[1] = 0;
+  cls_off[2] = cls_count[1];
+  cls_off[3] = cls_count[1] + cls_count[2];
+  int64_t fill[4] = {0, cls_off[1], cls_off[2], cls_off[3]};
+  for (int64_t s = 0; s < ns; ++s) {
+    const qflow_space& q = spaces[pl.perm[s]];
+    (*grouped)[fill[q.no]] = q;
+    (*gidx)[fill[q.no]] = s;
+    fill[q.no]++;
+  }
+  for (int k = 1; k <= 3; ++k) {
+    const int64_t b = cls_off[k], e = b + cls_count[k];
+    std::vector<int64_t> ord((size_t)(e - b));
+    std::iota(ord.begin(), ord.end(), b);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
+      for (int t = 0; t < 2 * k; ++t)
+        if ((*grouped)[x].orb[t] != (*grouped)[y].orb[t]) return (*grouped)[x].orb[t] < (*grouped)[y].orb[t];
+      return (*gidx)[x] < (*gidx)[y];
+    });
+    std::vector<qflow_space> gs(ord.size());
+    std::vector<int64_t> gi(ord.size());
+    for (size_t t = 0; t < ord.size(); ++t) {
+      gs[t] = (*grouped)[ord[t]];
+      gi[t] = (*gidx)[ord[t]];
+    }
+    std::copy(gs.begin(), gs.end(), grouped->begin() + b);
+    std::copy(gi.begin(), gi.end(), gidx->begin() + b);
+  }
+}
+
+// Shard `rank` of `nranks`: in every size class the class positions [lo[k], hi[k]) of the device
+// order (equal shares, the first ranks one smaller when the count does not divide).
+void shard_ranges(const int64_t cls_count[4], int rank, int nranks, int64_t lo[4], int64_t hi[4]) {
+  for (int k = 0; k < 4; ++k) {
+    lo[k] = cls_count[k] * rank / nranks;
+    hi[k] = cls_count[k] * (rank + 1) / nranks;
+  }
+}
+
+// Exchange masks of shard `rank`: space_mask[s] = 1 for the Delta-eps positions s the shard
+// solves; pool_mask[x] = 1 for the amplitudes (t1 then t2) whose owner space it solves.
+void shard_masks(const std::vector<int64_t>& gidx, const int64_t cls_count[4], const int64_t cls_off[4],
+                 const int32_t* own1, int64_t n1, const int32_t* own2, int64_t n2, int rank, int nranks,
+                 uint8_t* space_mask, uint8_t* pool_mask) {
+  int64_t lo[4], hi[4];
+  shard_ranges(cls_count, rank, nranks, lo, hi);
+  std::vector<uint8_t> sm(gidx.size(), 0);
+  for (int k = 1; k <= 3; ++k)
+    for (int64_t d = cls_off[k] + lo[k]; d < cls_off[k] + hi[k]; ++d) sm[(size_t)gidx[(size_t)d]] = 1;
+  if (space_mask) std::copy(sm.begin(), sm.end(), space_mask);
+  if (pool_mask) {
+    for (int64_t x = 0; x < n1; ++x) pool_mask[x] = (own1[x] >= 0) ? sm[(size_t)own1[x]] : 0;
+    for (int64_t x = 0; x < n2; ++x) pool_mask[n1 + x] = (own2[x] >= 0) ? sm[(size_t)own2[x]] : 0;
+  }
+}
+
 }  // namespace
 
 // ---- handle --------------------------------------------------------------------------------
@@ -173,6 +239,12 @@ struct qflow_ctx {
   int mlp_target = 0;              // kind of the stored pairs (QFLOW_MLP_TARGET_*)
   float *mlp_X = nullptr, *mlp_T = nullptr;
   uint8_t* mlp_mask = nullptr;
+  // sharded sweeps (qflow_set_shard): this rank solves class positions [lo[k], hi[k]) of class k
+  int shard_rank = 0, shard_n = 1;
+  int64_t shard_lo[4] = {0, 0, 0, 0}, shard_hi[4] = {0, 0, 0, 0};
+  uint8_t *space_mask = nullptr, *pool_mask = nullptr;  // device, see shard_masks
+  bool shard_open = false;  // between qflow_sweep_shard_begin and _end
+  bool shard_warm = false;  // that sweep started from the network's guesses
 };
 
 namespace {
@@ -193,7 +265,8 @@ void free_ctx(qflow_ctx* c) {
   if (c->diis) cudaFree(c->diis);
   if (c->W32) cudaFree(c->W32);
   if (c->queue) cudaFree(c->queue);
-  void* mptrs[] = {c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v, c->mlp_X, c->mlp_T, c->mlp_mask};
+  void* mptrs[] = {c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v, c->mlp_X, c->mlp_T, c->mlp_mask,
+                   c->space_mask, c->pool_mask};
   for (void* p : mptrs)
     if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -245,6 +318,26 @@ int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, cons
   return (pl.uncovered > 0) ? QFLOW_WARN_UNCOVERED : QFLOW_OK;
 }
 
+int qflow_shard_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
+                     int64_t nspaces, int32_t rank, int32_t nranks, uint8_t* space_mask, uint8_t* pool_mask) {
+  if (nranks < 1 || rank < 0 || rank >= nranks) return QFLOW_ERR_ARG;
+  int v = validate(h, eri, n, nocc, spaces, nspaces);
+  if (v != QFLOW_OK) return v;
+  try {
+    Plan pl;
+    make_plan(h, eri, n, nocc, spaces, nspaces, &pl, true);
+    std::vector<qflow_space> grouped;
+    std::vector<int64_t> gidx;
+    int64_t cnt[4], off[4];
+    group_spaces(spaces, nspaces, pl, &grouped, &gidx, cnt, off);
+    shard_masks(gidx, cnt, off, pl.own1.data(), (int64_t)pl.own1.size(), pl.own2.data(), (int64_t)pl.own2.size(),
+                rank, nranks, space_mask, pool_mask);
+  } catch (const std::bad_alloc&) {
+    return QFLOW_ERR_OOM;
+  }
+  return QFLOW_OK;
+}
+
 int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n, int32_t nocc,
                const qflow_space* spaces, int64_t nspaces, const qflow_options* opt) {
   if (!out) return QFLOW_ERR_ARG;
@@ -279,41 +372,9 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     return QFLOW_ERR_OOM;
   }
   c->perm = pl.perm;
-  // group by size class, sorted order within each class
-  std::vector<qflow_space> grouped((size_t)nspaces);
-  std::vector<int64_t> gidx((size_t)nspaces);
-  for (int64_t s = 0; s < nspaces; ++s) c->cls_count[spaces[pl.perm[s]].no]++;
-  c->cls_off[1] = 0;
-  c->cls_off[2] = c->cls_count[1];
-  c->cls_off[3] = c->cls_count[1] + c->cls_count[2];
-  int64_t fill[4] = {0, c->cls_off[1], c->cls_off[2], c->cls_off[3]};
-  for (int64_t s = 0; s < nspaces; ++s) {
-    const qflow_space& q = spaces[pl.perm[s]];
-    grouped[fill[q.no]] = q;
-    gidx[fill[q.no]] = s;
-    fill[q.no]++;
-  }
-  // Within a class the solve visits spaces in orbital-tuple order (occupied tuple, then virtual
-  // tuple) so that warps running at the same time gather overlapping rows of W from L2; the
-  // Delta-eps position of each space travels with it in gidx (owners, energies, statistics).
-  for (int k = 1; k <= 3; ++k) {
-    const int64_t b = c->cls_off[k], e = b + c->cls_count[k];
-    std::vector<int64_t> ord((size_t)(e - b));
-    std::iota(ord.begin(), ord.end(), b);
-    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
-      for (int t = 0; t < 2 * k; ++t)
-        if (grouped[x].orb[t] != grouped[y].orb[t]) return grouped[x].orb[t] < grouped[y].orb[t];
-      return gidx[x] < gidx[y];
-    });
-    std::vector<qflow_space> gs(ord.size());
-    std::vector<int64_t> gi(ord.size());
-    for (size_t t = 0; t < ord.size(); ++t) {
-      gs[t] = grouped[ord[t]];
-      gi[t] = gidx[ord[t]];
-    }
-    std::copy(gs.begin(), gs.end(), grouped.begin() + b);
-    std::copy(gi.begin(), gi.end(), gidx.begin() + b);
-  }
+  std::vector<qflow_space> grouped;
+  std::vector<int64_t> gidx;
+  group_spaces(spaces, nspaces, pl, &grouped, &gidx, c->cls_count, c->cls_off);
   const size_t n1 = n, n4 = n1 * n1 * n1 * n1;
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   c->dwork_bytes = (c->opt.precision == QFLOW_PREC_MIXED) ? qf::dress_workspace_bytes_mixed(n, nocc)
@@ -395,10 +456,11 @@ qf::SolveArgs solve_args(qflow_ctx* c, int k) {
   a.e0 = c->e0;
   a.F = c->F;
   a.W = c->W;
-  a.spaces = c->spaces + c->cls_off[k];
-  a.nspaces = c->cls_count[k];
+  const int64_t lo = (c->shard_n > 1) ? c->shard_lo[k] : 0;
+  a.spaces = c->spaces + c->cls_off[k] + lo;
+  a.nspaces = (c->shard_n > 1) ? c->shard_hi[k] - lo : c->cls_count[k];
   a.space_base = 0;
-  a.sorted_index = c->sorted_index + c->cls_off[k];
+  a.sorted_index = c->sorted_index + c->cls_off[k] + lo;
   a.owner1 = c->own1;
   a.owner2 = c->own2;
   a.t1_old = c->pool;
@@ -411,8 +473,11 @@ qf::SolveArgs solve_args(qflow_ctx* c, int k) {
   a.W32 = c->W32;
   // guess mode 1: start from and keep the previous roots; mode 2: keep 6e6o roots, start from
   // them only on a warm-start sweep (where the network has just written them)
-  a.guess = (c->opt.guess == 1 || c->mlp_guess_now) ? c->guess[k] : nullptr;
-  a.root_out = c->guess[k];
+  const size_t ndet[4] = {0, 4, 36, 400};
+  const size_t esz = (c->opt.precision == QFLOW_PREC_MIXED) ? sizeof(float) : sizeof(double);
+  void* roots = c->guess[k] ? static_cast<char*>(c->guess[k]) + (size_t)lo * ndet[k] * esz : nullptr;
+  a.guess = (c->opt.guess == 1 || c->mlp_guess_now) ? roots : nullptr;
+  a.root_out = roots;
   a.max_iter = c->opt.max_iter;
   a.tol = c->opt.tol;
   return a;
@@ -478,16 +543,24 @@ cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int
   return e;
 }
 
-// Steps (b)+(c): solves into pool_new, DIIS, reductions, pool_new -> pool, scalars to the host.
-cudaError_t enqueue_solve_merge(qflow_ctx* c, int64_t* launches) {
+// Step (b): pool_new <- pool, then the solves write t_old + X into pool_new for owned amplitudes.
+cudaError_t enqueue_solve_phase(qflow_ctx* c, int64_t* launches) {
   const size_t npool = (size_t)(c->n_t1 + c->n_t2);
   cudaError_t e = cudaMemcpyAsync(c->pool_new, c->pool, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = enqueue_solve(c, c->sched_persistent, c->sched_chunk, c->sched_ctas, 0, launches);
-  if (e == cudaSuccess && c->diis) {
+  return e;
+}
+
+// Step (c) after the solves: DIIS, phase mark 2 (unless already set), reductions,
+// pool_new -> pool, phase mark 3, scalars to the host.
+cudaError_t enqueue_merge_phase(qflow_ctx* c, bool mark2, int64_t* launches) {
+  const size_t npool = (size_t)(c->n_t1 + c->n_t2);
+  cudaError_t e = cudaSuccess;
+  if (c->diis) {
     e = qf::launch_diis(c->diis, c->opt.diis, c->pool, c->pool_new, (int64_t)npool, c->stream);
     *launches += 4;
   }
-  if (e == cudaSuccess) e = mark(c, 2);
+  if (e == cudaSuccess && mark2) e = mark(c, 2);
   if (e == cudaSuccess)
     e = qf::launch_reduce(c->energy, c->status, c->nspaces, c->pool, c->pool_new, (int64_t)npool, c->red, c->rwork,
                           c->stream);
@@ -497,6 +570,13 @@ cudaError_t enqueue_solve_merge(qflow_ctx* c, int64_t* launches) {
   if (e == cudaSuccess) e = mark(c, 3);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->red_host, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  return e;
+}
+
+// Steps (b)+(c) of an unsharded sweep.
+cudaError_t enqueue_solve_merge(qflow_ctx* c, int64_t* launches) {
+  cudaError_t e = enqueue_solve_phase(c, launches);
+  if (e == cudaSuccess) e = enqueue_merge_phase(c, true, launches);
   return e;
 }
 
@@ -618,16 +698,61 @@ cudaError_t autotune(qflow_ctx* c) {
   return cudaSuccess;
 }
 
+// A warm-start sweep: the network's guesses for the 6e6o spaces (outside any captured graph).
+bool warm_sweep(const qflow_ctx* c) {
+  return c->opt.guess == QFLOW_GUESS_NETWORK && c->mlp_pending && c->cls_count[3] > 0;
+}
+
+// Dressing, network guesses of a warm-start sweep, and the schedule calibration: the mixed
+// schedule is calibrated at the second sweep, whose work mix (most spaces near their root) is
+// that of the rest of a flow; the first sweep runs the default.
+cudaError_t enqueue_front(qflow_ctx* c, bool warm, int64_t* launches) {
+  cudaError_t e = enqueue_dress(c, launches);
+  if (e == cudaSuccess && warm) {
+    e = enqueue_mlp_guess(c, launches);
+    c->mlp_guess_now = true;
+  }
+  const bool mixed = c->opt.precision == QFLOW_PREC_MIXED;
+  if (e == cudaSuccess && !c->tuned && mixed && c->sweeps >= 1) e = autotune(c);
+  if (!mixed) c->tuned = true;  // FP64 runs per-class launches and needs no tuning
+  return e;
+}
+
+// Host side of a finished sweep (stream synchronised): energy change, scalars, status.
+int finish_sweep(qflow_ctx* c, bool warm, int64_t launches, double* d_e, double* max_dt, int32_t* nfailed) {
+  if (warm) c->mlp_pending = false;
+  c->fw_of_last_sweep = true;
+  ++c->sweeps;
+  c->last_launches = launches;
+  const double em = c->red_host[0];
+  const double de = c->have_energy ? em - c->e_mean : std::numeric_limits<double>::infinity();
+  c->e_mean = em;
+  c->have_energy = true;
+  if (d_e) *d_e = de;
+  if (max_dt) *max_dt = c->red_host[1];
+  const int32_t nf = (int32_t)c->red_host[2];
+  if (nfailed) *nfailed = nf;
+  if (!isfinite(em) || !isfinite(c->red_host[1])) return QFLOW_ERR_NONFINITE;
+  if (nf > 0) {
+    const int worst = (int)c->red_host[3];
+    if (worst == qf::kSpaceNonFinite) return QFLOW_ERR_NONFINITE;
+    if (worst == qf::kSpaceRoot) return QFLOW_ERR_ROOT;
+    return QFLOW_ERR_NOCONV;
+  }
+  return QFLOW_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
   if (!c) return QFLOW_ERR_ARG;
+  if (c->shard_n > 1 || c->shard_open) return QFLOW_ERR_STATE;  // sharded: begin / exchange / end
   int64_t launches = 0;
   cudaError_t e = cudaSuccess;
   // a warm-start sweep (network guesses for the 6e6o spaces) runs outside the captured graph
-  const bool warm = c->opt.guess == QFLOW_GUESS_NETWORK && c->mlp_pending && c->cls_count[3] > 0;
+  const bool warm = warm_sweep(c);
   if (c->opt.graph && !c->graph_exec && c->tuned && !warm) {
     // From the second sweep on: capture the sweep's device work once, then replay it.
     int64_t l2 = 0;
@@ -654,41 +779,91 @@ int qflow_sweep(qflow_handle c, double* d_e, double* max_dt, int32_t* nfailed) {
     e = cudaGraphLaunch(c->graph_exec, c->stream);
     launches = c->graph_launches;
   } else {
-    e = enqueue_dress(c, &launches);
-    if (e == cudaSuccess && warm) {
-      e = enqueue_mlp_guess(c, &launches);
-      c->mlp_guess_now = true;
-    }
-    // The mixed-precision schedule is calibrated at the second sweep, whose work mix (most
-    // spaces near their root) is that of the rest of a flow; the first sweep runs the default.
-    const bool mixed = c->opt.precision == QFLOW_PREC_MIXED;
-    if (e == cudaSuccess && !c->tuned && mixed && c->sweeps >= 1) e = autotune(c);
+    e = enqueue_front(c, warm, &launches);
     if (e == cudaSuccess) e = enqueue_solve_merge(c, &launches);
     c->mlp_guess_now = false;
-    if (!mixed) c->tuned = true;  // FP64 runs per-class launches and needs no tuning
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_status(e);
-  if (warm) c->mlp_pending = false;
-  c->fw_of_last_sweep = true;
-  ++c->sweeps;
+  return finish_sweep(c, warm, launches, d_e, max_dt, nfailed);
+}
+
+int qflow_set_shard(qflow_handle c, int32_t rank, int32_t nranks) {
+  if (!c || nranks < 1 || rank < 0 || rank >= nranks) return QFLOW_ERR_ARG;
+  if (c->shard_open) return QFLOW_ERR_STATE;
+  if (c->space_mask) cudaFree(c->space_mask);
+  if (c->pool_mask) cudaFree(c->pool_mask);
+  c->space_mask = c->pool_mask = nullptr;
+  c->shard_rank = rank;
+  c->shard_n = nranks;
+  shard_ranges(c->cls_count, rank, nranks, c->shard_lo, c->shard_hi);
+  // a captured sweep covers the whole list; sharded sweeps run plain launches
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  const int64_t ns = c->nspaces, npool = c->n_t1 + c->n_t2;
+  std::vector<int64_t> gidx((size_t)ns);
+  std::vector<int32_t> own((size_t)npool);
+  std::vector<uint8_t> smask((size_t)ns), pmask((size_t)npool);
+  cudaError_t e = cudaSuccess;
+  if (ns > 0)
+    e = cudaMemcpyAsync(gidx.data(), c->sorted_index, sizeof(int64_t) * (size_t)ns, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(own.data(), c->own1, sizeof(int32_t) * (size_t)c->n_t1, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(own.data() + c->n_t1, c->own2, sizeof(int32_t) * (size_t)c->n_t2, cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  shard_masks(gidx, c->cls_count, c->cls_off, own.data(), c->n_t1, own.data() + c->n_t1, c->n_t2, rank, nranks,
+              smask.data(), pmask.data());
+  e = dalloc(&c->space_mask, (size_t)std::max<int64_t>(ns, 1));
+  if (e == cudaSuccess) e = dalloc(&c->pool_mask, (size_t)npool);
+  if (e == cudaSuccess && ns > 0)
+    e = cudaMemcpyAsync(c->space_mask, smask.data(), (size_t)ns, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->pool_mask, pmask.data(), (size_t)npool, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+int64_t qflow_exchange_size(qflow_handle c) {
+  return c ? c->n_t1 + c->n_t2 + 3 * c->nspaces : 0;
+}
+
+int qflow_sweep_shard_begin(qflow_handle c, double* exchange) {
+  if (!c || !exchange) return QFLOW_ERR_ARG;
+  if (c->shard_open || !c->space_mask) return QFLOW_ERR_STATE;
+  int64_t launches = 0;
+  const bool warm = warm_sweep(c);
+  cudaError_t e = enqueue_front(c, warm, &launches);
+  if (e == cudaSuccess) e = enqueue_solve_phase(c, &launches);
+  c->mlp_guess_now = false;
+  if (e == cudaSuccess) e = mark(c, 2);
+  if (e == cudaSuccess)
+    e = qf::launch_exchange_pack(c->pool_new, c->pool_mask, c->n_t1 + c->n_t2, c->energy, c->status, c->iters,
+                                 c->space_mask, c->nspaces, exchange, c->stream);
+  ++launches;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  c->shard_open = true;
+  c->shard_warm = warm;
   c->last_launches = launches;
-  const double em = c->red_host[0];
-  const double de = c->have_energy ? em - c->e_mean : std::numeric_limits<double>::infinity();
-  c->e_mean = em;
-  c->have_energy = true;
-  if (d_e) *d_e = de;
-  if (max_dt) *max_dt = c->red_host[1];
-  const int32_t nf = (int32_t)c->red_host[2];
-  if (nfailed) *nfailed = nf;
-  if (!isfinite(em) || !isfinite(c->red_host[1])) return QFLOW_ERR_NONFINITE;
-  if (nf > 0) {
-    const int worst = (int)c->red_host[3];
-    if (worst == qf::kSpaceNonFinite) return QFLOW_ERR_NONFINITE;
-    if (worst == qf::kSpaceRoot) return QFLOW_ERR_ROOT;
-    return QFLOW_ERR_NOCONV;
-  }
   return QFLOW_OK;
+}
+
+int qflow_sweep_shard_end(qflow_handle c, const double* exchange, double* d_e, double* max_dt, int32_t* nfailed) {
+  if (!c || !exchange) return QFLOW_ERR_ARG;
+  if (!c->shard_open) return QFLOW_ERR_STATE;
+  c->shard_open = false;
+  int64_t launches = c->last_launches;
+  cudaError_t e = qf::launch_exchange_unpack(exchange, c->own1, c->n_t1, c->own2, c->n_t2, c->pool_new, c->energy,
+                                             c->status, c->iters, c->nspaces, c->stream);
+  ++launches;
+  if (e == cudaSuccess) e = enqueue_merge_phase(c, false, &launches);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return finish_sweep(c, c->shard_warm, launches, d_e, max_dt, nfailed);
 }
 
 int qflow_energy(qflow_handle c, double* e_mean, double* e_per_space) {
@@ -716,6 +891,7 @@ int qflow_amplitudes(qflow_handle c, double* t1, double* t2) {
 
 int qflow_set_amplitudes(qflow_handle c, const double* t1, const double* t2) {
   if (!c || !t1 || !t2) return QFLOW_ERR_ARG;
+  if (c->shard_open) return QFLOW_ERR_STATE;
   cudaError_t e = cudaMemcpyAsync(c->pool, t1, sizeof(double) * (size_t)c->n_t1, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->pool + c->n_t1, t2, sizeof(double) * (size_t)c->n_t2, cudaMemcpyHostToDevice, c->stream);
@@ -744,6 +920,7 @@ int qflow_space_stats(qflow_handle c, int32_t* iterations, int32_t* status) {
 
 int qflow_dressed(qflow_handle c, double* e0, double* F, double* W) {
   if (!c) return QFLOW_ERR_ARG;
+  if (c->shard_open) return QFLOW_ERR_STATE;
   const size_t n1 = c->n, n4 = n1 * n1 * n1 * n1;
   cudaError_t e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W,
                                    c->dwork, c->dwork_bytes, c->stream, c->W32);
@@ -924,8 +1101,10 @@ int qflow_mlp_get_model(qflow_handle c, float* model) {
 int qflow_mlp_collect(qflow_handle c, int32_t target, int64_t stride, int64_t max_pairs, int64_t* n_pairs) {
   if (!c || stride < 1 || max_pairs < 1) return QFLOW_ERR_ARG;
   if (target != QFLOW_MLP_TARGET_INCREMENT && target != QFLOW_MLP_TARGET_POOL) return QFLOW_ERR_ARG;
-  if (target == QFLOW_MLP_TARGET_INCREMENT &&
-      (c->opt.guess != QFLOW_GUESS_NETWORK || !c->have_energy || !c->fw_of_last_sweep || !c->guess[3]))
+  if (c->shard_open) return QFLOW_ERR_STATE;
+  // increment pairs read the roots of every 6e6o space: a shard holds only its own
+  if (target == QFLOW_MLP_TARGET_INCREMENT && (c->opt.guess != QFLOW_GUESS_NETWORK || !c->have_energy ||
+                                               !c->fw_of_last_sweep || !c->guess[3] || c->shard_n > 1))
     return QFLOW_ERR_STATE;
   if (c->mlp_cap > 0 && c->mlp_target != target) return QFLOW_ERR_STATE;  // one kind of pair per set
   cudaError_t e = cudaSuccess;
@@ -1045,7 +1224,7 @@ int qflow_mlp_train(qflow_handle c, int32_t epochs, int32_t batch, float lr, con
 
 int qflow_mlp_warm_pool(qflow_handle c) {
   if (!c) return QFLOW_ERR_ARG;
-  if (!c->mlp_model || !c->mlp_has_stats) return QFLOW_ERR_STATE;
+  if (!c->mlp_model || !c->mlp_has_stats || c->shard_open) return QFLOW_ERR_STATE;
   const int64_t n3 = c->cls_count[3];
   const int64_t CH = 131072;
   const int64_t rows = n3 < CH ? n3 : CH;

@@ -67,6 +67,16 @@ size_t mean_maxdiff_workspace(int64_t nspaces, int64_t nt);
 cudaError_t launch_reduce(const double* energy, const int32_t* status, int64_t nspaces, const double* t_old,
                           const double* t_new, int64_t nt, double* out4, void* work, cudaStream_t st);
 
+// Exchange vector of a sharded sweep, [pool | energy | status | iterations] in FP64, entries the
+// shard did not produce set to -0.0 (pack); after the element-wise sum over ranks, owned pool
+// entries and every per-space entry are taken from it (unpack).
+cudaError_t launch_exchange_pack(const double* pool_new, const uint8_t* pool_mask, int64_t np, const double* energy,
+                                 const int32_t* status, const int32_t* iters, const uint8_t* space_mask, int64_t ns,
+                                 double* x, cudaStream_t st);
+cudaError_t launch_exchange_unpack(const double* x, const int32_t* own1, int64_t n1, const int32_t* own2, int64_t n2,
+                                   double* pool_new, double* energy, int32_t* status, int32_t* iters, int64_t ns,
+                                   cudaStream_t st);
+
 // Pool DIIS (diis.cu): workspace size for a ring of m vectors of length N, the per-sweep step
 // (t_new is replaced by the extrapolation once two vectors are stored) and the history reset.
 size_t diis_workspace_bytes(int m, int64_t N);

@@ -6,6 +6,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "qflow_internal.h"
 
 namespace qf {
@@ -83,7 +85,68 @@ __global__ void k_final(const Partial* __restrict__ in, int64_t ns, double* __re
   }
 }
 
+// Exchange vector of a sharded sweep: [pool (np) | energy (ns) | status (ns) | iterations (ns)].
+// Entries this shard did not produce hold -0.0, the identity of floating-point addition for every
+// value (x + (-0.0) = x, also for x = +0.0 and -0.0), so the element-wise sum over the ranks
+// reproduces each produced entry exactly, in any summation order.
+__global__ void k_exchange_pack(const double* __restrict__ pool_new, const uint8_t* __restrict__ pool_mask, int64_t np,
+                                const double* __restrict__ energy, const int32_t* __restrict__ status,
+                                const int32_t* __restrict__ iters, const uint8_t* __restrict__ space_mask, int64_t ns,
+                                double* __restrict__ x) {
+  const int64_t total = np + 3 * ns;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = -0.0;
+    if (i < np) {
+      if (pool_mask[i]) v = pool_new[i];
+    } else {
+      const int64_t j = (i - np) % ns, seg = (i - np) / ns;
+      if (space_mask[j]) v = (seg == 0) ? energy[j] : (double)((seg == 1) ? status[j] : iters[j]);
+    }
+    x[i] = v;
+  }
+}
+
+// After the sum over ranks: owned amplitudes take the summed value (each has exactly one owner
+// space, solved by exactly one rank); unowned ones keep t_old (already in pool_new).
+__global__ void k_exchange_unpack(const double* __restrict__ x, const int32_t* __restrict__ own1, int64_t n1,
+                                  const int32_t* __restrict__ own2, int64_t n2, double* __restrict__ pool_new,
+                                  double* __restrict__ energy, int32_t* __restrict__ status,
+                                  int32_t* __restrict__ iters, int64_t ns) {
+  const int64_t np = n1 + n2, total = np + 3 * ns;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < np) {
+      const int32_t o = (i < n1) ? own1[i] : own2[i - n1];
+      if (o >= 0) pool_new[i] = x[i];
+    } else {
+      const int64_t j = (i - np) % ns, seg = (i - np) / ns;
+      if (seg == 0) energy[j] = x[i];
+      else if (seg == 1) status[j] = (int32_t)x[i];
+      else iters[j] = (int32_t)x[i];
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_exchange_pack(const double* pool_new, const uint8_t* pool_mask, int64_t np, const double* energy,
+                                 const int32_t* status, const int32_t* iters, const uint8_t* space_mask, int64_t ns,
+                                 double* x, cudaStream_t st) {
+  const int64_t total = np + 3 * ns;
+  if (total == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((total + RB - 1) / RB, 152 * 16);
+  k_exchange_pack<<<(unsigned)blocks, RB, 0, st>>>(pool_new, pool_mask, np, energy, status, iters, space_mask, ns, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exchange_unpack(const double* x, const int32_t* own1, int64_t n1, const int32_t* own2, int64_t n2,
+                                   double* pool_new, double* energy, int32_t* status, int32_t* iters, int64_t ns,
+                                   cudaStream_t st) {
+  const int64_t total = n1 + n2 + 3 * ns;
+  if (total == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((total + RB - 1) / RB, 152 * 16);
+  k_exchange_unpack<<<(unsigned)blocks, RB, 0, st>>>(x, own1, n1, own2, n2, pool_new, energy, status, iters, ns);
+  return cudaGetLastError();
+}
 
 size_t mean_maxdiff_workspace(int64_t, int64_t) { return sizeof(Partial) * RGRID; }
 

@@ -85,6 +85,11 @@ def lib() -> C.CDLL:
         "qflow_mlp_targets_device": (I32, [P, I64, P, P]),
         "qflow_mlp_guess_device": (I32, [P, I64, P, P]),
         "qflow_gemm_tf32x3_device": (I32, [I32, I32, I32, P, I32, P, I32, P, I32, P, P]),
+        "qflow_shard_plan": (I32, [P, P, I32, I32, P, I64, I32, I32, P, P]),
+        "qflow_set_shard": (I32, [P, I32, I32]),
+        "qflow_exchange_size": (I64, [P]),
+        "qflow_sweep_shard_begin": (I32, [P, P]),
+        "qflow_sweep_shard_end": (I32, [P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -133,6 +138,18 @@ def plan(h, eri, nocc: int, spaces):
     return perm, o1, o2, unc.value
 
 
+def shard_plan(h, eri, nocc: int, spaces, rank: int, nranks: int):
+    """(space_mask[nspaces] in sorted order, pool_mask[o*v + o^2 v^2]) of shard `rank` (host only)."""
+    h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
+    n = h.shape[0]
+    nv = n - nocc
+    smask = np.empty(len(sp), dtype=np.uint8)
+    pmask = np.empty(nocc * nv + (nocc * nv) ** 2, dtype=np.uint8)
+    _check(lib().qflow_shard_plan(_ptr(h), _ptr(eri), n, nocc, _ptr(sp), len(sp), rank, nranks, _ptr(smask),
+                                  _ptr(pmask)), "qflow_shard_plan")
+    return smask, pmask
+
+
 def default_options(precision: str = "fp64") -> Options:
     o = Options()
     lib().qflow_default_options(C.byref(o), PREC[precision])
@@ -179,6 +196,38 @@ class Flow:
         if raise_on_fail:
             _check(code, "qflow_sweep")
         return de.value, dt.value, nf.value, code
+
+    # ---- sharded sweeps (one process per GPU, summed exchange vectors) ----
+    def set_shard(self, rank: int, nranks: int):
+        _check(lib().qflow_set_shard(self._h, rank, nranks), "qflow_set_shard")
+
+    def exchange_size(self) -> int:
+        return int(lib().qflow_exchange_size(self._h))
+
+    def sweep_shard_begin(self, exchange):
+        """Dressing + this shard's solves into `exchange` (float64 CUDA tensor of exchange_size())."""
+        if exchange.dtype != _torch().float64 or exchange.numel() < self.exchange_size():
+            raise ValueError("exchange must be a float64 CUDA tensor of exchange_size() elements")
+        _check(lib().qflow_sweep_shard_begin(self._h, _dptr(exchange)), "qflow_sweep_shard_begin")
+
+    def sweep_shard_end(self, exchange, raise_on_fail: bool = True):
+        """Merge of the exchange vector summed over all ranks; returns what sweep() returns."""
+        if exchange.dtype != _torch().float64 or exchange.numel() < self.exchange_size():
+            raise ValueError("exchange must be a float64 CUDA tensor of exchange_size() elements")
+        de, dt, nf = C.c_double(), C.c_double(), C.c_int32()
+        code = lib().qflow_sweep_shard_end(self._h, _dptr(exchange), C.byref(de), C.byref(dt), C.byref(nf))
+        if raise_on_fail:
+            _check(code, "qflow_sweep_shard_end")
+        return de.value, dt.value, nf.value, code
+
+    def sweep_sharded(self, exchange, group=None, raise_on_fail: bool = True):
+        """One sharded sweep with torch.distributed: begin, all_reduce(sum) of the exchange
+        vector over `group`, end."""
+        torch = _torch()
+        self.sweep_shard_begin(exchange)
+        torch.distributed.all_reduce(exchange, op=torch.distributed.ReduceOp.SUM, group=group)
+        torch.cuda.current_stream(exchange.device).synchronize()
+        return self.sweep_shard_end(exchange, raise_on_fail)
 
     def energy(self, per_space: bool = False):
         e = C.c_double()
@@ -264,6 +313,11 @@ class Flow:
 
 
 # ---- device-level steps on torch CUDA tensors ------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
 
 def _dptr(t) -> int:
     if not t.is_cuda or not t.is_contiguous():
