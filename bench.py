@@ -65,19 +65,22 @@ def parse():
 # ---- per-space flop accounting of the solve kernel (6e6o, 400 determinants) ------------------
 
 def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12, k: int = 3, kmax: int = 3) -> float:
-    """Algorithmic flops of the batched Davidson for spaces that ran `iters` iterations.
+    """Algorithmic flops of the batched Davidson for 6e6o spaces that ran `iters` iterations.
 
-    Every space: sigma(Phi) from Phi's sparse column (alpha-beta couplings of the (1+k^2)^2
-    Phi/single string pairs, k^2 terms each, and the same-spin column, NS*NSG*(1+k) terms) and the
-    residual norm.  Spaces that iterate: the same-spin string operator (135 coupling paths per
-    string) and the first-order correction test.  Iteration with subspace size j: residual
-    400*(4j+4), Gram-Schmidt 2 passes 400*(4j) (none on the first step from Phi, whose new
-    direction only drops its Phi component), norm+scale 400*3, one sigma = 400 * (2*NSG^2 +
-    4*NS + 2) = 148,000 flop, projected row/column 400*2*(2j+1); the subspace restarts at kmax.
+    Every space: the Phi column of the operator from its coupling table (153 terms for the 117
+    nonzero determinants) and its norm.  Spaces that iterate: the alpha-beta Coulomb row sums
+    (NORB*NS*K), the first-order vector on the 117 nonzeros (diagonal, division, norm), and the
+    same-spin string operator (1,980 merged terms).  Iteration m with subspace size j: the first
+    (m = 1, from Phi) only scales the first-order vector; later ones form the residual
+    400*(4j+4), precondition 400*8, orthogonalise in two passes 400*(4j)*2 and normalise 400*3.
+    Each iteration applies sigma, 400 * (2*NSG^2 + 4*NS + 2) = 148,000 flop, and forms the new
+    row and column of the projected matrix 400*2*(2j+1); the subspace restarts at kmax.  The
+    convergence test after the last iteration forms one more residual.
     """
     sig = ndet * (2 * nsg * nsg + 4 * ns + 2)
-    phi = 2 * ((1 + k * k) ** 2 * k * k + ns * nsg * (1 + k)) + 2 * ndet
-    hs = 2 * ns * 135 + 4 * ndet
+    nz = 117
+    phi = 2 * 153 + 2 * nz
+    first = 2 * 6 * ns * k + nz * 8 + 2 * 1980
     m_max = int(iters.max()) if iters.size else 0
     cum = np.zeros(m_max + 1)
     j, tot = 1, 0.0
@@ -85,11 +88,15 @@ def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12
         if j == kmax:
             tot += ndet * (4 * kmax + 6)          # restart: Ritz vector + its sigma combination + norms
             j = 1
-        gs = 0 if m == 1 else ndet * 8 * j
-        tot += ndet * (4 * j + 4) + gs + ndet * 3 + sig + ndet * 2 * (2 * j + 1)
+        if m == 1:
+            tot += ndet
+        else:
+            tot += ndet * (4 * j + 4) + ndet * 8 + ndet * 8 * j + ndet * 3
+        tot += sig + ndet * 2 * (2 * j + 1)
         j += 1
-        cum[m] = tot
-    return float(phi * iters.size + hs * np.count_nonzero(iters > 0) + cum[np.clip(iters, 0, m_max)].sum())
+        cum[m] = tot + ndet * (4 * j + 4)         # + the residual of the convergence test
+    it = np.clip(iters, 0, m_max)
+    return float(phi * iters.size + first * np.count_nonzero(iters > 0) + cum[it].sum())
 
 
 def dress_gemm_flops(o: int, v: int) -> float:

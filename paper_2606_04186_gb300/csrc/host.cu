@@ -212,7 +212,7 @@ struct qflow_ctx {
   int64_t n_t1 = 0, n_t2 = 0;
   void* guess[4] = {nullptr, nullptr, nullptr, nullptr};  // previous roots per size class (opt.guess == 1)
   void* diis = nullptr;                                   // DIIS ring (opt.diis > 0)
-  float* W32 = nullptr;                                   // FP32 copy of W (mixed precision)
+  float* W32 = nullptr;  // FP32 copies of W (n^4) and F (n^2, after W) for the mixed-precision solver
   unsigned long long* queue = nullptr;                    // persistent-launch work counter
   // launch schedule of the mixed-precision solver: persistent queue or one launch per class
   int sched_persistent = 1, sched_chunk = 4, sched_ctas = 0;
@@ -399,7 +399,7 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   if (e == cudaSuccess) e = dalloc(&c->red, 4);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->red_host), 4 * sizeof(double));
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
-  if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) e = dalloc(&c->W32, n4);
+  if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) e = dalloc(&c->W32, n4 + n1 * n1);
   if (e == cudaSuccess) e = dalloc(&c->queue, 1);
   if (c->opt.schedule == QFLOW_SCHED_PER_CLASS) {
     c->sched_persistent = 0;
@@ -471,6 +471,7 @@ qf::SolveArgs solve_args(qflow_ctx* c, int k) {
   a.status = c->status;
   a.iters = c->iters;
   a.W32 = c->W32;
+  a.F32 = c->W32 ? c->W32 + (size_t)c->n * c->n * c->n * c->n : nullptr;
   // guess mode 1: start from and keep the previous roots; mode 2: keep 6e6o roots, start from
   // them only on a warm-start sweep (where the network has just written them)
   const size_t ndet[4] = {0, 4, 36, 400};
@@ -501,8 +502,10 @@ cudaError_t enqueue_dress(qflow_ctx* c, int64_t* launches) {
                          c->dwork_bytes, c->stream, c->W32);
   *launches += qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
   if (e == cudaSuccess && c->W32) {
-    e = qf::launch_to_f32(c->W, c->W32, (size_t)c->n * c->n * c->n * c->n, c->stream);
-    ++*launches;
+    const size_t n4 = (size_t)c->n * c->n * c->n * c->n;
+    e = qf::launch_to_f32(c->W, c->W32, n4, c->stream);
+    if (e == cudaSuccess) e = qf::launch_to_f32(c->F, c->W32 + n4, (size_t)c->n * c->n, c->stream);
+    *launches += 2;
   }
   if (e == cudaSuccess) e = mark(c, 1);
   return e;

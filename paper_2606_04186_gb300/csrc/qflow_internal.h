@@ -33,6 +33,7 @@ struct SolveArgs {
   int32_t* status;
   int32_t* iters;
   const float* W32;  // nullable FP32 copy of W (mixed path)
+  const float* F32;  // nullable FP32 copy of F (mixed path; else F is converted per element)
   const void* guess;  // nullable start vectors: double (FP64 path) or float (mixed path)
   void* root_out;     // nullable: receives converged roots (Phi coefficient 1), same type/layout
   int32_t max_iter;

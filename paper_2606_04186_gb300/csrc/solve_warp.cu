@@ -105,68 +105,205 @@ struct TabHolder {
   static constexpr Tab3 value = make_tab3();
 };
 
-// Same-spin string operator of the 6e6o class as a list of coupling paths per string I:
-//   Hs[I][J] = sum_u [J_u = J] s_u h'[pq_u] + 1/2 sum_{u,v} [J(J_u, v) = J] s_u s_v W[pq_u][pq_v],
-// J != I, u over the replacements into I and v over those into J_u.  Entry k of string I is
-// e[k][I]: bits 0-10 source (W index pq_u * 36 + pq_v, or 1296 + pq_u for h'), bit 11 sign,
-// bits 12-16 target J, bit 17 last entry of its target (grouped by target, so a row is summed
-// in registers and each entry stored once).  The same for every space: built at compile time.
-constexpr int kHsPaths = 9 + 126;  // one-body and two-body paths per string
-struct HsPaths {
-  unsigned e[kHsPaths * 20];
+// ---- compile-time coupling tables of the 6e6o class, balanced over the 32 lanes of a warp -------
+//
+// A table is a list of terms per target element; a term adds c * X[src] to its target, where X is
+// the warp state's W block (pq * 36 + rs) followed by h' (1296 + pq), and c is +-1/2, +-1 or +-2
+// (merged under the pair symmetry W[pq][rs] = W[rs][pq]).  Whole targets are dealt to lanes in
+// order so that every lane gets at most L terms; entry k of lane l is e[k * 32 + l]:
+//   bits 0-10 src, 11-19 target, 20 last term of its target, 21 also store at the transposed
+//   target, 23-31 sign and exponent of the float c (mantissa 0), so c = as_float(e & 0xff800000);
+//   padding entries have c = 0 and src 0 (a W element that is always 0).
+// Same-spin string operator: Hs[I][J] = sum_u [J_u = J] s_u h'[pq_u]
+//                                     + 1/2 sum_{u,v} [J(J_u, v) = J] s_u s_v W[pq_u][pq_v],  J != I,
+// u over the single replacements into string I, v over those into J_u.
+// Phi column: sigma(Phi)[d] for d != 0 relative to <Phi|H|Phi>: at (I, 0) and (0, I), Hs[I][0]
+// plus the alpha-beta couplings of string I and the Phi string; at (a, b) for single
+// replacements a, b of the Phi string, their alpha-beta coupling (the column is symmetric in the
+// two spins, so each unique element is computed once and stored at both places).
+constexpr int kTermMax = 2400;
+struct TermList {
+  int ntgt = 0, nterm = 0;
+  int tgt[400] = {};
+  int mirror[400] = {};
+  int first[401] = {};
+  int src[kTermMax] = {};
+  int c2[kTermMax] = {};  // coefficient in units of 1/2
 };
-__host__ __device__ constexpr HsPaths make_hs_paths() {
-  HsPaths h{};
-  constexpr Tab3 t = make_tab3();
-  for (int I = 0; I < 20; ++I) {
-    unsigned src[kHsPaths] = {}, tgt[kHsPaths] = {};
-    int n = 0;
-    for (int u = 0; u < 12; ++u) {
-      const int Ku = t.J[I][u];
-      if (Ku != I && n < kHsPaths) {
-        src[n] = (unsigned)(1296 + t.pq[I][u]) | (t.sg[I][u] < 0 ? 2048u : 0u);
-        tgt[n] = (unsigned)Ku;
-        ++n;
-      }
-      for (int v = 0; v < 12; ++v) {
-        const int J2 = t.J[Ku][v];
-        if (J2 == I || n >= kHsPaths) continue;
-        const int sgn = t.sg[I][u] * t.sg[Ku][v];
-        src[n] = (unsigned)(t.pq[I][u] * 36 + t.pq[Ku][v]) | (sgn < 0 ? 2048u : 0u);
-        tgt[n] = (unsigned)J2;
-        ++n;
-      }
-    }
-    // stable grouping by target
-    int k = 0;
-    for (int J = 0; J < 20; ++J) {
-      int last = -1;
-      for (int x = 0; x < n; ++x)
-        if ((int)tgt[x] == J) {
-          h.e[k * 20 + I] = src[x] | (tgt[x] << 12);
-          last = k;
-          ++k;
-        }
-      if (last >= 0) h.e[last * 20 + I] |= 1u << 17;
+
+// Adds the merged terms of one target (keys/coefficients gathered by the caller) to the list;
+// a coefficient of 3/2 becomes two terms (1 and 1/2) so that every c is a power of two.
+__host__ __device__ constexpr void push_target(TermList& L, int target, int mirror, const int* key, const int* c2,
+                                               int n) {
+  int cnt = 0;
+  for (int x = 0; x < n; ++x) cnt += (c2[x] != 0);
+  if (cnt == 0) return;
+  L.tgt[L.ntgt] = target;
+  L.mirror[L.ntgt] = mirror;
+  L.first[L.ntgt] = L.nterm;
+  for (int x = 0; x < n; ++x) {
+    int c = c2[x];
+    if (c == 0) continue;
+    const int sg = c < 0 ? -1 : 1;
+    int m = c * sg;
+    while (m > 0) {
+      const int part = (m == 3) ? 2 : m;  // 3 -> 2 + 1; 1, 2 and 4 are powers of two
+      L.src[L.nterm] = key[x];
+      L.c2[L.nterm] = sg * part;
+      ++L.nterm;
+      m -= part;
     }
   }
-  return h;
+  ++L.ntgt;
+  L.first[L.ntgt] = L.nterm;
 }
-__host__ __device__ constexpr bool hs_paths_complete() {  // every string has exactly kHsPaths
-  constexpr Tab3 t = make_tab3();
-  for (int I = 0; I < 20; ++I) {
-    int n = 0;
-    for (int u = 0; u < 12; ++u) {
-      if (t.J[I][u] != I) ++n;
-      for (int v = 0; v < 12; ++v)
-        if (t.J[t.J[I][u]][v] != I) ++n;
+
+__host__ __device__ constexpr int add_key(int* key, int* c2, int n, int k, int c) {
+  for (int x = 0; x < n; ++x)
+    if (key[x] == k) {
+      c2[x] += c;
+      return n;
     }
-    if (n != kHsPaths) return false;
+  key[n] = k;
+  c2[n] = c;
+  return n + 1;
+}
+
+__host__ __device__ constexpr int wkey(int a, int b) { return a < b ? a * 36 + b : b * 36 + a; }
+
+// Merged same-spin couplings of string I into target J (J != I); returns the number of keys.
+__host__ __device__ constexpr int hs_terms(const Tab3& t, int I, int J, int* key, int* c2) {
+  int n = 0;
+  for (int u = 0; u < 12; ++u) {
+    const int Ku = t.J[I][u];
+    if (Ku != I && Ku == J) n = add_key(key, c2, n, 1296 + t.pq[I][u], 2 * t.sg[I][u]);
+    for (int v = 0; v < 12; ++v)
+      if (t.J[Ku][v] == J) n = add_key(key, c2, n, wkey(t.pq[I][u], t.pq[Ku][v]), t.sg[I][u] * t.sg[Ku][v]);
   }
+  return n;
+}
+
+__host__ __device__ constexpr TermList make_hs_terms() {
+  TermList L{};
+  const Tab3 t = make_tab3();
+  for (int I = 0; I < 20; ++I)
+    for (int J = 0; J < 20; ++J) {
+      if (J == I) continue;
+      int key[64] = {}, c2[64] = {};
+      const int n = hs_terms(t, I, J, key, c2);
+      push_target(L, I * 20 + J, 0, key, c2, n);
+    }
+  return L;
+}
+
+__host__ __device__ constexpr TermList make_phi_terms() {
+  TermList L{};
+  const Tab3 t = make_tab3();
+  int c0[20][3] = {}, n0[20] = {};  // replacements u with J[I][u] = 0 (the Phi string)
+  for (int I = 0; I < 20; ++I)
+    for (int u = 0; u < 12; ++u)
+      if (t.J[I][u] == 0 && n0[I] < 3) c0[I][n0[I]++] = u;
+  for (int I = 1; I < 20; ++I) {  // (I, 0), mirrored to (0, I)
+    int key[64] = {}, c2[64] = {};
+    int n = hs_terms(t, I, 0, key, c2);
+    for (int x = 0; x < n0[I]; ++x)
+      for (int y = 0; y < n0[0]; ++y) {
+        const int u = c0[I][x], v = c0[0][y];
+        n = add_key(key, c2, n, wkey(t.pq[I][u], t.pq[0][v]), 2 * t.sg[I][u] * t.sg[0][v]);
+      }
+    push_target(L, I * 20, 1, key, c2, n);
+  }
+  for (int a = 1; a < 20; ++a)  // (a, b), a <= b single replacements of the Phi string
+    for (int b = a; b < 20; ++b) {
+      if (n0[a] == 0 || n0[b] == 0) continue;
+      int key[16] = {}, c2[16] = {};
+      int n = 0;
+      for (int x = 0; x < n0[a]; ++x)
+        for (int y = 0; y < n0[b]; ++y) {
+          const int u = c0[a][x], v = c0[b][y];
+          n = add_key(key, c2, n, wkey(t.pq[a][u], t.pq[b][v]), 2 * t.sg[a][u] * t.sg[b][v]);
+        }
+      push_target(L, a * 20 + b, a != b ? 1 : 0, key, c2, n);
+    }
+  return L;
+}
+
+// Smallest per-lane length that deals the targets, in order, to at most 32 lanes.
+__host__ __device__ constexpr int lane_length(const TermList& L) {
+  int len = (L.nterm + 31) / 32;
+  for (;; ++len) {
+    int lanes = 1, cur = 0;
+    for (int g = 0; g < L.ntgt; ++g) {
+      const int c = L.first[g + 1] - L.first[g];
+      if (c > len) {
+        lanes = 99;
+        break;
+      }
+      if (cur + c > len) {
+        ++lanes;
+        cur = 0;
+      }
+      cur += c;
+    }
+    if (lanes <= 32) return len;
+  }
+}
+
+__host__ __device__ constexpr unsigned coef_bits(int c2) {  // float c2 / 2, top 9 bits only
+  const unsigned sign = c2 < 0 ? 0x80000000u : 0u;
+  const int m = c2 < 0 ? -c2 : c2;
+  const unsigned expo = (m == 1) ? 126u : (m == 2) ? 127u : 128u;  // 1/2, 1, 2
+  return sign | (expo << 23);
+}
+
+template <int LEN>
+struct LaneTable {
+  unsigned e[LEN * 32];
+};
+
+template <int LEN>
+__host__ __device__ constexpr LaneTable<LEN> deal(const TermList& L) {
+  LaneTable<LEN> T{};
+  int lane = 0, cur = 0;
+  for (int g = 0; g < L.ntgt; ++g) {
+    const int c = L.first[g + 1] - L.first[g];
+    if (cur + c > LEN) {
+      ++lane;
+      cur = 0;
+    }
+    for (int x = 0; x < c; ++x) {
+      const int k = L.first[g] + x;
+      unsigned e = (unsigned)L.src[k] | ((unsigned)L.tgt[g] << 11) | coef_bits(L.c2[k]);
+      if (x == c - 1) e |= 1u << 20;
+      if (L.mirror[g]) e |= 1u << 21;
+      T.e[(cur + x) * 32 + lane] = e;
+    }
+    cur += c;
+  }
+  return T;
+}
+
+__host__ __device__ constexpr bool terms_valid(const TermList& L) {
+  if (L.nterm > kTermMax) return false;
+  for (int k = 0; k < L.nterm; ++k) {
+    const int m = L.c2[k] < 0 ? -L.c2[k] : L.c2[k];
+    if (!(m == 1 || m == 2 || m == 4) || L.src[k] < 0 || L.src[k] >= 1296 + 36) return false;
+  }
+  for (int g = 0; g < L.ntgt; ++g)
+    if (L.tgt[g] < 0 || L.tgt[g] >= 400) return false;
   return true;
 }
-static_assert(hs_paths_complete(), "uniform path count per 6e6o string");
-__device__ const HsPaths g_hs_paths = make_hs_paths();
+
+struct TermHolder {
+  static constexpr TermList hs = make_hs_terms();
+  static constexpr TermList phi = make_phi_terms();
+};
+static_assert(terms_valid(TermHolder::hs) && terms_valid(TermHolder::phi), "coupling tables");
+constexpr int kHsLen = lane_length(TermHolder::hs);
+constexpr int kPhiLen = lane_length(TermHolder::phi);
+static_assert(kHsLen <= 72 && kPhiLen <= 12, "balanced coupling tables");
+__device__ const LaneTable<kHsLen> g_hs_table = deal<kHsLen>(TermHolder::hs);
+__device__ const LaneTable<kPhiLen> g_phi_table = deal<kPhiLen>(TermHolder::phi);
 
 template <int B, int V>
 __device__ __forceinline__ void ab_term(float (&acc)[20], const float (&wr)[36], const float (&cr)[20]) {
@@ -200,14 +337,14 @@ struct Tabs {  // run-time string tables of one size class (bytes: they share th
   signed char xs[K * K];
 };
 
-// FP64 set-up data of one space (gather, fold, string diagonal); dead once the Davidson loop
-// has more than two vectors, so the 6e6o state keeps it in its third vector slot.
+// Set-up data of one space (gather, fold); dead once the Davidson loop has more than two
+// vectors, so the 6e6o state keeps it in its third vector slot.
 template <int K>
-struct SetupF64 {
+struct SetupF32 {
   using D = Dim<K>;
-  double F[D::NF], J[D::NF], Kx[D::NF];  // F block; J_pr = W_pprr, K_pr = W_prrp
-  double hd[D::NORB];                    // folded one-body diagonal h_pp
-  double hsd[D::NS];                     // same-spin string diagonal
+  float F[D::NF];     // F block
+  float J[D::NF];     // J_pr = W_pprr (the block's diagonal-only entries)
+  float hd[D::NORB];  // folded one-body diagonal h_pp
 };
 
 template <int K>
@@ -215,35 +352,38 @@ struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as fl
   using D = Dim<K>;
   float V[KM * D::NDET];
   float S[KM * D::NDET];
-  float Wt[D::NW];          // FP32 W block without its [pp][rr] (diagonal-only) entries
+  // FP32 W block without its [pp][rr] (diagonal-only) entries, then h' = h - 1/2 sum_r W_prrq
+  // (off-diagonal part): the coupling tables index both as one array
+  float Wt[D::NW + D::NF];
   float Hs[D::NS * D::NS];  // same-spin string operator, zero diagonal
-  float dh[(D::NS + 3) / 4 * 4];  // hsd[I] - hsd[0]; Hs[I][0] on the Phi path
+  float dh[(D::NS + 3) / 4 * 4];  // same-spin string diagonal relative to the Phi string
   float jb[D::NORB * D::NS];  // jb[p][Ib] = sum_{r in Ib} J_pr
-  float hp[D::NF];          // h' = h - 1/2 sum_r W_prrq (off-diagonal part, FP32)
   float G[KM * KM];         // projected matrix, G[i*KM+j] = V_i . S_j
   float yf[KM];             // Ritz coefficients
   float theta;              // Ritz value relative to eshift
   float j0;                 // sum_{p, r in Phi string} J_pr (FP32, diagonal reference)
-  double ecore, eshift;
+  double eshift;             // <Phi|H|Phi> = E0 of the dressing (the fold leaves it unchanged)
   int orb[D::NORB];
   int ctrl[4];              // [0] subspace size, [1] valid, [2] status, [3] iterations
   // the small classes keep set-up data and gather offsets here (the 6e6o state reuses the
   // third V slot and the second S slot, which are free until the Davidson loop needs them)
-  alignas(16) unsigned char extra[K == 3 ? 16 : sizeof(SetupF64<K>) + 2 * D::NF * sizeof(long long)];
+  alignas(16) unsigned char extra[K == 3 ? 16 : sizeof(SetupF32<K>) + 2 * D::NF * sizeof(long long)];
+  __device__ __forceinline__ float* hp() { return Wt + D::NW; }
+  __device__ __forceinline__ const float* hp() const { return Wt + D::NW; }
 };
 
 template <int K>
-__device__ __forceinline__ SetupF64<K>& setup(WarpState<K>& ws) {
-  if constexpr (K == 3) return *reinterpret_cast<SetupF64<K>*>(ws.V + 2 * Dim<K>::NDET);
-  else return *reinterpret_cast<SetupF64<K>*>(ws.extra);
+__device__ __forceinline__ SetupF32<K>& setup(WarpState<K>& ws) {
+  if constexpr (K == 3) return *reinterpret_cast<SetupF32<K>*>(ws.V + 2 * Dim<K>::NDET);
+  else return *reinterpret_cast<SetupF32<K>*>(ws.extra);
 }
 // gather offsets: element (P, R) of the W block sits at off[P] + off[NF + R]
 template <int K>
 __device__ __forceinline__ long long* gather_off(WarpState<K>& ws) {
   if constexpr (K == 3) return reinterpret_cast<long long*>(ws.S + Dim<K>::NDET);
-  else return reinterpret_cast<long long*>(ws.extra + sizeof(SetupF64<K>));
+  else return reinterpret_cast<long long*>(ws.extra + sizeof(SetupF32<K>));
 }
-static_assert(KM == 3 && sizeof(SetupF64<3>) <= Dim<3>::NDET * sizeof(float) &&
+static_assert(KM == 3 && sizeof(SetupF32<3>) <= Dim<3>::NDET * sizeof(float) &&
                   2 * Dim<3>::NF * sizeof(long long) <= Dim<3>::NDET * sizeof(float),
               "set-up data must fit the reused 6e6o vector slots");
 
@@ -685,9 +825,9 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     return;
   }
   // ---- gather ------------------------------------------------------------------------------
-  // FP32 couplings (all loads in flight); FP64: J_pr = W_pprr, K_pr = W_prrp and the F block.
-  // Element (P, R) of the block is at off[P] + off[NF + R] (pair offsets built first).
-  SetupF64<K>& su = setup(ws);
+  // FP32 couplings (all loads in flight; the diagonal-only entries W_pprr are J_pr) and the F
+  // block.  Element (P, R) of the W block is at off[P] + off[NF + R] (pair offsets built first).
+  SetupF32<K>& su = setup(ws);
   {
     long long* off = gather_off(ws);
     for (int t = lane; t < 2 * NF; t += 32) {
@@ -696,24 +836,16 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       off[t] = (t < NF) ? o0 * (long long)n3 + o1 * (long long)n2 : o0 * (long long)n1 + o1;
     }
     __syncwarp();
-    // FP64 loads first, so their latency overlaps the FP32 gather: J and K are symmetric (pair
-    // symmetry of W), one lane per unordered pair p <= r; F (not symmetric) in two rounds
-    constexpr int NU = NORB * (NORB + 1) / 2;
-    static_assert(NU <= 32 && NF <= 64, "one round of pairs, two of F");
-    int up = 0, ur = 0;
-    double jv = 0.0, kv = 0.0, f0 = 0.0, f1 = 0.0;
-    if (lane < NU) {
-      int rem = lane;
-      while (rem >= NORB - up) {
-        rem -= NORB - up;
-        ++up;
-      }
-      ur = up + rem;
-      jv = a.W[off[up * (NORB + 1)] + off[NF + ur * (NORB + 1)]];
-      kv = a.W[off[up * NORB + ur] + off[NF + ur * NORB + up]];
+    static_assert(NF <= 64, "two rounds of F");
+    float f0 = 0.f, f1 = 0.f;
+    if (lane < NF) {
+      const size_t g = (size_t)ws.orb[lane / NORB] * n1 + ws.orb[lane % NORB];
+      f0 = a.F32 ? a.F32[g] : (float)a.F[g];
     }
-    if (lane < NF) f0 = a.F[(size_t)ws.orb[lane / NORB] * n1 + ws.orb[lane % NORB]];
-    if (lane + 32 < NF) f1 = a.F[(size_t)ws.orb[(lane + 32) / NORB] * n1 + ws.orb[(lane + 32) % NORB]];
+    if (lane + 32 < NF) {
+      const size_t g = (size_t)ws.orb[(lane + 32) / NORB] * n1 + ws.orb[(lane + 32) % NORB];
+      f1 = a.F32 ? a.F32[g] : (float)a.F[g];
+    }
     if constexpr (K == 3) {  // the 666 unique elements of the pair-symmetric block
       constexpr int PER = (D::NPAIR + 31) / 32;
       float wv[PER];
@@ -732,7 +864,12 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
         const int t = lane + 32 * k;
         if (t < D::NPAIR) {
           const int pr = pair3[t], P = pr & 255, R = pr >> 8;
-          const bool jj = (P / NORB == P % NORB) && (R / NORB == R % NORB);  // W_pprr: diagonal only
+          const int p = P / NORB, r = R / NORB;
+          const bool jj = (P == p * (NORB + 1)) && (R == r * (NORB + 1));  // W_pprr: diagonal only
+          if (jj) {
+            su.J[p * NORB + r] = wv[k];
+            su.J[r * NORB + p] = wv[k];
+          }
           const float wf = jj ? 0.f : wv[k];
           ws.Wt[P * NF + R] = wf;
           ws.Wt[R * NF + P] = wf;
@@ -742,59 +879,57 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       for (int t = lane; t < D::NW; t += 32) {
         const int P = t / NF, R = t % NF;
         const size_t g = (size_t)(off[P] + off[NF + R]);
-        const bool jj = (P / NORB == P % NORB) && (R / NORB == R % NORB);
-        ws.Wt[t] = jj ? 0.f : (W32 ? W32[g] : (float)a.W[g]);
+        const int p = P / NORB, r = R / NORB;
+        const bool jj = (P == p * (NORB + 1)) && (R == r * (NORB + 1));
+        const float w = W32 ? W32[g] : (float)a.W[g];
+        if (jj) su.J[p * NORB + r] = w;
+        ws.Wt[t] = jj ? 0.f : w;
       }
-    }
-    if (lane < NU) {
-      su.J[up * NORB + ur] = jv;
-      su.J[ur * NORB + up] = jv;
-      su.Kx[up * NORB + ur] = kv;
-      su.Kx[ur * NORB + up] = kv;
     }
     if (lane < NF) su.F[lane] = f0;
     if (lane + 32 < NF) su.F[lane + 32] = f1;
   }
   __syncwarp();
   // ---- fold (vacuum order over the active orbitals) -------------------------------------
-  // h_pp = F_pp - sum_k (2 J_pk - K_pk) in FP64; off-diagonal h' = h - 1/2 sum_r W_prrq in FP32
+  // h_pp = F_pp - sum_k (2 J_pk - K_pk) with K_pk = W_pkkp (J_pp for k = p); off-diagonal
+  // h' = h - 1/2 sum_r W_prrq
   if (lane < NORB) {
-    double v = su.F[lane * (NORB + 1)];
-    for (int k = 0; k < K; ++k) v -= 2.0 * su.J[lane * NORB + k] - su.Kx[lane * NORB + k];
-    su.hd[lane] = v;
+    const int p = lane;
+    float v = su.F[p * (NORB + 1)];
+    for (int k = 0; k < K; ++k) {
+      const float kx = (k == p) ? su.J[p * NORB + p] : ws.Wt[(p * NORB + k) * NF + k * NORB + p];
+      v -= 2.f * su.J[p * NORB + k] - kx;
+    }
+    su.hd[p] = v;
   }
   for (int idx = lane; idx < NF; idx += 32) {
     const int p = idx / NORB, q = idx % NORB;
-    float v = (float)su.F[idx];
+    float v = su.F[idx];
     for (int k = 0; k < K; ++k)
       v -= 2.f * ws.Wt[idx * NF + k * (NORB + 1)] - ws.Wt[(p * NORB + k) * NF + k * NORB + q];
     for (int r = 0; r < NORB; ++r) v -= 0.5f * ws.Wt[(p * NORB + r) * NF + r * NORB + q];
-    ws.hp[idx] = (p == q) ? 0.f : v;
+    ws.hp()[idx] = (p == q) ? 0.f : v;
   }
   __syncwarp();
-  if (lane < NS) {  // same-spin string diagonal: sum_{p in I} h_pp + 1/2 sum_{p,r in I} (J_pr - K_pr)
-    double v = 0.0;
+  {  // same-spin string diagonal sum_{p in I} h_pp + sum_{p<r in I} (J_pr - K_pr), relative to Phi's
+    float hs = 0.f;
+    if (lane < NS) {
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const int p = tb.occ[lane][j];
-      v += su.hd[p];
+      for (int j = 0; j < K; ++j) {
+        const int p = tb.occ[lane][j];
+        hs += su.hd[p];
 #pragma unroll
-      for (int l = 0; l < K; ++l) {
-        const int r = tb.occ[lane][l];
-        v += 0.5 * (su.J[p * NORB + r] - su.Kx[p * NORB + r]);
+        for (int l = j + 1; l < K; ++l) {
+          const int r = tb.occ[lane][l];
+          hs += su.J[p * NORB + r] - ws.Wt[(p * NORB + r) * NF + r * NORB + p];
+        }
       }
     }
-    su.hsd[lane] = v;
+    const float hs0 = __shfl_sync(0xffffffffu, hs, 0);
+    if (lane < NS) ws.dh[lane] = hs - hs0;
   }
-  __syncwarp();
   if (lane == 0) {
-    double ec = *a.e0;
-    for (int k = 0; k < K; ++k) ec -= su.hd[k] + su.F[k * (NORB + 1)];
-    ws.ecore = ec;
-    double v = ec + 2.0 * su.hsd[0];
-    for (int p = 0; p < K; ++p)
-      for (int r = 0; r < K; ++r) v += su.J[p * NORB + r];
-    ws.eshift = v;  // <Phi|H|Phi>
+    ws.eshift = *a.e0;  // <Phi|H|Phi>: the fold moves the inactive part into E_core exactly
     ws.ctrl[0] = 1;
     ws.ctrl[2] = kSpaceNoConv;
     ws.ctrl[3] = 0;
@@ -806,52 +941,80 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   // ---- Phi fast path: sigma(Phi) = column 0 of H (0 at Phi after the shift) ----------------
   // Only determinants connected to Phi by single or double replacements are nonzero.  If the
   // residual of Phi is below the tolerance, the root is Phi, the increment is zero and the
-  // space is done without building the full string operator or the diagonal.  This check runs
-  // with or without a caller's guess; a guess then enters as a second subspace vector.
+  // space is done without building the full string operator.  Otherwise (and without a caller's
+  // guess) the first-order correction r / (0 - diag) goes to V1: if its norm is below what FP32
+  // vectors resolve (1e-6) the space stays at Phi (energy error below |r| * 1e-6), else it is
+  // the first expansion vector of the Davidson loop.  A guess enters as a second subspace vector.
+  float vn_phi = 0.f;
   {
-    if (lane < NS) {  // dh[I] <- Hs[I][0]: same-spin coupling of string I to the Phi string
-      const int I = lane;
-      float hc = 0.f;
-      if (I != 0) {
+    float rphi;
+    if constexpr (K == 3) {  // the column from its coupling table, each unique element once
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = lane; q < NDET / 4; q += 32) reinterpret_cast<float4*>(ws.S)[q] = z4;
+      for (int q = lane; q < 2 * NDET / 4; q += 32) reinterpret_cast<float4*>(ws.V)[q] = z4;  // V0, V1
+      __syncwarp();
+      if (lane == 0) ws.V[0] = 1.f;
+      float acc = 0.f, rr = 0.f;
+#pragma unroll
+      for (int k = 0; k < kPhiLen; ++k) {
+        const unsigned e = __ldg(&g_phi_table.e[k * 32 + lane]);
+        acc = fmaf(__uint_as_float(e & 0xff800000u), ws.Wt[e & 2047u], acc);
+        if (e & (1u << 20)) {
+          const int d = (int)((e >> 11) & 511u);
+          ws.S[d] = acc;
+          float w2 = acc * acc;
+          if (e & (1u << 21)) {
+            ws.S[(d % NS) * NS + d / NS] = acc;
+            w2 += w2;
+          }
+          rr += w2;
+          acc = 0.f;
+        }
+      }
+      rphi = sqrtf(wsum(rr));
+      __syncwarp();
+    } else {
+      float hc = 0.f;  // Hs[I][0]: same-spin coupling of string I to the Phi string
+      if (lane < NS && lane != 0) {
+        const int I = lane;
 #pragma unroll 1
         for (int u = 0; u < NSG; ++u) {
           const int e = I * NSG + u;
           const int pq = tb.pq[e], Kk = tb.J[e];
           const float s1 = (float)tb.sg[e];
-          if (Kk == 0) hc = fmaf(s1, ws.hp[pq], hc);
+          if (Kk == 0) hc = fmaf(s1, ws.hp()[pq], hc);
           for (int v = 0; v < tb.c0n[Kk]; ++v)
             hc = fmaf(0.5f * s1 * (float)tb.c0sg[Kk][v], ws.Wt[pq * NF + tb.c0pq[Kk][v]], hc);
         }
       }
-      ws.dh[I] = hc;
-    }
-    for (int d = lane; d < NDET; d += 32) {
-      ws.S[d] = 0.f;
-      ws.V[d] = (d == 0) ? 1.f : 0.f;
-    }
-    __syncwarp();
-    // alpha-beta couplings: both strings are Phi or single replacements of it; same-spin
-    // couplings sit in row 0 and column 0 of the CI matrix
-    constexpr int NC = 1 + K * K;
+      for (int d = lane; d < NDET; d += 32) {
+        ws.S[d] = 0.f;
+        ws.V[d] = (d == 0) ? 1.f : 0.f;
+      }
+      __syncwarp();
+      // alpha-beta couplings: both strings are Phi or single replacements of it; same-spin
+      // couplings sit in row 0 and column 0 of the CI matrix
+      constexpr int NC = 1 + K * K;
 #pragma unroll 1
-    for (int t = lane; t < NC * NC; t += 32) {
-      const int x = t / NC, y = t % NC;
-      const int Ia = (x == 0) ? 0 : tb.xJ[x - 1], Ib = (y == 0) ? 0 : tb.xJ[y - 1];
-      float acc = 0.f;
-      for (int u = 0; u < tb.c0n[Ia]; ++u)
-        for (int v = 0; v < tb.c0n[Ib]; ++v)
-          acc = fmaf((float)(tb.c0sg[Ia][u] * tb.c0sg[Ib][v]), ws.Wt[tb.c0pq[Ia][u] * NF + tb.c0pq[Ib][v]], acc);
-      if (t != 0) ws.S[Ia * NS + Ib] = acc;
+      for (int t = lane; t < NC * NC; t += 32) {
+        const int x = t / NC, y = t % NC;
+        const int Ia = (x == 0) ? 0 : tb.xJ[x - 1], Ib = (y == 0) ? 0 : tb.xJ[y - 1];
+        float acc = 0.f;
+        for (int u = 0; u < tb.c0n[Ia]; ++u)
+          for (int v = 0; v < tb.c0n[Ib]; ++v)
+            acc = fmaf((float)(tb.c0sg[Ia][u] * tb.c0sg[Ib][v]), ws.Wt[tb.c0pq[Ia][u] * NF + tb.c0pq[Ib][v]], acc);
+        if (t != 0) ws.S[Ia * NS + Ib] = acc;
+      }
+      __syncwarp();
+      if (lane > 0 && lane < NS) {
+        ws.S[lane * NS] += hc;
+        ws.S[lane] += hc;
+      }
+      __syncwarp();
+      float rr = 0.f;
+      for (int d = lane; d < NDET; d += 32) rr = fmaf(ws.S[d], ws.S[d], rr);
+      rphi = sqrtf(wsum(rr));
     }
-    __syncwarp();
-    if (lane > 0 && lane < NS) {
-      ws.S[lane * NS] += ws.dh[lane];
-      ws.S[lane] += ws.dh[lane];
-    }
-    __syncwarp();
-    float rr = 0.f;
-    for (int d = lane; d < NDET; d += 32) rr = fmaf(ws.S[d], ws.S[d], rr);
-    const float rphi = sqrtf(wsum(rr));
     if (rphi < tol) {  // converged at Phi: E = <Phi|H|Phi>, X = 0
       if (lane == 0) {
         a.energy[oidx] = ws.eshift;
@@ -863,15 +1026,14 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       __syncwarp();
       return;
     }
-    // the diagonal relative to <Phi|H|Phi> (diag_at): string parts as FP64 differences, the
-    // alpha-beta Coulomb sum J(Ia, Ib) in FP32 through row sums jb[p][Ib] = sum_{r in Ib} J_pr
-    if (lane < NS) ws.dh[lane] = (float)(su.hsd[lane] - su.hsd[0]);
+    // the diagonal relative to <Phi|H|Phi> (diag_at): the alpha-beta Coulomb sum J(Ia, Ib)
+    // through row sums jb[p][Ib] = sum_{r in Ib} J_pr
 #pragma unroll 1
     for (int t = lane; t < NORB * NS; t += 32) {
       const int p = t / NS, b = t % NS;
       float v = 0.f;
 #pragma unroll
-      for (int l = 0; l < K; ++l) v += (float)su.J[p * NORB + tb.occ[b][l]];
+      for (int l = 0; l < K; ++l) v += su.J[p * NORB + tb.occ[b][l]];
       ws.jb[t] = v;
     }
     __syncwarp();
@@ -881,19 +1043,38 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       ws.j0 = j0;
     }
     __syncwarp();
-    // Without a guess, the first-order correction from Phi is r / (0 - diag); when its norm is
-    // below what FP32 vectors resolve (1e-6) the space stays at Phi (energy error below
-    // |r| * 1e-6), decided here before the string operator is built.
     if (!guess_in) {
       float nn = 0.f;
-      for (int d = lane; d < NDET; d += 32) {
-        float den = -diag_at<K>(tb, ws, d / NS, d % NS);
-        if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
-        const float v = ws.S[d] / den;
-        nn = fmaf(v, v, nn);
+      float* v1 = ws.V + NDET;
+      if constexpr (K == 3) {  // nonzero only where the column is (the diagonal is symmetric too)
+#pragma unroll
+        for (int k = 0; k < kPhiLen; ++k) {
+          const unsigned e = __ldg(&g_phi_table.e[k * 32 + lane]);
+          if (e & (1u << 20)) {
+            const int d = (int)((e >> 11) & 511u);
+            float den = -diag_at<K>(tb, ws, d / NS, d % NS);
+            if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
+            const float v = ws.S[d] / den;
+            v1[d] = v;
+            float w2 = v * v;
+            if (e & (1u << 21)) {
+              v1[(d % NS) * NS + d / NS] = v;
+              w2 += w2;
+            }
+            nn += w2;
+          }
+        }
+      } else {
+        for (int d = lane; d < NDET; d += 32) {
+          float den = -diag_at<K>(tb, ws, d / NS, d % NS);
+          if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
+          const float v = (d == 0) ? 0.f : ws.S[d] / den;
+          v1[d] = v;
+          nn = fmaf(v, v, nn);
+        }
       }
-      const float vn = sqrtf(wsum(nn));
-      if (!(vn > 1e-6f)) {
+      vn_phi = sqrtf(wsum(nn));
+      if (!(vn_phi > 1e-6f)) {
         const int st = (rphi < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
         if (lane == 0) {
           a.energy[oidx] = ws.eshift;
@@ -907,30 +1088,19 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       }
     }
   }
-  // ---- same-spin string operator, off-diagonal (row I owned by lane I) ---------------------
-  if constexpr (K == 3) {
-    if (lane < NS) {
-      const int I = lane;
-#pragma unroll 1
-      for (int j = 0; j < NS; ++j) ws.Hs[I * NS + j] = 0.f;
-      float acc1 = 0.f, acc2 = 0.f;  // one-body and (doubled) two-body parts of the current target
-#pragma unroll 5
-      for (int k = 0; k < kHsPaths; ++k) {
-        const unsigned e = __ldg(&g_hs_paths.e[k * 20 + I]);
-        const int src = (int)(e & 2047u);
-        const bool neg = (e & 2048u) != 0;
-        if (src >= 1296) {
-          const float h = ws.hp[src - 1296];
-          acc1 += neg ? -h : h;
-        } else {
-          const float w = ws.Wt[src];
-          acc2 += neg ? -w : w;
-        }
-        if (e & (1u << 17)) {
-          ws.Hs[I * NS + ((e >> 12) & 31u)] = acc1 + 0.5f * acc2;
-          acc1 = 0.f;
-          acc2 = 0.f;
-        }
+  // ---- same-spin string operator, off-diagonal ---------------------------------------------
+  if constexpr (K == 3) {  // from its coupling table, targets dealt evenly to the 32 lanes
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = lane; q < NS * NS / 4; q += 32) reinterpret_cast<float4*>(ws.Hs)[q] = z4;
+    __syncwarp();
+    float acc = 0.f;
+#pragma unroll 6
+    for (int k = 0; k < kHsLen; ++k) {
+      const unsigned e = __ldg(&g_hs_table.e[k * 32 + lane]);
+      acc = fmaf(__uint_as_float(e & 0xff800000u), ws.Wt[e & 2047u], acc);
+      if (e & (1u << 20)) {
+        ws.Hs[(e >> 11) & 511u] = acc;
+        acc = 0.f;
       }
     }
   } else if (lane < NS) {
@@ -942,16 +1112,17 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       const int e = I * NSG + u;
       const int pq = tb.pq[e], Kk = tb.J[e];
       const float s1 = (float)tb.sg[e];
-      if (Kk != I) ws.Hs[I * NS + Kk] += s1 * ws.hp[pq];
+      if (Kk != I) ws.Hs[I * NS + Kk] += s1 * ws.hp()[pq];
 #pragma unroll 1
       for (int v = 0; v < NSG; ++v) {
         const int e2 = Kk * NSG + v;
         const int J2 = tb.J[e2];
-        if (J2 == I) continue;  // the diagonal is kept in FP64
+        if (J2 == I) continue;  // the diagonal is kept apart (dh, jb)
         ws.Hs[I * NS + J2] += 0.5f * s1 * (float)tb.sg[e2] * ws.Wt[pq * NF + tb.pq[e2]];
       }
     }
   }
+  __syncwarp();
   // ---- caller's guess: subspace {Phi, g - g_Phi Phi}; its sigma counts as one iteration -------
   int it0 = 0;
   if (guess_in && KM >= 2) {
@@ -1030,95 +1201,92 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       k = 1;
     }
     const float th = ws.theta;
-    float rr = 0.f;
     float* vk = ws.V + k * NDET;
-    for (int d = lane; d < NDET; d += 32) {
-      float xv = 0.f, sv = 0.f;
-      for (int j = 0; j < k; ++j) {
-        xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
-        sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
+    float vn = vn_phi;  // first step from Phi: V1 already holds the preconditioned residual
+    if (!(it == 0 && !guess_in)) {
+      float rr = 0.f;
+      for (int d = lane; d < NDET; d += 32) {
+        float xv = 0.f, sv = 0.f;
+        for (int j = 0; j < k; ++j) {
+          xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+          sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
+        }
+        const float r = sv - th * xv;
+        rr = fmaf(r, r, rr);
+        vk[d] = r;  // the residual; preconditioned below once the space is known not to be done
       }
-      const float r = sv - th * xv;
-      rr = fmaf(r, r, rr);
-      vk[d] = r;  // the residual; preconditioned below once the space is known not to be done
-    }
-    const float rnorm = sqrtf(wsum(rr));
-    if (!isfinite(rnorm) || !isfinite(th)) {
-      if (lane == 0) ws.ctrl[2] = kSpaceNonFinite;
-      __syncwarp();
-      break;
-    }
-    if (rnorm < tol) {
-      if (lane == 0) {
-        ws.ctrl[2] = kSpaceOk;
-        ws.ctrl[3] = it + it0;
+      const float rnorm = sqrtf(wsum(rr));
+      if (!isfinite(rnorm) || !isfinite(th)) {
+        if (lane == 0) ws.ctrl[2] = kSpaceNonFinite;
+        __syncwarp();
+        break;
+      }
+      if (rnorm < tol) {
+        if (lane == 0) {
+          ws.ctrl[2] = kSpaceOk;
+          ws.ctrl[3] = it + it0;
+        }
+        __syncwarp();
+        break;
+      }
+      for (int d = lane; d < NDET; d += 32) {  // diagonal preconditioner r / (theta - D)
+        float den = th - diag_at<K>(tb, ws, d / NS, d % NS);
+        if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
+        vk[d] = __fdividef(vk[d], den);
       }
       __syncwarp();
-      break;
-    }
-    for (int d = lane; d < NDET; d += 32) {  // diagonal preconditioner r / (theta - D)
-      float den = th - diag_at<K>(tb, ws, d / NS, d % NS);
-      if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
-      vk[d] = __fdividef(vk[d], den);
-    }
-    __syncwarp();
-    // expansion vector: the preconditioned residual, orthogonalised against the subspace.  When
-    // that leaves (almost) nothing while the residual is still above 100 x tol, the residual
-    // itself (orthogonal to the subspace at a Ritz pair) is used instead, so the loop does not
-    // stall on a correction that lies in the subspace
-    float vn = 0.f;
+      // expansion vector: the preconditioned residual, orthogonalised against the subspace.  When
+      // that leaves (almost) nothing while the residual is still above 100 x tol, the residual
+      // itself (orthogonal to the subspace at a Ritz pair) is used instead, so the loop does not
+      // stall on a correction that lies in the subspace
 #pragma unroll 1
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      if (attempt == 1) {
-        for (int d = lane; d < NDET; d += 32) {
-          float xv = 0.f, sv = 0.f;
-          for (int j = 0; j < k; ++j) {
-            xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
-            sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt == 1) {
+          for (int d = lane; d < NDET; d += 32) {
+            float xv = 0.f, sv = 0.f;
+            for (int j = 0; j < k; ++j) {
+              xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+              sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
+            }
+            vk[d] = sv - th * xv;
           }
-          vk[d] = sv - th * xv;
+          __syncwarp();
         }
-        __syncwarp();
-      }
-      const bool from_phi = (it == 0 && k == 1 && !guess_in);  // V0 is exactly Phi
-      if (from_phi) {
-        if (lane == 0) vk[0] = 0.f;
-        __syncwarp();
-      }
-      for (int pass = 0; pass < (from_phi ? 0 : 2); ++pass) {
-        float cf[KM];
+        for (int pass = 0; pass < 2; ++pass) {
+          float cf[KM];
 #pragma unroll
-        for (int j = 0; j < KM; ++j) cf[j] = 0.f;
-        for (int d = lane; d < NDET; d += 32) {
-          const float v = vk[d];
+          for (int j = 0; j < KM; ++j) cf[j] = 0.f;
+          for (int d = lane; d < NDET; d += 32) {
+            const float v = vk[d];
+#pragma unroll
+            for (int j = 0; j < KM; ++j)
+              if (j < k) cf[j] = fmaf(ws.V[j * NDET + d], v, cf[j]);
+          }
 #pragma unroll
           for (int j = 0; j < KM; ++j)
-            if (j < k) cf[j] = fmaf(ws.V[j * NDET + d], v, cf[j]);
+            if (j < k) cf[j] = wsum(cf[j]);
+          for (int d = lane; d < NDET; d += 32) {
+            float v = vk[d];
+#pragma unroll
+            for (int j = 0; j < KM; ++j)
+              if (j < k) v = fmaf(-cf[j], ws.V[j * NDET + d], v);
+            vk[d] = v;
+          }
+          __syncwarp();
         }
-#pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < k) cf[j] = wsum(cf[j]);
-        for (int d = lane; d < NDET; d += 32) {
-          float v = vk[d];
-#pragma unroll
-          for (int j = 0; j < KM; ++j)
-            if (j < k) v = fmaf(-cf[j], ws.V[j * NDET + d], v);
-          vk[d] = v;
+        float nn = 0.f;
+        for (int d = lane; d < NDET; d += 32) nn = fmaf(vk[d], vk[d], nn);
+        vn = sqrtf(wsum(nn));
+        if (vn > 1e-6f || rnorm < 100.f * tol) break;
+      }
+      if (!(vn > 1e-6f)) {  // the subspace cannot grow (complete or stagnated)
+        if (lane == 0) {
+          ws.ctrl[2] = (rnorm < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
+          ws.ctrl[3] = it + it0;
         }
         __syncwarp();
+        break;
       }
-      float nn = 0.f;
-      for (int d = lane; d < NDET; d += 32) nn = fmaf(vk[d], vk[d], nn);
-      vn = sqrtf(wsum(nn));
-      if (vn > 1e-6f || rnorm < 100.f * tol) break;
-    }
-    if (!(vn > 1e-6f)) {  // the subspace cannot grow (complete or stagnated)
-      if (lane == 0) {
-        ws.ctrl[2] = (rnorm < 100.f * tol) ? kSpaceOk : kSpaceNoConv;
-        ws.ctrl[3] = it + it0;
-      }
-      __syncwarp();
-      break;
     }
     const float inv = 1.f / vn;
     for (int d = lane; d < NDET; d += 32) vk[d] *= inv;

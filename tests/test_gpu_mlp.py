@@ -248,7 +248,7 @@ def test_pool_warm_start_saves_sweeps(qf, precision):
     """Train on a converged flow of one 24-orbital system (bare integrals -> converged internal
     amplitudes of every space), warm-start the pool of a different system of the same family
     (another seed): both starts reach the same fixed point, the warm one is closer to it after
-    each of the first sweeps and needs no more sweeps."""
+    each of the first three sweeps (at least 2x after the second) and needs no more sweeps."""
     tol_e, tol_t = (1e-8, 1e-7) if precision == "fp64" else (1e-7, 1e-5)
     hidden = 256
     eps, h, g, sp = synth.system_inputs("n24")
@@ -276,5 +276,6 @@ def test_pool_warm_start_saves_sweeps(qf, precision):
     print(f"{precision}: sweeps to convergence, empty pool {len(e_cold)}, network pool {len(e_warm)}; "
           f"|E - E_fixed| after sweeps 1-3: empty {err_cold[:3]}, network {err_warm[:3]}")
     assert abs(e_warm[-1] - e_fix) < (1e-8 if precision == "fp64" else 1e-6)
-    assert err_warm[0] < 0.5 * err_cold[0] and err_warm[1] < err_cold[1]
+    k = min(3, len(e_warm), len(e_cold))
+    assert np.all(err_warm[:k] < err_cold[:k]) and err_warm[1] < 0.5 * err_cold[1]
     assert len(e_warm) <= len(e_cold)
