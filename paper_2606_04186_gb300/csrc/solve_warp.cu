@@ -34,7 +34,7 @@ namespace qf {
 namespace {
 
 constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
-constexpr int WARPS = 4;  // spaces (warps) per CTA
+constexpr int WARPS = 13;  // spaces (warps) per CTA: one CTA fills the shared memory of an SM
 
 template <int K>
 struct Dim {
@@ -407,6 +407,7 @@ static_assert(sizeof(WarpState<3>) % 16 == 0 && offsetof(WarpState<3>, S) % 16 =
                   (2 * Dim<3>::NDET * sizeof(float)) % 16 == 0,
               "float4 rows of the 6e6o state");
 static_assert(offsetof(CtaSmem, w) % 16 == 0 && sizeof(AnyWarpState) % 16 == 0, "warp state alignment");
+static_assert(sizeof(CtaSmem) <= 232448, "one CTA within the 227 KB of shared memory a block may use");
 
 template <int K>
 __device__ Tabs<K>& tabs(CtaSmem& cs);
