@@ -34,7 +34,7 @@ namespace qf {
 namespace {
 
 constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
-constexpr int WARPS = 13;  // spaces (warps) per CTA: one CTA fills the shared memory of an SM
+constexpr int WARPS = 14;  // spaces (warps) per CTA: one CTA fills the shared memory of an SM
 
 template <int K>
 struct Dim {
@@ -350,8 +350,8 @@ struct SetupF32 {
 template <int K>
 struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as float4
   using D = Dim<K>;
-  float V[KM * D::NDET];
-  float S[KM * D::NDET];
+  float V[(KM - 1) * D::NDET];  // V_1 .. V_{KM-1}; V_0 = Phi is implicit (Phi stays in the subspace)
+  float S[KM * D::NDET];        // S_j = sigma(V_j)
   // FP32 W block without its [pp][rr] (diagonal-only) entries, then h' = h - 1/2 sum_r W_prrq
   // (off-diagonal part): the coupling tables index both as one array
   float Wt[D::NW + D::NF];
@@ -365,8 +365,8 @@ struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as fl
   double eshift;             // <Phi|H|Phi> = E0 of the dressing (the fold leaves it unchanged)
   int orb[D::NORB];
   int ctrl[4];              // [0] subspace size, [1] valid, [2] status, [3] iterations
-  // the small classes keep set-up data and gather offsets here (the 6e6o state reuses the
-  // third V slot and the second S slot, which are free until the Davidson loop needs them)
+  // the small classes keep set-up data and gather offsets here (the 6e6o state keeps them in
+  // the string operator's slot and the second S slot, which are free until they are filled)
   alignas(16) unsigned char extra[K == 3 ? 16 : sizeof(SetupF32<K>) + 2 * D::NF * sizeof(long long)];
   __device__ __forceinline__ float* hp() { return Wt + D::NW; }
   __device__ __forceinline__ const float* hp() const { return Wt + D::NW; }
@@ -374,7 +374,7 @@ struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as fl
 
 template <int K>
 __device__ __forceinline__ SetupF32<K>& setup(WarpState<K>& ws) {
-  if constexpr (K == 3) return *reinterpret_cast<SetupF32<K>*>(ws.V + 2 * Dim<K>::NDET);
+  if constexpr (K == 3) return *reinterpret_cast<SetupF32<K>*>(ws.Hs);
   else return *reinterpret_cast<SetupF32<K>*>(ws.extra);
 }
 // gather offsets: element (P, R) of the W block sits at off[P] + off[NF + R]
@@ -383,9 +383,9 @@ __device__ __forceinline__ long long* gather_off(WarpState<K>& ws) {
   if constexpr (K == 3) return reinterpret_cast<long long*>(ws.S + Dim<K>::NDET);
   else return reinterpret_cast<long long*>(ws.extra + sizeof(SetupF32<K>));
 }
-static_assert(KM == 3 && sizeof(SetupF32<3>) <= Dim<3>::NDET * sizeof(float) &&
+static_assert(KM == 3 && sizeof(SetupF32<3>) <= sizeof(WarpState<3>::Hs) &&
                   2 * Dim<3>::NF * sizeof(long long) <= Dim<3>::NDET * sizeof(float),
-              "set-up data must fit the reused 6e6o vector slots");
+              "set-up data must fit the reused 6e6o slots");
 
 union alignas(16) AnyWarpState {
   WarpState<3> w3;
@@ -654,6 +654,10 @@ __device__ __forceinline__ void sigma(const Tabs<K>& tb, const WarpState<K>& ws,
 // from the previous Ritz value, then Rayleigh-quotient refinement.  The projected matrix is
 // built from FP32 vectors, so it is solved in FP32 too.
 __device__ __noinline__ void small_eig(const float* G, int k, float shift, float* y, float* theta) {
+  // The closed forms below lose absolute accuracy to cancellation (the root sought is small next
+  // to the other diagonal entries).  Each root is therefore polished with the Phi row of
+  // G y = lambda y, lambda = (G y)_0 / y_0 (exact for an eigenpair; G_00 = Phi . sigma(Phi)),
+  // alternating with the eigenvector twice: the error shrinks by about |G_0j| / gap per pass.
   if (k == 2) {  // closed form: the eigenvalue nearest the shift and its eigenvector
     const float g00 = G[0], g01 = G[1], g10 = G[KM], g11 = G[KM + 1];
     const float tr = 0.5f * (g00 + g11), df = 0.5f * (g00 - g11);
@@ -661,18 +665,22 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
     if (disc >= 0.f && isfinite(disc)) {
       const float sq = sqrtf(disc);
       const float l1 = tr + sq, l2 = tr - sq;
-      const float lam = (fabsf(l1 - shift) <= fabsf(l2 - shift)) ? l1 : l2;
-      // (G - lam) y = 0: take the better conditioned of the two rows
-      float y0, y1;
-      if (fabsf(g01) + fabsf(lam - g00) >= fabsf(g10) + fabsf(lam - g11)) {
-        y0 = g01;
-        y1 = lam - g00;
-      } else {
-        y0 = lam - g11;
-        y1 = g10;
+      float lam = (fabsf(l1 - shift) <= fabsf(l2 - shift)) ? l1 : l2;
+      float y0 = 0.f, y1 = 0.f;
+      for (int pass = 0; pass < 3; ++pass) {
+        // (G - lam) y = 0: take the better conditioned of the two rows
+        if (fabsf(g01) + fabsf(lam - g00) >= fabsf(g10) + fabsf(lam - g11)) {
+          y0 = g01;
+          y1 = lam - g00;
+        } else {
+          y0 = lam - g11;
+          y1 = g10;
+        }
+        if (pass == 2 || !(fabsf(y0) >= 0.3f * sqrtf(y0 * y0 + y1 * y1))) break;
+        lam = (g00 * y0 + g01 * y1) / y0;
       }
       const float nrm = sqrtf(y0 * y0 + y1 * y1);
-      if (nrm > 0.f && isfinite(nrm)) {
+      if (nrm > 0.f && isfinite(nrm) && isfinite(lam)) {
         const float sc = ((y0 < 0.f) ? -1.f : 1.f) / nrm;
         y[0] = sc * y0;
         y[1] = sc * y1;
@@ -707,24 +715,32 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
     float lam = root[0];
     for (int j = 1; j < nr; ++j)
       if (fabsf(root[j] - shift) < fabsf(lam - shift)) lam = root[j];
-    // null vector of G - lam I: the largest cross product of two of its rows
-    const float r0[3] = {g00 - lam, g01, g02}, r1[3] = {g10, g11 - lam, g12}, r2[3] = {g20, g21, g22 - lam};
     auto cross = [](const float* u, const float* w, float* o) {
       o[0] = u[1] * w[2] - u[2] * w[1];
       o[1] = u[2] * w[0] - u[0] * w[2];
       o[2] = u[0] * w[1] - u[1] * w[0];
     };
-    float c01[3], c02[3], c12[3];
-    cross(r0, r1, c01);
-    cross(r0, r2, c02);
-    cross(r1, r2, c12);
-    const float n01 = c01[0] * c01[0] + c01[1] * c01[1] + c01[2] * c01[2];
-    const float n02 = c02[0] * c02[0] + c02[1] * c02[1] + c02[2] * c02[2];
-    const float n12 = c12[0] * c12[0] + c12[1] * c12[1] + c12[2] * c12[2];
-    const float* vb = c01;
-    float nb = n01;
-    if (n02 > nb) { vb = c02; nb = n02; }
-    if (n12 > nb) { vb = c12; nb = n12; }
+    float vb[3] = {0.f, 0.f, 0.f}, nb = 0.f;
+    for (int pass = 0; pass < 3; ++pass) {
+      // null vector of G - lam I: the largest cross product of two of its rows
+      const float r0[3] = {g00 - lam, g01, g02}, r1[3] = {g10, g11 - lam, g12}, r2[3] = {g20, g21, g22 - lam};
+      float c01[3], c02[3], c12[3];
+      cross(r0, r1, c01);
+      cross(r0, r2, c02);
+      cross(r1, r2, c12);
+      const float n01 = c01[0] * c01[0] + c01[1] * c01[1] + c01[2] * c01[2];
+      const float n02 = c02[0] * c02[0] + c02[1] * c02[1] + c02[2] * c02[2];
+      const float n12 = c12[0] * c12[0] + c12[1] * c12[1] + c12[2] * c12[2];
+      const float* best = c01;
+      nb = n01;
+      if (n02 > nb) { best = c02; nb = n02; }
+      if (n12 > nb) { best = c12; nb = n12; }
+      vb[0] = best[0];
+      vb[1] = best[1];
+      vb[2] = best[2];
+      if (pass == 2 || !(fabsf(vb[0]) >= 0.3f * sqrtf(nb))) break;
+      lam = (g00 * vb[0] + g01 * vb[1] + g02 * vb[2]) / vb[0];
+    }
     if (nb > 0.f && isfinite(nb) && isfinite(lam)) {
       const float sc = ((vb[0] < 0.f) ? -1.f : 1.f) / sqrtf(nb);
       y[0] = sc * vb[0];
@@ -951,10 +967,11 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     float rphi;
     if constexpr (K == 3) {  // the column from its coupling table, each unique element once
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int q = lane; q < NDET / 4; q += 32) reinterpret_cast<float4*>(ws.S)[q] = z4;
-      for (int q = lane; q < 2 * NDET / 4; q += 32) reinterpret_cast<float4*>(ws.V)[q] = z4;  // V0, V1
+      for (int q = lane; q < NDET / 4; q += 32) {
+        reinterpret_cast<float4*>(ws.S)[q] = z4;  // S0 = sigma(Phi)
+        reinterpret_cast<float4*>(ws.V)[q] = z4;  // V1
+      }
       __syncwarp();
-      if (lane == 0) ws.V[0] = 1.f;
       float acc = 0.f, rr = 0.f;
 #pragma unroll
       for (int k = 0; k < kPhiLen; ++k) {
@@ -988,10 +1005,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
             hc = fmaf(0.5f * s1 * (float)tb.c0sg[Kk][v], ws.Wt[pq * NF + tb.c0pq[Kk][v]], hc);
         }
       }
-      for (int d = lane; d < NDET; d += 32) {
-        ws.S[d] = 0.f;
-        ws.V[d] = (d == 0) ? 1.f : 0.f;
-      }
+      for (int d = lane; d < NDET; d += 32) ws.S[d] = 0.f;
       __syncwarp();
       // alpha-beta couplings: both strings are Phi or single replacements of it; same-spin
       // couplings sit in row 0 and column 0 of the CI matrix
@@ -1046,7 +1060,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     __syncwarp();
     if (!guess_in) {
       float nn = 0.f;
-      float* v1 = ws.V + NDET;
+      float* v1 = ws.V;
       if constexpr (K == 3) {  // nonzero only where the column is (the diagonal is symmetric too)
 #pragma unroll
         for (int k = 0; k < kPhiLen; ++k) {
@@ -1127,7 +1141,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   // ---- caller's guess: subspace {Phi, g - g_Phi Phi}; its sigma counts as one iteration -------
   int it0 = 0;
   if (guess_in && KM >= 2) {
-    float* v1 = ws.V + NDET;
+    float* v1 = ws.V;
     float p = 0.f;
     for (int d = lane; d < NDET; d += 32) {
       const float gv = (d == 0) ? 0.f : guess_in[(size_t)s * NDET + d];
@@ -1167,49 +1181,55 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     }
   }
   // ---- Davidson ----------------------------------------------------------------------------
+  // Subspace {Phi = V_0, V_1, ..}: V_0 is implicit (unit vector e_0) and every stored V_j is
+  // orthogonal to it (its component 0 is zero), so products with V_0 are single elements.
   constexpr int KMX = (NDET < KM) ? NDET : KM;  // the 2e2o space has only 4 determinants
 #pragma unroll 1
   for (int it = 0; it < a.max_iter; ++it) {
     int k = ws.ctrl[0];
-    if (k == KMX) {  // restart on the Ritz vector
-      float pv = 0.f, ps = 0.f;
+    if (k == KMX) {  // restart on {Phi, Ritz vector}: x = y_0 Phi + x', x' = sum_{j>=1} y_j V_j is
+                     // already orthogonal to Phi, and sigma(x') = sum_{j>=1} y_j S_j
+      float pv = 0.f, p0 = 0.f, p1 = 0.f;
       for (int d = lane; d < NDET; d += 32) {
         float xv = 0.f, sv = 0.f;
-        for (int j = 0; j < k; ++j) {
-          xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+        for (int j = 1; j < k; ++j) {
+          xv = fmaf(ws.yf[j], ws.V[(j - 1) * NDET + d], xv);
           sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
         }
         ws.V[d] = xv;
-        ws.S[d] = sv;
+        ws.S[NDET + d] = sv;
         pv = fmaf(xv, xv, pv);
-        ps = fmaf(xv, sv, ps);
+        p0 = fmaf(xv, ws.S[d], p0);
+        p1 = fmaf(xv, sv, p1);
       }
       pv = wsum(pv);
-      ps = wsum(ps);
-      const float inv = 1.f / sqrtf(pv);
+      p0 = wsum(p0);
+      p1 = wsum(p1);
+      const float nx = sqrtf(pv), inv = 1.f / nx;
       for (int d = lane; d < NDET; d += 32) {
         ws.V[d] *= inv;
-        ws.S[d] *= inv;
+        ws.S[NDET + d] *= inv;
       }
       __syncwarp();
-      if (lane == 0) {
-        ws.G[0] = ps / pv;
-        ws.theta = ws.G[0];
-        ws.yf[0] = 1.f;
-        ws.ctrl[0] = 1;
+      if (lane == 0) {  // projected matrix of {Phi, V_1}; G[0] (Phi . S_0 = 0) is unchanged
+        ws.G[1] = ws.S[NDET];
+        ws.G[KM] = p0 * inv;
+        ws.G[KM + 1] = p1 * inv * inv;
+        ws.yf[1] = nx;
+        ws.ctrl[0] = 2;
       }
       __syncwarp();
-      k = 1;
+      k = 2;
     }
     const float th = ws.theta;
-    float* vk = ws.V + k * NDET;
+    float* vk = ws.V + (k - 1) * NDET;
     float vn = vn_phi;  // first step from Phi: V1 already holds the preconditioned residual
     if (!(it == 0 && !guess_in)) {
       float rr = 0.f;
       for (int d = lane; d < NDET; d += 32) {
-        float xv = 0.f, sv = 0.f;
-        for (int j = 0; j < k; ++j) {
-          xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+        float xv = (d == 0) ? ws.yf[0] : 0.f, sv = ws.yf[0] * ws.S[d];
+        for (int j = 1; j < k; ++j) {
+          xv = fmaf(ws.yf[j], ws.V[(j - 1) * NDET + d], xv);
           sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
         }
         const float r = sv - th * xv;
@@ -1244,34 +1264,34 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       for (int attempt = 0; attempt < 2; ++attempt) {
         if (attempt == 1) {
           for (int d = lane; d < NDET; d += 32) {
-            float xv = 0.f, sv = 0.f;
-            for (int j = 0; j < k; ++j) {
-              xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+            float xv = (d == 0) ? ws.yf[0] : 0.f, sv = ws.yf[0] * ws.S[d];
+            for (int j = 1; j < k; ++j) {
+              xv = fmaf(ws.yf[j], ws.V[(j - 1) * NDET + d], xv);
               sv = fmaf(ws.yf[j], ws.S[j * NDET + d], sv);
             }
             vk[d] = sv - th * xv;
           }
           __syncwarp();
         }
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < 2; ++pass) {  // against Phi: drop component 0
           float cf[KM];
 #pragma unroll
           for (int j = 0; j < KM; ++j) cf[j] = 0.f;
           for (int d = lane; d < NDET; d += 32) {
             const float v = vk[d];
 #pragma unroll
-            for (int j = 0; j < KM; ++j)
-              if (j < k) cf[j] = fmaf(ws.V[j * NDET + d], v, cf[j]);
+            for (int j = 1; j < KM; ++j)
+              if (j < k) cf[j] = fmaf(ws.V[(j - 1) * NDET + d], v, cf[j]);
           }
 #pragma unroll
-          for (int j = 0; j < KM; ++j)
+          for (int j = 1; j < KM; ++j)
             if (j < k) cf[j] = wsum(cf[j]);
           for (int d = lane; d < NDET; d += 32) {
             float v = vk[d];
 #pragma unroll
-            for (int j = 0; j < KM; ++j)
-              if (j < k) v = fmaf(-cf[j], ws.V[j * NDET + d], v);
-            vk[d] = v;
+            for (int j = 1; j < KM; ++j)
+              if (j < k) v = fmaf(-cf[j], ws.V[(j - 1) * NDET + d], v);
+            vk[d] = (d == 0) ? 0.f : v;
           }
           __syncwarp();
         }
@@ -1301,16 +1321,19 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     for (int d = lane; d < NDET; d += 32) {
       const float vkd = vk[d], skd = sk[d];
       gkk = fmaf(vkd, skd, gkk);
+      gr[0] = fmaf(vkd, ws.S[d], gr[0]);
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
+      for (int j = 1; j < KM; ++j)
         if (j < k) {
-          gc[j] = fmaf(ws.V[j * NDET + d], skd, gc[j]);
+          gc[j] = fmaf(ws.V[(j - 1) * NDET + d], skd, gc[j]);
           gr[j] = fmaf(vkd, ws.S[j * NDET + d], gr[j]);
         }
     }
     gkk = wsum(gkk);
+    gr[0] = wsum(gr[0]);
+    gc[0] = sk[0];  // Phi . sigma(V_k)
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
+    for (int j = 1; j < KM; ++j)
       if (j < k) {
         gc[j] = wsum(gc[j]);
         gr[j] = wsum(gr[j]);
@@ -1337,8 +1360,8 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   const int k = ws.ctrl[0];
   float xx = 0.f;
   for (int d = lane; d < NDET; d += 32) {
-    float xv = 0.f;
-    for (int j = 0; j < k; ++j) xv = fmaf(ws.yf[j], ws.V[j * NDET + d], xv);
+    float xv = (d == 0) ? ws.yf[0] : 0.f;
+    for (int j = 1; j < k; ++j) xv = fmaf(ws.yf[j], ws.V[(j - 1) * NDET + d], xv);
     ws.S[d] = xv;
     xx = fmaf(xv, xv, xx);
   }
