@@ -34,7 +34,7 @@ namespace qf {
 namespace {
 
 constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
-constexpr int WARPS = 14;  // spaces (warps) per CTA: one CTA fills the shared memory of an SM
+constexpr int WARPS = 15;  // spaces (warps) per CTA: one CTA fills the shared memory of an SM
 
 template <int K>
 struct Dim {
@@ -357,7 +357,7 @@ struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as fl
   float Wt[D::NW + D::NF];
   float Hs[D::NS * D::NS];  // same-spin string operator, zero diagonal
   float dh[(D::NS + 3) / 4 * 4];  // same-spin string diagonal relative to the Phi string
-  float jb[D::NORB * D::NS];  // jb[p][Ib] = sum_{r in Ib} J_pr
+  float Jc[D::NF];          // J_pr = W_pprr: the alpha-beta Coulomb part of the diagonal
   float G[KM * KM];         // projected matrix, G[i*KM+j] = V_i . S_j
   float yf[KM];             // Ritz coefficients
   float theta;              // Ritz value relative to eshift
@@ -403,7 +403,7 @@ struct alignas(16) CtaSmem {
 
 static_assert(sizeof(WarpState<3>) % 16 == 0 && offsetof(WarpState<3>, S) % 16 == 0 &&
                   offsetof(WarpState<3>, Wt) % 16 == 0 && offsetof(WarpState<3>, Hs) % 16 == 0 &&
-                  offsetof(WarpState<3>, dh) % 16 == 0 && offsetof(WarpState<3>, jb) % 16 == 0 &&
+                  offsetof(WarpState<3>, dh) % 16 == 0 && offsetof(WarpState<3>, Jc) % 16 == 0 &&
                   (2 * Dim<3>::NDET * sizeof(float)) % 16 == 0,
               "float4 rows of the 6e6o state");
 static_assert(offsetof(CtaSmem, w) % 16 == 0 && sizeof(AnyWarpState) % 16 == 0, "warp state alignment");
@@ -431,9 +431,15 @@ __device__ __forceinline__ WarpState<1>& state<1>(AnyWarpState& a) { return a.w1
 template <int K>
 __device__ __forceinline__ float diag_at(const Tabs<K>& tb, const WarpState<K>& ws, int ia, int ib) {
   constexpr int NS = Dim<K>::NS;
+  constexpr int NORB = Dim<K>::NORB;
   float jj = 0.f;
 #pragma unroll
-  for (int l = 0; l < K; ++l) jj += ws.jb[tb.occ[ia][l] * NS + ib];
+  for (int l = 0; l < K; ++l) {
+    const float* row = ws.Jc + tb.occ[ia][l] * NORB;
+#pragma unroll
+    for (int m = 0; m < K; ++m) jj += row[tb.occ[ib][m]];
+  }
+  (void)NS;
   return ws.dh[ia] + ws.dh[ib] + (jj - ws.j0);
 }
 
@@ -519,6 +525,24 @@ __device__ __forceinline__ float wsum(float v) {
 
 // ---- sigma ------------------------------------------------------------------------------------
 
+// jab[B] = sum_{r in string B} jp[r] (string B's orbitals from the compile-time tables).
+template <int B>
+__device__ __forceinline__ float coulomb_row(const float (&jp)[6]) {
+  constexpr int m = TabHolder::value.mask[B];
+  float v = 0.f;
+  if constexpr (m & 1) v += jp[0];
+  if constexpr (m & 2) v += jp[1];
+  if constexpr (m & 4) v += jp[2];
+  if constexpr (m & 8) v += jp[3];
+  if constexpr (m & 16) v += jp[4];
+  if constexpr (m & 32) v += jp[5];
+  return v;
+}
+template <int... B>
+__device__ __forceinline__ void coulomb_rows(std::integer_sequence<int, B...>, float (&jab)[20], const float (&jp)[6]) {
+  ((jab[B] = coulomb_row<B>(jp)), ...);
+}
+
 // 6e6o: sigma = H c restricted to off-diagonal couplings plus the shifted diagonal.
 __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, const float* __restrict__ c,
                                      float* __restrict__ out, int lane) {
@@ -527,20 +551,24 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
     const int Ia = lane;
     float acc[NS];
     {  // diagonal and alpha-alpha: acc[b] = diag * c + sum_J Hs[Ia][J] c[J][b]
-      // diag(Ia, b) = dh[Ia] + dh[b] + (sum_{p in Ia} jb[p][b] - j0), as diag_at
-      const float4* j0r = reinterpret_cast<const float4*>(ws.jb + tb.occ[Ia][0] * NS);
-      const float4* j1r = reinterpret_cast<const float4*>(ws.jb + tb.occ[Ia][1] * NS);
-      const float4* j2r = reinterpret_cast<const float4*>(ws.jb + tb.occ[Ia][2] * NS);
+      // diag(Ia, b) = dh[Ia] + dh[b] + (sum_{p in Ia, r in b} J_pr - j0), as diag_at, with the
+      // row sums jp[r] = sum_{p in Ia} J_pr in registers and b's orbitals known at compile time
+      float jp[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+        jp[r] = ws.Jc[tb.occ[Ia][0] * 6 + r] + ws.Jc[tb.occ[Ia][1] * 6 + r] + ws.Jc[tb.occ[Ia][2] * 6 + r];
+      float jab[NS];
+      coulomb_rows(std::make_integer_sequence<int, NS>{}, jab, jp);
       const float4* dhr = reinterpret_cast<const float4*>(ws.dh);
       const float4* crow = reinterpret_cast<const float4*>(c + Ia * NS);
       const float dha = ws.dh[Ia], jz = ws.j0;
 #pragma unroll
       for (int q = 0; q < NS / 4; ++q) {
-        const float4 a0 = j0r[q], a1 = j1r[q], a2 = j2r[q], dv = dhr[q], cv = crow[q];
-        acc[4 * q + 0] = (dha + dv.x + (a0.x + a1.x + a2.x - jz)) * cv.x;
-        acc[4 * q + 1] = (dha + dv.y + (a0.y + a1.y + a2.y - jz)) * cv.y;
-        acc[4 * q + 2] = (dha + dv.z + (a0.z + a1.z + a2.z - jz)) * cv.z;
-        acc[4 * q + 3] = (dha + dv.w + (a0.w + a1.w + a2.w - jz)) * cv.w;
+        const float4 dv = dhr[q], cv = crow[q];
+        acc[4 * q + 0] = (dha + dv.x + (jab[4 * q + 0] - jz)) * cv.x;
+        acc[4 * q + 1] = (dha + dv.y + (jab[4 * q + 1] - jz)) * cv.y;
+        acc[4 * q + 2] = (dha + dv.z + (jab[4 * q + 2] - jz)) * cv.z;
+        acc[4 * q + 3] = (dha + dv.w + (jab[4 * q + 3] - jz)) * cv.w;
       }
     }
 #pragma unroll 2
@@ -1041,20 +1069,13 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       __syncwarp();
       return;
     }
-    // the diagonal relative to <Phi|H|Phi> (diag_at): the alpha-beta Coulomb sum J(Ia, Ib)
-    // through row sums jb[p][Ib] = sum_{r in Ib} J_pr
-#pragma unroll 1
-    for (int t = lane; t < NORB * NS; t += 32) {
-      const int p = t / NS, b = t % NS;
-      float v = 0.f;
-#pragma unroll
-      for (int l = 0; l < K; ++l) v += su.J[p * NORB + tb.occ[b][l]];
-      ws.jb[t] = v;
-    }
-    __syncwarp();
+    // the diagonal relative to <Phi|H|Phi> (diag_at) needs the J block for its alpha-beta
+    // Coulomb sum J(Ia, Ib) = sum_{p in Ia, r in Ib} J_pr (the set-up slot is reused later)
+    for (int t = lane; t < NF; t += 32) ws.Jc[t] = su.J[t];
     if (lane == 0) {
       float j0 = 0.f;
-      for (int l = 0; l < K; ++l) j0 += ws.jb[tb.occ[0][l] * NS + 0];
+      for (int l = 0; l < K; ++l)
+        for (int m = 0; m < K; ++m) j0 += su.J[tb.occ[0][l] * NORB + tb.occ[0][m]];
       ws.j0 = j0;
     }
     __syncwarp();
@@ -1132,7 +1153,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       for (int v = 0; v < NSG; ++v) {
         const int e2 = Kk * NSG + v;
         const int J2 = tb.J[e2];
-        if (J2 == I) continue;  // the diagonal is kept apart (dh, jb)
+        if (J2 == I) continue;  // the diagonal is kept apart (dh, Jc)
         ws.Hs[I * NS + J2] += 0.5f * s1 * (float)tb.sg[e2] * ws.Wt[pq * NF + tb.pq[e2]];
       }
     }
