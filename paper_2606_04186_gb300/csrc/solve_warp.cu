@@ -571,7 +571,7 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
         acc[4 * q + 3] = (dha + dv.w + (jab[4 * q + 3] - jz)) * cv.w;
       }
     }
-#pragma unroll 2
+#pragma unroll 4
     for (int J = 0; J < NS; ++J) {
       const float hj = ws.Hs[Ia * NS + J];
       const float4* crow = reinterpret_cast<const float4*>(c + J * NS);
@@ -595,7 +595,7 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
         ca[4 * q + 2] = cv.z;
         ca[4 * q + 3] = cv.w;
       }
-#pragma unroll 4
+#pragma unroll
       for (int b = 0; b < NS; ++b) {
         const float4* hrow = reinterpret_cast<const float4*>(ws.Hs + b * NS);
         float s = 0.f;
@@ -1130,7 +1130,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     for (int q = lane; q < NS * NS / 4; q += 32) reinterpret_cast<float4*>(ws.Hs)[q] = z4;
     __syncwarp();
     float acc = 0.f;
-#pragma unroll 6
+#pragma unroll 11
     for (int k = 0; k < kHsLen; ++k) {
       const unsigned e = __ldg(&g_hs_table.e[k * 32 + lane]);
       acc = fmaf(__uint_as_float(e & 0xff800000u), ws.Wt[e & 2047u], acc);
