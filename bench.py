@@ -109,8 +109,8 @@ def dress_gemm_flops(o: int, v: int) -> float:
     return 2.0 * mnk
 
 
-# solve-kernel DRAM traffic per space, sweep 3 (ncu capture of the 500,000-space n82 subset)
-TRAFFIC_PER_SPACE = {"n82": 148.9}
+# solve-kernel DRAM traffic per space, sweep 3 (ncu capture of the 477,120-space n82 subset)
+TRAFFIC_PER_SPACE = {"n82": 156.6}
 
 
 # ---- clocks ------------------------------------------------------------------------------------
