@@ -142,6 +142,53 @@ class Flow:
         nfail = int(sum(r[3] != 0 for r in res))
         return e_mean, de, float(dt), nfail
 
+    def sweep_waves(self, wave: int):
+        """One sweep in waves of `wave` spaces in Delta-eps order (Numerical Implementation: the
+        pool is populated progressively as spaces are traversed; process groups take the spaces
+        in list order, so the spaces running together see the same pool).  Each wave is
+        downfolded with the pool left by the waves before it, and its owned amplitudes are updated
+        before the next wave starts.  wave >= nspaces is the Jacobi sweep.  Returns what sweep()
+        returns; max|dt| is taken over the whole sweep and DIIS (if on) acts on the sweep's start
+        and end pools."""
+        if wave < 1:
+            raise ValueError("wave must be >= 1")
+        t1s, t2s = self.t1, self.t2
+        t1c, t2c = t1s.copy(), t2s.copy()
+        ns = len(self.spaces)
+        energies = np.zeros(ns)
+        status = np.zeros(ns, dtype=int)
+        for lo in range(0, ns, wave):
+            hi = min(ns, lo + wave)
+            e0, F, W = hbar.hbar2(self.h, self.g, t1c, t2c, self.nocc)
+            res = solve_all(e0, F, W, self.spaces[lo:hi], self.pool)
+            for s, (row, r) in enumerate(zip(self.spaces[lo:hi], res), start=lo):
+                occ, vir = space_orbitals(row)
+                va = [a - self.nocc for a in vir]
+                energies[s], x1, x2, status[s] = r
+                for ii, i in enumerate(occ):
+                    for aa, a in enumerate(va):
+                        if self.own1[i, a] == s:
+                            t1c[i, a] = t1c[i, a] + x1[ii, aa]
+                    for jj, j in enumerate(occ):
+                        for aa, a in enumerate(va):
+                            for bb, b in enumerate(va):
+                                if self.own2[i, j, a, b] == s:
+                                    t2c[i, j, a, b] = t2c[i, j, a, b] + x2[ii, jj, aa, bb]
+        t1n, t2n = t1c, t2c
+        if self.diis is not None:
+            vec = np.concatenate([t1n.ravel(), t2n.ravel()])
+            err = np.concatenate([(t1n - t1s).ravel(), (t2n - t2s).ravel()])
+            vec = self.diis.push(vec, err)
+            t1n = vec[:t1s.size].reshape(t1s.shape)
+            t2n = vec[t1s.size:].reshape(t2s.shape)
+        dt = max(np.abs(t1n - t1s).max(initial=0.0), np.abs(t2n - t2s).max(initial=0.0))
+        self.t1, self.t2 = t1n, t2n
+        self.energies = energies
+        e_mean = float(np.mean(energies))
+        de = float("inf") if self.e_mean is None else e_mean - self.e_mean
+        self.e_mean = e_mean
+        return e_mean, de, float(dt), int((status != 0).sum())
+
     def run(self, tol_e: float = 1e-8, tol_t: float = 1e-7, max_sweeps: int = 100):
         hist = []
         for _ in range(max_sweeps):

@@ -84,3 +84,70 @@ def test_flow_converges_to_ccsd(n10, use_diis):
     # the paper's convergence picture: per-space changes shrink sweep over sweep
     des = [abs(x[1]) for x in hist[1:]]
     assert des[-1] < des[0]
+
+
+# ---- wave-ordered sweeps (the progressive pool update of the Numerical Implementation) --------
+
+def test_waves_wider_than_the_list_are_the_jacobi_sweep(n10):
+    eps, h, g, sp = n10
+    fj = flow.Flow(h, g, 3, sp)
+    fw = flow.Flow(h, g, 3, sp)
+    for _ in range(2):
+        rj = fj.sweep()
+        rw = fw.sweep_waves(len(sp))
+        assert rj[0] == rw[0] and rj[2] == rw[2]
+        assert np.array_equal(fj.energies, fw.energies)
+        assert np.array_equal(fj.t1, fw.t1) and np.array_equal(fj.t2, fw.t2)
+
+
+@pytest.mark.parametrize("wave", [1, 4])
+def test_waves_keep_the_ccsd_fixed_point(n10, wave):
+    eps, h, g, sp = n10
+    e_cc, t1, t2, _ = ccsd.ccsd(h, g, 3, tol=1e-13)
+    f = flow.Flow(h, g, 3, sp, t1=t1, t2=t2)
+    e, de, dt, nf = f.sweep_waves(wave)
+    assert nf == 0 and dt < 1e-10
+    assert np.abs(f.energies - e_cc).max() < 1e-10
+
+
+def test_first_wave_sees_the_bare_hamiltonian_and_the_second_the_first_ones_pool(n10):
+    """Wave 1 (spaces 0..K-1) solves on the bare Hamiltonian like a Jacobi first sweep; wave 2
+    solves on the pool those K spaces leave, which a Jacobi sweep over just those K spaces
+    (they own the same amplitudes: owners are taken in list order) reproduces."""
+    eps, h, g, sp = n10
+    K = 5
+    fw = flow.Flow(h, g, 3, sp)
+    fw.sweep_waves(K)
+    fj = flow.Flow(h, g, 3, sp)
+    fj.sweep()
+    assert np.array_equal(fw.energies[:K], fj.energies[:K])
+    first = flow.Flow(h, g, 3, fw.spaces[:K])   # already sorted: keeps the order and the owners
+    first.sweep()
+    e0, F, W = first.dress()
+    for s in range(K, 2 * K):
+        occ, vir = flow.space_orbitals(fw.spaces[s])
+        e_ref = flow.cas.solve_space(e0, F, W, occ, vir)[0]
+        assert abs(fw.energies[s] - e_ref) < 1e-12
+    assert np.abs(fw.energies[K:2 * K] - fj.energies[K:2 * K]).max() > 1e-6
+
+
+@pytest.fixture(scope="module")
+def jacobi_run(n10):
+    eps, h, g, sp = n10
+    f = flow.Flow(h, g, 3, sp)
+    return f.run(tol_e=1e-10, tol_t=1e-9, max_sweeps=40)
+
+
+def test_waves_converge_to_ccsd(n10, jacobi_run):
+    eps, h, g, sp = n10
+    e_cc, t1, t2, _ = ccsd.ccsd(h, g, 3, tol=1e-13)
+    f = flow.Flow(h, g, 3, sp)
+    hist = []
+    for _ in range(40):
+        e, de, dt, nf = f.sweep_waves(5)
+        hist.append((e, de, dt))
+        if abs(de) < 1e-10 and dt < 1e-9:
+            break
+    assert abs(f.e_mean - e_cc) < 1e-9
+    assert np.abs(f.t2 - t2).max() < 1e-8 and np.abs(f.t1 - t1).max() < 1e-8
+    assert len(hist) <= len(jacobi_run)   # the progressive update needs no more sweeps than Jacobi
