@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=800, help="spaces solved by the oracle for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "persistent", "per_class"])
+    ap.add_argument("--waves", type=int, default=0,
+                    help="wave-ordered sweeps: the pool is updated after every K spaces (0 = Jacobi)")
     ap.add_argument("--sharded", action="store_true",
                     help="sharded sweep path (begin / exchange / end) also at N = 1")
     ap.add_argument("--spaces-limit", type=int, default=0,
@@ -292,11 +294,15 @@ def run_ours(args):
     stream = torch.cuda.ExternalStream(fl.stream())
     log(f"init {t_init:.1f} s")
     sharded = world > 1 or args.sharded
+    if sharded and args.waves:
+        raise SystemExit("--waves runs on one GPU (the waves follow each other)")
     if sharded:
         fl.set_shard(rank, world)
         xbuf = torch.empty(fl.exchange_size(), dtype=torch.float64, device="cuda")
 
     def sweep():
+        if args.waves:
+            return fl.sweep_waves(args.waves, raise_on_fail=False)
         if not sharded:
             return fl.sweep(raise_on_fail=False)
         if world > 1:
@@ -395,7 +401,10 @@ def run_ours(args):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             barrier()
             a.record(s64)
-            f64.sweep(raise_on_fail=False)
+            if args.waves:
+                f64.sweep_waves(args.waves, raise_on_fail=False)
+            else:
+                f64.sweep(raise_on_fail=False)
             b.record(s64)
             barrier()
             ms.append(a.elapsed_time(b))
@@ -430,8 +439,11 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} spaces "
                                f"({', '.join(f'{int((sp[:, 0] == k).sum())} ({k},{k})' for k in (3, 2, 1) if (sp[:, 0] == k).any())})",
-                   "precision": args.precision, "sweep_s": sweep_ms / 1e3, "l2": "inputs larger than L2 (W = "
-                   f"{8 * s.n ** 4 / 1e6:.0f} MB)", "e_sweep3": e_mean,
+                   "precision": args.precision, "sweep_s": sweep_ms / 1e3, "l2": (f"inputs larger than L2 (W = {8 * s.n ** 4 / 1e6:.0f} MB)" if 8 * s.n ** 4 > 126e6
+                          else f"inputs smaller than L2 (W = {8 * s.n ** 4 / 1e6:.1f} MB), not flushed"), "e_sweep3": e_mean,
+                   "sweep_order": (f"waves of {args.waves} spaces in Delta-eps order, pool updated between "
+                                f"waves ({-(-len(sp) // args.waves)} dressings per sweep)") if args.waves
+                   else "Jacobi (all spaces read the pool of the last barrier)",
                    "parallelism": (f"sharded over {world} GPUs: per-class blocks, one allreduce of "
                                    f"{8 * fl_xsize / 1e6:.0f} MB per sweep") if sharded else "one GPU",
                    "step": "third sweep of the flow (pool after two sweeps restored before each step)",

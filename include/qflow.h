@@ -149,6 +149,17 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
  * space failed (its owned amplitudes then keep their old value). */
 int qflow_sweep(qflow_handle hnd, double* d_e, double* max_dt, int32_t* nfailed);
 
+/* One sweep in waves of `wave` spaces in Delta-eps order: every wave is downfolded with the pool
+ * the waves before it left, and its owned amplitudes are updated before the next wave starts
+ * (the paper's pool is populated progressively as the process groups traverse the sorted list,
+ * Numerical Implementation; the spaces of one wave run together).  Energies, max|t_new - t_old|
+ * (over the whole sweep) and failures as qflow_sweep; DIIS (if on) acts on the sweep's start and
+ * end pools.  wave >= nspaces is qflow_sweep (Jacobi).  Each wave runs the full dressing, so a
+ * sweep costs about nspaces / wave dressings.  Wave sweeps run plain launches, do not apply the
+ * network's start vectors and keep the current launch schedule.  Errors: QFLOW_ERR_ARG
+ * (wave < 1), QFLOW_ERR_STATE (sharded handle). */
+int qflow_sweep_waves(qflow_handle hnd, int64_t wave, double* d_e, double* max_dt, int32_t* nfailed);
+
 /* ---- sharded sweeps: every rank holds a handle of the whole problem ----------------------
  * After qflow_set_shard(h, rank, nranks) a sweep is three calls: qflow_sweep_shard_begin
  * dresses (replicated: every rank dresses the same pool), solves the shard's spaces (see

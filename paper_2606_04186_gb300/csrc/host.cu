@@ -245,6 +245,11 @@ struct qflow_ctx {
   uint8_t *space_mask = nullptr, *pool_mask = nullptr;  // device, see shard_masks
   bool shard_open = false;  // between qflow_sweep_shard_begin and _end
   bool shard_warm = false;  // that sweep started from the network's guesses
+  // wave-ordered sweeps: class positions of each class sorted by Delta-eps position (device),
+  // and those positions' sorted indices (host, ascending) to cut a wave into per-class ranges
+  int64_t* wave_items = nullptr;
+  std::vector<int64_t> wave_sidx[4];
+  double* pool_start = nullptr;  // the pool at the start of a wave-ordered sweep
 };
 
 namespace {
@@ -266,7 +271,7 @@ void free_ctx(qflow_ctx* c) {
   if (c->W32) cudaFree(c->W32);
   if (c->queue) cudaFree(c->queue);
   void* mptrs[] = {c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v, c->mlp_X, c->mlp_T, c->mlp_mask,
-                   c->space_mask, c->pool_mask};
+                   c->space_mask, c->pool_mask, c->wave_items, c->pool_start};
   for (void* p : mptrs)
     if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -513,6 +518,8 @@ cudaError_t enqueue_dress(qflow_ctx* c, int64_t* launches) {
 
 // The per-space solves with a given schedule; `count` > 0 limits every class to its first
 // `count` spaces (autotuner calibration).
+cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches);
+
 cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int64_t count, int64_t* launches) {
   SolveArgs cls[4];
   for (int k = 1; k <= 3; ++k) {
@@ -523,6 +530,11 @@ cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int
       cls[k].root_out = nullptr;
     }
   }
+  return enqueue_solve_cls(c, cls, persistent, chunk, ctas, launches);
+}
+
+// The solves of the given per-class arguments (cls[1..3]) with a given schedule.
+cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches) {
   if (c->opt.precision != QFLOW_PREC_MIXED) {
     cudaError_t e = cudaSuccess;
     for (int k = 1; k <= 3 && e == cudaSuccess; ++k) {
@@ -828,6 +840,85 @@ int qflow_set_shard(qflow_handle c, int32_t rank, int32_t nranks) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->pool_mask, pmask.data(), (size_t)npool, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_status(e);
+}
+
+int qflow_sweep_waves(qflow_handle c, int64_t wave, double* d_e, double* max_dt, int32_t* nfailed) {
+  if (!c || wave < 1) return QFLOW_ERR_ARG;
+  if (c->shard_n > 1 || c->shard_open) return QFLOW_ERR_STATE;
+  if (wave >= c->nspaces) return qflow_sweep(c, d_e, max_dt, nfailed);  // one wave: Jacobi
+  const int64_t ns = c->nspaces;
+  const size_t npool = (size_t)(c->n_t1 + c->n_t2);
+  cudaError_t e = cudaSuccess;
+  if (!c->wave_items) {  // per class, positions in Delta-eps order
+    std::vector<int64_t> gidx((size_t)ns), items((size_t)ns);
+    e = cudaMemcpyAsync(gidx.data(), c->sorted_index, sizeof(int64_t) * (size_t)ns, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 1; k <= 3; ++k) {
+      const int64_t b = c->cls_off[k], n = c->cls_count[k];
+      std::vector<int64_t> ord((size_t)n);
+      std::iota(ord.begin(), ord.end(), (int64_t)0);
+      std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return gidx[(size_t)(b + x)] < gidx[(size_t)(b + y)]; });
+      c->wave_sidx[k].resize((size_t)n);
+      for (int64_t t = 0; t < n; ++t) {
+        items[(size_t)(b + t)] = ord[(size_t)t];
+        c->wave_sidx[k][(size_t)t] = gidx[(size_t)(b + ord[(size_t)t])];
+      }
+    }
+    e = dalloc(&c->wave_items, (size_t)std::max<int64_t>(ns, 1));
+    if (e == cudaSuccess) e = dalloc(&c->pool_start, npool);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->wave_items, items.data(), sizeof(int64_t) * (size_t)ns, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  int64_t launches = 0;
+  e = cudaMemcpyAsync(c->pool_start, c->pool, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = mark(c, 0);
+  for (int64_t lo = 0; lo < ns && e == cudaSuccess; lo += wave) {
+    const int64_t hi = std::min<int64_t>(ns, lo + wave);
+    // dressing of the pool the earlier waves left
+    e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
+                         c->dwork_bytes, c->stream, c->W32);
+    launches += qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
+    if (e == cudaSuccess && c->W32) {
+      const size_t n4 = (size_t)c->n * c->n * c->n * c->n;
+      e = qf::launch_to_f32(c->W, c->W32, n4, c->stream);
+      if (e == cudaSuccess) e = qf::launch_to_f32(c->F, c->W32 + n4, (size_t)c->n * c->n, c->stream);
+      launches += 2;
+    }
+    if (e == cudaSuccess && lo == 0) e = mark(c, 1);
+    // this wave's spaces of every class; owned amplitudes are updated in place (each has one
+    // owner, whose warp reads the old value and writes the new one)
+    SolveArgs cls[4];
+    for (int k = 1; k <= 3; ++k) {
+      cls[k] = solve_args(c, k);
+      const std::vector<int64_t>& v = c->wave_sidx[k];
+      const int64_t a0 = std::lower_bound(v.begin(), v.end(), lo) - v.begin();
+      const int64_t a1 = std::lower_bound(v.begin(), v.end(), hi) - v.begin();
+      cls[k].items = c->wave_items + c->cls_off[k] + a0;
+      cls[k].nspaces = a1 - a0;
+      cls[k].t1_new = c->pool;
+      cls[k].t2_new = c->pool + c->n_t1;
+    }
+    if (e == cudaSuccess) e = enqueue_solve_cls(c, cls, c->sched_persistent, c->sched_chunk, c->sched_ctas, &launches);
+  }
+  if (e == cudaSuccess) e = mark(c, 2);
+  if (e == cudaSuccess && c->diis) {
+    e = qf::launch_diis(c->diis, c->opt.diis, c->pool_start, c->pool, (int64_t)npool, c->stream);
+    launches += 4;
+  }
+  if (e == cudaSuccess)
+    e = qf::launch_reduce(c->energy, c->status, ns, c->pool_start, c->pool, (int64_t)npool, c->red, c->rwork,
+                          c->stream);
+  launches += 2;
+  if (e == cudaSuccess) e = mark(c, 3);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->red_host, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (c->opt.precision != QFLOW_PREC_MIXED) c->tuned = true;
+  return finish_sweep(c, false, launches, d_e, max_dt, nfailed);
 }
 
 int64_t qflow_exchange_size(qflow_handle c) {

@@ -23,6 +23,7 @@ struct SolveArgs {
   int64_t nspaces;
   int64_t space_base;
   const int64_t* sorted_index;  // nullable: sorted index of spaces[s]; else space_base + s
+  const int64_t* items;         // nullable: item i of a launch is space items[i]; else space i
   const int32_t* owner1;
   const int32_t* owner2;
   const double* t1_old;

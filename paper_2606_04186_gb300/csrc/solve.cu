@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
   const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
   const T tol = (T)a.tol;
 
-  for (int64_t s = blockIdx.x; s < a.nspaces; s += gridDim.x) {
+  for (int64_t item = blockIdx.x; item < a.nspaces; item += gridDim.x) {
+    const int64_t s = a.items ? a.items[item] : item;
     // ---- gather + fold ---------------------------------------------------------------
     if (tid == 0) {
       const qflow_space& q = a.spaces[s];

@@ -1455,7 +1455,7 @@ __global__ void __launch_bounds__(32 * WARPS) solve_class_kernel(SolveArgs a, co
   WarpState<K>& ws = state<K>(cs.w[warp]);
 #pragma unroll 1
   for (int64_t s = (int64_t)blockIdx.x * WARPS + warp; s < a.nspaces; s += (int64_t)gridDim.x * WARPS)
-    solve_one<K>(tabs<K>(cs), cs.pair3, ws, a, W32, guess_in, guess_out, s, lane);
+    solve_one<K>(tabs<K>(cs), cs.pair3, ws, a, W32, guess_in, guess_out, a.items ? a.items[s] : s, lane);
 }
 
 struct PersistentArgs {
@@ -1488,15 +1488,17 @@ __global__ void __maxnreg__(128) solve_persistent_kernel(PersistentArgs p) {
       if (it < n3) {
         const SolveArgs& a = p.cls[3];
         solve_one<3>(cs.t3, cs.pair3, state<3>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
-                     static_cast<float*>(a.root_out), it, lane);
+                     static_cast<float*>(a.root_out), a.items ? a.items[it] : it, lane);
       } else if (it < n3 + n2) {
         const SolveArgs& a = p.cls[2];
+        const int64_t l = it - n3;
         solve_one<2>(cs.t2, cs.pair3, state<2>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
-                     static_cast<float*>(a.root_out), it - n3, lane);
+                     static_cast<float*>(a.root_out), a.items ? a.items[l] : l, lane);
       } else {
         const SolveArgs& a = p.cls[1];
+        const int64_t l = it - n3 - n2;
         solve_one<1>(cs.t1, cs.pair3, state<1>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
-                     static_cast<float*>(a.root_out), it - n3 - n2, lane);
+                     static_cast<float*>(a.root_out), a.items ? a.items[l] : l, lane);
       }
     }
   }

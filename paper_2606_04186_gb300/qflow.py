@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
         "qflow_mlp_targets_device": (I32, [P, I64, P, P]),
         "qflow_mlp_guess_device": (I32, [P, I64, P, P]),
         "qflow_gemm_tf32x3_device": (I32, [I32, I32, I32, P, I32, P, I32, P, I32, P, P]),
+        "qflow_sweep_waves": (I32, [P, I64, P, P, P]),
         "qflow_shard_plan": (I32, [P, P, I32, I32, P, I64, I32, I32, P, P]),
         "qflow_set_shard": (I32, [P, I32, I32]),
         "qflow_exchange_size": (I64, [P]),
@@ -195,6 +196,14 @@ class Flow:
         code = lib().qflow_sweep(self._h, C.byref(de), C.byref(dt), C.byref(nf))
         if raise_on_fail:
             _check(code, "qflow_sweep")
+        return de.value, dt.value, nf.value, code
+
+    def sweep_waves(self, wave: int, raise_on_fail: bool = True):
+        """One sweep in waves of `wave` spaces in Delta-eps order (pool updated between waves)."""
+        de, dt, nf = C.c_double(), C.c_double(), C.c_int32()
+        code = lib().qflow_sweep_waves(self._h, int(wave), C.byref(de), C.byref(dt), C.byref(nf))
+        if raise_on_fail:
+            _check(code, "qflow_sweep_waves")
         return de.value, dt.value, nf.value, code
 
     # ---- sharded sweeps (one process per GPU, summed exchange vectors) ----
