@@ -121,6 +121,24 @@ void qflow_default_options(qflow_options* opt, int32_t precision);
 int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
                int64_t nspaces, int64_t* perm, int32_t* owner1, int32_t* owner2, int64_t* n_uncovered);
 
+/* Coverage-driven active-space sampling (Numerical Implementation, Algorithm 1), host only.
+ * Candidates draw `no` of the nocc occupied and `nv` of the nvir virtual orbitals uniformly
+ * without replacement; a candidate is kept when it covers at least one (o1 < o2, v1 < v2) tuple
+ * no earlier kept candidate covered; sampling stops when every tuple is covered; the kept spaces
+ * are returned sorted by ascending Delta-eps (sum eps_v - sum eps_o, each sum in ascending
+ * orbital order; ties keep the sampling order).  Random numbers: SplitMix64 from state `seed`; a
+ * draw of k of m is a partial Fisher-Yates shuffle of 0..m-1 restarted from the identity, element
+ * i swapped with i + (u mod (m - i)); occupied orbitals are drawn first.
+ *   eps[nocc + nvir]   orbital energies (host), finite
+ *   no, nv             2 <= no <= min(3, nocc), 2 <= nv <= min(3, nvir)
+ *   out[capacity]      host records (no, nv, absolute orbitals, unused slots -1);
+ *                      capacity C(nocc,2) C(nvir,2) always suffices (every kept space covers a
+ *                      new tuple); NULL allowed with capacity 0 to ask for the count
+ *   count              out: spaces in the cycle;  draws (nullable) out: candidates drawn
+ * Errors: QFLOW_ERR_ARG; QFLOW_ERR_TOO_LARGE when capacity < count (count is still set). */
+int qflow_sample_spaces(int32_t nocc, int32_t nvir, int32_t no, int32_t nv, const double* eps, uint64_t seed,
+                        qflow_space* out, int64_t capacity, int64_t* count, int64_t* draws);
+
 /* Shard `rank` of `nranks` of a space list, for sweeps split over several processes (one GPU
  * each; the paper's cycles run in process groups that meet at a barrier after every cycle,
  * Numerical Implementation).  The device order of the list is grouped by size class and, within

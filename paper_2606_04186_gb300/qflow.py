@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
         "qflow_mlp_guess_device": (I32, [P, I64, P, P]),
         "qflow_gemm_tf32x3_device": (I32, [I32, I32, I32, P, I32, P, I32, P, I32, P, P]),
         "qflow_sweep_waves": (I32, [P, I64, P, P, P]),
+        "qflow_sample_spaces": (I32, [I32, I32, I32, I32, P, C.c_uint64, P, I64, P, P]),
         "qflow_shard_plan": (I32, [P, P, I32, I32, P, I64, I32, I32, P, P]),
         "qflow_set_shard": (I32, [P, I32, I32]),
         "qflow_exchange_size": (I64, [P]),
@@ -137,6 +138,19 @@ def plan(h, eri, nocc: int, spaces):
     _check(lib().qflow_plan(_ptr(h), _ptr(eri), n, nocc, _ptr(sp), len(sp), _ptr(perm), _ptr(o1), _ptr(o2),
                             C.byref(unc)), "qflow_plan")
     return perm, o1, o2, unc.value
+
+
+def sample_spaces(eps, nocc: int, no: int, nv: int, seed: int):
+    """Algorithm 1's cycle of (no, nv) spaces for orbital energies eps (host only):
+    (spaces int32 (count, 8) sorted by Delta-eps, candidates drawn)."""
+    eps = _f64(eps)
+    nvir = len(eps) - nocc
+    cap = max(1, (nocc * (nocc - 1) // 2) * (nvir * (nvir - 1) // 2))
+    out = np.empty((cap, 8), dtype=np.int32)
+    n, d = C.c_int64(), C.c_int64()
+    _check(lib().qflow_sample_spaces(nocc, nvir, no, nv, _ptr(eps), seed, _ptr(out), cap, C.byref(n), C.byref(d)),
+           "qflow_sample_spaces")
+    return out[:n.value].copy(), d.value
 
 
 def shard_plan(h, eri, nocc: int, spaces, rank: int, nranks: int):
