@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=800, help="spaces solved by the oracle for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "persistent", "per_class"])
+    ap.add_argument("--sampler", type=int, default=-1,
+                    help="space list from Algorithm 1 (greedy coverage cycle of (3,3) spaces) with this seed")
     ap.add_argument("--waves", type=int, default=0,
                     help="wave-ordered sweeps: the pool is updated after every K spaces (0 = Jacobi)")
     ap.add_argument("--sharded", action="store_true",
@@ -284,6 +286,11 @@ def run_ours(args):
     name = args.workload
     s = synth.SYSTEMS[name]
     eps, h, g, sp = synth.system_inputs(name)
+    if args.sampler >= 0:   # one cycle of Algorithm 1 from the Fock diagonal of the system
+        from paper_2606_04186_gb300 import qflow as _q
+        _q.lib()
+        fd = np.array([h[p, p] + sum(2 * g[p, p, k, k] - g[p, k, k, p] for k in range(s.nocc)) for p in range(s.n)])
+        sp, _ = _q.sample_spaces(fd, s.nocc, 3, 3, args.sampler)
     if args.spaces_limit and len(sp) > args.spaces_limit:
         sp = np.ascontiguousarray(sp[::-(-len(sp) // args.spaces_limit)])
     no, nv = s.nocc, s.n - s.nocc
@@ -441,6 +448,9 @@ def run_ours(args):
                                f"({', '.join(f'{int((sp[:, 0] == k).sum())} ({k},{k})' for k in (3, 2, 1) if (sp[:, 0] == k).any())})",
                    "precision": args.precision, "sweep_s": sweep_ms / 1e3, "l2": (f"inputs larger than L2 (W = {8 * s.n ** 4 / 1e6:.0f} MB)" if 8 * s.n ** 4 > 126e6
                           else f"inputs smaller than L2 (W = {8 * s.n ** 4 / 1e6:.1f} MB), not flushed"), "e_sweep3": e_mean,
+                   "space_list": (f"Algorithm 1 cycle, seed {args.sampler}" if args.sampler >= 0
+                                  else "every (3,3) space" if len(sp) == math.comb(no, 3) * math.comb(nv, 3)
+                                  else "list of the workload"),
                    "sweep_order": (f"waves of {args.waves} spaces in Delta-eps order, pool updated between "
                                 f"waves ({-(-len(sp) // args.waves)} dressings per sweep)") if args.waves
                    else "Jacobi (all spaces read the pool of the last barrier)",

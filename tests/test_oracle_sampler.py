@@ -108,3 +108,16 @@ def test_library_sampler_rejects_bad_sizes(qf):
         qf.sample_spaces(_eps(4, 7), 4, 1, 2, 0)
     with pytest.raises(qf.QFlowError):
         qf.sample_spaces(_eps(4, 7), 4, 5, 2, 0)
+
+
+def test_sampled_cycle_flow_reaches_ccsd(n10):
+    """A cycle that covers every double reaches the CCSD fixed point (every amplitude is owned)."""
+    from oracle import ccsd, flow
+    eps, h, g, _ = n10
+    fd = ccsd.fock_diagonal(h, g, 3)
+    sp, _ = sampler.sample_spaces(fd, 3, 7, 3, 3, 21)
+    f = flow.Flow(h, g, 3, sp)
+    assert f.uncovered() == 0
+    e_cc = ccsd.ccsd(h, g, 3, tol=1e-13)[0]
+    f.run(tol_e=1e-10, tol_t=1e-9, max_sweeps=60)
+    assert abs(f.e_mean - e_cc) < 1e-9
