@@ -131,8 +131,9 @@ __device__ __forceinline__ size_t t1_index(const Dims& d, int p, size_t rest) {
 
 template <typename A, int POS>
 __global__ void k_t1_creator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
-  extern __shared__ double t1s[];  // [o][v]
-  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = t1[x];
+  extern __shared__ double t1raw[];  // [o][v], converted once to the accumulation type
+  A* t1s = reinterpret_cast<A*>(t1raw);
+  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = to_acc<A>(t1[x]);
   __syncthreads();
   const size_t m = (size_t)d.n * d.n * d.n;
   for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
@@ -143,7 +144,7 @@ __global__ void k_t1_creator_fast(double* __restrict__ W, const double* __restri
       A acc = 0;
 #pragma unroll
       for (int i = 0; i < kT1Omax; ++i)
-        if (i < d.o) acc += to_acc<A>(t1s[i * d.v + a]) * wi[i];
+        if (i < d.o) acc += t1s[i * d.v + a] * wi[i];
       W[t1_index<A, POS>(d, d.o + a, rest)] -= from_acc<A>(acc);
     }
   }
@@ -151,8 +152,9 @@ __global__ void k_t1_creator_fast(double* __restrict__ W, const double* __restri
 
 template <typename A, int POS>
 __global__ void k_t1_annihilator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
-  extern __shared__ double t1s[];
-  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = t1[x];
+  extern __shared__ double t1raw[];
+  A* t1s = reinterpret_cast<A*>(t1raw);
+  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = to_acc<A>(t1[x]);
   __syncthreads();
   const size_t m = (size_t)d.n * d.n * d.n;
   for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
@@ -163,7 +165,7 @@ __global__ void k_t1_annihilator_fast(double* __restrict__ W, const double* __re
       const A wa = to_acc<A>(W[t1_index<A, POS>(d, d.o + a, rest)]);
 #pragma unroll
       for (int q = 0; q < kT1Omax; ++q)
-        if (q < d.o) acc[q] += to_acc<A>(t1s[q * d.v + a]) * wa;
+        if (q < d.o) acc[q] += t1s[q * d.v + a] * wa;
     }
 #pragma unroll
     for (int q = 0; q < kT1Omax; ++q)
@@ -664,10 +666,18 @@ struct LRingB {  // swap 0: g[m E n F], 1: g[m F n E]
     return swap ? c.G(m, c.o + f, nn, c.o + e) : c.G(m, c.o + e, nn, c.o + f);
   }
 };
+// Stores of the GEMM epilogue: run(r, col, vals, cnt) writes vals[j] at (r, col + j), j < cnt
+// (<= 32).  The column index is split into its two factors once and then walked, so the
+// epilogue does no division per element.
 struct StoreRows {
   float* p;
   int ld;
-  __device__ void operator()(int m, int n, float v) const { p[(size_t)m * ld + n] = v; }
+  __device__ void run(int m, int n, const float (&v)[32], int cnt) const {
+    float* q = p + (size_t)m * ld + n;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < cnt) q[j] = v[j];
+  }
 };
 
 // r2, ladder + oooo: rows (i, j), cols (a, b), k = (e, f) then (m, n)
@@ -695,18 +705,31 @@ struct LR2G1B {
 struct StoreR2 {
   float* acc;
   int o, v, mode;  // 0: (i a)(j b)  1: (j a)(i b)  2: (i b)(j a)  3: (j b)(i a)  4: (i j)(a b)
-  __device__ void operator()(int r, int col, float val) const {
-    int i, j, a, b;
+  __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
     if (mode == 4) {
-      acc[(size_t)r * v * v + col] = val;
+      float* q = acc + (size_t)r * v * v + col;
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < cnt) q[t] = val[t];
       return;
     }
-    const int r1 = r / v, r2 = r % v, c1 = col / v, c2 = col % v;
-    if (mode == 0) { i = r1; a = r2; j = c1; b = c2; }
-    else if (mode == 1) { j = r1; a = r2; i = c1; b = c2; }
-    else if (mode == 2) { i = r1; b = r2; j = c1; a = c2; }
-    else { j = r1; b = r2; i = c1; a = c2; }
-    acc[(((size_t)i * o + j) * v + a) * v + b] = val;
+    const int r1 = r / v, r2 = r % v;
+    int c1 = col / v, c2 = col % v;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) {
+        int i, j, a, b;
+        if (mode == 0) { i = r1; a = r2; j = c1; b = c2; }
+        else if (mode == 1) { j = r1; a = r2; i = c1; b = c2; }
+        else if (mode == 2) { i = r1; b = r2; j = c1; a = c2; }
+        else { j = r1; b = r2; i = c1; a = c2; }
+        acc[(((size_t)i * o + j) * v + a) * v + b] = val[t];
+      }
+      if (++c2 == v) {
+        c2 = 0;
+        ++c1;
+      }
+    }
   }
 };
 // rows (i, a), cols (j, b): linear rings through (m, e) and quadratic rings through (n, f)
@@ -792,9 +815,21 @@ struct LV4B {
 struct StoreV4 {  // rows (e, f), cols (a, b): consecutive lanes write consecutive f
   double* W;
   int n, o, v;
-  __device__ void operator()(int r, int col, float val) const {
-    const size_t x = (((size_t)(o + col / v) * n + (o + r / v)) * n + (o + col % v)) * n + (o + r % v);
-    W[x] += (double)val;
+  __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
+    const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
+    const size_t base = (size_t)(o + r / v) * n2 + (size_t)(o + r % v);
+    int a = col / v, b = col % v;
+    size_t x = base + (size_t)(o + a) * n3 + (size_t)(o + b) * n1;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) W[x] += (double)val[t];
+      x += n1;
+      if (++b == v) {
+        b = 0;
+        ++a;
+        x = base + (size_t)(o + a) * n3 + (size_t)o * n1;
+      }
+    }
   }
 };
 
@@ -816,12 +851,22 @@ struct LOVB {
 struct StoreOV {
   double* W;
   int n, o, v;
-  __device__ void operator()(int r, int col, float val) const {
-    const int m = r / v, E = o + r % v, j = col / v, B = o + col % v;
-    const size_t x = (((size_t)m * n + E) * n + B) * n + j, y = (((size_t)B * n + j) * n + m) * n + E;
-    const double w = W[x] + (double)val;
-    W[x] = w;
-    W[y] = w;
+  __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
+    const int m = r / v, E = o + r % v;
+    int j = col / v, B = o + col % v;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) {
+        const size_t x = (((size_t)m * n + E) * n + B) * n + j, y = (((size_t)B * n + j) * n + m) * n + E;
+        const double w = W[x] + (double)val[t];
+        W[x] = w;
+        W[y] = w;
+      }
+      if (++B == o + v) {
+        B = o;
+        ++j;
+      }
+    }
   }
 };
 
@@ -839,12 +884,22 @@ struct LOOB {
 struct StoreOO {
   double* W;
   int n, o, v;
-  __device__ void operator()(int r, int col, float val) const {
-    const int i = r / v, B = o + r % v, j = col / v, A = o + col % v;
-    const size_t x = (((size_t)i * n + j) * n + A) * n + B, y = (((size_t)A * n + B) * n + i) * n + j;
-    const double w = W[x] + (double)val;
-    W[x] = w;
-    W[y] = w;
+  __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
+    const int i = r / v, B = o + r % v;
+    int j = col / v, A = o + col % v;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) {
+        const size_t x = (((size_t)i * n + j) * n + A) * n + B, y = (((size_t)A * n + B) * n + i) * n + j;
+        const double w = W[x] + (double)val[t];
+        W[x] = w;
+        W[y] = w;
+      }
+      if (++A == o + v) {
+        A = o;
+        ++j;
+      }
+    }
   }
 };
 
@@ -862,9 +917,17 @@ struct LOVOB {
 struct StoreOVO {
   float* acc;
   int o, v;
-  __device__ void operator()(int r, int col, float val) const {
-    const int m = r / v, b = r % v, i = col / o, j = col % o;
-    acc[(((size_t)m * o + i) * v + b) * o + j] = val;
+  __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
+    const int m = r / v, b = r % v;
+    int i = col / o, j = col % o;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) acc[(((size_t)m * o + i) * v + b) * o + j] = val[t];
+      if (++j == o) {
+        j = 0;
+        ++i;
+      }
+    }
   }
 };
 
@@ -904,12 +967,23 @@ struct LVV3B {  // cols (a, i): t[m i a f]
 struct StoreVV {  // each job its own buffer
   float* acc;
   int o, v, mode;  // 0: (a e)(b i)  1: (a b)(e i)  2: (e b)(a i)
-  __device__ void operator()(int r, int col, float val) const {
-    int a, e, b, i;
-    if (mode == 0) { a = r / v; e = r % v; b = col / o; i = col % o; }
-    else if (mode == 1) { a = r / v; b = r % v; e = col / o; i = col % o; }
-    else { e = r / v; b = r % v; a = col / o; i = col % o; }
-    acc[(((size_t)a * v + e) * v + b) * o + i] = val;
+  __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
+    const int r1 = r / v, r2 = r % v;
+    int c1 = col / o, c2 = col % o;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) {
+        int a, e, b;
+        if (mode == 0) { a = r1; e = r2; b = c1; }
+        else if (mode == 1) { a = r1; b = r2; e = c1; }
+        else { e = r1; b = r2; a = c1; }
+        acc[(((size_t)a * v + e) * v + b) * o + c2] = val[t];
+      }
+      if (++c2 == o) {
+        c2 = 0;
+        ++c1;
+      }
+    }
   }
 };
 

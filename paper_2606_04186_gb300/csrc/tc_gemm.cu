@@ -18,6 +18,12 @@ struct StoreRowMajor {
   float* p;
   int ld;
   __device__ void operator()(int m, int n, float v) const { p[(size_t)m * ld + n] = v; }
+  __device__ void run(int m, int n, const float (&v)[32], int cnt) const {
+    float* q = p + (size_t)m * ld + n;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < cnt) q[j] = v[j];
+  }
 };
 
 }  // namespace

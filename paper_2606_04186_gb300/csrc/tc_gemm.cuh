@@ -454,12 +454,13 @@ __global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs,
       const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
       tmem_ld32(tmem + lane_base + (uint32_t)c, v);
       tmem_ld32(tmem + lane_base + (uint32_t)(BN + c), w);
-      if (m < jb.M) {
+      if (m < jb.M && n0 + c < jb.N) {
+        // 32 consecutive columns of row m in one call, so the store can walk its output indices
+        // instead of splitting every column index
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c + j;
-          if (n < jb.N) jb.st(m, n, v[j] + w[j]);
-        }
+        for (int j = 0; j < 32; ++j) v[j] += w[j];
+        const int cnt = (jb.N - (n0 + c) < 32) ? jb.N - (n0 + c) : 32;
+        jb.st.run(m, n0 + c, v, cnt);
       }
     }
   }
