@@ -1378,6 +1378,32 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     __syncwarp();
   }
   // ---- root, increment, merge ------------------------------------------------------------
+  // owners and old amplitudes of the space's internal amplitudes are loaded first, so their
+  // latency overlaps the Ritz vector and the extraction (only an owner writes an amplitude, so
+  // the values read here are the ones the merge below updates)
+  constexpr int K4 = K * K * K * K, R2 = (K4 + 31) / 32;
+  int32_t own1 = -1, own2[R2];
+  double old1 = 0.0, old2[R2];
+  size_t g1 = 0, g2[R2];
+  if (a.owner1 && lane < K * K) {
+    g1 = (size_t)ws.orb[lane / K] * a.nvir + (ws.orb[K + lane % K] - a.nocc);
+    own1 = a.owner1[g1];
+    old1 = a.t1_old[g1];
+  }
+#pragma unroll
+  for (int r = 0; r < R2; ++r) {
+    const int idx = lane + 32 * r;
+    own2[r] = -1;
+    old2[r] = 0.0;
+    g2[r] = 0;
+    if (a.owner2 && idx < K4) {
+      const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
+      g2[r] = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[K + aa] - a.nocc)) * a.nvir +
+              (ws.orb[K + b] - a.nocc);
+      own2[r] = a.owner2[g2[r]];
+      old2[r] = a.t2_old[g2[r]];
+    }
+  }
   const int k = ws.ctrl[0];
   float xx = 0.f;
   for (int d = lane; d < NDET; d += 32) {
@@ -1404,7 +1430,6 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     x1[lane] = 0.5f * f * (ws.S[J * NS] + ws.S[J]);
   }
   __syncwarp();
-  constexpr int K4 = K * K * K * K;
 #pragma unroll 1
   for (int idx = lane; idx < K4; idx += 32) {
     const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
@@ -1413,25 +1438,15 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     x2[idx] = f * ws.S[tb.xJ[xa] * NS + tb.xJ[xb]] - x1[xa] * x1[xb];
   }
   __syncwarp();
-  // owner and old value are loaded together (independent loads, one latency)
-  if (st == kSpaceOk && a.owner1 && lane < K * K) {
-    const int i = lane / K, aa = lane % K;
-    const size_t g = (size_t)ws.orb[i] * a.nvir + (ws.orb[K + aa] - a.nocc);
-    const int32_t own = a.owner1[g];
-    const double old = a.t1_old[g];
-    if (own == sidx) a.t1_new[g] = old + (double)x1[lane];
-  }
+  if (st == kSpaceOk && a.owner1 && lane < K * K && own1 == sidx) a.t1_new[g1] = old1 + (double)x1[lane];
   if (st == kSpaceOk && a.owner2) {
 #pragma unroll
-    for (int r = 0; r < (K4 + 31) / 32; ++r) {
+    for (int r = 0; r < R2; ++r) {
       const int idx = lane + 32 * r;
-      if (idx >= K4) break;
-      const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
-      const size_t g = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[K + aa] - a.nocc)) * a.nvir +
-                       (ws.orb[K + b] - a.nocc);
-      const int32_t own = a.owner2[g];
-      const double old = a.t2_old[g];
-      if (own == sidx) a.t2_new[g] = old + (double)(0.5f * (x2[idx] + x2[((j * K + i) * K + b) * K + aa]));
+      if (idx < K4 && own2[r] == sidx) {
+        const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
+        a.t2_new[g2[r]] = old2[r] + (double)(0.5f * (x2[idx] + x2[((j * K + i) * K + b) * K + aa]));
+      }
     }
   }
   if (lane == 0) {
