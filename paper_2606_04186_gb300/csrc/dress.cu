@@ -815,14 +815,32 @@ struct LV4B {
 struct StoreV4 {  // rows (e, f), cols (a, b): consecutive lanes write consecutive f
   double* W;
   int n, o, v;
+  // all 32 old values are loaded before any is written back, so the read-modify-writes do not
+  // wait on one another (the addresses are distinct)
   __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
     const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
     const size_t base = (size_t)(o + r / v) * n2 + (size_t)(o + r % v);
-    int a = col / v, b = col % v;
+    const int a0 = col / v, b0 = col % v;
+    double old[32];
+    {
+      int a = a0, b = b0;
+      size_t x = base + (size_t)(o + a) * n3 + (size_t)(o + b) * n1;
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        old[t] = (t < cnt) ? W[x] : 0.0;
+        x += n1;
+        if (++b == v) {
+          b = 0;
+          ++a;
+          x = base + (size_t)(o + a) * n3 + (size_t)o * n1;
+        }
+      }
+    }
+    int a = a0, b = b0;
     size_t x = base + (size_t)(o + a) * n3 + (size_t)(o + b) * n1;
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
-      if (t < cnt) W[x] += (double)val[t];
+      if (t < cnt) W[x] = old[t] + (double)val[t];
       x += n1;
       if (++b == v) {
         b = 0;
@@ -853,12 +871,24 @@ struct StoreOV {
   int n, o, v;
   __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
     const int m = r / v, E = o + r % v;
+    double old[32];
+    {
+      int j = col / v, B = o + col % v;
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        old[t] = (t < cnt) ? W[(((size_t)m * n + E) * n + B) * n + j] : 0.0;
+        if (++B == o + v) {
+          B = o;
+          ++j;
+        }
+      }
+    }
     int j = col / v, B = o + col % v;
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
       if (t < cnt) {
         const size_t x = (((size_t)m * n + E) * n + B) * n + j, y = (((size_t)B * n + j) * n + m) * n + E;
-        const double w = W[x] + (double)val[t];
+        const double w = old[t] + (double)val[t];
         W[x] = w;
         W[y] = w;
       }
@@ -886,12 +916,24 @@ struct StoreOO {
   int n, o, v;
   __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
     const int i = r / v, B = o + r % v;
+    double old[32];
+    {
+      int j = col / v, A = o + col % v;
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        old[t] = (t < cnt) ? W[(((size_t)i * n + j) * n + A) * n + B] : 0.0;
+        if (++A == o + v) {
+          A = o;
+          ++j;
+        }
+      }
+    }
     int j = col / v, A = o + col % v;
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
       if (t < cnt) {
         const size_t x = (((size_t)i * n + j) * n + A) * n + B, y = (((size_t)A * n + B) * n + i) * n + j;
-        const double w = W[x] + (double)val[t];
+        const double w = old[t] + (double)val[t];
         W[x] = w;
         W[y] = w;
       }
