@@ -283,8 +283,18 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 //   Fvv[a][e] = f~_ae - sum_mnf g~_menf u_mn^af           (next v^2 blocks)
 //   R1[a][i]  = f~_ai + sum_me f~_me u_im^ae + sum_mef g~_aemf u_im^ef - sum_mne g~_mine u_mn^ae
 //   Woooo[k][i][l][j] = g~_kilj + sum_ef g~_kelf t_ij^ef
+// u[i j a b] = 2 t_ij^ab - t_ij^ba once per dressing (the small blocks read it many times)
+__global__ void k_make_u(const double* __restrict__ t2, double* __restrict__ U, Dims d) {
+  const size_t m = (size_t)d.o * d.o * d.v * d.v;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m; x += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(x % d.v), a = (int)((x / d.v) % d.v);
+    const int j = (int)((x / ((size_t)d.v * d.v)) % d.o), i = (int)(x / ((size_t)d.v * d.v * d.o));
+    U[x] = Ut(t2, d, i, j, a, b);
+  }
+}
+
 __global__ void k_small_blocks(const double* __restrict__ F, const double* __restrict__ W,
-                               const double* __restrict__ t2, double* __restrict__ foo, double* __restrict__ fvv,
+                               const double* __restrict__ U, const double* __restrict__ t2, double* __restrict__ foo, double* __restrict__ fvv,
                                double* __restrict__ r1, double* __restrict__ wo, Dims d) {
   __shared__ double red[TPB];
   const int o = d.o, v = d.v;
@@ -294,7 +304,7 @@ __global__ void k_small_blocks(const double* __restrict__ F, const double* __res
     const int m = x / o, i = x % o;
     for (int t = threadIdx.x; t < o * v * v; t += TPB) {
       const int nn = t / (v * v), e = (t / v) % v, f = t % v;
-      acc += W[gi(d, m, o + e, nn, o + f)] * Ut(t2, d, i, nn, e, f);
+      acc += W[gi(d, m, o + e, nn, o + f)] * U[ti(d, i, nn, e, f)];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) foo[x] = F[m * d.n + i] + acc;
@@ -302,7 +312,7 @@ __global__ void k_small_blocks(const double* __restrict__ F, const double* __res
     const int y = x - o * o, a = y / v, e = y % v;
     for (int t = threadIdx.x; t < o * o * v; t += TPB) {
       const int m = t / (o * v), nn = (t / v) % o, f = t % v;
-      acc -= W[gi(d, m, o + e, nn, o + f)] * Ut(t2, d, m, nn, a, f);
+      acc -= W[gi(d, m, o + e, nn, o + f)] * U[ti(d, m, nn, a, f)];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) fvv[y] = F[(o + a) * d.n + o + e] + acc;
@@ -310,15 +320,15 @@ __global__ void k_small_blocks(const double* __restrict__ F, const double* __res
     const int y = x - o * o - v * v, a = y / o, i = y % o;
     for (int t = threadIdx.x; t < o * v * v; t += TPB) {
       const int m = t / (v * v), e = (t / v) % v, f = t % v;
-      acc += W[gi(d, o + a, o + e, m, o + f)] * Ut(t2, d, i, m, e, f);
+      acc += W[gi(d, o + a, o + e, m, o + f)] * U[ti(d, i, m, e, f)];
     }
     for (int t = threadIdx.x; t < o * o * v; t += TPB) {
       const int m = t / (o * v), nn = (t / v) % o, e = t % v;
-      acc -= W[gi(d, m, i, nn, o + e)] * Ut(t2, d, m, nn, a, e);
+      acc -= W[gi(d, m, i, nn, o + e)] * U[ti(d, m, nn, a, e)];
     }
     for (int t = threadIdx.x; t < o * v; t += TPB) {
       const int m = t / v, e = t % v;
-      acc += F[m * d.n + o + e] * Ut(t2, d, i, m, a, e);
+      acc += F[m * d.n + o + e] * U[ti(d, i, m, a, e)];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) r1[y] = F[(o + a) * d.n + i] + acc;
@@ -600,10 +610,10 @@ size_t dress_workspace_bytes_mixed(int n, int nocc) {
 }
 
 int dress_launch_count(int n, int nocc, bool mixed) {
-  // copy, 4 T1 passes, h~, f~, 2 energy, small blocks, finalize; T2 terms: 7 SIMT kernels
+  // copy, 4 T1 passes, h~, f~, 2 energy, u, small blocks, finalize; T2 terms: 7 SIMT kernels
   // (FP64) or 2 FP32 copies + 29 operand packs + 8 GEMM launches + 3 finalize kernels + error
   // check (mixed)
-  return (n - nocc > 0 && nocc > 0) ? (mixed ? 11 + 43 : 11 + 7) : 5;
+  return (n - nocc > 0 && nocc > 0) ? (mixed ? 12 + 43 : 12 + 7) : 5;
 }
 
 namespace {
@@ -1332,8 +1342,10 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
   k_energy_part<<<EGRID, TPB, 0, st>>>(w.ht, W, t2, w.epart, d);
   k_energy_sum<<<1, EGRID, 0, st>>>(w.epart, e0);
   if (v > 0 && o > 0) {
-    k_small_blocks<<<(unsigned)(o * o + v * v + v * o + o * o * o * o), TPB, 0, st>>>(F, W, t2, w.foo, w.fvv, w.r1,
-                                                                                     w.wo, d);
+    // U lives in the r2 slot until the doubles residual is written there
+    k_make_u<<<blocks_for(o * o * v * v), TPB, 0, st>>>(t2, w.r2, d);
+    k_small_blocks<<<(unsigned)(o * o + v * v + v * o + o * o * o * o), TPB, 0, st>>>(F, W, w.r2, t2, w.foo, w.fvv,
+                                                                                     w.r1, w.wo, d);
     if (g32) {  // contractions of the T2 terms in FP32 (mixed precision), bases kept in FP64
       float* t2f = reinterpret_cast<float*>(w.t2f);
       const unsigned gg = blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4);
