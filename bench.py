@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 1.25                              # GB300 FP64 (nominal)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="n82", choices=sorted(synth.SYSTEMS))
@@ -114,7 +114,7 @@ def dress_gemm_flops(o: int, v: int) -> float:
 
 
 # solve-kernel DRAM traffic per space, sweep 3 (ncu capture of the 477,120-space n82 subset)
-TRAFFIC_PER_SPACE = {"n82": 156.6}
+TRAFFIC_PER_SPACE = {"n82": 146.5}
 
 
 # ---- clocks ------------------------------------------------------------------------------------
