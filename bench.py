@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed sweeps of the plain FP64 form (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample", type=int, default=800, help="spaces solved by the oracle for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=3000, help="spaces solved by the oracle for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "persistent", "per_class"])
     ap.add_argument("--sampler", type=int, default=-1,
