@@ -549,28 +549,13 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
   constexpr int NS = 20, NSG = 12, NF = 36;
   if (lane < NS) {
     const int Ia = lane;
+    constexpr unsigned kRows = (1u << NS) - 1u;  // lanes 0..19
     float acc[NS];
-    {  // diagonal and alpha-alpha: acc[b] = diag * c + sum_J Hs[Ia][J] c[J][b]
-      // diag(Ia, b) = dh[Ia] + dh[b] + (sum_{p in Ia, r in b} J_pr - j0), as diag_at, with the
-      // row sums jp[r] = sum_{p in Ia} J_pr in registers and b's orbitals known at compile time
-      float jp[6];
+    // alpha-alpha: A[Ia][b] = sum_J Hs[Ia][J] c[J][b].  The vectors are symmetric under the spin
+    // flip (c[a][b] = c[b][a]: Phi is, and the spin-free operator commutes with the flip), so the
+    // beta-beta part is A^T: row Ia of A goes through `out` and comes back as column Ia.
 #pragma unroll
-      for (int r = 0; r < 6; ++r)
-        jp[r] = ws.Jc[tb.occ[Ia][0] * 6 + r] + ws.Jc[tb.occ[Ia][1] * 6 + r] + ws.Jc[tb.occ[Ia][2] * 6 + r];
-      float jab[NS];
-      coulomb_rows(std::make_integer_sequence<int, NS>{}, jab, jp);
-      const float4* dhr = reinterpret_cast<const float4*>(ws.dh);
-      const float4* crow = reinterpret_cast<const float4*>(c + Ia * NS);
-      const float dha = ws.dh[Ia], jz = ws.j0;
-#pragma unroll
-      for (int q = 0; q < NS / 4; ++q) {
-        const float4 dv = dhr[q], cv = crow[q];
-        acc[4 * q + 0] = (dha + dv.x + (jab[4 * q + 0] - jz)) * cv.x;
-        acc[4 * q + 1] = (dha + dv.y + (jab[4 * q + 1] - jz)) * cv.y;
-        acc[4 * q + 2] = (dha + dv.z + (jab[4 * q + 2] - jz)) * cv.z;
-        acc[4 * q + 3] = (dha + dv.w + (jab[4 * q + 3] - jz)) * cv.w;
-      }
-    }
+    for (int b = 0; b < NS; ++b) acc[b] = 0.f;
 #pragma unroll 4
     for (int J = 0; J < NS; ++J) {
       const float hj = ws.Hs[Ia * NS + J];
@@ -584,32 +569,33 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
         acc[4 * q + 3] = fmaf(hj, cv.w, acc[4 * q + 3]);
       }
     }
-    {  // beta-beta: acc[b] += sum_J Hs[b][J] c[Ia][J]
-      float ca[NS];
+    {
+      float4* orow = reinterpret_cast<float4*>(out + Ia * NS);
+#pragma unroll
+      for (int q = 0; q < NS / 4; ++q) orow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+    __syncwarp(kRows);
+    {  // + A^T and the diagonal: diag(Ia, b) = dh[Ia] + dh[b] + (sum_{p in Ia, r in b} J_pr - j0),
+       // as diag_at, with jp[r] = sum_{p in Ia} J_pr in registers and b's orbitals at compile time
+      float jp[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+        jp[r] = ws.Jc[tb.occ[Ia][0] * 6 + r] + ws.Jc[tb.occ[Ia][1] * 6 + r] + ws.Jc[tb.occ[Ia][2] * 6 + r];
+      float jab[NS];
+      coulomb_rows(std::make_integer_sequence<int, NS>{}, jab, jp);
+      const float4* dhr = reinterpret_cast<const float4*>(ws.dh);
       const float4* crow = reinterpret_cast<const float4*>(c + Ia * NS);
+      const float dha = ws.dh[Ia], jz = ws.j0;
 #pragma unroll
       for (int q = 0; q < NS / 4; ++q) {
-        const float4 cv = crow[q];
-        ca[4 * q] = cv.x;
-        ca[4 * q + 1] = cv.y;
-        ca[4 * q + 2] = cv.z;
-        ca[4 * q + 3] = cv.w;
-      }
-#pragma unroll
-      for (int b = 0; b < NS; ++b) {
-        const float4* hrow = reinterpret_cast<const float4*>(ws.Hs + b * NS);
-        float s = 0.f;
-#pragma unroll
-        for (int q = 0; q < NS / 4; ++q) {
-          const float4 hv = hrow[q];
-          s = fmaf(hv.x, ca[4 * q], s);
-          s = fmaf(hv.y, ca[4 * q + 1], s);
-          s = fmaf(hv.z, ca[4 * q + 2], s);
-          s = fmaf(hv.w, ca[4 * q + 3], s);
-        }
-        acc[b] += s;
+        const float4 dv = dhr[q], cv = crow[q];
+        acc[4 * q + 0] += out[(4 * q + 0) * NS + Ia] + (dha + dv.x + (jab[4 * q + 0] - jz)) * cv.x;
+        acc[4 * q + 1] += out[(4 * q + 1) * NS + Ia] + (dha + dv.y + (jab[4 * q + 1] - jz)) * cv.y;
+        acc[4 * q + 2] += out[(4 * q + 2) * NS + Ia] + (dha + dv.z + (jab[4 * q + 2] - jz)) * cv.z;
+        acc[4 * q + 3] += out[(4 * q + 3) * NS + Ia] + (dha + dv.w + (jab[4 * q + 3] - jz)) * cv.w;
       }
     }
+    __syncwarp(kRows);  // every column read before a row of out is written again
     // alpha-beta: the 12 replacements into Ia, register tiles of W and C rows
 #pragma unroll 1
     for (int u = 0; u < NSG; ++u) {
@@ -1164,8 +1150,9 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   if (guess_in && KM >= 2) {
     float* v1 = ws.V;
     float p = 0.f;
-    for (int d = lane; d < NDET; d += 32) {
-      const float gv = (d == 0) ? 0.f : guess_in[(size_t)s * NDET + d];
+    for (int d = lane; d < NDET; d += 32) {  // spin-flip symmetric part (where the Phi root lies)
+      const int dt = (d % NS) * NS + d / NS;
+      const float gv = (d == 0) ? 0.f : 0.5f * (guess_in[(size_t)s * NDET + d] + guess_in[(size_t)s * NDET + dt]);
       v1[d] = gv;
       p = fmaf(gv, gv, p);
     }
