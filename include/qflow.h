@@ -72,8 +72,9 @@ typedef struct {
 
 typedef enum {
   QFLOW_SCHED_AUTO = 0,       /* mixed precision: the first sweep runs the persistent queue;
-                                 at the second sweep the autotuner times the candidates on a
-                                 calibration subset and keeps the fastest                     */
+                                 at the second sweep the autotuner times its items-per-fetch
+                                 candidates (1, 2, 4, 8, 16) on a calibration subset and keeps
+                                 the fastest                                                  */
   QFLOW_SCHED_PER_CLASS = 1,  /* one grid-stride launch per size class                        */
   QFLOW_SCHED_PERSISTENT = 2  /* one persistent launch; warps take spaces of every class from a
                                  single work queue, 6e6o first                                 */

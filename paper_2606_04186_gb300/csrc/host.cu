@@ -674,8 +674,11 @@ cudaError_t autotune(qflow_ctx* c) {
       return cudaSuccess;
     }
   }
-  // candidates: (persistent, chunk, CTAs per SM)
-  const int cand[6][3] = {{0, 1, 0}, {1, 1, 0}, {1, 4, 0}, {1, 16, 0}, {0, 1, 1}, {1, 4, 1}};
+  // candidates: (persistent, chunk, CTAs per SM).  Only the persistent queue: one CTA of the
+  // warp solver fills an SM, and the per-class grid-stride launch, which can tie on a calibration
+  // prefix, loses its L2 locality over a whole list (n82: 90 ms against 76 ms).
+  constexpr int kCand = 5;
+  const int cand[kCand][3] = {{1, 1, 0}, {1, 2, 0}, {1, 4, 0}, {1, 8, 0}, {1, 16, 0}};
   // calibration prefix of every class: large enough that the warps' drift through the list
   // (which decides L2 reuse of the W blocks) shows, small next to a full solve
   const int64_t count = 262144;
@@ -685,7 +688,7 @@ cudaError_t autotune(qflow_ctx* c) {
   float best = 1e30f;
   int bi = 0;
   int64_t dummy = 0;
-  for (int ci = 0; ci < 6 && e == cudaSuccess; ++ci) {
+  for (int ci = 0; ci < kCand && e == cudaSuccess; ++ci) {
     float ms = 0.f;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
       e = cudaEventRecord(t0, c->stream);
@@ -703,7 +706,7 @@ cudaError_t autotune(qflow_ctx* c) {
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if (e != cudaSuccess) return e;
-  c->tune_count = 6;
+  c->tune_count = kCand;
   c->sched_persistent = cand[bi][0];
   c->sched_chunk = cand[bi][1];
   c->sched_ctas = cand[bi][2];

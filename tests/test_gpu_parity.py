@@ -272,5 +272,6 @@ def test_autotuner_times_candidates(qf):
     assert f.schedule()["candidate_ms"] == []     # calibration happens at the second sweep
     f.sweep()
     sch = f.schedule()
-    assert len(sch["candidate_ms"]) == 6 and min(sch["candidate_ms"]) > 0
+    assert len(sch["candidate_ms"]) == 5 and min(sch["candidate_ms"]) > 0
+    assert sch["persistent"] and sch["chunk"] in (1, 2, 4, 8, 16)
     f.close()
