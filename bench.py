@@ -77,11 +77,13 @@ def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12
     same-spin string operator (1,980 merged terms).  Iteration m with subspace size j: the first
     (m = 1, from Phi) only scales the first-order vector; later ones form the residual
     400*(4j+4), precondition 400*8, orthogonalise in two passes 400*(4j)*2 and normalise 400*3.
-    Each iteration applies sigma, 400 * (2*NSG^2 + 4*NS + 2) = 148,000 flop, and forms the new
+    Each iteration applies sigma, 400 * (2*NSG^2 + 2*NS + 3) = 132,400 flop (alpha-beta, the
+    alpha-alpha product whose transpose is the beta-beta part, the transpose added, the diagonal
+    term), and forms the new
     row and column of the projected matrix 400*2*(2j+1); the subspace restarts at kmax.  The
     convergence test after the last iteration forms one more residual.
     """
-    sig = ndet * (2 * nsg * nsg + 4 * ns + 2)
+    sig = ndet * (2 * nsg * nsg + 2 * ns + 3)
     nz = 117
     phi = 2 * 153 + 2 * nz
     first = 2 * 6 * ns * k + nz * 8 + 2 * 1980
@@ -114,7 +116,7 @@ def dress_gemm_flops(o: int, v: int) -> float:
 
 
 # solve-kernel DRAM traffic per space, sweep 3 (ncu capture of the 477,120-space n82 subset)
-TRAFFIC_PER_SPACE = {"n82": 146.5}
+TRAFFIC_PER_SPACE = {"n82": 141.7}
 
 
 # ---- clocks ------------------------------------------------------------------------------------
@@ -255,7 +257,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {s.n} orbitals ({s.nocc} occ), all (3,3) spaces", "precision": "fp64",
                    "note": "each step: full oracle dressing + a seeded sample of spaces solved on all host cores; "
                            "sweep time extrapolated linearly in the number of spaces"},
@@ -442,7 +444,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": sweep_ms, "higher_is_better": True,
-        "scaling": "strong" if world > 1 else "weak",
+        "scaling": "strong",   # every N sweeps the same list of spaces
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} spaces "
                                f"({', '.join(f'{int((sp[:, 0] == k).sum())} ({k},{k})' for k in (3, 2, 1) if (sp[:, 0] == k).any())})",

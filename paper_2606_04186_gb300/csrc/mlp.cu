@@ -1,7 +1,7 @@
 // Warm-start network for the 6e6o solver (not in the paper; the paper mentions learning only
 // for the choice of active spaces).  A small FP32 network maps the folded integrals of a
 // (3,3) space to its CI -> CC increment; the increment is expanded into a start vector for the
-// Davidson solver, which stays the judge of every energy and amplitude.
+// Davidson solver, which alone decides every energy and amplitude.
 //
 //   features (708): vacuum-ordered h[p][q] over the six local orbitals (36, row-major), the
 //       pair-symmetric W[p][q][r][s] once per P = 6p+q <= R = 6r+s (666, row-major over (P,R)),
