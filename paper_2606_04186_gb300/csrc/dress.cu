@@ -1200,11 +1200,12 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
     ar.reset();
     Op a1, b1;
     QF_TRY(pack_op(LR2G1A{c}, oo, vv + oo, kTileM, ar, &a1, st));
-    QF_TRY(pack_op(LR2G1B{c}, vv, vv + oo, 32, ar, &b1, st));
+    QF_TRY(pack_op(LR2G1B{c}, vv, vv + oo, 64, ar, &b1, st));
     tc::PackedJobs<StoreR2> js{};
     js.j[0] = job(a1, b1, StoreR2{acc, o, v, 4});
     js.count = 1;
-    QF_TRY((run_jobs<32>(js, ar, err, st)));
+    // 64-column tiles: v^2 / 64 tiles fit one wave of CTAs at o = 10 (162 tiles of 32 took two)
+    QF_TRY((run_jobs<64>(js, ar, err, st)));
   }
   // r2: rings (four output maps, one launch)
   {
