@@ -1287,11 +1287,11 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
     ar.reset();
     Op a1, b1, a2, b2, a3, b3;
     QF_TRY(pack_op(LVV1A{c}, vv, 2 * ov, kTileM, ar, &a1, st));
-    QF_TRY(pack_op(LVV1B{c}, v * o, 2 * ov, 64, ar, &b1, st));
+    QF_TRY(pack_op(LVV1B{c}, v * o, 2 * ov, 128, ar, &b1, st));
     QF_TRY(pack_op(LVV2A{c}, vv, oo, kTileM, ar, &a2, st));
-    QF_TRY(pack_op(LVV2B{c}, v * o, oo, 64, ar, &b2, st));
+    QF_TRY(pack_op(LVV2B{c}, v * o, oo, 128, ar, &b2, st));
     QF_TRY(pack_op(LVV3A{c}, vv, ov, kTileM, ar, &a3, st));
-    QF_TRY(pack_op(LVV3B{c}, v * o, ov, 64, ar, &b3, st));
+    QF_TRY(pack_op(LVV3B{c}, v * o, ov, 128, ar, &b3, st));
     const size_t n_vvvo = (size_t)vv * v * o;
     float* p1 = ar.take(n_vvvo);
     float* p2 = ar.take(n_vvvo);
@@ -1300,7 +1300,8 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
     js.j[1] = job(a2, b2, StoreVV{p1, o, v, 1});
     js.j[2] = job(a3, b3, StoreVV{p2, o, v, 2});
     js.count = 3;
-    QF_TRY((run_jobs<64>(js, ar, err, st)));
+    // 128-column tiles: half the re-reads of the v^2-row operand from L2
+    QF_TRY((run_jobs<128>(js, ar, err, st)));
     if (run && e == cudaSuccess) {
       k_vvvo_fin<<<blocks_for(n_vvvo), TPB, 0, st>>>(W, F, t2, acc, p1, p2, d);
       e = cudaGetLastError();

@@ -290,9 +290,14 @@ cudaError_t gemm_tf32x3(int M, int N, int K, LoadA la, LoadB lb, Store st, int* 
 // into the canonical layout with 16-byte cp.async (no index arithmetic, no registers) while the
 // tensor cores work on the previous slab.  Up to kMaxJobs independent jobs of one store type
 // share a launch (blockIdx.z selects the job); jobs may also be K-ranges of one product
-// (split K) writing separate partial outputs.
+// (split K) writing separate partial outputs.  A CTA has two warpgroups: both issue the slab
+// copies, and in the epilogue warps w and w + 4 read the same 32 accumulator lanes (a warp reaches
+// the lanes 32 (w mod 4) .. 32 (w mod 4) + 31) and take alternate 32-column chunks, so twice as
+// many output loads and stores are in flight as with one warpgroup.
 namespace qf {
 namespace tc {
+
+constexpr int PTHREADS = 256;  // threads of a packed-engine CTA
 
 // out_hi/out_lo[r][k] = split(L(r, k)) for r < rows, k < K; zero in the padding.
 template <class L>
@@ -343,7 +348,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void slab_copy(const float* hi, const float* lo, int ld, int r0, int nrows, int s,
                                           float* shi, float* slo, int tid) {
   const int chunks = nrows * 8;  // 16-byte chunks per array
-  for (int c = tid; c < chunks; c += THREADS) {
+  for (int c = tid; c < chunks; c += PTHREADS) {
     const int row = c >> 3, k4 = (c & 7) * 4;
     const size_t g = (size_t)(r0 + row) * ld + (size_t)s * BK + k4;
     const uint32_t o = slab_off(row, k4);
@@ -369,7 +374,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // S-stage pipeline: slabs s+1 .. s+S-2 are in flight while the tensor cores work on slab s; the
 // stage of slab s-1 is refilled (with slab s+S-1) once its MMAs have completed.
 template <int BN, int S, class Store>
-__global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs, int* __restrict__ err) {
+__global__ void __launch_bounds__(PTHREADS, 1) k_gemm_packed(PackedJobs<Store> jobs, int* __restrict__ err) {
   static_assert(S >= 2 && S <= 4, "stages");
   if ((int)blockIdx.z >= jobs.count) return;
   const PackedJob<Store>& jb = jobs.j[blockIdx.z];
@@ -447,11 +452,12 @@ __global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs,
   tc_fence_after();
   const bool ok = (sm.abort == 0);
   if (ok && nslab > 0) {
-    const int m = m0 + warp * 32 + (tid & 31);
+    const int quad = warp & 3;  // accumulator lanes 32 quad .. 32 quad + 31
+    const int m = m0 + quad * 32 + (tid & 31);
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
+    for (int c = (warp >> 2) * 32; c < BN; c += 64) {
       float v[32], w[32];
-      const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+      const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
       tmem_ld32(tmem + lane_base + (uint32_t)c, v);
       tmem_ld32(tmem + lane_base + (uint32_t)(BN + c), w);
       if (m < jb.M && n0 + c < jb.N) {
@@ -475,18 +481,19 @@ __global__ void __launch_bounds__(THREADS) k_gemm_packed(PackedJobs<Store> jobs,
 
 template <int BN, class Store>
 cudaError_t gemm_packed(const PackedJobs<Store>& jobs, int* err, cudaStream_t stream) {
-  constexpr int S = (BN <= 32) ? 4 : (BN <= 64 ? 3 : 2);
+  constexpr int S = (BN <= 32) ? 4 : 3;  // 3 x 64 KB stages at BN = 128
   int gx = 1, gy = 1;
   for (int i = 0; i < jobs.count; ++i) {
     const int x = (jobs.j[i].N + BN - 1) / BN, y = (jobs.j[i].M + BM - 1) / BM;
     gx = x > gx ? x : gx;
     gy = y > gy ? y : gy;
   }
+  static_assert(sizeof(SmemP<BN, S>) + 1024 <= 232448, "stages within the shared memory of a block");
   const size_t smem = sizeof(SmemP<BN, S>) + 1024;
   auto kern = k_gemm_packed<BN, S, Store>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)jobs.count), THREADS, smem, stream>>>(jobs, err);
+  kern<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)jobs.count), PTHREADS, smem, stream>>>(jobs, err);
   return cudaGetLastError();
 }
 
