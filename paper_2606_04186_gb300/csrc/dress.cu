@@ -1116,15 +1116,16 @@ struct Arena {
   void reset() { used = 0; }
 };
 
-struct Op {  // a packed operand: hi / lo parts, rows padded to the tile, K padded to 32
+struct Op {  // a packed operand: hi / lo parts, rows padded to the tile (rows_p), K padded to 32
   float *hi, *lo;
-  int rows, K, ld;
+  int rows, rows_p, K, ld;
 };
 
 template <class L>
 cudaError_t pack_op(L ld, int rows, int K, int tile, Arena& ar, Op* out, cudaStream_t st) {
   const int rows_p = tc::pad_to(rows, tile), Kp = tc::pad_to(K, tc::BK);
   out->rows = rows;
+  out->rows_p = rows_p;
   out->K = K;
   out->ld = Kp;
   out->hi = ar.take((size_t)rows_p * Kp);
@@ -1145,6 +1146,8 @@ tc::PackedJob<Store> job(const Op& a, const Op& b, Store st, int split = 0, int 
   j.blo = b.lo;
   j.M = a.rows;
   j.N = b.rows;
+  j.ma_p = a.rows_p;
+  j.nb_p = b.rows_p;
   j.ld = a.ld;
   const int slabs = a.ld / tc::BK, per = (slabs + nsplit - 1) / nsplit;
   j.k_begin = split * per * tc::BK;

@@ -20,6 +20,8 @@
 // Every mbarrier wait is bounded; on timeout the CTA records an error, stops issuing work,
 // waits (bounded) for its committed MMAs, frees its tensor memory and returns.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -286,14 +288,14 @@ cudaError_t gemm_tf32x3(int M, int N, int K, LoadA la, LoadB lb, Store st, int* 
 
 // ---- packed operands --------------------------------------------------------------------------
 // A second engine for operands prepared by k_pack: hi and lo TF32 parts as row-major FP32
-// matrices with K padded to a multiple of 32 and rows padded to the tile, so a slab is copied
-// into the canonical layout with 16-byte cp.async (no index arithmetic, no registers) while the
-// tensor cores work on the previous slab.  Up to kMaxJobs independent jobs of one store type
-// share a launch (blockIdx.z selects the job); jobs may also be K-ranges of one product
-// (split K) writing separate partial outputs.  A CTA has two warpgroups: both issue the slab
-// copies, and in the epilogue warps w and w + 4 read the same 32 accumulator lanes (a warp reaches
-// the lanes 32 (w mod 4) .. 32 (w mod 4) + 31) and take alternate 32-column chunks, so twice as
-// many output loads and stores are in flight as with one warpgroup.
+// matrices with K padded to a multiple of 32 and rows padded to the tile.  A slab (32 K x tile
+// rows, 128-byte rows) is one TMA box per array, written to shared memory with the 128-byte
+// swizzle that the MMA descriptors read, while the tensor cores work on the previous slabs.  Up
+// to kMaxJobs independent jobs of one store type share a launch (blockIdx.z selects the job);
+// jobs may also be K-ranges of one product (split K) writing separate partial outputs.  A CTA has
+// two warpgroups: in the epilogue warps w and w + 4 read the same 32 accumulator lanes (a warp
+// reaches the lanes 32 (w mod 4) .. 32 (w mod 4) + 31) and take alternate 32-column chunks, so
+// twice as many output loads and stores are in flight as with one warpgroup.
 namespace qf {
 namespace tc {
 
@@ -326,8 +328,12 @@ __host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m 
 
 template <class Store>
 struct PackedJob {
-  const float *ahi, *alo, *bhi, *blo;  // [M_p][ld], [N_p][ld]
+  // tensor maps of the four packed arrays (filled by gemm_packed from the pointers below): 2-D
+  // views [rows_p][ld] whose boxes are one slab (32 K x tile rows) with the 128-byte swizzle
+  CUtensorMap tahi, talo, tbhi, tblo;
+  const float *ahi, *alo, *bhi, *blo;  // [ma_p][ld], [nb_p][ld]
   int M, N, ld;                        // ld = padded K of the packed arrays
+  int ma_p, nb_p;                      // allocated (padded) rows of the A and B arrays
   int k_begin, k_slabs;                // slabs [k_begin / 32, k_begin / 32 + k_slabs)
   Store st;
 };
@@ -339,42 +345,64 @@ struct PackedJobs {
   int count;
 };
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Copy slab s of rows [r0, r0 + nrows) of a packed pair into a stage (canonical layout).
-__device__ __forceinline__ void slab_copy(const float* hi, const float* lo, int ld, int r0, int nrows, int s,
-                                          float* shi, float* slo, int tid) {
-  const int chunks = nrows * 8;  // 16-byte chunks per array
-  for (int c = tid; c < chunks; c += PTHREADS) {
-    const int row = c >> 3, k4 = (c & 7) * 4;
-    const size_t g = (size_t)(r0 + row) * ld + (size_t)s * BK + k4;
-    const uint32_t o = slab_off(row, k4);
-    cp_async16(smem_u32(shi) + o, hi + g);
-    cp_async16(smem_u32(slo) + o, lo + g);
-  }
-}
-
 template <int BN, int S>
-struct SmemP {  // S-stage buffers of the packed engine
+struct SmemP {  // S-stage buffers of the packed engine (each slab 128-byte rows, swizzled)
   float a_hi[S][BM * BK], a_lo[S][BM * BK];
   float b_hi[S][BN * BK], b_lo[S][BN * BK];
-  uint64_t bar[S];
+  uint64_t full[S];  // slab landed (TMA transaction count)
+  uint64_t bar[S];   // MMAs of the slab done (stage free)
   uint32_t tmem;
   int abort;
 };
 
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+// Non-blocking probe of a phase; polled a bounded number of times.
+__device__ __forceinline__ bool mbar_probe(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_probe(uint64_t* bar, uint32_t parity) {
+  for (unsigned it = 0; it < kSpinLimit; ++it)
+    if (mbar_probe(bar, parity)) return true;
+  return false;
 }
 
-// S-stage pipeline: slabs s+1 .. s+S-2 are in flight while the tensor cores work on slab s; the
-// stage of slab s-1 is refilled (with slab s+S-1) once its MMAs have completed.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// One box of a 2-D tensor map (x = K element, y = row) into shared memory, counted on `bar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with the 128-byte swizzle: rows of 128 bytes
+// (32 TF32), 8-row groups 1 KB apart (SBO); the leading offset is unused for this layout.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;  // layout: 128-byte swizzle
+  return d;
+}
+
+// S-stage pipeline driven by one thread: TMA brings slab s+S-1 while the tensor cores work on
+// slab s; a stage is refilled once the MMAs that read it have completed.  The other threads wait
+// at the barrier before the epilogue.  Every wait is a bounded poll; on a timeout the CTA records
+// an error and waits (bounded) for what it has in flight before it frees its tensor memory.
 template <int BN, int S, class Store>
-__global__ void __launch_bounds__(PTHREADS, 1) k_gemm_packed(PackedJobs<Store> jobs, int* __restrict__ err) {
+__global__ void __launch_bounds__(PTHREADS, 1) k_gemm_packed(const __grid_constant__ PackedJobs<Store> jobs,
+                                                             int* __restrict__ err) {
   static_assert(S >= 2 && S <= 4, "stages");
   if ((int)blockIdx.z >= jobs.count) return;
   const PackedJob<Store>& jb = jobs.j[blockIdx.z];
@@ -384,69 +412,84 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_gemm_packed(PackedJobs<Store> j
   SmemP<BN, S>& sm = *reinterpret_cast<SmemP<BN, S>*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
-    for (int i = 0; i < S; ++i) mbar_init(&sm.bar[i], 1);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&sm.full[i], 1);
+      mbar_init(&sm.bar[i], 1);
+    }
     sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
   }
   if (warp == 0) tmem_alloc(&sm.tmem, 2 * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm.tmem;
-  constexpr uint32_t idesc = idesc_tf32(BN);
   const int nslab = jb.k_slabs, s0 = jb.k_begin / BK;
-  uint32_t phase = 0u;  // bit i: parity to wait for on bar[i]
-  uint32_t issued = 0u;  // bit i: bar[i] has a commit not yet waited for
-#pragma unroll
-  for (int p = 0; p < S - 1; ++p) {
-    if (p < nslab) {
-      slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0 + p, sm.a_hi[p], sm.a_lo[p], tid);
-      slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0 + p, sm.b_hi[p], sm.b_lo[p], tid);
-    }
-    cp_async_commit();
-  }
-  for (int s = 0; s < nslab; ++s) {
-    const int st = s % S;
-    cp_async_wait<S - 2>();  // slab s has landed
-    fence_async_smem();
-    __syncthreads();
-    if (sm.abort) break;
-    if (tid == 0) {
+  if (tid == 0 && nslab > 0) {
+    constexpr uint32_t idesc = idesc_tf32(BN);
+    constexpr uint32_t kStageBytes = (uint32_t)(BM + BN) * BK * 4u * 2u;
+    uint32_t fph = 0u, mph = 0u;       // parity to wait for, per stage, on full[] and bar[]
+    uint32_t loaded = 0u, pend = 0u;   // stages with a load / an MMA commit not yet waited for
+    bool bad = false;
+    auto load = [&](int slab, int st) {
+      const int kx = (s0 + slab) * BK;
+      mbar_expect_tx(&sm.full[st], kStageBytes);
+      tma_load_2d(smem_u32(sm.a_hi[st]), &jb.tahi, kx, m0, &sm.full[st]);
+      tma_load_2d(smem_u32(sm.a_lo[st]), &jb.talo, kx, m0, &sm.full[st]);
+      tma_load_2d(smem_u32(sm.b_hi[st]), &jb.tbhi, kx, n0, &sm.full[st]);
+      tma_load_2d(smem_u32(sm.b_lo[st]), &jb.tblo, kx, n0, &sm.full[st]);
+      loaded |= 1u << st;
+    };
+    for (int p = 0; p < S && p < nslab; ++p) load(p, p);
+    for (int s = 0; s < nslab; ++s) {
+      const int st = s % S;
+      if (!mbar_wait_probe(&sm.full[st], (fph >> st) & 1u)) {
+        bad = true;
+        break;
+      }
+      fph ^= 1u << st;
+      loaded &= ~(1u << st);
       tc_fence_after();
       const uint32_t ah = smem_u32(sm.a_hi[st]), al = smem_u32(sm.a_lo[st]);
       const uint32_t bh = smem_u32(sm.b_hi[st]), bl = smem_u32(sm.b_lo[st]);
 #pragma unroll
       for (int ks = 0; ks < BK / 8; ++ks) {
-        const uint32_t koff = (uint32_t)ks * 256;
-        const uint64_t dah = smem_desc(ah + koff, 128, 1024), dal = smem_desc(al + koff, 128, 1024);
-        const uint64_t dbh = smem_desc(bh + koff, 128, 1024), dbl = smem_desc(bl + koff, 128, 1024);
+        const uint32_t koff = (uint32_t)ks * 32;  // 8 TF32 along the 128-byte row
+        const uint64_t dah = smem_desc_sw128(ah + koff), dal = smem_desc_sw128(al + koff);
+        const uint64_t dbh = smem_desc_sw128(bh + koff), dbl = smem_desc_sw128(bl + koff);
         const uint32_t acc0 = (s > 0 || ks > 0) ? 1u : 0u;
         mma_tf32(tmem, dah, dbh, idesc, acc0);
         mma_tf32(tmem + BN, dah, dbl, idesc, acc0);
         mma_tf32(tmem + BN, dal, dbh, idesc, 1u);
       }
       mma_commit(&sm.bar[st]);
-    }
-    issued |= 1u << st;
-    // refill the stage of slab s-1 with slab s+S-1 once its MMAs are done
-    const int nxt = s + S - 1;
-    if (nxt < nslab) {
-      const int ps = nxt % S;
-      if (issued & (1u << ps)) {
-        if (!mbar_wait(&sm.bar[ps], (phase >> ps) & 1u)) sm.abort = 1;
-        phase ^= 1u << ps;
-        issued &= ~(1u << ps);
+      pend |= 1u << st;
+      // refill the stage of slab s-1 with slab s-1+S once its MMAs are done
+      const int nxt = s - 1 + S;
+      if (s >= 1 && nxt < nslab) {
+        const int ps = (s - 1) % S;
+        if (!mbar_wait_probe(&sm.bar[ps], (mph >> ps) & 1u)) {
+          bad = true;
+          break;
+        }
+        mph ^= 1u << ps;
+        pend &= ~(1u << ps);
+        load(nxt, ps);
       }
-      slab_copy(jb.ahi, jb.alo, jb.ld, m0, BM, s0 + nxt, sm.a_hi[ps], sm.a_lo[ps], tid);
-      slab_copy(jb.bhi, jb.blo, jb.ld, n0, BN, s0 + nxt, sm.b_hi[ps], sm.b_lo[ps], tid);
     }
-    cp_async_commit();
+    for (int b = 0; b < S; ++b) {
+      if ((pend >> b) & 1u) {
+        if (!mbar_wait_probe(&sm.bar[b], (mph >> b) & 1u)) bad = true;
+        mph ^= 1u << b;
+      }
+      if ((loaded >> b) & 1u) {  // only after a failure: copies still in flight
+        if (!mbar_wait_probe(&sm.full[b], (fph >> b) & 1u)) bad = true;
+        fph ^= 1u << b;
+      }
+    }
+    if (bad) sm.abort = 1;
   }
-  cp_async_wait<0>();
-  for (int b = 0; b < S; ++b)
-    if (issued & (1u << b)) {
-      if (!mbar_wait(&sm.bar[b], (phase >> b) & 1u)) sm.abort = 1;
-      phase ^= 1u << b;
-    }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -479,12 +522,46 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_gemm_packed(PackedJobs<Store> j
   }
 }
 
+// cuTensorMapEncodeTiled from the driver (through the runtime, no link against libcuda).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// 2-D view [rows_p][ld] of one packed array; box = one slab (32 K) of `box_rows` rows.
+inline bool encode_operand(CUtensorMap* m, const float* p, int rows_p, int ld, int box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !p || ((uintptr_t)p & 15u) != 0 || ld % BK != 0 || rows_p % box_rows != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows_p};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN, class Store>
-cudaError_t gemm_packed(const PackedJobs<Store>& jobs, int* err, cudaStream_t stream) {
+cudaError_t gemm_packed(const PackedJobs<Store>& in, int* err, cudaStream_t stream) {
   constexpr int S = (BN <= 32) ? 4 : 3;  // 3 x 64 KB stages at BN = 128
+  PackedJobs<Store> jobs = in;
   int gx = 1, gy = 1;
   for (int i = 0; i < jobs.count; ++i) {
-    const int x = (jobs.j[i].N + BN - 1) / BN, y = (jobs.j[i].M + BM - 1) / BM;
+    PackedJob<Store>& j = jobs.j[i];
+    const int ma = j.ma_p, nb = j.nb_p;
+    // every box of the grid must lie inside the allocated rows
+    if (ma < pad_to(j.M, BM) || nb < pad_to(j.N, BN)) return cudaErrorInvalidValue;
+    if (!encode_operand(&j.tahi, j.ahi, ma, j.ld, BM) || !encode_operand(&j.talo, j.alo, ma, j.ld, BM) ||
+        !encode_operand(&j.tbhi, j.bhi, nb, j.ld, BN) || !encode_operand(&j.tblo, j.blo, nb, j.ld, BN))
+      return cudaErrorInvalidValue;
+    const int x = (j.N + BN - 1) / BN, y = (j.M + BM - 1) / BM;
     gx = x > gx ? x : gx;
     gy = y > gy ? y : gy;
   }
