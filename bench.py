@@ -204,6 +204,13 @@ def oracle_sweep_sample(name: str, sample: int, pool, seed: int = 7):
             "solve_s_sample": t_solve, "sample": len(pick), "nspaces": len(sp)}
 
 
+def workload_desc(name: str, s, sp: np.ndarray) -> str:
+    """The workload as both arms name it: system, orbital counts, xi and the space list by class."""
+    no, nv = s.nocc, s.n - s.nocc
+    classes = ', '.join(f'{int((sp[:, 0] == k).sum())} ({k},{k})' for k in (3, 2, 1) if (sp[:, 0] == k).any())
+    return f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} spaces ({classes})"
+
+
 def log(msg: str):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
@@ -258,11 +265,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {s.n} orbitals ({s.nocc} occ), all (3,3) spaces", "precision": "fp64",
+        "config": {"workload": workload_desc(args.workload, s, synth.system_inputs(args.workload)[3]), "precision": "fp64",
                    "note": "each step: full oracle dressing + a seeded sample of spaces solved on all host cores; "
                            "sweep time extrapolated linearly in the number of spaces"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} spaces per step of {r['nspaces']} + full dressing, extrapolated"},
+                         "sample": f"{r['sample']} spaces per step of {r['nspaces']} + full dressing, extrapolated"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -446,8 +453,7 @@ def run_ours(args):
         "warmup": max(3, args.warmup), "ms_per_step": sweep_ms, "higher_is_better": True,
         "scaling": "strong",   # every N sweeps the same list of spaces
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"{name}: {s.n} orbitals ({no} occ, {nv} virt), xi={s.xi}, {len(sp)} spaces "
-                               f"({', '.join(f'{int((sp[:, 0] == k).sum())} ({k},{k})' for k in (3, 2, 1) if (sp[:, 0] == k).any())})",
+        "config": {"workload": workload_desc(name, s, sp),
                    "precision": args.precision, "sweep_s": sweep_ms / 1e3, "l2": (f"inputs larger than L2 (W = {8 * s.n ** 4 / 1e6:.0f} MB)" if 8 * s.n ** 4 > 126e6
                           else f"inputs smaller than L2 (W = {8 * s.n ** 4 / 1e6:.1f} MB), not flushed"), "e_sweep3": e_mean,
                    "space_list": (f"Algorithm 1 cycle, seed {args.sampler}" if args.sampler >= 0
