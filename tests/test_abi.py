@@ -68,3 +68,31 @@ def test_plan_rejects_bad_spaces(qf):
     empty = sp[:0]
     perm, o1, o2, unc = qf.plan(h, g, 3, empty)
     assert perm.size == 0 and unc == o1.size + o2.size
+
+
+def test_init_rejects_bad_arguments_before_any_device_work(qf):
+    """Argument errors come back as QFLOW_ERR_ARG with no handle, before the library touches a GPU
+    (this runs on a machine without one)."""
+    import ctypes as C
+    eps, h, g, sp = synth.system_inputs("n10")
+    L = qf.lib()
+    rows = qf._spaces(sp)
+
+    def init(n, nocc, spaces, opt):
+        hdl = C.c_void_p()
+        code = L.qflow_init(C.byref(hdl), qf._ptr(h), qf._ptr(g), n, nocc, qf._ptr(spaces), len(spaces),
+                            C.byref(opt) if opt is not None else None)
+        return code, hdl.value
+
+    for n, nocc in ((129, 3), (1, 0), (10, 10), (10, 0)):
+        assert init(n, nocc, rows, None) == (qf.ERR_ARG, None), (n, nocc)
+    bad = rows.copy()
+    bad[0, 2] = 7                       # an occupied slot that names a virtual orbital
+    assert init(10, 3, bad, None) == (qf.ERR_ARG, None)
+    bad = rows.copy()
+    bad[0, 5], bad[0, 6] = bad[0, 6], bad[0, 5]   # virtual orbitals out of ascending order
+    assert init(10, 3, bad, None) == (qf.ERR_ARG, None)
+    for field, value in (("precision", 5), ("diis", 1), ("diis", -1), ("guess", 9)):
+        opt = qf.default_options("mixed")
+        setattr(opt, field, value)
+        assert init(10, 3, rows, opt) == (qf.ERR_ARG, None), field
