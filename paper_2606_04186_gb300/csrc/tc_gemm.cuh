@@ -6,7 +6,8 @@
 // from loader functors (any layout, any permutation of a 4-index block), the result goes to a
 // store functor, so a contraction needs no transposed copies in HBM.
 //
-// One CTA of 128 threads computes a 128 x BN tile:
+// The general engine (loader functors, used by the device-level GEMM entry point): one CTA of
+// 128 threads computes a 128 x BN tile:
 //   * all threads load a 128 x 32 slab of A and a BN x 32 slab of B, split them and write them
 //     to shared memory in the canonical K-major, no-swizzle layout (core matrices of 8 rows x
 //     16 bytes; LBO = 128 B between core matrices along K, SBO = 1 KB between 8-row groups);
@@ -19,6 +20,8 @@
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns rows 32w..32w+31).
 // Every mbarrier wait is bounded; on timeout the CTA records an error, stops issuing work,
 // waits (bounded) for its committed MMAs, frees its tensor memory and returns.
+// The packed engine further down, which the dressing uses, takes operands split ahead of time and
+// brings them in with TMA (see its own description).
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
