@@ -93,3 +93,36 @@ def test_feature_packing_reproduces_cas_operator():
     assert np.abs(ref - mat - c * np.eye(ref.shape[0])).max() < 1e-12
     orb = list(occ) + list(vir)
     assert np.array_equal(fd, np.diag(F)[orb])
+
+
+def test_adam_first_step_is_the_normalised_gradient():
+    # Kingma and Ba (2015), Algorithm 1: at t = 1 the bias-corrected moments are m = g and v = g*g,
+    # so every parameter moves by -lr * g / (|g| + eps), whatever beta1 and beta2 are.
+    rng = np.random.default_rng(5)
+    p = rng.standard_normal(40)
+    g = rng.standard_normal(40) * np.logspace(-3, 2, 40)
+    z = np.zeros(40)
+    p1, m1, v1 = mlp.adam_step(p, g, z, z, 1, 0.05)
+    np.testing.assert_allclose(p1 - p, -0.05 * g / (np.abs(g) + 1e-8), rtol=1e-13, atol=0.0)
+    np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-12)  # 1 - 0.9 rounds
+    np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-12)
+
+
+def test_adam_second_step_hand_computed():
+    # One scalar parameter, p0 = 0.5, gradients g1 = 1 then g2 = -2, lr = 0.1, betas (0.9, 0.999),
+    # eps = 1e-8, worked by hand from Kingma and Ba (2015), Algorithm 1:
+    #   t = 1: m = 0.1, v = 0.001, m^ = 1, v^ = 1               -> p1 = 0.5 - 0.1 / (1 + 1e-8)
+    #   t = 2: m = 0.09 - 0.2 = -0.11, v = 0.000999 + 0.004 = 0.004999,
+    #          m^ = -0.11 / 0.19 = -11/19, v^ = 0.004999 / 0.001999 = 4999/1999
+    #                                                           -> p2 = p1 + 0.1 (11/19) / (sqrt(4999/1999) + 1e-8)
+    # Swapping the betas or dropping either bias correction changes p2 in the third digit.
+    p = np.array([0.5])
+    z = np.zeros(1)
+    p1, m, v = mlp.adam_step(p, np.array([1.0]), z, z, 1, 0.1)
+    p2, m, v = mlp.adam_step(p1, np.array([-2.0]), m, v, 2, 0.1)
+    want1 = 0.5 - 0.1 / (1.0 + 1e-8)
+    want2 = want1 + 0.1 * (11.0 / 19.0) / (np.sqrt(4999.0 / 1999.0) + 1e-8)
+    assert abs(p1[0] - want1) < 1e-15
+    assert abs(m[0] - (-0.11)) < 1e-15 and abs(v[0] - 0.004999) < 1e-17
+    assert abs(p2[0] - want2) < 1e-14
+    assert abs(want2 - 0.4366103534720748) < 1e-15
