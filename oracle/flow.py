@@ -80,12 +80,16 @@ def solve_all(e0, F, W, spaces_sorted, pool=None):
 
 
 def merge(t1, t2, spaces_sorted, results, own1, own2, nocc):
-    """t_new[x] = t_old[x] + X_owner(x)[x]; unowned amplitudes unchanged."""
+    """t_new[x] = t_old[x] + X_owner(x)[x]; unowned amplitudes unchanged.  A space whose root
+    is flagged (status != 0: complex, or |c_Phi| below the limit) has no usable increment, so
+    the amplitudes it owns keep their value as well."""
     t1n, t2n = t1.copy(), t2.copy()
     for s, (row, res) in enumerate(zip(spaces_sorted, results)):
         occ, vir = space_orbitals(row)
         va = [a - nocc for a in vir]
-        _, x1, x2, _ = res
+        _, x1, x2, st = res
+        if st != 0:
+            continue
         for ii, i in enumerate(occ):
             for aa, a in enumerate(va):
                 if own1[i, a] == s:
@@ -165,6 +169,8 @@ class Flow:
                 occ, vir = space_orbitals(row)
                 va = [a - self.nocc for a in vir]
                 energies[s], x1, x2, status[s] = r
+                if status[s] != 0:  # a flagged root leaves its owned amplitudes unchanged
+                    continue
                 for ii, i in enumerate(occ):
                     for aa, a in enumerate(va):
                         if self.own1[i, a] == s:
