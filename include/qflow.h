@@ -61,8 +61,11 @@ typedef enum {
   QFLOW_PREC_MIXED = 1   /* dressing: FP64 integrals with FP32 T1 correction sums, reference
                             energy and Fock-like sums in FP64, T2 contractions as tensor-core
                             GEMMs (three-term TF32, FP32 accumulation) added to FP64 bases;
-                            solver: FP32 sigma, vectors and projected eigenproblem, FP64
-                            diagonal/energy shift; FP64 energy and amplitude update          */
+                            solver: FP32 gather/fold/set-up, sigma and Davidson vectors;
+                            Rayleigh-Ritz matrix, projected root and Gram-Schmidt coefficients
+                            to FP64 accuracy (double-float); FP64 energy, amplitude update,
+                            DIIS and reductions.  Spaces the FP32 warp pass leaves unconverged
+                            after 16 steps are re-solved by the FP64 solver in the same sweep */
 } qflow_precision;
 
 typedef struct {
@@ -82,7 +85,8 @@ typedef enum {
 
 typedef struct {
   int32_t precision;          /* qflow_precision                                            */
-  int32_t max_iter;           /* Davidson iteration limit per space (default 60)            */
+  int32_t max_iter;           /* Davidson iteration limit per space (default 60); mixed:
+                                 the warp pass stops at 16, later steps run in FP64         */
   double tol;                 /* Davidson residual 2-norm (default 1e-9 fp64, 1e-6 mixed)   */
   int32_t diis;               /* 0 = off, else Pulay DIIS on the pool with a history of 2..8
                                  sweeps (FP64, on the device; not in the paper: it accelerates
@@ -280,7 +284,11 @@ int qflow_dress_device(const double* h, const double* eri, const double* t1, con
  *             the solver first tests Phi (converged there: done), else starts from the span
  *             of Phi and the guess, whose sigma counts as one iteration.  Receives the
  *             converged root (Phi coefficient 1) when save_root != 0
- *   precision qflow_precision; max_iter, tol as in qflow_options. */
+ *   precision qflow_precision; max_iter, tol as in qflow_options.
+ * Mixed: the warp solver runs at most min(max_iter, 16) Davidson steps; when max_iter > 16 the
+ * spaces it leaves unconverged are then solved by the FP64 solver (start from Phi, max_iter
+ * steps), which needs 8 bytes of device scratch per space: the call allocates and frees it
+ * on `stream` (cudaMallocAsync / cudaFreeAsync). */
 int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* F, const double* W,
                        int32_t size_class, const qflow_space* spaces, int64_t nspaces, int64_t space_base, const int32_t* owner1,
                        const int32_t* owner2, const double* t1_old, const double* t2_old, double* t1_new,
@@ -296,6 +304,15 @@ int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* 
 int qflow_gemm_tf32x3_device(int32_t M, int32_t N, int32_t K, const float* A, int32_t lda, const float* B,
                              int32_t ldb, float* C, int32_t ldc, int32_t* err, void* stream);
 
+/* ---- measurement: FMA peaks -------------------------------------------------------------
+ * The paper has no counterpart; the solver's roofline divides by these rates.  Measures the
+ * FMA throughput of this GPU in FP64 (precision QFLOW_PREC_FP64) or FP32 (QFLOW_PREC_MIXED):
+ * every SM runs as many 256-thread blocks as fit, each thread eight independent fma chains;
+ * *tflops = 2 x FMAs / CUDA-event time of the launch, best of three after a warm-up (about
+ * 30 ms per launch).  Allocates a small output buffer on `stream` (stream-ordered) and
+ * synchronises `stream` before returning.  Errors: QFLOW_ERR_ARG, QFLOW_ERR_CUDA. */
+int qflow_fma_peak(int32_t precision, double* tflops, void* stream);
+
 /* ---- allocation-free dressing ---------------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot call
  * cudaMalloc: applications whose device memory belongs to another allocator (an arena or pool
@@ -310,12 +327,16 @@ int qflow_gemm_tf32x3_device(int32_t M, int32_t N, int32_t K, const float* A, in
  *   - Limit: the call returns QFLOW_ERR_TOO_LARGE when qflow_dress_workspace(n, nocc) exceeds
  *     QFLOW_STATIC_SCRATCH_BYTES (4 MiB, e.g. 40 orbitals with 6 occupied fit, 82 do not).
  *   - Set-up: the first call on a device looks up the device address of the array on that
- *     device (with it current); make that first call before any stream capture.
+ *     device (with it current) and keeps it for that device's current context; make that first
+ *     call before any stream capture.  A call that would do the look-up while `stream` is
+ *     capturing returns QFLOW_ERR_STATE and enqueues nothing.  After a device reset (or any
+ *     re-creation of the context) the kept address is dropped and looked up again.
  *   - Sharing: every call on a device uses the same array, which keeps the last call's data;
  *     the kernels write every scratch element before reading it, so nothing needs clearing.
  *     Calls whose work overlaps on the GPU (other streams, other threads) race on the array:
  *     order them on one stream or serialise them.
- * Other arguments, layouts and errors: as qflow_dress_device. */
+ * Other arguments, layouts and errors: as qflow_dress_device (QFLOW_ERR_OOM for an allocation
+ * failure reported by the runtime, QFLOW_ERR_CUDA for any other CUDA failure). */
 #define QFLOW_STATIC_SCRATCH_BYTES (4u * 1024u * 1024u)
 int qflow_dress_device_static(const double* h, const double* eri, const double* t1, const double* t2, int32_t n,
                               int32_t nocc, double* e0, double* F, double* W, void* stream);

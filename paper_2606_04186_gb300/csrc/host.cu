@@ -17,6 +17,7 @@
 #include "qflow_internal.h"
 
 using qf::SolveArgs;
+using qf::cuda_status;
 
 namespace {
 
@@ -214,6 +215,8 @@ struct qflow_ctx {
   void* diis = nullptr;                                   // DIIS ring (opt.diis > 0)
   float* W32 = nullptr;  // FP32 copies of W (n^4) and F (n^2, after W) for the mixed-precision solver
   unsigned long long* queue = nullptr;                    // persistent-launch work counter
+  int64_t* rescue_items = nullptr;  // mixed path: positions of spaces the warp pass left unconverged
+  unsigned long long* rescue_count = nullptr;  // and their count (device)
   // launch schedule of the mixed-precision solver: persistent queue or one launch per class
   int sched_persistent = 1, sched_chunk = 4, sched_ctas = 0;
   bool tuned = false;
@@ -270,6 +273,8 @@ void free_ctx(qflow_ctx* c) {
   if (c->diis) cudaFree(c->diis);
   if (c->W32) cudaFree(c->W32);
   if (c->queue) cudaFree(c->queue);
+  if (c->rescue_items) cudaFree(c->rescue_items);
+  if (c->rescue_count) cudaFree(c->rescue_count);
   void* mptrs[] = {c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v, c->mlp_X, c->mlp_T, c->mlp_mask,
                    c->space_mask, c->pool_mask, c->wave_items, c->pool_start};
   for (void* p : mptrs)
@@ -281,12 +286,6 @@ void free_ctx(qflow_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
-}
-
-int cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return QFLOW_OK;
-  if (e == cudaErrorMemoryAllocation) return QFLOW_ERR_OOM;
-  return QFLOW_ERR_CUDA;
 }
 
 }  // namespace
@@ -406,6 +405,12 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
   if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) e = dalloc(&c->W32, n4 + n1 * n1);
   if (e == cudaSuccess) e = dalloc(&c->queue, 1);
+  if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) {
+    int64_t most = 1;
+    for (int k = 1; k <= 3; ++k) most = std::max(most, c->cls_count[k]);
+    e = dalloc(&c->rescue_items, (size_t)most);
+    if (e == cudaSuccess) e = dalloc(&c->rescue_count, 1);
+  }
   if (c->opt.schedule == QFLOW_SCHED_PER_CLASS) {
     c->sched_persistent = 0;
     c->tuned = true;
@@ -518,7 +523,8 @@ cudaError_t enqueue_dress(qflow_ctx* c, int64_t* launches) {
 
 // The per-space solves with a given schedule; `count` > 0 limits every class to its first
 // `count` spaces (autotuner calibration).
-cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches);
+cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches,
+                              bool calibrating);
 
 cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int64_t count, int64_t* launches) {
   SolveArgs cls[4];
@@ -530,11 +536,14 @@ cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int
       cls[k].root_out = nullptr;
     }
   }
-  return enqueue_solve_cls(c, cls, persistent, chunk, ctas, launches);
+  return enqueue_solve_cls(c, cls, persistent, chunk, ctas, launches, count > 0);
 }
 
-// The solves of the given per-class arguments (cls[1..3]) with a given schedule.
-cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches) {
+// The solves of the given per-class arguments (cls[1..3]) with a given schedule.  In the mixed
+// path the warp solver's pass stops at qf::kWarpIterCap steps; unless `calibrating`, the spaces it
+// leaves unconverged are then solved again by the FP64 solver within max_iter steps.
+cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches,
+                              bool calibrating) {
   if (c->opt.precision != QFLOW_PREC_MIXED) {
     cudaError_t e = cudaSuccess;
     for (int k = 1; k <= 3 && e == cudaSuccess; ++k) {
@@ -544,16 +553,27 @@ cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int 
     }
     return e;
   }
-  if (persistent) {
-    *launches += 2;  // queue reset + kernel
-    return qf::launch_solve_persistent(cls, c->W32, c->queue, chunk, ctas, c->stream);
+  SolveArgs warp[4];
+  for (int k = 1; k <= 3; ++k) {
+    warp[k] = cls[k];
+    if (warp[k].max_iter > qf::kWarpIterCap) warp[k].max_iter = qf::kWarpIterCap;
   }
   cudaError_t e = cudaSuccess;
-  for (int k = 3; k >= 1 && e == cudaSuccess; --k) {
-    if (cls[k].nspaces == 0) continue;
-    e = qf::launch_solve_warp(k, cls[k], c->W32, static_cast<const float*>(cls[k].guess),
-                              static_cast<float*>(cls[k].root_out), ctas, c->stream);
-    ++*launches;
+  if (persistent) {
+    *launches += 2;  // queue reset + kernel
+    e = qf::launch_solve_persistent(warp, c->W32, c->queue, chunk, ctas, c->stream);
+  } else {
+    for (int k = 3; k >= 1 && e == cudaSuccess; --k) {
+      if (warp[k].nspaces == 0) continue;
+      e = qf::launch_solve_warp(k, warp[k], c->W32, static_cast<const float*>(warp[k].guess),
+                                static_cast<float*>(warp[k].root_out), ctas, c->stream);
+      ++*launches;
+    }
+  }
+  for (int k = 3; k >= 1 && e == cudaSuccess && !calibrating; --k) {
+    if (cls[k].nspaces == 0 || cls[k].max_iter <= qf::kWarpIterCap) continue;
+    e = qf::launch_solve_rescue(k, cls[k], c->rescue_items, c->rescue_count, c->stream);
+    *launches += 3;
   }
   return e;
 }
@@ -904,7 +924,8 @@ int qflow_sweep_waves(qflow_handle c, int64_t wave, double* d_e, double* max_dt,
       cls[k].t1_new = c->pool;
       cls[k].t2_new = c->pool + c->n_t1;
     }
-    if (e == cudaSuccess) e = enqueue_solve_cls(c, cls, c->sched_persistent, c->sched_chunk, c->sched_ctas, &launches);
+    if (e == cudaSuccess)
+      e = enqueue_solve_cls(c, cls, c->sched_persistent, c->sched_chunk, c->sched_ctas, &launches, false);
   }
   if (e == cudaSuccess) e = mark(c, 2);
   if (e == cudaSuccess && c->diis) {
@@ -1131,7 +1152,16 @@ int qflow_solve_device(int32_t n, int32_t nocc, const double* e0, const double* 
   a.root_out = save_root ? guess : nullptr;
   a.max_iter = max_iter;
   a.tol = tol;
-  return cuda_status(qf::launch_solve(size_class, precision, a, (cudaStream_t)stream));
+  const cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = qf::launch_solve(size_class, precision, a, st);
+  if (e != cudaSuccess || precision != QFLOW_PREC_MIXED || max_iter <= qf::kWarpIterCap) return cuda_status(e);
+  // spaces the warp pass left unconverged: the FP64 solver, on stream-ordered scratch
+  int64_t* items = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void**>(&items), (size_t)nspaces * sizeof(int64_t) + 16, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = qf::launch_solve_rescue(size_class, a, items, reinterpret_cast<unsigned long long*>(items + nspaces), st);
+  const cudaError_t f = cudaFreeAsync(items, st);
+  return cuda_status(e != cudaSuccess ? e : f);
 }
 
 }  // extern "C"

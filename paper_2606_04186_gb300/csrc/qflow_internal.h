@@ -11,6 +11,14 @@
 
 namespace qf {
 
+// Library error code of a failed CUDA runtime call: an allocation failure is QFLOW_ERR_OOM,
+// every other failure QFLOW_ERR_CUDA.
+inline int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QFLOW_OK;
+  if (e == cudaErrorMemoryAllocation) return QFLOW_ERR_OOM;
+  return QFLOW_ERR_CUDA;
+}
+
 // Per-space solver status codes written by the solve kernels.
 enum SpaceStatus : int32_t { kSpaceOk = 0, kSpaceNoConv = 1, kSpaceRoot = 2, kSpaceNonFinite = 3, kSpaceInvalid = 4 };
 
@@ -35,6 +43,7 @@ struct SolveArgs {
   int32_t* iters;
   const float* W32;  // nullable FP32 copy of W (mixed path)
   const float* F32;  // nullable FP32 copy of F (mixed path; else F is converted per element)
+  const unsigned long long* count_dev;  // nullable: the launch covers items [0, *count_dev) instead
   const void* guess;  // nullable start vectors: double (FP64 path) or float (mixed path)
   void* root_out;     // nullable: receives converged roots (Phi coefficient 1), same type/layout
   int32_t max_iter;
@@ -45,6 +54,18 @@ struct SolveArgs {
 cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st);
 // Warp-per-space mixed-precision solvers (solve_warp.cu).  W32: optional FP32 copy of W (same
 // layout); NULL reads and converts the FP64 W.  ctas_per_sm: 0 = as many as fit.
+// Iteration cap of the warp solver's pass in the mixed path: spaces still unconverged after it
+// (a few hard spaces whose Phi-dominant root has lower roots close by) are solved again by the
+// FP64 solver, whose larger subspace converges on them, within max_iter steps.
+constexpr int kWarpIterCap = 16;
+
+// The FP64 solver on the spaces of class k that a previous solve left with status kSpaceNoConv:
+// their positions are collected into items (device, a.nspaces entries) with the count in
+// *count (device); then the solver runs on that list.  Start vectors and saved roots are not
+// used.  Three launches (count reset, collection, solve); graph-capturable.
+cudaError_t launch_solve_rescue(int k, const SolveArgs& a, int64_t* items, unsigned long long* count,
+                                cudaStream_t st);
+
 cudaError_t launch_solve_warp(int k, const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
                               int ctas_per_sm, cudaStream_t st);
 // One persistent launch over every size class (cls[k], k = 1..3; guesses from cls[k].guess):

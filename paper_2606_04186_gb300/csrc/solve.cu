@@ -186,9 +186,11 @@ __device__ void sigma(Smem<K, T>& sm, const T* __restrict__ c, T* __restrict__ o
 }
 
 // Phi-tracking eigenpair of the k x k projected matrix (FP64, one thread): shifted inverse
-// iteration from the previous Ritz value, then Rayleigh-quotient refinement.
+// iteration from the previous Ritz value, then Rayleigh-quotient refinement.  Returns 1 when
+// the result is not an eigenpair of G (|G y - theta y| above 1e-8 of G's scale): real inverse
+// iteration cannot settle on a root that is one of a complex pair; else 0.
 template <int KM>
-__device__ void small_eig(const double* G, int k, double shift, double* y, double* theta) {
+__device__ int small_eig(const double* G, int k, double shift, double* y, double* theta) {
   double a[KM * KM], z[KM];
   for (int phase = 0; phase < 8; ++phase) {
     const double sg = (phase < 4) ? shift : *theta;
@@ -243,6 +245,16 @@ __device__ void small_eig(const double* G, int k, double shift, double* y, doubl
     }
     *theta = num;  // y has unit norm
   }
+  double scale = 0.0, res = 0.0;
+  for (int i = 0; i < k; ++i) {
+    double gy = -(*theta) * y[i];
+    for (int j = 0; j < k; ++j) {
+      gy += G[i * KM + j] * y[j];
+      scale = fmax(scale, fabs(G[i * KM + j]));
+    }
+    res += gy * gy;
+  }
+  return (sqrt(res) > 1e-8 * fmax(1.0, scale)) ? 1 : 0;
 }
 
 template <int K, typename T>
@@ -256,7 +268,8 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
   const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
   const T tol = (T)a.tol;
 
-  for (int64_t item = blockIdx.x; item < a.nspaces; item += gridDim.x) {
+  const int64_t nitems = a.count_dev ? (int64_t)*a.count_dev : a.nspaces;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int64_t s = a.items ? a.items[item] : item;
     // ---- gather + fold ---------------------------------------------------------------
     if (tid == 0) {
@@ -507,13 +520,16 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
         const int kk = k + 1;
         for (int j = 0; j < kk; ++j) sm.ynew[j] = (j < k) ? sm.y[j] : 0.0;
         double thn = sm.theta;
-        small_eig<C::KMAX>(sm.G, kk, sm.theta - 1e-2, sm.ynew, &thn);
+        const int cx = small_eig<C::KMAX>(sm.G, kk, sm.theta - 1e-2, sm.ynew, &thn);
         for (int j = 0; j < kk; ++j) sm.y[j] = sm.ynew[j];
         sm.theta = thn;
         sm.ctrl[0] = kk;
         sm.ctrl[3] = it + 1;
+        sm.ctrl[1] = cx ? sm.ctrl[1] + 1 : 0;  // consecutive steps with a complex projected root
+        if (sm.ctrl[1] >= 2) sm.ctrl[2] = kSpaceRoot;
       }
       __syncthreads();
+      if (sm.ctrl[1] >= 2) break;  // the selected root is complex: no real root to converge to
     }
 
     // ---- root, increment, merge --------------------------------------------------------
@@ -531,6 +547,7 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
     const double xn = sqrt(sm.out[0]);
     const double c0 = (double)sm.S[0];
     int st = sm.ctrl[2];
+    if (st == kSpaceNoConv && sm.ctrl[1] > 0) st = kSpaceRoot;  // stopped on a complex projected root
     if (st == kSpaceOk && !(fabs(c0) >= 1e-3 * xn)) st = kSpaceRoot;
     if (!isfinite(c0) || !isfinite(sm.theta)) st = kSpaceNonFinite;
     const double inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.0 / c0 : 0.0;
@@ -607,18 +624,51 @@ cudaError_t launch_k(const SolveArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-}  // namespace
+// Positions (in a's item numbering) of the spaces whose status is kSpaceNoConv.
+__global__ void k_collect_noconv(SolveArgs a, int64_t* __restrict__ items, unsigned long long* __restrict__ count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.nspaces; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = a.items ? a.items[i] : i;
+    const int64_t o = a.sorted_index ? a.sorted_index[s] : s;
+    if (a.status[o] == kSpaceNoConv) items[atomicAdd(count, 1ull)] = s;
+  }
+}
 
-cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st) {
-  if (precision == QFLOW_PREC_MIXED)
-    return launch_solve_warp(k, a, a.W32, static_cast<const float*>(a.guess), static_cast<float*>(a.root_out), 0,
-                             st);
+cudaError_t launch_fp64(int k, const SolveArgs& a, cudaStream_t st) {
   switch (k) {
     case 1: return launch_k<1, double>(a, st);
     case 2: return launch_k<2, double>(a, st);
     case 3: return launch_k<3, double>(a, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+}  // namespace
+
+cudaError_t launch_solve_rescue(int k, const SolveArgs& a, int64_t* items, unsigned long long* count,
+                                cudaStream_t st) {
+  if (a.nspaces <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (a.nspaces + 255) / 256;
+  k_collect_noconv<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(a, items, count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  SolveArgs b = a;
+  b.items = items;  // positions are class positions: b.spaces / b.sorted_index index them as before
+  b.count_dev = count;
+  b.guess = nullptr;
+  b.root_out = nullptr;
+  return launch_fp64(k, b, st);
+}
+
+cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st) {
+  if (precision == QFLOW_PREC_MIXED) {
+    SolveArgs w = a;
+    if (w.max_iter > kWarpIterCap) w.max_iter = kWarpIterCap;
+    return launch_solve_warp(k, w, a.W32, static_cast<const float*>(a.guess), static_cast<float*>(a.root_out), 0,
+                             st);
+  }
+  return launch_fp64(k, a, st);
 }
 
 }  // namespace qf

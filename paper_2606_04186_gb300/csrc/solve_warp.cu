@@ -9,14 +9,25 @@
 //     row.  For each of the 12 single replacements (pq, J_alpha, s) into I_alpha it holds the W
 //     row W[pq][*] (36 values) and the CI row C[J_alpha][*] (20 values) in registers and applies
 //     the whole beta-side replacement table, a compile-time constant (the same for every space),
-//     as 240 register-only FMAs; the same-spin parts are two 20 x 20 x 20 products from
-//     vectorised shared-memory rows.  The small classes use a determinant-per-lane sigma;
-//   * the operator diagonal is built in FP64 relative to E_Phi = <Phi|H|Phi> and removed from
-//     the sigma operands, so FP32 sums only off-diagonal couplings;
+//     as 240 register-only FMAs; the alpha-alpha part is a 20 x 20 x 20 product from vectorised
+//     shared-memory rows and the beta-beta part its transpose (every vector is symmetric under
+//     the spin flip).  The small classes use a determinant-per-lane sigma;
+//   * the operator diagonal is built relative to E_Phi = <Phi|H|Phi> (which is E0 of the
+//     dressing) and kept out of the sigma operands, so the sums carry only off-diagonal
+//     couplings;
 //   * before anything else a space checks the residual of Phi from Phi's sparse column; spaces
 //     already at their root (most of a mid-flow sweep) stop there;
-//   * FP64 is kept for the fold, the diagonal, the energy and the amplitude update; FP32 for
-//     couplings, the determinant vectors, sigma and the small projected eigenproblem.
+//   * precision: FP32 for the gathered couplings, the fold and set-up (the folded one-body
+//     diagonal and the string diagonal, both differences of O(1) terms), the determinant
+//     vectors and sigma; FP64 accuracy for the Rayleigh-Ritz step (projected matrix, its root,
+//     the Gram-Schmidt coefficients) in double-float arithmetic; FP64 for the energy
+//     E0 + theta and the amplitude update;
+//   * the root of the projected problem is the real Ritz pair with the largest Phi weight (the
+//     space's root is the eigenvector with the largest |c_Phi|); a complex pair with more Phi
+//     weight flags the space;
+//   * the warp pass runs at most kWarpIterCap Davidson steps: the few spaces it leaves
+//     unconverged are solved again by solve.cu's FP64 solver (a larger subspace) in the same
+//     sweep.
 // Kernels: one per size class (grid-stride over that class), and a persistent kernel whose
 // warps take work items from one queue holding every class (largest spaces first).
 // Every loop is bounded; a warp never waits on another warp (the queue is a single atomic
@@ -347,6 +358,71 @@ struct SetupF32 {
   float hd[D::NORB];  // folded one-body diagonal h_pp
 };
 
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- precision of the Rayleigh-Ritz step -----------------------------------------------------
+// The projected matrix, the Gram-Schmidt coefficients and the Ritz value are kept to FP64
+// accuracy as double-float pairs (hi + lo, two FP32 numbers, a 48-bit significand): on this GPU a
+// native FP64 instruction occupies the SM's FP64 pipe for about 19 cycles whether one lane or all
+// 32 use it, so FP64 arithmetic inside the per-space loop would cost more than the sigma-vectors.
+// Inner products of the FP32 vectors are formed as error-free FP32 products summed with
+// compensated additions (each lane, then across the warp), and the projected root is refined by
+// a Newton step in double-float arithmetic; the energy is E0 + hi + lo in FP64.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_norm(float a, float b) {  // |a| >= |b| or a = 0: exact renormalisation
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_sum(float a, float b) {  // a + b = hi + lo exactly
+  const float s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = two_sum(x.hi, y.hi);
+  return df_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float e = __fmaf_rn(x.hi, y.hi, -p);  // x.hi y.hi = p + e exactly
+  return df_norm(p, __fadd_rn(e, __fadd_rn(__fmul_rn(x.hi, y.lo), __fmul_rn(x.lo, y.hi))));
+}
+__device__ __forceinline__ DF df_mulf(DF x, float y) { return df_mul(x, DF{y, 0.f}); }
+__device__ __forceinline__ float df_f(DF x) { return __fadd_rn(x.hi, x.lo); }
+
+// Per-lane sum of products a b, exact products and compensated sums; total() adds the lanes'
+// pairs the same way (every lane gets the same pair: each step's exact error term does not
+// depend on the order of its two operands).
+struct RRAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);  // a b = p + e exactly
+    const DF s = two_sum(hi, p);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, e));
+  }
+  __device__ __forceinline__ DF total() const {
+    float h = hi, l = lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      const DF s = two_sum(h, h2);
+      h = s.hi;
+      l = __fadd_rn(__fadd_rn(l, l2), s.lo);
+    }
+    return df_norm(h, l);
+  }
+};
+
 template <int K>
 struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as float4
   using D = Dim<K>;
@@ -358,11 +434,11 @@ struct alignas(16) WarpState {  // 16-byte rows: the 6e6o sigma reads them as fl
   float Hs[D::NS * D::NS];  // same-spin string operator, zero diagonal
   float dh[(D::NS + 3) / 4 * 4];  // same-spin string diagonal relative to the Phi string
   float Jc[D::NF];          // J_pr = W_pprr: the alpha-beta Coulomb part of the diagonal
-  float G[KM * KM];         // projected matrix, G[i*KM+j] = V_i . S_j
-  float yf[KM];             // Ritz coefficients
-  float theta;              // Ritz value relative to eshift
+  float yf[KM];             // Ritz coefficients (FP32 for the vector updates)
   float j0;                 // sum_{p, r in Phi string} J_pr (FP32, diagonal reference)
   double eshift;             // <Phi|H|Phi> = E0 of the dressing (the fold leaves it unchanged)
+  DF theta;                 // Ritz value relative to eshift
+  DF G[KM * KM];            // projected matrix, G[i*KM+j] = V_i . S_j
   int orb[D::NORB];
   int ctrl[4];              // [0] subspace size, [1] valid, [2] status, [3] iterations
   // the small classes keep set-up data and gather offsets here (the 6e6o state keeps them in
@@ -408,6 +484,11 @@ static_assert(sizeof(WarpState<3>) % 16 == 0 && offsetof(WarpState<3>, S) % 16 =
               "float4 rows of the 6e6o state");
 static_assert(offsetof(CtaSmem, w) % 16 == 0 && sizeof(AnyWarpState) % 16 == 0, "warp state alignment");
 static_assert(sizeof(CtaSmem) <= 232448, "one CTA within the 227 KB of shared memory a block may use");
+
+// Entries of the 6e6o coupling tables (read-only global data, cached on the SM).  A per-CTA
+// shared-memory copy was measured slower: it costs one of the 15 warps an SM holds.
+__device__ __forceinline__ unsigned phi_entry(const CtaSmem&, int i) { return __ldg(&g_phi_table.e[i]); }
+__device__ __forceinline__ unsigned hs_entry(const CtaSmem&, int i) { return __ldg(&g_hs_table.e[i]); }
 
 template <int K>
 __device__ Tabs<K>& tabs(CtaSmem& cs);
@@ -515,12 +596,6 @@ __device__ void build_all_tabs(CtaSmem& cs) {
       for (int R = P; R < Dim<3>::NF; ++R) cs.pair3[t++] = (unsigned short)(P | (R << 8));
   }
   __syncthreads();
-}
-
-__device__ __forceinline__ float wsum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
 }
 
 // ---- sigma ------------------------------------------------------------------------------------
@@ -664,32 +739,51 @@ __device__ __forceinline__ void sigma(const Tabs<K>& tb, const WarpState<K>& ws,
   else sigma_small<K>(tb, ws, c, out, lane);
 }
 
-// Phi-tracking eigenpair of the k x k projected matrix (lane 0): shifted inverse iteration
-// from the previous Ritz value, then Rayleigh-quotient refinement.  The projected matrix is
-// built from FP32 vectors, so it is solved in FP32 too.
-__device__ __noinline__ void small_eig(const float* G, int k, float shift, float* y, float* theta) {
+// Imaginary part above which a projected root counts as complex (FP32 closed forms resolve the
+// real part of a near-degenerate real pair to about 1e-7 of the matrix scale).
+constexpr float kImagMin = 1e-5f;
+
+// Phi-dominant eigenpair of the k x k projected matrix (lane 0).  The subspace basis is Phi
+// (component 0 of every other basis vector is exactly zero), so the Phi weight of a Ritz vector
+// with coefficients y is |y_0| / |y|: of the real roots, the one with the largest Phi weight is
+// taken (the space's root is the eigenvector with the largest |c_Phi|); shifted inverse
+// iteration from `shift` is the fallback when the closed forms fail.  Returns 1 when a complex
+// pair carries more Phi weight than every real root (the real candidate is still returned),
+// else 0.  The projected matrix is built from FP32 vectors, so it is solved in FP32 too.
+__device__ __noinline__ int small_eig(const float* G, int k, float shift, float* y, float* theta) {
+  int cx = 0;
   // The closed forms below lose absolute accuracy to cancellation (the root sought is small next
-  // to the other diagonal entries).  Each root is therefore polished with the Phi row of
+  // to the other diagonal entries).  The chosen root is therefore polished with the Phi row of
   // G y = lambda y, lambda = (G y)_0 / y_0 (exact for an eigenpair; G_00 = Phi . sigma(Phi)),
   // alternating with the eigenvector twice: the error shrinks by about |G_0j| / gap per pass.
-  if (k == 2) {  // closed form: the eigenvalue nearest the shift and its eigenvector
+  if (k == 2) {
     const float g00 = G[0], g01 = G[1], g10 = G[KM], g11 = G[KM + 1];
     const float tr = 0.5f * (g00 + g11), df = 0.5f * (g00 - g11);
     const float disc = df * df + g01 * g10;
+    // eigenvector of G for root lam: the better conditioned of the two rows of (G - lam) y = 0
+    auto vec2 = [&](float lam, float* y0, float* y1) {
+      if (fabsf(g01) + fabsf(lam - g00) >= fabsf(g10) + fabsf(lam - g11)) {
+        *y0 = g01;
+        *y1 = lam - g00;
+      } else {
+        *y0 = lam - g11;
+        *y1 = g10;
+      }
+    };
+    if (disc < 0.f && sqrtf(-disc) > kImagMin * fmaxf(1.f, fabsf(tr))) cx = 1;  // no real root
     if (disc >= 0.f && isfinite(disc)) {
       const float sq = sqrtf(disc);
-      const float l1 = tr + sq, l2 = tr - sq;
-      float lam = (fabsf(l1 - shift) <= fabsf(l2 - shift)) ? l1 : l2;
+      float lam = tr + sq;
+      {  // the root with the larger Phi weight
+        float a0, a1, b0, b1;
+        vec2(tr + sq, &a0, &a1);
+        vec2(tr - sq, &b0, &b1);
+        const float wa = a0 * a0 / fmaxf(a0 * a0 + a1 * a1, 1e-30f), wb = b0 * b0 / fmaxf(b0 * b0 + b1 * b1, 1e-30f);
+        if (wb > wa) lam = tr - sq;
+      }
       float y0 = 0.f, y1 = 0.f;
       for (int pass = 0; pass < 3; ++pass) {
-        // (G - lam) y = 0: take the better conditioned of the two rows
-        if (fabsf(g01) + fabsf(lam - g00) >= fabsf(g10) + fabsf(lam - g11)) {
-          y0 = g01;
-          y1 = lam - g00;
-        } else {
-          y0 = lam - g11;
-          y1 = g10;
-        }
+        vec2(lam, &y0, &y1);
         if (pass == 2 || !(fabsf(y0) >= 0.3f * sqrtf(y0 * y0 + y1 * y1))) break;
         lam = (g00 * y0 + g01 * y1) / y0;
       }
@@ -699,44 +793,21 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
         y[0] = sc * y0;
         y[1] = sc * y1;
         *theta = lam;
-        return;
+        return cx;
       }
     }
   }
-  if (k == 3) {  // real roots of the characteristic cubic; eigenvector from a cross product
+  if (k == 3) {  // roots of the characteristic cubic; eigenvectors from cross products
     const float* g = G;
     const float g00 = g[0], g01 = g[1], g02 = g[2], g10 = g[KM], g11 = g[KM + 1], g12 = g[KM + 2];
     const float g20 = g[2 * KM], g21 = g[2 * KM + 1], g22 = g[2 * KM + 2];
-    // det(lambda I - G) = lambda^3 + a2 lambda^2 + a1 lambda + a0
-    const float a2 = -(g00 + g11 + g22);
-    const float a1 = g00 * g11 - g01 * g10 + g00 * g22 - g02 * g20 + g11 * g22 - g12 * g21;
-    const float a0 = -(g00 * (g11 * g22 - g12 * g21) - g01 * (g10 * g22 - g12 * g20) + g02 * (g10 * g21 - g11 * g20));
-    // lambda = mu - a2 / 3:  mu^3 + p mu + q = 0
-    const float p = a1 - a2 * a2 / 3.f, q = 2.f * a2 * a2 * a2 / 27.f - a2 * a1 / 3.f + a0;
-    float root[3];
-    int nr = 0;
-    const float disc = q * q / 4.f + p * p * p / 27.f;
-    if (disc < 0.f && p < 0.f) {  // three real roots (trigonometric form)
-      const float m = 2.f * sqrtf(-p / 3.f);
-      float c = 3.f * q / (p * m);
-      c = fminf(1.f, fmaxf(-1.f, c));
-      const float phi = acosf(c) / 3.f;
-      for (int j = 0; j < 3; ++j) root[nr++] = m * cosf(phi - 2.0943951f * (float)j) - a2 / 3.f;
-    } else {  // one real root
-      const float sq = sqrtf(fmaxf(disc, 0.f));
-      root[nr++] = cbrtf(-q / 2.f + sq) + cbrtf(-q / 2.f - sq) - a2 / 3.f;
-    }
-    float lam = root[0];
-    for (int j = 1; j < nr; ++j)
-      if (fabsf(root[j] - shift) < fabsf(lam - shift)) lam = root[j];
     auto cross = [](const float* u, const float* w, float* o) {
       o[0] = u[1] * w[2] - u[2] * w[1];
       o[1] = u[2] * w[0] - u[0] * w[2];
       o[2] = u[0] * w[1] - u[1] * w[0];
     };
-    float vb[3] = {0.f, 0.f, 0.f}, nb = 0.f;
-    for (int pass = 0; pass < 3; ++pass) {
-      // null vector of G - lam I: the largest cross product of two of its rows
+    // null vector of G - lam I (the largest cross product of two of its rows) and its norm^2
+    auto vec3 = [&](float lam, float* vb) {
       const float r0[3] = {g00 - lam, g01, g02}, r1[3] = {g10, g11 - lam, g12}, r2[3] = {g20, g21, g22 - lam};
       float c01[3], c02[3], c12[3];
       cross(r0, r1, c01);
@@ -746,12 +817,62 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
       const float n02 = c02[0] * c02[0] + c02[1] * c02[1] + c02[2] * c02[2];
       const float n12 = c12[0] * c12[0] + c12[1] * c12[1] + c12[2] * c12[2];
       const float* best = c01;
-      nb = n01;
+      float nb = n01;
       if (n02 > nb) { best = c02; nb = n02; }
       if (n12 > nb) { best = c12; nb = n12; }
       vb[0] = best[0];
       vb[1] = best[1];
       vb[2] = best[2];
+      return nb;
+    };
+    // det(lambda I - G) = lambda^3 + a2 lambda^2 + a1 lambda + a0
+    const float a2 = -(g00 + g11 + g22);
+    const float a1 = g00 * g11 - g01 * g10 + g00 * g22 - g02 * g20 + g11 * g22 - g12 * g21;
+    const float a0 = -(g00 * (g11 * g22 - g12 * g21) - g01 * (g10 * g22 - g12 * g20) + g02 * (g10 * g21 - g11 * g20));
+    // lambda = mu - a2 / 3:  mu^3 + p mu + q = 0
+    const float p = a1 - a2 * a2 / 3.f, q = 2.f * a2 * a2 * a2 / 27.f - a2 * a1 / 3.f + a0;
+    float root[3];
+    int nr = 0;
+    float cre = 0.f, cim = 0.f;  // complex pair re +- i im (one-real-root case)
+    const float disc = q * q / 4.f + p * p * p / 27.f;
+    if (disc < 0.f && p < 0.f) {  // three real roots (trigonometric form)
+      const float m = 2.f * sqrtf(-p / 3.f);
+      float c = 3.f * q / (p * m);
+      c = fminf(1.f, fmaxf(-1.f, c));
+      const float phi = acosf(c) / 3.f;
+      for (int j = 0; j < 3; ++j) root[nr++] = m * cosf(phi - 2.0943951f * (float)j) - a2 / 3.f;
+    } else {  // one real root
+      const float sq = sqrtf(fmaxf(disc, 0.f));
+      const float u = cbrtf(-q / 2.f + sq), v = cbrtf(-q / 2.f - sq);
+      root[nr++] = u + v - a2 / 3.f;
+      // the other two roots: -(u + v) / 2 - a2 / 3 +- i sqrt(3) / 2 (u - v)
+      cre = -0.5f * (u + v) - a2 / 3.f;
+      cim = 0.8660254f * fabsf(u - v);
+    }
+    float lam = root[0], wbest = -1.f;
+    for (int j = 0; j < nr; ++j) {  // the real root with the largest Phi weight
+      float vb[3];
+      const float nb = vec3(root[j], vb);
+      const float w = vb[0] * vb[0] / fmaxf(nb, 1e-30f);
+      if (w > wbest) {
+        wbest = w;
+        lam = root[j];
+      }
+    }
+    if (nr == 1 && cim > kImagMin * fmaxf(1.f, fabsf(cre))) {
+      // Phi weight of the complex pair's eigenvector: cross product of rows 0 and 1 of G - z I,
+      // z = cre + i cim (the pair's weights are equal), in real and imaginary parts
+      const float ar = g00 - cre, br = g11 - cre, ci = -cim;  // diagonal entries: (ar + i ci), (br + i ci)
+      // v0 = g01 g12 - g02 (g11 - z); v1 = g02 g10 - (g00 - z) g12; v2 = (g00 - z)(g11 - z) - g01 g10
+      const float v0r = g01 * g12 - g02 * br, v0i = -g02 * ci;
+      const float v1r = g02 * g10 - ar * g12, v1i = -ci * g12;
+      const float v2r = ar * br - ci * ci - g01 * g10, v2i = ar * ci + ci * br;
+      const float n2 = v0r * v0r + v0i * v0i + v1r * v1r + v1i * v1i + v2r * v2r + v2i * v2i;
+      if (n2 > 0.f && (v0r * v0r + v0i * v0i) / n2 > wbest) cx = 1;
+    }
+    float vb[3] = {0.f, 0.f, 0.f}, nb = 0.f;
+    for (int pass = 0; pass < 3; ++pass) {
+      nb = vec3(lam, vb);
       if (pass == 2 || !(fabsf(vb[0]) >= 0.3f * sqrtf(nb))) break;
       lam = (g00 * vb[0] + g01 * vb[1] + g02 * vb[2]) / vb[0];
     }
@@ -761,7 +882,7 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
       y[1] = sc * vb[1];
       y[2] = sc * vb[2];
       *theta = lam;
-      return;
+      return cx;
     }
   }
   float a[KM * KM], z[KM];
@@ -817,17 +938,57 @@ __device__ __noinline__ void small_eig(const float* G, int k, float shift, float
     }
     *theta = num;
   }
+  return cx;
+}
+
+// The Phi-dominant eigenpair of the projected matrix to FP64 accuracy: the FP32 closed forms
+// choose the root (and flag a complex one) and give its eigenvector (the coefficients scale FP32
+// vectors); one Newton step on the characteristic polynomial of the double-float matrix, with the
+// polynomial in double-float arithmetic and the FP32 derivative (the step is a small correction),
+// refines the root.  A step that is not finite or moves the root by more than 1e-3 is dropped.
+__device__ __noinline__ int small_eig_rr(const DF* G, int k, DF shift, float* y, DF* theta) {
+  float Gf[KM * KM];
+  for (int i = 0; i < KM * KM; ++i) Gf[i] = df_f(G[i]);
+  float th = df_f(*theta);
+  const int cx = small_eig(Gf, k, df_f(shift), y, &th);
+  float delta = 0.f;
+  const DF lam{th, 0.f};
+  if (k == 2) {  // det(lam - G) = (lam - g00)(lam - g11) - g01 g10
+    const DF a = df_add(lam, df_neg(G[0])), b = df_add(lam, df_neg(G[KM + 1]));
+    const DF f = df_add(df_mul(a, b), df_neg(df_mul(G[1], G[KM])));
+    const float fp = 2.f * th - Gf[0] - Gf[KM + 1];
+    delta = -df_f(f) / fp;
+  } else if (k == 3) {  // det(lam - G) by the rule of Sarrus on the double-float entries of lam - G
+    DF m[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) m[i * 3 + j] = (i == j) ? df_add(lam, df_neg(G[i * KM + j])) : df_neg(G[i * KM + j]);
+    auto t3 = [&](int a, int b, int c) { return df_mul(df_mul(m[a], m[b]), m[c]); };
+    DF f = df_add(df_add(t3(0, 4, 8), t3(1, 5, 6)), t3(2, 3, 7));
+    f = df_add(f, df_neg(df_add(df_add(t3(2, 4, 6), t3(0, 5, 7)), t3(1, 3, 8))));
+    // d/dlam det(lam - G) = sum of the principal 2 x 2 minors of (lam - G), in FP32
+    const float* g = Gf;
+    const float d00 = th - g[0], d11 = th - g[KM + 1], d22 = th - g[2 * KM + 2];
+    const float fp = (d11 * d22 - g[KM + 2] * g[2 * KM + 1]) + (d00 * d22 - g[2] * g[2 * KM]) +
+                     (d00 * d11 - g[1] * g[KM]);
+    delta = -df_f(f) / fp;
+  }
+  if (isfinite(delta) && fabsf(delta) <= 1e-3f * (1.f + fabsf(th)))
+    *theta = two_sum(th, delta);
+  else
+    *theta = DF{th, 0.f};
+  return cx;
 }
 
 // ---- one space -----------------------------------------------------------------------------------
 
 // Solve space s of the class list in `a` (s: index in that list) with the warp's state `ws`.
 template <int K>
-__device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ pair3, WarpState<K>& ws,
+__device__ void solve_one(const Tabs<K>& tb, const CtaSmem& cs, WarpState<K>& ws,
                           const SolveArgs& a, const float* __restrict__ W32, const float* __restrict__ guess_in,
                           float* __restrict__ guess_out, int64_t s, int lane) {
   using D = Dim<K>;
   constexpr int NS = D::NS, NSG = D::NSG, NDET = D::NDET, NORB = D::NORB, NF = D::NF;
+  const unsigned short* __restrict__ pair3 = cs.pair3;
   const int n = a.n;
   const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
   const float tol = (float)a.tol;
@@ -962,10 +1123,11 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   if (lane == 0) {
     ws.eshift = *a.e0;  // <Phi|H|Phi>: the fold moves the inactive part into E_core exactly
     ws.ctrl[0] = 1;
+    ws.ctrl[1] = 0;  // from here on: consecutive steps whose projected root was complex
     ws.ctrl[2] = kSpaceNoConv;
     ws.ctrl[3] = 0;
-    ws.theta = 0.f;
-    ws.G[0] = 0.f;
+    ws.theta = DF{0.f, 0.f};
+    ws.G[0] = DF{0.f, 0.f};
     ws.yf[0] = 1.f;
   }
   __syncwarp();
@@ -989,7 +1151,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       float acc = 0.f, rr = 0.f;
 #pragma unroll
       for (int k = 0; k < kPhiLen; ++k) {
-        const unsigned e = __ldg(&g_phi_table.e[k * 32 + lane]);
+        const unsigned e = phi_entry(cs, k * 32 + lane);
         acc = fmaf(__uint_as_float(e & 0xff800000u), ws.Wt[e & 2047u], acc);
         if (e & (1u << 20)) {
           const int d = (int)((e >> 11) & 511u);
@@ -1071,7 +1233,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       if constexpr (K == 3) {  // nonzero only where the column is (the diagonal is symmetric too)
 #pragma unroll
         for (int k = 0; k < kPhiLen; ++k) {
-          const unsigned e = __ldg(&g_phi_table.e[k * 32 + lane]);
+          const unsigned e = phi_entry(cs, k * 32 + lane);
           if (e & (1u << 20)) {
             const int d = (int)((e >> 11) & 511u);
             float den = -diag_at<K>(tb, ws, d / NS, d % NS);
@@ -1118,7 +1280,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     float acc = 0.f;
 #pragma unroll 11
     for (int k = 0; k < kHsLen; ++k) {
-      const unsigned e = __ldg(&g_hs_table.e[k * 32 + lane]);
+      const unsigned e = hs_entry(cs, k * 32 + lane);
       acc = fmaf(__uint_as_float(e & 0xff800000u), ws.Wt[e & 2047u], acc);
       if (e & (1u << 20)) {
         ws.Hs[(e >> 11) & 511u] = acc;
@@ -1163,23 +1325,22 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       __syncwarp();
       float* s1 = ws.S + NDET;
       sigma<K>(tb, ws, v1, s1, lane);
-      float g01 = 0.f, g10 = 0.f, g11 = 0.f;
+      RRAcc a10, a11;
       for (int d = lane; d < NDET; d += 32) {
-        g10 = fmaf(v1[d], ws.S[d], g10);
-        g11 = fmaf(v1[d], s1[d], g11);
+        a10.add(v1[d], ws.S[d]);
+        a11.add(v1[d], s1[d]);
       }
-      g10 = wsum(g10);
-      g11 = wsum(g11);
-      g01 = s1[0];  // Phi . sigma(v1)
+      const DF g10 = a10.total(), g11 = a11.total();
+      const DF g01{s1[0], 0.f};  // Phi . sigma(v1)
       if (lane == 0) {
-        ws.G[0] = 0.f;  // Phi . sigma(Phi) relative to <Phi|H|Phi>
+        ws.G[0] = DF{0.f, 0.f};  // Phi . sigma(Phi) relative to <Phi|H|Phi>
         ws.G[1] = g01;
         ws.G[KM] = g10;
         ws.G[KM + 1] = g11;
         float yn[KM];
         for (int j = 0; j < KM; ++j) yn[j] = (j == 0) ? 1.f : 0.f;
-        float thn = 0.f;
-        small_eig(ws.G, 2, -1e-2f, yn, &thn);
+        DF thn{0.f, 0.f};
+        ws.ctrl[1] = small_eig_rr(ws.G, 2, DF{-1e-2f, 0.f}, yn, &thn);
         for (int j = 0; j < KM; ++j) ws.yf[j] = yn[j];
         ws.theta = thn;
         ws.ctrl[0] = 2;
@@ -1197,7 +1358,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     int k = ws.ctrl[0];
     if (k == KMX) {  // restart on {Phi, Ritz vector}: x = y_0 Phi + x', x' = sum_{j>=1} y_j V_j is
                      // already orthogonal to Phi, and sigma(x') = sum_{j>=1} y_j S_j
-      float pv = 0.f, p0 = 0.f, p1 = 0.f;
+      RRAcc apv, ap0, ap1;
       for (int d = lane; d < NDET; d += 32) {
         float xv = 0.f, sv = 0.f;
         for (int j = 1; j < k; ++j) {
@@ -1206,30 +1367,28 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
         }
         ws.V[d] = xv;
         ws.S[NDET + d] = sv;
-        pv = fmaf(xv, xv, pv);
-        p0 = fmaf(xv, ws.S[d], p0);
-        p1 = fmaf(xv, sv, p1);
+        apv.add(xv, xv);
+        ap0.add(xv, ws.S[d]);
+        ap1.add(xv, sv);
       }
-      pv = wsum(pv);
-      p0 = wsum(p0);
-      p1 = wsum(p1);
-      const float nx = sqrtf(pv), inv = 1.f / nx;
+      const DF pv = apv.total(), p0 = ap0.total(), p1 = ap1.total();
+      const float nx = sqrtf(df_f(pv)), inv = 1.f / nx;
       for (int d = lane; d < NDET; d += 32) {
         ws.V[d] *= inv;
         ws.S[NDET + d] *= inv;
       }
       __syncwarp();
       if (lane == 0) {  // projected matrix of {Phi, V_1}; G[0] (Phi . S_0 = 0) is unchanged
-        ws.G[1] = ws.S[NDET];
-        ws.G[KM] = p0 * inv;
-        ws.G[KM + 1] = p1 * inv * inv;
+        ws.G[1] = DF{ws.S[NDET], 0.f};
+        ws.G[KM] = df_mulf(p0, inv);
+        ws.G[KM + 1] = df_mulf(df_mulf(p1, inv), inv);
         ws.yf[1] = nx;
         ws.ctrl[0] = 2;
       }
       __syncwarp();
       k = 2;
     }
-    const float th = ws.theta;
+    const float th = df_f(ws.theta);
     float* vk = ws.V + (k - 1) * NDET;
     float vn = vn_phi;  // first step from Phi: V1 already holds the preconditioned residual
     if (!(it == 0 && !guess_in)) {
@@ -1282,18 +1441,16 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
           __syncwarp();
         }
         for (int pass = 0; pass < 2; ++pass) {  // against Phi: drop component 0
+          RRAcc acf[KM];
           float cf[KM];
-#pragma unroll
-          for (int j = 0; j < KM; ++j) cf[j] = 0.f;
           for (int d = lane; d < NDET; d += 32) {
             const float v = vk[d];
 #pragma unroll
             for (int j = 1; j < KM; ++j)
-              if (j < k) cf[j] = fmaf(ws.V[(j - 1) * NDET + d], v, cf[j]);
+              if (j < k) acf[j].add(ws.V[(j - 1) * NDET + d], v);
           }
 #pragma unroll
-          for (int j = 1; j < KM; ++j)
-            if (j < k) cf[j] = wsum(cf[j]);
+          for (int j = 0; j < KM; ++j) cf[j] = (j >= 1 && j < k) ? df_f(acf[j].total()) : 0.f;
           for (int d = lane; d < NDET; d += 32) {
             float v = vk[d];
 #pragma unroll
@@ -1322,30 +1479,27 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     __syncwarp();
     float* sk = ws.S + k * NDET;
     sigma<K>(tb, ws, vk, sk, lane);
-    float gc[KM], gr[KM];
-#pragma unroll
-    for (int j = 0; j < KM; ++j) gc[j] = gr[j] = 0.f;
-    float gkk = 0.f;
+    RRAcc agc[KM], agr[KM], akk;
     for (int d = lane; d < NDET; d += 32) {
       const float vkd = vk[d], skd = sk[d];
-      gkk = fmaf(vkd, skd, gkk);
-      gr[0] = fmaf(vkd, ws.S[d], gr[0]);
+      akk.add(vkd, skd);
+      agr[0].add(vkd, ws.S[d]);
 #pragma unroll
       for (int j = 1; j < KM; ++j)
         if (j < k) {
-          gc[j] = fmaf(ws.V[(j - 1) * NDET + d], skd, gc[j]);
-          gr[j] = fmaf(vkd, ws.S[j * NDET + d], gr[j]);
+          agc[j].add(ws.V[(j - 1) * NDET + d], skd);
+          agr[j].add(vkd, ws.S[j * NDET + d]);
         }
     }
-    gkk = wsum(gkk);
-    gr[0] = wsum(gr[0]);
-    gc[0] = sk[0];  // Phi . sigma(V_k)
+    DF gc[KM], gr[KM];
+    const DF gkk = akk.total();
+    gr[0] = agr[0].total();
+    gc[0] = DF{sk[0], 0.f};  // Phi . sigma(V_k)
 #pragma unroll
-    for (int j = 1; j < KM; ++j)
-      if (j < k) {
-        gc[j] = wsum(gc[j]);
-        gr[j] = wsum(gr[j]);
-      }
+    for (int j = 1; j < KM; ++j) {
+      gc[j] = (j < k) ? agc[j].total() : DF{0.f, 0.f};
+      gr[j] = (j < k) ? agr[j].total() : DF{0.f, 0.f};
+    }
     if (lane == 0) {
       for (int j = 0; j < k; ++j) {
         ws.G[j * KM + k] = gc[j];
@@ -1355,14 +1509,17 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
       const int kk = k + 1;
       float yn[KM];
       for (int j = 0; j < kk; ++j) yn[j] = (j < k) ? ws.yf[j] : 0.f;
-      float thn = ws.theta;
-      small_eig(ws.G, kk, ws.theta - 1e-2f, yn, &thn);
+      DF thn = ws.theta;
+      const int cx = small_eig_rr(ws.G, kk, df_add(ws.theta, DF{-1e-2f, 0.f}), yn, &thn);
       for (int j = 0; j < kk; ++j) ws.yf[j] = yn[j];
       ws.theta = thn;
       ws.ctrl[0] = kk;
       ws.ctrl[3] = it + 1 + it0;
+      ws.ctrl[1] = cx ? ws.ctrl[1] + 1 : 0;
+      if (ws.ctrl[1] >= 2) ws.ctrl[2] = kSpaceRoot;  // a complex root twice in a row: no real root
     }
     __syncwarp();
+    if (ws.ctrl[1] >= 2) break;
   }
   // ---- root, increment, merge ------------------------------------------------------------
   // owners and old amplitudes of the space's internal amplitudes are loaded first, so their
@@ -1404,8 +1561,9 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
   const float xn = sqrtf(xx);
   const float c0 = ws.S[0];
   int st = ws.ctrl[2];
+  if (st == kSpaceNoConv && ws.ctrl[1] > 0) st = kSpaceRoot;  // stopped on a complex projected root
   if (st == kSpaceOk && !(fabsf(c0) >= 1e-3f * xn)) st = kSpaceRoot;
-  if (!isfinite(c0) || !isfinite(ws.theta)) st = kSpaceNonFinite;
+  if (!isfinite(c0) || !isfinite(df_f(ws.theta))) st = kSpaceNonFinite;
   const float inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.f / c0 : 0.f;
   if (guess_out && st == kSpaceOk)
     for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = ws.S[d] * inv0;
@@ -1437,7 +1595,7 @@ __device__ void solve_one(const Tabs<K>& tb, const unsigned short* __restrict__ 
     }
   }
   if (lane == 0) {
-    a.energy[oidx] = ws.eshift + (double)ws.theta;
+    a.energy[oidx] = ws.eshift + ((double)ws.theta.hi + (double)ws.theta.lo);
     a.status[oidx] = st;
     if (a.iters) a.iters[oidx] = ws.ctrl[3];
   }
@@ -1457,7 +1615,7 @@ __global__ void __launch_bounds__(32 * WARPS) solve_class_kernel(SolveArgs a, co
   WarpState<K>& ws = state<K>(cs.w[warp]);
 #pragma unroll 1
   for (int64_t s = (int64_t)blockIdx.x * WARPS + warp; s < a.nspaces; s += (int64_t)gridDim.x * WARPS)
-    solve_one<K>(tabs<K>(cs), cs.pair3, ws, a, W32, guess_in, guess_out, a.items ? a.items[s] : s, lane);
+    solve_one<K>(tabs<K>(cs), cs, ws, a, W32, guess_in, guess_out, a.items ? a.items[s] : s, lane);
 }
 
 struct PersistentArgs {
@@ -1489,17 +1647,17 @@ __global__ void __maxnreg__(128) solve_persistent_kernel(PersistentArgs p) {
       const int64_t it = (int64_t)item;
       if (it < n3) {
         const SolveArgs& a = p.cls[3];
-        solve_one<3>(cs.t3, cs.pair3, state<3>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+        solve_one<3>(cs.t3, cs, state<3>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
                      static_cast<float*>(a.root_out), a.items ? a.items[it] : it, lane);
       } else if (it < n3 + n2) {
         const SolveArgs& a = p.cls[2];
         const int64_t l = it - n3;
-        solve_one<2>(cs.t2, cs.pair3, state<2>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+        solve_one<2>(cs.t2, cs, state<2>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
                      static_cast<float*>(a.root_out), a.items ? a.items[l] : l, lane);
       } else {
         const SolveArgs& a = p.cls[1];
         const int64_t l = it - n3 - n2;
-        solve_one<1>(cs.t1, cs.pair3, state<1>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+        solve_one<1>(cs.t1, cs, state<1>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
                      static_cast<float*>(a.root_out), a.items ? a.items[l] : l, lane);
       }
     }
