@@ -4,8 +4,8 @@ pool, every active space gathered + folded + solved by the batched Davidson kern
 increments merged by owner, mean energy and convergence reductions).
 
 Default workload: the 82-orbital synthetic system (10 occupied, 72 virtual, xi = 5) with all
-C(10,3) C(72,3) = 7,156,800 (3,3) active spaces per sweep, mixed precision (FP32 sigma-vectors,
-FP64 dressing / projected eigenproblem / energy / amplitude update).  Warm-up sweeps move the
+C(10,3) C(72,3) = 7,156,800 (3,3) active spaces per sweep, in the mixed form (the precision of
+each step is listed in the output line under config.precision_steps).  Warm-up sweeps move the
 pool from empty to a mid-flow state before the timed sweeps; the plain FP64 GPU form of the
 same sweep is timed beside it, and the FP64 oracle is timed on the host cores on a bounded
 sample (cpu_baseline).  The inputs (W: 362 MB) are larger than the 126 MB L2.
@@ -38,8 +38,21 @@ from paper_2606_04186_gb300 import synth  # noqa: E402
 
 METRIC = "QFlow sweep time (s) + active spaces/s vs plain FP64 GPU form at |ΔE|≤1e-6 Eh"
 UNIT = "active spaces/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
-FP64_PEAK_TFLOPS = 1.25                              # GB300 FP64 (nominal)
+# precision of each step of a sweep, per form (what the library computes in; see include/qflow.h)
+PRECISION_STEPS = {
+    "mixed": {
+        "dressing_integrals_e0_fock": "f64 (T1 correction sums f32, added to f64)",
+        "dressing_t2_contractions": "tcgen05 three-term tf32 products, f32 accumulation, added to f64 bases",
+        "gather_fold_setup": "f32 (operator diagonal relative to <Phi|H|Phi>)",
+        "sigma_vectors_davidson_vectors": "f32",
+        "rayleigh_ritz_matrix_and_gram_schmidt_coefficients": "f64 (exact f32 products, compensated sums, "
+                                                             "rounded to f64)",
+        "projected_eigenproblem_ritz_value": "f64 (root chosen in f32 closed form, refined by f64 Newton steps)",
+        "energy_amplitude_update_diis_reductions": "f64",
+        "hard_spaces": "spaces the f32 warp pass leaves unconverged are re-solved in f64",
+    },
+    "fp64": {"every_step": "f64"},
+}
 
 
 def parse():
@@ -61,6 +74,9 @@ def parse():
                     help="wave-ordered sweeps: the pool is updated after every K spaces (0 = Jacobi)")
     ap.add_argument("--sharded", action="store_true",
                     help="sharded sweep path (begin / exchange / end) also at N = 1")
+    ap.add_argument("--launch-loop", action="store_true",
+                    help="also time the solve as one launch per space (a per-space launch loop) against one "
+                         "launch for every space, on the dressing of the timed pool (3,3 spaces only)")
     ap.add_argument("--spaces-limit", type=int, default=0,
                     help="keep an evenly strided subset of at most this many spaces (small profiling case)")
     return ap.parse_args()
@@ -254,11 +270,12 @@ def run_reference(args):
     sample = max(64, args.cpu_sample // 3)
     for _ in range(args.warmup):
         oracle_sweep_sample(args.workload, sample, pool)
-    vals, secs = [], []
+    vals, secs, timed = [], [], []
     for k in range(args.steps):
         r = oracle_sweep_sample(args.workload, sample, pool, seed=11 + k)
         vals.append(r["value"])
         secs.append(r["sweep_s_extrapolated"])
+        timed.append(r["dress_s"] + r["solve_s_sample"])
     pool.close()
     value = statistics.median(vals)
     line = {
@@ -269,13 +286,62 @@ def run_reference(args):
                    "note": "each step: full oracle dressing + a seeded sample of spaces solved on all host cores; "
                            "sweep time extrapolated linearly in the number of spaces"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{r['sample']} spaces per step of {r['nspaces']} + full dressing, extrapolated"},
+                         "sample": f"{r['sample']} spaces per step of {r['nspaces']} + full dressing, extrapolated",
+                         "timed_s_per_step": statistics.median(timed), "dress_s": r["dress_s"],
+                         "solve_s_sample": r["solve_s_sample"], "extrapolated_sweep_s": statistics.median(secs)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ---- GPU leg ---------------------------------------------------------------------------------------
+
+def launch_loop_leg(qflow, fl, h, g, no, sp, precision):
+    """The solve step of the timed pool's dressing (steps b + c for every (3,3) space) as one
+    qflow_solve_device launch per space, against one launch for all spaces; CUDA events around
+    each on the default stream.  Both use the warp pass alone (iteration cap 16)."""
+    import torch
+    e0, F, W = fl.dressed()
+    t1, t2 = fl.amplitudes()
+    perm = fl.order()
+    sps = np.ascontiguousarray(sp[perm])
+    keep = np.flatnonzero(sps[:, 0] == 3)
+    _, o1, o2, _ = qflow.plan(h, g, no, sp)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    e0d, Fd, Wd = d(np.array([e0])), d(F), d(W)
+    spd, o1d, o2d = d(sps[keep]), d(o1.astype(np.int32)), d(o2.astype(np.int32))
+    t1o, t2o = d(t1), d(t2)
+    n, ns = h.shape[0], len(keep)
+    energy = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    status = torch.zeros(ns, dtype=torch.int32, device="cuda")
+
+    def run(per_space: bool) -> float:
+        t1n, t2n = t1o.clone(), t2o.clone()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        if per_space:
+            for i in range(ns):
+                qflow.solve_device(n, no, e0d, Fd, Wd, 3, spd[i:i + 1], energy[i:i + 1], status[i:i + 1],
+                                   owner1=o1d, owner2=o2d, t1_old=t1o, t2_old=t2o, t1_new=t1n, t2_new=t2n,
+                                   space_base=int(keep[i]), precision=precision, max_iter=16)
+        else:
+            qflow.solve_device(n, no, e0d, Fd, Wd, 3, spd, energy, status, owner1=o1d, owner2=o2d, t1_old=t1o,
+                               t2_old=t2o, t1_new=t1n, t2_new=t2n, space_base=int(keep[0]), precision=precision,
+                               max_iter=16)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    if not (np.diff(keep) == 1).all():
+        return None  # the one-launch form needs the (3,3) spaces contiguous in the sorted list
+    run(False)
+    one = min(run(False) for _ in range(3))
+    loop = run(True)
+    log(f"launch loop: {ns} launches {loop:.1f} ms, one launch {one:.2f} ms")
+    return {"spaces": ns, "per_space_launches_ms": loop, "one_launch_ms": one, "ratio": loop / one,
+            "note": "qflow_solve_device per space (host launch loop) vs once over all spaces, same dressing"}
+
 
 def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -344,6 +410,12 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the solver's roofline denominators, measured on this GPU (FMA chains on every SM)
+    peaks = {"fp32_tflops": qflow.fma_peak("mixed"), "fp64_tflops": qflow.fma_peak("fp64"),
+             "method": "qflow_fma_peak: 8 independent fma chains per thread, every SM full, "
+                       "best of 3 CUDA-event-timed launches"}
+    log(f"measured FMA peaks: {peaks['fp32_tflops']:.1f} FP32, {peaks['fp64_tflops']:.3f} FP64 TFLOP/s")
+
     phases, launches, codes = [], 0, []
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -379,7 +451,7 @@ def run_ours(args):
     else:
         flops = solver_flops(it.astype(np.int64))
     achieved = flops / (solve_ms / 1e3) / 1e12
-    peak = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
+    peak = peaks["fp32_tflops"] if args.precision == "mixed" else peaks["fp64_tflops"]
 
     # end-to-end through the public API with host buffers: pool H2D (pinned), sweep,
     # per-space energies + pool D2H, every step
@@ -403,6 +475,11 @@ def run_ours(args):
     log(f"e2e {e2e_s:.3f} s per step")
     pool_bytes = 8 * (t1h.numel() + t2h.numel())
     fl_xsize = fl.exchange_size()
+    # the dressing of the pool p2 (the last e2e step dressed it), kept to state the mixed form's
+    # error per block against the plain FP64 form's dressing of the same pool
+    dressed_mixed = fl.dressed() if (args.precision == "mixed" and args.fp64_steps > 0 and world == 1
+                                     and s.n <= 82 and not args.waves) else None
+    loop = launch_loop_leg(qflow, fl, h, g, no, sp, args.precision) if (args.launch_loop and world == 1) else None
     fl.close()
 
     # plain FP64 GPU form of the same sweep (pool after the same number of sweeps as the first
@@ -427,12 +504,26 @@ def run_ours(args):
             log(f"fp64 sweep: {ms[-1]:.1f} ms, phases {f64.last_sweep_info()[0]}")
         ms64 = statistics.median(ms)
         e64 = f64.energy()
+        dress_err = None
+        if dressed_mixed is not None:
+            e0d, Fd, Wd = f64.dressed()
+            e0m, Fm, Wm = dressed_mixed
+            o_, v_ = slice(0, no), slice(no, s.n)
+            sl = {"o": o_, "v": v_}
+            dress_err = {"e0": abs(e0m - e0d), "F": float(np.abs(Fm - Fd).max())}
+            for blk in ("oooo", "ooov", "oovv", "ovov", "ovvo", "vovo", "vvoo", "vovv", "vvvo", "vvvv", "vooo",
+                        "ovoo", "voov", "ovvv", "vvov", "oovo"):
+                idx = tuple(sl[c] for c in blk)
+                dress_err["W_" + blk] = float(np.abs(Wm[idx] - Wd[idx]).max())
+            del Wm, Wd
+            log(f"mixed - fp64 dressing, max |error| per block: {dress_err}")
         ph64, _ = f64.last_sweep_info()
         it64, _ = f64.stats()
         fp64 = {"sweep_s": ms64 / 1e3, "spaces_per_s": len(sp) / (ms64 / 1e3), "solve_ms": float(ph64[1]),
                 "dress_ms": float(ph64[0]), "davidson_iters_mean": float(it64.mean()),
                 "solve_tflops": solver_flops(it64.astype(np.int64)) / (ph64[1] / 1e3) / 1e12,
-                "e_sweep3": e64, "mixed_minus_fp64_e_sweep3": e3 - e64}
+                "e_sweep3": e64, "mixed_minus_fp64_e_sweep3": e3 - e64,
+                "mixed_minus_fp64_dressing_max_abs": dress_err}
         f64.close()
 
     if rank != 0:
@@ -446,8 +537,10 @@ def run_ours(args):
         log(f"oracle: {r}")
         pool.close()
         cpu = {"value": r["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"full dressing + {r['sample']} of {r['nspaces']} spaces on a spawn pool, sweep time "
-                         f"extrapolated ({r['sweep_s_extrapolated']:.1f} s)"}
+               "sample": (f"full dressing + {r['sample']} of {r['nspaces']} spaces on a spawn pool, sweep time "
+                          f"extrapolated ({r['sweep_s_extrapolated']:.1f} s)") if r["sample"] < r["nspaces"]
+               else f"full sweep: dressing + all {r['nspaces']} spaces on a spawn pool",
+               "timed_s": r["dress_s"] + r["solve_s_sample"], "sweep_s": r["sweep_s_extrapolated"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": sweep_ms, "higher_is_better": True,
@@ -465,6 +558,7 @@ def run_ours(args):
                    "parallelism": (f"sharded over {world} GPUs: per-class blocks, one allreduce of "
                                    f"{8 * fl_xsize / 1e6:.0f} MB per sweep") if sharded else "one GPU",
                    "step": "third sweep of the flow (pool after two sweeps restored before each step)",
+                   "precision_steps": PRECISION_STEPS[args.precision],
                    "init_s": t_init},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
@@ -474,8 +568,9 @@ def run_ours(args):
                      "kernel": ("solve_persistent_kernel" if sched["persistent"] else "solve_class_kernel<K>")
                      if args.precision == "mixed" else "solve_kernel<K,double>",
                      "flops_per_launch": flops, "launch_ms": solve_ms,
-                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "mixed"
-                     else "GB300 FP64 nominal"},
+                     "peak_note": ("measured FP32 FMA peak of this GPU" if args.precision == "mixed"
+                                   else "measured FP64 FMA peak of this GPU") + " (" + peaks["method"] + ")",
+                     "peaks_measured": {k: v for k, v in peaks.items() if k != "method"}},
         "schedule": sched,
         "dress_tensor": ({"gemm_flops": dress_gemm_flops(no, nv), "phase_ms": float(ph[:, 0].mean()),
                           "tflops_over_phase": dress_gemm_flops(no, nv) / (float(ph[:, 0].mean()) / 1e3) / 1e12,
@@ -487,6 +582,7 @@ def run_ours(args):
         "failed_spaces": int((st != 0).sum()),
         "sweep_codes": sorted(set(int(c) for c in codes)),
         "fp64_form": fp64,
+        "launch_loop": loop,
         "speedup_vs_fp64": (fp64["sweep_s"] / (sweep_ms / 1e3)) if fp64 else None,
         "cpu_baseline": cpu,
         "e2e": {"value": len(sp) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": pool_bytes,

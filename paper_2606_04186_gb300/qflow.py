@@ -67,6 +67,7 @@ def lib() -> C.CDLL:
         "qflow_dress_workspace": (C.c_size_t, [I32, I32]),
         "qflow_dress_device_static": (I32, [P, P, P, P, I32, I32, P, P, P, P]),
         "qflow_static_scratch_bytes": (C.c_size_t, []),
+        "qflow_fma_peak": (I32, [I32, P, P]),
         "qflow_dress_device": (I32, [P, P, P, P, I32, I32, P, P, P, P, C.c_size_t, P]),
         "qflow_solve_device": (I32, [I32, I32, P, P, P, I32, P, I64, I64, P, P, P, P, P, P, P, P, P, P, I32, I32,
                                      I32, D, P]),
@@ -366,6 +367,13 @@ def dress_device_static(h, eri, t1, t2, nocc: int, e0, F, W, stream: int = 0):
 
 def static_scratch_bytes() -> int:
     return int(lib().qflow_static_scratch_bytes())
+
+
+def fma_peak(precision: str, stream: int = 0) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (precision "fp64" or "mixed" = FP32)."""
+    out = C.c_double(0.0)
+    _check(lib().qflow_fma_peak(PREC[precision], C.byref(out), stream or None), "qflow_fma_peak")
+    return float(out.value)
 
 
 def dress_workspace(n: int, nocc: int) -> int:
