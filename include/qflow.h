@@ -73,6 +73,22 @@ typedef struct {
   int32_t orb[6];
 } qflow_space;
 
+/* Downfolding form of a space's effective Hamiltonian (Eqs. 1-8 with N = 1).
+ *   QFLOW_FORM_SESCC: sigma read as the cluster operator T (SES-CC); H-bar = e^{-T} H e^{T}
+ *     truncated to <= two-body, one dressing for every space, increments X added to the pool.
+ *   QFLOW_FORM_DUCC: the paper's anti-Hermitian sigma = T - T^+ (DUCC); a space's operator is
+ *     [H + [H, s] + 1/2 [[F, s], s]]_(<=2), s = sigma_ext = the pool's amplitudes with an index
+ *     outside the space, F the Fock operator (all terms through second order; each commutator
+ *     normal ordered with respect to Phi and kept to <= two-body: the paper leaves the truncation
+ *     open).  Computed as a part common to every space (eight FP64 dressings per sweep) minus the
+ *     space's internal part (per space, in the solver).  The operator is Hermitian; the root's
+ *     cluster amplitudes (C1, C2 - C1^2 / 2) replace the owned amplitudes.  Requires
+ *     QFLOW_PREC_FP64; no network guesses; no wave-ordered sweeps (QFLOW_ERR_STATE). */
+typedef enum {
+  QFLOW_FORM_SESCC = 0,
+  QFLOW_FORM_DUCC = 1
+} qflow_form;
+
 typedef enum {
   QFLOW_SCHED_AUTO = 0,       /* mixed precision: the first sweep runs the persistent queue;
                                  at the second sweep the autotuner times its items-per-fetch
@@ -106,7 +122,8 @@ typedef struct {
   int32_t graph;              /* 1 = once the schedule is fixed (mixed: from the third sweep,
                                  FP64: from the second), capture the sweep's device work in a
                                  CUDA graph and replay it (default 1)                        */
-  int32_t reserved[6];
+  int32_t form;               /* qflow_form: the downfolding form (default QFLOW_FORM_SESCC)  */
+  int32_t reserved[5];
 } qflow_options;
 
 /* Fill *opt with the defaults above for the given precision. */

@@ -44,6 +44,9 @@ struct SolveArgs {
   const float* W32;  // nullable FP32 copy of W (mixed path)
   const float* F32;  // nullable FP32 copy of F (mixed path; else F is converted per element)
   const unsigned long long* count_dev;  // nullable: the launch covers items [0, *count_dev) instead
+  const double* ducc_eri;  // non-null: DUCC form (FP64 solver): bare integrals (pq|rs), n^4
+  const double* ducc_F0;   // and the bare Fock matrix, n^2; the solver subtracts the space's
+                           // internal part from the gathered G block and replaces owned amplitudes
   const void* guess;  // nullable start vectors: double (FP64 path) or float (mixed path)
   void* root_out;     // nullable: receives converged roots (Phi coefficient 1), same type/layout
   int32_t max_iter;
@@ -84,6 +87,14 @@ int dress_launch_count(int n, int nocc, bool mixed);  // kernels one launch_dres
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
                          double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st,
                          float* g32 = nullptr);
+
+// Step (a) in the Hermitian (DUCC) form (ducc.cu): e0, F, W of the part G common to every space,
+// and F0 = the bare Fock matrix (the per-space part needs it).  FP64.
+size_t ducc_workspace_bytes(int n, int nocc);
+int ducc_launch_count(int n, int nocc);
+cudaError_t launch_dress_ducc(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
+                              double* e0, double* F, double* W, double* F0, void* work, size_t work_bytes,
+                              cudaStream_t st);
 
 // Sweep reductions (step c): out4 = [mean E, max |t_new - t_old|, failed spaces, worst status].
 size_t mean_maxdiff_workspace(int64_t nspaces, int64_t nt);
@@ -131,6 +142,11 @@ cudaError_t mlp_pool_targets(const double* pool, const qflow_space* spaces, int6
 cudaError_t mlp_pool_from_pred(const float* pred, const float* mu, const float* sd, const qflow_space* spaces,
                                const int64_t* sorted_index, int64_t rows, int nocc, int nvir, const int32_t* owner1,
                                const int32_t* owner2, double* pool, cudaStream_t st);
+// The spaces of one class list (rows records with their sorted indices) that own an amplitude,
+// gathered into out_sp / out_idx with their count (device); flag: nspaces bytes of scratch.
+cudaError_t mlp_owner_spaces(const int32_t* owner1, int64_t n1, const int32_t* owner2, int64_t n2, int64_t nspaces,
+                             const qflow_space* spaces, const int64_t* sorted_index, int64_t rows, uint8_t* flag,
+                             qflow_space* out_sp, int64_t* out_idx, unsigned long long* count, cudaStream_t st);
 // out[i] = 1 / sd[i] (0 where sd[i] <= 0)
 cudaError_t mlp_invert(const float* sd, int n, float* out, cudaStream_t st);
 // start vectors guess[r][400] (double when fp64, else float) from outputs pred[r][54];

@@ -257,11 +257,328 @@ __device__ int small_eig(const double* G, int k, double shift, double* y, double
   return (sqrt(res) > 1e-8 * fmax(1.0, scale)) ? 1 : 0;
 }
 
-template <int K, typename T>
+// Symmetric projected problem (DUCC form, Hermitian operator; one thread): G is symmetrised and
+// diagonalised by cyclic Jacobi rotations; of its eigenpairs the one whose Ritz vector has the
+// largest Phi component (sum_j y_j V_j[Phi]) is taken, as the space's root is the eigenvector
+// with the largest |c_Phi|.  y receives the unit eigenvector, theta its eigenvalue.
+template <int KM>
+__device__ void small_eig_sym(const double* G, int k, const double* v0, double* y, double* theta) {
+  double a[KM * KM], z[KM * KM];
+  double scale = 0.0;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      a[i * KM + j] = 0.5 * (G[i * KM + j] + G[j * KM + i]);
+      z[i * KM + j] = (i == j) ? 1.0 : 0.0;
+      scale = fmax(scale, fabs(a[i * KM + j]));
+    }
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) off = fmax(off, fabs(a[p * KM + q]));
+    if (!(off > 1e-15 * fmax(scale, 1e-300))) break;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = a[p * KM + q];
+        if (apq == 0.0) continue;
+        const double tau = (a[q * KM + q] - a[p * KM + p]) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int r = 0; r < k; ++r) {  // columns p, q
+          const double arp = a[r * KM + p], arq = a[r * KM + q];
+          a[r * KM + p] = c * arp - s * arq;
+          a[r * KM + q] = s * arp + c * arq;
+        }
+        for (int r = 0; r < k; ++r) {  // rows p, q
+          const double apr = a[p * KM + r], aqr = a[q * KM + r];
+          a[p * KM + r] = c * apr - s * aqr;
+          a[q * KM + r] = s * apr + c * aqr;
+        }
+        for (int r = 0; r < k; ++r) {
+          const double zrp = z[r * KM + p], zrq = z[r * KM + q];
+          z[r * KM + p] = c * zrp - s * zrq;
+          z[r * KM + q] = s * zrp + c * zrq;
+        }
+      }
+  }
+  int best = 0;
+  double wbest = -1.0;
+  for (int m = 0; m < k; ++m) {
+    double c0 = 0.0;
+    for (int j = 0; j < k; ++j) c0 += z[j * KM + m] * v0[j];
+    if (fabs(c0) > wbest) {
+      wbest = fabs(c0);
+      best = m;
+    }
+  }
+  double c0 = 0.0;
+  for (int j = 0; j < k; ++j) c0 += z[j * KM + best] * v0[j];
+  const double sg = (c0 < 0.0) ? -1.0 : 1.0;
+  for (int j = 0; j < k; ++j) y[j] = sg * z[j * KM + best];
+  *theta = a[best * KM + best];
+}
+
+// ---- DUCC form: the space's internal part L_A ------------------------------------------------------
+//
+// In the DUCC form (ducc.cu) a space's operator is G|_A - L_A, where
+//   L_A = X_A + X_A^+ + 1/2 (Y_A + Y_A^+),  X_A = [H_A, T_A]_(<=2),  Y_A = [B_A, T_A]_(<=2),
+// H_A the Hamiltonian and B_A = D.T_A + (D.T_A)^+ restricted to the space's 2K orbitals, T_A the
+// space's internal amplitudes.  [O, T]_(<=2) is the T-linear part of the SES-CC dressing
+// e^{-T} O e^{T} (its one- and two-body parts normal ordered with respect to Phi): the
+// linearisation of the T1 orbital transformation (creators by -K, annihilators by +K, K_ai = t_i^a)
+// plus the connected T2-linear terms, each below.  Local orbitals: 0..K-1 occupied, K..2K-1 virtual.
+template <int K>
+struct DuccSmem {
+  static constexpr int NO = 2 * K, NW = NO * NO * NO * NO, NF = NO * NO;
+  double g[NW];    // two-body elements of the operator (first H_A, then B_A)
+  double Wx[NW];   // [O, T]: two-body part
+  double f0[NF];   // bare Fock block of the space
+  double h[NF];    // operator's one-body part, vacuum order
+  double f[NF];    // operator's one-body part, normal order
+  double Fx[NF];   // [O, T]: one-body part
+  double t1[K * K];
+  double t2[K * K * K * K];
+  double ex;       // [O, T]: zero-body part
+};
+
+template <int K>
+struct LinDress {
+  static constexpr int NO = 2 * K;
+  const DuccSmem<K>& d;
+  __device__ double g(int p, int q, int r, int s) const { return d.g[((p * NO + q) * NO + r) * NO + s]; }
+  __device__ double t(int i, int j, int a, int b) const { return d.t2[((i * K + j) * K + a) * K + b]; }
+  __device__ double u(int i, int j, int a, int b) const { return 2.0 * t(i, j, a, b) - t(i, j, b, a); }
+  __device__ double t1(int i, int a) const { return d.t1[i * K + a]; }
+  __device__ double f(int p, int q) const { return d.f[p * NO + q]; }
+  __device__ double h(int p, int q) const { return d.h[p * NO + q]; }
+  // T1 linearisation: creators (p, r) by -K, annihilators (q, s) by +K
+  __device__ double dg(int p, int q, int r, int s) const {
+    double v = 0.0;
+    for (int x = 0; x < K; ++x) {
+      if (p >= K) v -= t1(x, p - K) * g(x, q, r, s);
+      if (q < K) v += g(p, K + x, r, s) * t1(q, x);
+      if (r >= K) v -= t1(x, r - K) * g(p, q, x, s);
+      if (s < K) v += g(p, q, r, K + x) * t1(s, x);
+    }
+    return v;
+  }
+  __device__ double dh(int p, int q) const {
+    double v = 0.0;
+    for (int x = 0; x < K; ++x) {
+      if (q < K) v += h(p, K + x) * t1(q, x);
+      if (p >= K) v -= t1(x, p - K) * h(x, q);
+    }
+    return v;
+  }
+  // T2-linear two-body terms of element (p, q, r, s) (creators p, r; annihilators q, s)
+  __device__ double w2(int p, int q, int r, int s) const {
+    const int blk = ((p >= K) << 3) | ((q >= K) << 2) | ((r >= K) << 1) | (s >= K);
+    double v = 0.0;
+    switch (blk) {
+      case 0x0:  // oooo (k i l j): sum_ef g_kelf t_ijef
+        for (int e = 0; e < K; ++e)
+          for (int ff = 0; ff < K; ++ff) v += g(p, K + e, r, K + ff) * t(q, s, e, ff);
+        break;
+      case 0xF:  // vvvv (a e b f): sum_mn g_menf t_mnab
+        for (int m = 0; m < K; ++m)
+          for (int nn = 0; nn < K; ++nn) v += g(m, q, nn, s) * t(m, nn, p - K, r - K);
+        break;
+      case 0x6:  // ovvo (m e b j)
+      case 0x9: {  // voov (b j m e) = ovvo (m e b j)
+        const int m = (blk == 0x6) ? p : r, e = (blk == 0x6) ? q : s, b = (blk == 0x6) ? r : p, j = (blk == 0x6) ? s : q;
+        for (int nn = 0; nn < K; ++nn)
+          for (int ff = 0; ff < K; ++ff)
+            v += g(m, e, nn, K + ff) * u(j, nn, b - K, ff) - g(m, K + ff, nn, e) * t(j, nn, b - K, ff);
+        break;
+      }
+      case 0x3:  // oovv (i j a b)
+      case 0xC: {  // vvoo (a b i j) = oovv (i j a b)
+        const int i = (blk == 0x3) ? p : r, j = (blk == 0x3) ? q : s, a = (blk == 0x3) ? r : p, b = (blk == 0x3) ? s : q;
+        for (int ff = 0; ff < K; ++ff)
+          for (int nn = 0; nn < K; ++nn) v -= g(i, K + ff, nn, b) * t(j, nn, ff, a - K);
+        break;
+      }
+      case 0x2:  // oovo (m i b j)
+      case 0x8: {  // vooo (b j m i) = oovo (m i b j)
+        const int m = (blk == 0x2) ? p : r, i = (blk == 0x2) ? q : s, b = (blk == 0x2) ? r : p, j = (blk == 0x2) ? s : q;
+        for (int e = 0; e < K; ++e) {
+          v += f(m, K + e) * t(i, j, e, b - K);
+          for (int ff = 0; ff < K; ++ff) v += g(m, K + e, b, K + ff) * t(i, j, e, ff);
+          for (int nn = 0; nn < K; ++nn)
+            v += g(m, i, nn, K + e) * u(j, nn, b - K, e) - g(m, K + e, nn, i) * t(j, nn, b - K, e) -
+                 g(m, K + e, nn, j) * t(i, nn, e, b - K);
+        }
+        break;
+      }
+      case 0xE:  // vvvo (a e b i)
+      case 0xB: {  // vovv (b i a e) = vvvo (a e b i)
+        const int a = (blk == 0xE) ? p : r, e = (blk == 0xE) ? q : s, b = (blk == 0xE) ? r : p, i = (blk == 0xE) ? s : q;
+        for (int m = 0; m < K; ++m) {
+          v -= f(m, e) * t(m, i, a - K, b - K);
+          for (int nn = 0; nn < K; ++nn) v += g(m, e, nn, i) * t(m, nn, a - K, b - K);
+          for (int ff = 0; ff < K; ++ff)
+            v += g(m, K + ff, a, e) * u(m, i, ff, b - K) - g(m, e, b, K + ff) * t(m, i, a - K, ff) -
+                 g(m, e, a, K + ff) * t(m, i, ff, b - K);
+        }
+        break;
+      }
+      case 0xA: {  // vovo (a i b j): the doubles block
+        const int a = p - K, i = q, b = r - K, j = s;
+        for (int e = 0; e < K; ++e) v += f(K + b, K + e) * t(i, j, a, e) + f(K + a, K + e) * t(i, j, e, b);
+        for (int m = 0; m < K; ++m) v -= f(m, j) * t(i, m, a, b) + f(m, i) * t(m, j, a, b);
+        for (int m = 0; m < K; ++m)
+          for (int nn = 0; nn < K; ++nn) v += g(m, i, nn, j) * t(m, nn, a, b);
+        for (int e = 0; e < K; ++e)
+          for (int ff = 0; ff < K; ++ff) v += g(K + a, K + e, K + b, K + ff) * t(i, j, e, ff);
+        for (int m = 0; m < K; ++m)
+          for (int e = 0; e < K; ++e)
+            v += g(m, K + e, K + b, j) * u(i, m, a, e) - g(m, j, K + b, K + e) * t(i, m, a, e) -
+                 g(m, i, K + b, K + e) * t(j, m, e, a) - g(m, j, K + a, K + e) * t(i, m, e, b) +
+                 g(m, K + e, K + a, i) * u(j, m, b, e) - g(m, i, K + a, K + e) * t(j, m, b, e);
+        break;
+      }
+      default:
+        break;  // ooov, ovoo, ovov, ovvv, vvov: no T2-linear term
+    }
+    return v;
+  }
+  // T2-linear one-body terms
+  __device__ double f2(int p, int q) const {
+    double v = 0.0;
+    if (p < K && q < K) {  // oo (m i): sum_nef g_menf u_inef
+      for (int nn = 0; nn < K; ++nn)
+        for (int e = 0; e < K; ++e)
+          for (int ff = 0; ff < K; ++ff) v += g(p, K + e, nn, K + ff) * u(q, nn, e, ff);
+    } else if (p >= K && q >= K) {  // vv (a e): -sum_mnf g_menf u_mnaf
+      for (int m = 0; m < K; ++m)
+        for (int nn = 0; nn < K; ++nn)
+          for (int ff = 0; ff < K; ++ff) v -= g(m, q, nn, K + ff) * u(m, nn, p - K, ff);
+    } else if (p >= K && q < K) {  // vo (a i)
+      const int a = p - K, i = q;
+      for (int m = 0; m < K; ++m)
+        for (int e = 0; e < K; ++e) {
+          v += f(m, K + e) * u(i, m, a, e);
+          for (int ff = 0; ff < K; ++ff) v += g(p, K + e, m, K + ff) * u(i, m, e, ff);
+          for (int nn = 0; nn < K; ++nn) v -= g(m, i, nn, K + e) * u(m, nn, a, e);
+        }
+    }
+    return v;
+  }
+};
+
+// Wx, Fx, ex = [O, T]_(<=2) for the operator in d.h (vacuum order), d.f (normal order), d.g.
+template <int K, int NT>
+__device__ void lin_dress(DuccSmem<K>& d) {
+  constexpr int NO = 2 * K, NW = NO * NO * NO * NO, NF = NO * NO;
+  const LinDress<K> L{d};
+  for (int x = threadIdx.x; x < NW; x += NT) {
+    const int p = x / (NO * NO * NO), q = (x / (NO * NO)) % NO, r = (x / NO) % NO, s = x % NO;
+    d.Wx[x] = L.dg(p, q, r, s) + L.w2(p, q, r, s);
+  }
+  for (int x = threadIdx.x; x < NF; x += NT) {
+    const int p = x / NO, q = x % NO;
+    double v = L.dh(p, q) + L.f2(p, q);
+    for (int k = 0; k < K; ++k) v += 2.0 * L.dg(p, q, k, k) - L.dg(p, k, k, q);
+    d.Fx[x] = v;
+  }
+  if (threadIdx.x == NT - 1) {
+    double e = 0.0;
+    for (int k = 0; k < K; ++k) e += 2.0 * L.dh(k, k);
+    for (int k = 0; k < K; ++k)
+      for (int l = 0; l < K; ++l) e += 2.0 * L.dg(k, k, l, l) - L.dg(k, l, l, k);
+    for (int i = 0; i < K; ++i)
+      for (int aa = 0; aa < K; ++aa)
+        for (int j = 0; j < K; ++j)
+          for (int b = 0; b < K; ++b) e += L.g(i, K + aa, j, K + b) * L.u(i, j, aa, b);
+    d.ex = e;
+  }
+  __syncthreads();
+}
+
+// W -= c (Wx + Wx^+), F -= c (Fx + Fx^+), e0 -= 2 c ex.
+template <int K, int NT>
+__device__ void sub_hermitian(const DuccSmem<K>& d, double c, double* W, double* F, double* e0) {
+  constexpr int NO = 2 * K, NW = NO * NO * NO * NO, NF = NO * NO;
+  for (int x = threadIdx.x; x < NW; x += NT) {
+    const int p = x / (NO * NO * NO), q = (x / (NO * NO)) % NO, r = (x / NO) % NO, s = x % NO;
+    W[x] -= c * (d.Wx[x] + d.Wx[((q * NO + p) * NO + s) * NO + r]);
+  }
+  for (int x = threadIdx.x; x < NF; x += NT) F[x] -= c * (d.Fx[x] + d.Fx[(x % NO) * NO + x / NO]);
+  if (threadIdx.x == 0) *e0 -= 2.0 * c * d.ex;
+  __syncthreads();
+}
+
+// The operator's one-body part in normal order: f = h + sum_k (2 g_pqkk - g_pkkq).
+template <int K, int NT>
+__device__ void fold_up(DuccSmem<K>& d) {
+  constexpr int NO = 2 * K, NF = NO * NO;
+  for (int x = threadIdx.x; x < NF; x += NT) {
+    const int p = x / NO, q = x % NO;
+    double v = d.h[x];
+    for (int k = 0; k < K; ++k) v += 2.0 * d.g[((p * NO + q) * NO + k) * NO + k] - d.g[((p * NO + k) * NO + k) * NO + q];
+    d.f[x] = v;
+  }
+  __syncthreads();
+}
+
+// G|_A (gathered into W, F, e0) minus the space's internal part L_A.
+template <int K, int NT>
+__device__ void ducc_local(DuccSmem<K>& d, const SolveArgs& a, const int* orb, double* W, double* F, double* e0) {
+  constexpr int NO = 2 * K, NW = NO * NO * NO * NO, NF = NO * NO;
+  const size_t n1 = a.n, n2 = n1 * n1, n3 = n2 * n1;
+  for (int x = threadIdx.x; x < NW; x += NT) {
+    const int p = x / (NO * NO * NO), q = (x / (NO * NO)) % NO, r = (x / NO) % NO, s = x % NO;
+    d.g[x] = a.ducc_eri[(size_t)orb[p] * n3 + (size_t)orb[q] * n2 + (size_t)orb[r] * n1 + orb[s]];
+  }
+  for (int x = threadIdx.x; x < NF; x += NT) d.f0[x] = a.ducc_F0[(size_t)orb[x / NO] * n1 + orb[x % NO]];
+  for (int x = threadIdx.x; x < K * K; x += NT)
+    d.t1[x] = a.t1_old[(size_t)orb[x / K] * a.nvir + (orb[K + x % K] - a.nocc)];
+  for (int x = threadIdx.x; x < K * K * K * K; x += NT) {
+    const int i = x / (K * K * K), j = (x / (K * K)) % K, aa = (x / K) % K, b = x % K;
+    d.t2[x] = a.t2_old[(((size_t)orb[i] * a.nocc + orb[j]) * a.nvir + (orb[K + aa] - a.nocc)) * a.nvir +
+                       (orb[K + b] - a.nocc)];
+  }
+  __syncthreads();
+  // X_A: H_A in vacuum order on the space (its normal order gives back the Fock block f0)
+  for (int x = threadIdx.x; x < NF; x += NT) {
+    const int p = x / NO, q = x % NO;
+    double v = d.f0[x];
+    for (int k = 0; k < K; ++k) v -= 2.0 * d.g[((p * NO + q) * NO + k) * NO + k] - d.g[((p * NO + k) * NO + k) * NO + q];
+    d.h[x] = v;
+    d.f[x] = d.f0[x];
+  }
+  __syncthreads();
+  lin_dress<K, NT>(d);
+  sub_hermitian<K, NT>(d, 1.0, W, F, e0);
+  // Y_A: B_A = D.T_A + (D.T_A)^+, D from the Fock diagonal
+  auto eps = [&](int p) { return d.f0[p * NO + p]; };
+  for (int x = threadIdx.x; x < NW; x += NT) {
+    const int p = x / (NO * NO * NO), q = (x / (NO * NO)) % NO, r = (x / NO) % NO, s = x % NO;
+    double v = 0.0;
+    if (p >= K && q < K && r >= K && s < K)
+      v = (eps(p) + eps(r) - eps(q) - eps(s)) * d.t2[((q * K + s) * K + (p - K)) * K + (r - K)];
+    else if (p < K && q >= K && r < K && s >= K)
+      v = (eps(q) + eps(s) - eps(p) - eps(r)) * d.t2[((p * K + r) * K + (q - K)) * K + (s - K)];
+    d.g[x] = v;
+  }
+  for (int x = threadIdx.x; x < NF; x += NT) {
+    const int p = x / NO, q = x % NO;
+    double v = 0.0;
+    if (p >= K && q < K) v = (eps(p) - eps(q)) * d.t1[q * K + (p - K)];
+    if (p < K && q >= K) v = (eps(q) - eps(p)) * d.t1[p * K + (q - K)];
+    d.h[x] = v;
+  }
+  __syncthreads();
+  fold_up<K, NT>(d);
+  lin_dress<K, NT>(d);
+  sub_hermitian<K, NT>(d, 0.5, W, F, e0);
+}
+
+template <int K, typename T, bool DUCC>
 __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
   using C = Cas<K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<K, T>& sm = *reinterpret_cast<Smem<K, T>*>(smem_raw);
+  constexpr size_t kDuccOff = (sizeof(Smem<K, T>) + 15) / 16 * 16;
   const int tid = threadIdx.x;
   build_tables<K, T>(sm);
   const int n = a.n;
@@ -305,6 +622,13 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
     for (int idx = tid; idx < C::NF; idx += C::NT)
       sm.F[idx] = a.F[(size_t)sm.orb[idx / C::NORB] * n1 + sm.orb[idx % C::NORB]];
     __syncthreads();
+    if constexpr (DUCC) {  // G|_A minus the space's internal part
+      DuccSmem<K>& dz = *reinterpret_cast<DuccSmem<K>*>(smem_raw + kDuccOff);
+      ducc_local<K, C::NT>(dz, a, sm.orb, sm.W, sm.F, &sm.e0);
+      if constexpr (!std::is_same<T, double>::value)
+        for (int idx = tid; idx < C::NW; idx += C::NT) sm.Wt[idx] = (T)sm.W[idx];
+      __syncthreads();
+    }
     for (int idx = tid; idx < C::NF; idx += C::NT) {
       const int p = idx / C::NORB, q = idx % C::NORB;
       double v = sm.F[idx];
@@ -520,7 +844,14 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
         const int kk = k + 1;
         for (int j = 0; j < kk; ++j) sm.ynew[j] = (j < k) ? sm.y[j] : 0.0;
         double thn = sm.theta;
-        const int cx = small_eig<C::KMAX>(sm.G, kk, sm.theta - 1e-2, sm.ynew, &thn);
+        int cx = 0;
+        if constexpr (DUCC) {  // Hermitian operator: symmetric projected problem, Phi-weight root
+          double v0[C::KMAX];
+          for (int j = 0; j < kk; ++j) v0[j] = (double)sm.V[j * C::NDET];
+          small_eig_sym<C::KMAX>(sm.G, kk, v0, sm.ynew, &thn);
+        } else {
+          cx = small_eig<C::KMAX>(sm.G, kk, sm.theta - 1e-2, sm.ynew, &thn);
+        }
         for (int j = 0; j < kk; ++j) sm.y[j] = sm.ynew[j];
         sm.theta = thn;
         sm.ctrl[0] = kk;
@@ -581,7 +912,7 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
       for (int idx = tid; idx < K * K; idx += C::NT) {
         const int i = idx / K, aa = idx % K;
         const size_t g = (size_t)sm.orb[i] * a.nvir + (sm.orb[K + aa] - a.nocc);
-        if (a.owner1[g] == sidx) a.t1_new[g] = a.t1_old[g] + sm.x1[idx];
+        if (a.owner1[g] == sidx) a.t1_new[g] = (DUCC ? 0.0 : a.t1_old[g]) + sm.x1[idx];  // DUCC: replaced
       }
     }
     if (write && a.owner2) {
@@ -591,7 +922,7 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
                          (sm.orb[K + b] - a.nocc);
         if (a.owner2[g] == sidx) {
           const double x = 0.5 * (sm.x2raw[idx] + sm.x2raw[((j * K + i) * K + b) * K + aa]);
-          a.t2_new[g] = a.t2_old[g] + x;
+          a.t2_new[g] = (DUCC ? 0.0 : a.t2_old[g]) + x;
         }
       }
     }
@@ -605,22 +936,23 @@ __global__ void __launch_bounds__(Cas<K>::NT) solve_kernel(SolveArgs a) {
   }
 }
 
-template <int K, typename T>
+template <int K, typename T, bool DUCC>
 cudaError_t launch_k(const SolveArgs& a, cudaStream_t st) {
   using C = Cas<K>;
   if (a.nspaces <= 0) return cudaSuccess;
-  const size_t smem = sizeof(Smem<K, T>);
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (sizeof(Smem<K, T>) + 15) / 16 * 16 + (DUCC ? sizeof(DuccSmem<K>) : 0);
+  cudaError_t e =
+      cudaFuncSetAttribute(solve_kernel<K, T, DUCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<K, T>, C::NT, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<K, T, DUCC>, C::NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > a.nspaces) grid = a.nspaces;
-  solve_kernel<K, T><<<(unsigned)grid, C::NT, smem, st>>>(a);
+  solve_kernel<K, T, DUCC><<<(unsigned)grid, C::NT, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -634,10 +966,11 @@ __global__ void k_collect_noconv(SolveArgs a, int64_t* __restrict__ items, unsig
 }
 
 cudaError_t launch_fp64(int k, const SolveArgs& a, cudaStream_t st) {
+  const bool ducc = a.ducc_eri != nullptr && a.ducc_F0 != nullptr;
   switch (k) {
-    case 1: return launch_k<1, double>(a, st);
-    case 2: return launch_k<2, double>(a, st);
-    case 3: return launch_k<3, double>(a, st);
+    case 1: return ducc ? launch_k<1, double, true>(a, st) : launch_k<1, double, false>(a, st);
+    case 2: return ducc ? launch_k<2, double, true>(a, st) : launch_k<2, double, false>(a, st);
+    case 3: return ducc ? launch_k<3, double, true>(a, st) : launch_k<3, double, false>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
