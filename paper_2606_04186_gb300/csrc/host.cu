@@ -215,6 +215,7 @@ struct qflow_ctx {
   void* diis = nullptr;                                   // DIIS ring (opt.diis > 0)
   float* W32 = nullptr;  // FP32 copies of W (n^4) and F (n^2, after W) for the mixed-precision solver
   unsigned long long* queue = nullptr;                    // persistent-launch work counter
+  double* F0 = nullptr;  // DUCC form: the bare Fock matrix (the per-space part of the operator needs it)
   int64_t* rescue_items = nullptr;  // mixed path: positions of spaces the warp pass left unconverged
   unsigned long long* rescue_count = nullptr;  // and their count (device)
   // launch schedule of the mixed-precision solver: persistent queue or one launch per class
@@ -274,6 +275,7 @@ void free_ctx(qflow_ctx* c) {
   if (c->W32) cudaFree(c->W32);
   if (c->queue) cudaFree(c->queue);
   if (c->rescue_items) cudaFree(c->rescue_items);
+  if (c->F0) cudaFree(c->F0);
   if (c->rescue_count) cudaFree(c->rescue_count);
   void* mptrs[] = {c->mlp_model, c->mlp_grad, c->mlp_m, c->mlp_v, c->mlp_X, c->mlp_T, c->mlp_mask,
                    c->space_mask, c->pool_mask, c->wave_items, c->pool_start};
@@ -302,6 +304,7 @@ void qflow_default_options(qflow_options* opt, int32_t precision) {
   opt->guess = 0;
   opt->schedule = QFLOW_SCHED_AUTO;
   opt->graph = 1;
+  opt->form = QFLOW_FORM_SESCC;
 }
 
 int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
@@ -355,6 +358,14 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     delete c;
     return QFLOW_ERR_ARG;
   }
+  if (c->opt.form != QFLOW_FORM_SESCC && c->opt.form != QFLOW_FORM_DUCC) {
+    delete c;
+    return QFLOW_ERR_ARG;
+  }
+  if (c->opt.form == QFLOW_FORM_DUCC && (c->opt.precision != QFLOW_PREC_FP64 || c->opt.guess == QFLOW_GUESS_NETWORK)) {
+    delete c;
+    return QFLOW_ERR_ARG;
+  }
   if (c->opt.max_iter <= 0) c->opt.max_iter = 60;
   if (c->opt.diis < 0 || c->opt.diis > QFLOW_DIIS_MAX || c->opt.diis == 1 || c->opt.guess < 0 ||
       c->opt.guess > QFLOW_GUESS_NETWORK) {
@@ -382,6 +393,7 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   const size_t n1 = n, n4 = n1 * n1 * n1 * n1;
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   c->dwork_bytes = (c->opt.precision == QFLOW_PREC_MIXED) ? qf::dress_workspace_bytes_mixed(n, nocc)
+                   : (c->opt.form == QFLOW_FORM_DUCC)      ? qf::ducc_workspace_bytes(n, nocc)
                                                           : qf::dress_workspace_bytes(n, nocc);
   const size_t npool = (size_t)(c->n_t1 + c->n_t2);
   if (e == cudaSuccess) e = dalloc(&c->h, n1 * n1);
@@ -404,6 +416,7 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->red_host), 4 * sizeof(double));
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
   if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) e = dalloc(&c->W32, n4 + n1 * n1);
+  if (c->opt.form == QFLOW_FORM_DUCC && e == cudaSuccess) e = dalloc(&c->F0, n1 * n1);
   if (e == cudaSuccess) e = dalloc(&c->queue, 1);
   if (c->opt.precision == QFLOW_PREC_MIXED && e == cudaSuccess) {
     int64_t most = 1;
@@ -491,6 +504,10 @@ qf::SolveArgs solve_args(qflow_ctx* c, int k) {
   a.root_out = roots;
   a.max_iter = c->opt.max_iter;
   a.tol = c->opt.tol;
+  if (c->opt.form == QFLOW_FORM_DUCC) {
+    a.ducc_eri = c->eri;
+    a.ducc_F0 = c->F0;
+  }
   return a;
 }
 
@@ -504,13 +521,26 @@ cudaError_t mark(qflow_ctx* c, int k) {
                                   cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
+// e0, F, W of the operator every space gathers, for the pool (t1, t2): the SES-CC dressing, or the
+// common part G of the DUCC form (which also leaves the bare Fock matrix in F0).
+cudaError_t dress_pool(qflow_ctx* c, const double* t1, const double* t2) {
+  if (c->opt.form == QFLOW_FORM_DUCC)
+    return qf::launch_dress_ducc(c->h, c->eri, t1, t2, c->n, c->nocc, c->e0, c->F, c->W, c->F0, c->dwork,
+                                 c->dwork_bytes, c->stream);
+  return qf::launch_dress(c->h, c->eri, t1, t2, c->n, c->nocc, c->e0, c->F, c->W, c->dwork, c->dwork_bytes, c->stream,
+                          c->W32);
+}
+
+int dress_pool_launches(const qflow_ctx* c) {
+  return (c->opt.form == QFLOW_FORM_DUCC) ? qf::ducc_launch_count(c->n, c->nocc)
+                                          : qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
+}
+
 // Step (a): dressing (+ the FP32 copy of W for the mixed solver).
 cudaError_t enqueue_dress(qflow_ctx* c, int64_t* launches) {
   cudaError_t e = mark(c, 0);
-  if (e == cudaSuccess)
-    e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
-                         c->dwork_bytes, c->stream, c->W32);
-  *launches += qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
+  if (e == cudaSuccess) e = dress_pool(c, c->pool, c->pool + c->n_t1);
+  *launches += dress_pool_launches(c);
   if (e == cudaSuccess && c->W32) {
     const size_t n4 = (size_t)c->n * c->n * c->n * c->n;
     e = qf::launch_to_f32(c->W, c->W32, n4, c->stream);
@@ -643,8 +673,7 @@ float* mlp_stats(qflow_ctx* c, int which) {
 cudaError_t dress_bare(qflow_ctx* c) {
   cudaError_t e = cudaMemsetAsync(c->pool_new, 0, sizeof(double) * (size_t)(c->n_t1 + c->n_t2), c->stream);
   if (e == cudaSuccess)
-    e = qf::launch_dress(c->h, c->eri, c->pool_new, c->pool_new + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
-                         c->dwork_bytes, c->stream, c->W32);
+    e = dress_pool(c, c->pool_new, c->pool_new + c->n_t1);
   c->fw_of_last_sweep = false;
   return e;
 }
@@ -868,6 +897,9 @@ int qflow_set_shard(qflow_handle c, int32_t rank, int32_t nranks) {
 int qflow_sweep_waves(qflow_handle c, int64_t wave, double* d_e, double* max_dt, int32_t* nfailed) {
   if (!c || wave < 1) return QFLOW_ERR_ARG;
   if (c->shard_n > 1 || c->shard_open) return QFLOW_ERR_STATE;
+  // the DUCC form reads every internal amplitude of a space, which other spaces of the same wave
+  // update in place: waves run in the SES-CC form only
+  if (c->opt.form == QFLOW_FORM_DUCC) return QFLOW_ERR_STATE;
   if (wave >= c->nspaces) return qflow_sweep(c, d_e, max_dt, nfailed);  // one wave: Jacobi
   const int64_t ns = c->nspaces;
   const size_t npool = (size_t)(c->n_t1 + c->n_t2);
@@ -901,9 +933,8 @@ int qflow_sweep_waves(qflow_handle c, int64_t wave, double* d_e, double* max_dt,
   for (int64_t lo = 0; lo < ns && e == cudaSuccess; lo += wave) {
     const int64_t hi = std::min<int64_t>(ns, lo + wave);
     // dressing of the pool the earlier waves left
-    e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W, c->dwork,
-                         c->dwork_bytes, c->stream, c->W32);
-    launches += qf::dress_launch_count(c->n, c->nocc, c->W32 != nullptr);
+    e = dress_pool(c, c->pool, c->pool + c->n_t1);
+    launches += dress_pool_launches(c);
     if (e == cudaSuccess && c->W32) {
       const size_t n4 = (size_t)c->n * c->n * c->n * c->n;
       e = qf::launch_to_f32(c->W, c->W32, n4, c->stream);
@@ -1040,8 +1071,7 @@ int qflow_dressed(qflow_handle c, double* e0, double* F, double* W) {
   if (!c) return QFLOW_ERR_ARG;
   if (c->shard_open) return QFLOW_ERR_STATE;
   const size_t n1 = c->n, n4 = n1 * n1 * n1 * n1;
-  cudaError_t e = qf::launch_dress(c->h, c->eri, c->pool, c->pool + c->n_t1, c->n, c->nocc, c->e0, c->F, c->W,
-                                   c->dwork, c->dwork_bytes, c->stream, c->W32);
+  cudaError_t e = dress_pool(c, c->pool, c->pool + c->n_t1);
   c->fw_of_last_sweep = false;
   if (e0 && e == cudaSuccess) e = cudaMemcpyAsync(e0, c->e0, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (F && e == cudaSuccess) e = cudaMemcpyAsync(F, c->F, sizeof(double) * n1 * n1, cudaMemcpyDeviceToHost, c->stream);
@@ -1354,32 +1384,50 @@ int qflow_mlp_warm_pool(qflow_handle c) {
   if (!c->mlp_model || !c->mlp_has_stats || c->shard_open) return QFLOW_ERR_STATE;
   const int64_t n3 = c->cls_count[3];
   const int64_t CH = 131072;
-  const int64_t rows = n3 < CH ? n3 : CH;
   const int H = c->mlp_hidden;
   cudaError_t e = dress_bare(c);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->pool, 0, sizeof(double) * (size_t)(c->n_t1 + c->n_t2), c->stream);
+  // only the 6e6o spaces that own an amplitude reach the pool: infer on those alone
+  char* own = nullptr;
+  const size_t o_flag = 0, o_sp = (((size_t)c->nspaces + 255) / 256) * 256,
+               o_idx = o_sp + (((size_t)n3 * sizeof(qflow_space) + 255) / 256) * 256,
+               o_cnt = o_idx + (((size_t)n3 * sizeof(int64_t) + 255) / 256) * 256;
+  if (e == cudaSuccess && n3 > 0) e = cudaMalloc(reinterpret_cast<void**>(&own), o_cnt + 256);
+  int64_t nown = 0;
+  if (e == cudaSuccess && n3 > 0) {
+    unsigned long long cnt = 0;
+    e = qf::mlp_owner_spaces(c->own1, c->n_t1, c->own2, c->n_t2, c->nspaces, c->spaces + c->cls_off[3],
+                             c->sorted_index + c->cls_off[3], n3, reinterpret_cast<uint8_t*>(own + o_flag),
+                             reinterpret_cast<qflow_space*>(own + o_sp), reinterpret_cast<int64_t*>(own + o_idx),
+                             reinterpret_cast<unsigned long long*>(own + o_cnt), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, own + o_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    nown = (int64_t)cnt;
+  }
+  const qflow_space* osp = reinterpret_cast<const qflow_space*>(own + o_sp);
+  const int64_t* oidx = reinterpret_cast<const int64_t*>(own + o_idx);
+  const int64_t rows = nown < CH ? nown : CH;
   char* buf = nullptr;
   const size_t fx = ((size_t)rows * QFLOW_MLP_NIN * sizeof(float) + 255) / 256 * 256;
   const size_t fy = ((size_t)rows * QFLOW_MLP_NOUT * sizeof(float) + 255) / 256 * 256;
   if (e == cudaSuccess && rows > 0)
     e = cudaMalloc(reinterpret_cast<void**>(&buf), fx + fy + qf::mlp_workspace_bytes(QFLOW_MLP_NIN, H, QFLOW_MLP_NOUT, rows));
-  for (int64_t off = 0; off < n3 && e == cudaSuccess; off += CH) {
-    const int64_t r = (n3 - off < CH) ? n3 - off : CH;
+  for (int64_t off = 0; off < nown && e == cudaSuccess; off += CH) {
+    const int64_t r = (nown - off < CH) ? nown - off : CH;
     float* X = reinterpret_cast<float*>(buf);
     float* Y = reinterpret_cast<float*>(buf + fx);
-    e = qf::mlp_features(c->n, c->F, c->W, c->spaces + c->cls_off[3] + off, r, 1, mlp_stats(c, 0), mlp_stats(c, 1), X,
-                         c->stream);
+    e = qf::mlp_features(c->n, c->F, c->W, osp + off, r, 1, mlp_stats(c, 0), mlp_stats(c, 1), X, c->stream);
     if (e == cudaSuccess)
       e = qf::mlp_forward(QFLOW_MLP_NIN, H, QFLOW_MLP_NOUT, c->mlp_model, X, r, Y, buf + fx + fy, c->stream);
     if (e == cudaSuccess)
-      e = qf::mlp_pool_from_pred(Y, mlp_stats(c, 2), mlp_stats(c, 3), c->spaces + c->cls_off[3] + off,
-                                 c->sorted_index + c->cls_off[3] + off, r, c->nocc, c->nvir, c->own1, c->own2, c->pool,
-                                 c->stream);
+      e = qf::mlp_pool_from_pred(Y, mlp_stats(c, 2), mlp_stats(c, 3), osp + off, oidx + off, r, c->nocc, c->nvir,
+                                 c->own1, c->own2, c->pool, c->stream);
   }
   if (e == cudaSuccess && c->diis) e = qf::diis_reset(c->diis, c->opt.diis, c->n_t1 + c->n_t2, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (buf) cudaFree(buf);
+  if (own) cudaFree(own);
   return cuda_status(e);
 }
 

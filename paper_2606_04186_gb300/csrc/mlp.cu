@@ -625,6 +625,41 @@ cudaError_t mlp_pool_from_pred(const float* pred, const float* mu, const float* 
   return cudaGetLastError();
 }
 
+// Spaces that own at least one amplitude: flag[sorted index] = 1 from the owner maps; then the
+// flagged positions of one class list are gathered (space records and sorted indices) in any
+// order, with their count.  Only those spaces' predictions reach the pool in a warm start.
+__global__ void k_flag_owners(const int32_t* __restrict__ own, int64_t m, uint8_t* __restrict__ flag) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < m; x += (int64_t)gridDim.x * blockDim.x)
+    if (own[x] >= 0) flag[own[x]] = 1;
+}
+
+__global__ void k_gather_flagged(const qflow_space* __restrict__ spaces, const int64_t* __restrict__ sorted_index,
+                                 int64_t rows, const uint8_t* __restrict__ flag, qflow_space* __restrict__ out_sp,
+                                 int64_t* __restrict__ out_idx, unsigned long long* __restrict__ count) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t si = sorted_index[r];
+    if (flag[si]) {
+      const unsigned long long k = atomicAdd(count, 1ull);
+      out_sp[k] = spaces[r];
+      out_idx[k] = si;
+    }
+  }
+}
+
+cudaError_t mlp_owner_spaces(const int32_t* owner1, int64_t n1, const int32_t* owner2, int64_t n2, int64_t nspaces,
+                             const qflow_space* spaces, const int64_t* sorted_index, int64_t rows, uint8_t* flag,
+                             qflow_space* out_sp, int64_t* out_idx, unsigned long long* count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)nspaces, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_flag_owners<<<grid1(n1, 256) > 4096 ? 4096 : grid1(n1, 256), 256, 0, st>>>(owner1, n1, flag);
+  k_flag_owners<<<grid1(n2, 256) > 4096 ? 4096 : grid1(n2, 256), 256, 0, st>>>(owner2, n2, flag);
+  if (rows > 0)
+    k_gather_flagged<<<grid1(rows, 256) > 4096 ? 4096 : grid1(rows, 256), 256, 0, st>>>(spaces, sorted_index, rows,
+                                                                                        flag, out_sp, out_idx, count);
+  return cudaGetLastError();
+}
+
 cudaError_t mlp_invert(const float* sd, int n, float* out, cudaStream_t st) {
   k_invert<<<grid1(n, 128), 128, 0, st>>>(sd, n, out);
   return cudaGetLastError();
