@@ -52,6 +52,9 @@ PRECISION_STEPS = {
         "hard_spaces": "spaces the f32 warp pass leaves unconverged are re-solved in f64",
     },
     "fp64": {"every_step": "f64"},
+    "ducc": {"every_step": "f64",
+             "form": "DUCC: [H + [H, s] + 1/2 [[F, s], s]]_(<=2), s = T_ext - T_ext^+; common part from eight "
+                     "FP64 dressings per sweep, each space's internal part subtracted in its solve"},
 }
 
 
@@ -63,6 +66,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="n82", choices=sorted(synth.SYSTEMS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--form", default="ses", choices=["ses", "ducc"],
+                    help="downfolding form: SES-CC (default) or the Hermitian DUCC form (FP64 only)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed sweeps of the plain FP64 form (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=3000, help="spaces solved by the oracle for cpu_baseline")
@@ -77,6 +82,9 @@ def parse():
     ap.add_argument("--launch-loop", action="store_true",
                     help="also time the solve as one launch per space (a per-space launch loop) against one "
                          "launch for every space, on the dressing of the timed pool (3,3 spaces only)")
+    ap.add_argument("--no-mlp", action="store_true",
+                    help="skip the warm-start network leg (mlp_vs_cold: flows to convergence from an empty pool "
+                         "and from the network's pool, on a second system of the same recipe)")
     ap.add_argument("--spaces-limit", type=int, default=0,
                     help="keep an evenly strided subset of at most this many spaces (small profiling case)")
     return ap.parse_args()
@@ -296,6 +304,76 @@ def run_reference(args):
 
 # ---- GPU leg ---------------------------------------------------------------------------------------
 
+def _converge(fl, stream, tol_e, tol_t, max_sweeps=40):
+    """Sweeps until |dE| < tol_e and max|dt| < tol_t; returns (sweeps, CUDA-event seconds of the
+    sweeps, energy after each sweep)."""
+    import torch
+    ms, es = 0.0, []
+    for _ in range(max_sweeps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        de, dt, nf, code = fl.sweep(raise_on_fail=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        es.append(fl.energy())
+        if abs(de) < tol_e and dt < tol_t:
+            break
+    return len(es), ms / 1e3, es
+
+
+def mlp_leg(qflow, name, s, h, g, sp, precision, sweep_ms, hidden=256, max_pairs=100000):
+    """Warm-start network (not in the paper) at this workload: trained on the converged flow of
+    the timed system (bare integrals of each space -> its converged internal amplitudes), then a
+    second system of the same recipe (another seed) is run to convergence from an empty pool and
+    from the network's pool; the warm start's inference (features, network, pool) is timed with
+    CUDA events and counted in its time to convergence."""
+    import torch
+    no = s.nocc
+    tol_e, tol_t = (1e-8, 1e-7) if precision == "fp64" else (1e-7, 1e-5)
+    fa = qflow.Flow(h, g, no, sp, precision=precision)
+    sa = torch.cuda.ExternalStream(fa.stream())
+    _converge(fa, sa, tol_e, tol_t)
+    stride = max(1, len(sp) // max_pairs)
+    n = fa.mlp_collect(stride=stride, max_pairs=max_pairs, target="pool")
+    fa.mlp_set_model(synth.mlp_init_model(hidden, 2), hidden, has_stats=False)
+    t0 = time.perf_counter()
+    loss = fa.mlp_train(epochs=60, batch=128, lr=2e-3, order=np.random.default_rng(4).permutation(n))
+    t_train = time.perf_counter() - t0
+    model = fa.mlp_get_model()
+    fa.close()
+    _, h2, g2 = synth.make_system(s.n, s.nocc, s.xi, s.seed + 100)
+    cold = qflow.Flow(h2, g2, no, sp, precision=precision)
+    k_cold, t_cold, e_cold = _converge(cold, torch.cuda.ExternalStream(cold.stream()), tol_e, tol_t)
+    cold.close()
+    warm = qflow.Flow(h2, g2, no, sp, precision=precision)
+    sw = torch.cuda.ExternalStream(warm.stream())
+    warm.mlp_set_model(model, hidden, has_stats=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(sw)
+    warm.mlp_warm_pool()
+    b.record(sw)
+    torch.cuda.synchronize()
+    t_inf = a.elapsed_time(b) / 1e3
+    k_warm, t_warm, e_warm = _converge(warm, sw, tol_e, tol_t)
+    warm.close()
+    e_fix = e_cold[-1]
+    err_cold = [abs(e - e_fix) for e in e_cold[:3]]
+    err_warm = [abs(e - e_fix) for e in e_warm[:3]]
+    log(f"mlp: trained on {n} pairs in {t_train:.1f} s (loss {loss[0]:.3g} -> {loss[-1]:.3g}); cold {k_cold} sweeps "
+        f"{t_cold:.3f} s, warm {k_warm} sweeps {t_warm:.3f} s + inference {1e3 * t_inf:.1f} ms; |E - E_fixed| after "
+        f"sweeps 1-3: cold {err_cold}, warm {err_warm}")
+    return {"train_pairs": n, "train_s": t_train, "loss_first_last": [float(loss[0]), float(loss[-1])],
+            "system": f"{name} recipe, seed {s.seed + 100}", "tol": [tol_e, tol_t],
+            "cold": {"sweeps": k_cold, "seconds": t_cold, "energy": e_cold[-1], "abs_error_sweeps_1_3": err_cold},
+            "warm": {"sweeps": k_warm, "seconds_incl_inference": t_warm + t_inf, "energy": e_warm[-1],
+                     "abs_error_sweeps_1_3": err_warm},
+            "inference_ms": 1e3 * t_inf, "inference_over_timed_sweep": (1e3 * t_inf) / sweep_ms,
+            "energy_difference": e_warm[-1] - e_cold[-1],
+            "note": "network used to start the pool only; the plain flow is the judge (same fixed point)"}
+
+
 def launch_loop_leg(qflow, fl, h, g, no, sp, precision):
     """The solve step of the timed pool's dressing (steps b + c for every (3,3) space) as one
     qflow_solve_device launch per space, against one launch for all spaces; CUDA events around
@@ -371,7 +449,9 @@ def run_ours(args):
     no, nv = s.nocc, s.n - s.nocc
     log(f"inputs ready: {name}, {len(sp)} spaces")
     t_init = time.perf_counter()
-    fl = qflow.Flow(h, g, no, sp, precision=args.precision, schedule=args.schedule)
+    if args.form == "ducc":
+        args.precision = "fp64"   # the DUCC form is FP64 throughout; its FP64 leg is the run itself
+    fl = qflow.Flow(h, g, no, sp, precision=args.precision, schedule=args.schedule, form=args.form)
     t_init = time.perf_counter() - t_init
     stream = torch.cuda.ExternalStream(fl.stream())
     log(f"init {t_init:.1f} s")
@@ -482,6 +562,11 @@ def run_ours(args):
     loop = launch_loop_leg(qflow, fl, h, g, no, sp, args.precision) if (args.launch_loop and world == 1) else None
     fl.close()
 
+    mlp = None
+    if not args.no_mlp and world == 1 and not args.waves and not sharded and args.form == "ses" and \
+            args.sampler < 0 and not args.spaces_limit and (sp[:, 0] == 3).all():
+        mlp = mlp_leg(qflow, name, s, h, g, sp, args.precision, sweep_ms)
+
     # plain FP64 GPU form of the same sweep (pool after the same number of sweeps as the first
     # warm-up of the mixed run: compare energies after sweep 2)
     fp64 = None
@@ -558,7 +643,8 @@ def run_ours(args):
                    "parallelism": (f"sharded over {world} GPUs: per-class blocks, one allreduce of "
                                    f"{8 * fl_xsize / 1e6:.0f} MB per sweep") if sharded else "one GPU",
                    "step": "third sweep of the flow (pool after two sweeps restored before each step)",
-                   "precision_steps": PRECISION_STEPS[args.precision],
+                   "precision_steps": PRECISION_STEPS["ducc" if args.form == "ducc" else args.precision],
+                   "form": "DUCC (Hermitian)" if args.form == "ducc" else "SES-CC",
                    "init_s": t_init},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
@@ -566,7 +652,8 @@ def run_ours(args):
                                  if name in TRAFFIC_PER_SPACE and args.precision == "mixed" and not args.spaces_limit
                                  else None),
                      "kernel": ("solve_persistent_kernel" if sched["persistent"] else "solve_class_kernel<K>")
-                     if args.precision == "mixed" else "solve_kernel<K,double>",
+                     if args.precision == "mixed" else ("solve_kernel<K,double,DUCC>" if args.form == "ducc"
+                                                        else "solve_kernel<K,double>"),
                      "flops_per_launch": flops, "launch_ms": solve_ms,
                      "peak_note": ("measured FP32 FMA peak of this GPU" if args.precision == "mixed"
                                    else "measured FP64 FMA peak of this GPU") + " (" + peaks["method"] + ")",
@@ -583,6 +670,7 @@ def run_ours(args):
         "sweep_codes": sorted(set(int(c) for c in codes)),
         "fp64_form": fp64,
         "launch_loop": loop,
+        "mlp_vs_cold": mlp,
         "speedup_vs_fp64": (fp64["sweep_s"] / (sweep_ms / 1e3)) if fp64 else None,
         "cpu_baseline": cpu,
         "e2e": {"value": len(sp) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": pool_bytes,
