@@ -91,9 +91,9 @@ typedef enum {
 
 typedef enum {
   QFLOW_SCHED_AUTO = 0,       /* mixed precision: the first sweep runs the persistent queue;
-                                 at the second sweep the autotuner times its items-per-fetch
-                                 candidates (1, 2, 4, 8, 16) on a calibration subset and keeps
-                                 the fastest                                                  */
+                                 at the second sweep the autotuner times its candidates, items
+                                 per fetch (1, 2, 4, 8) x warps per CTA (15, 12), on a
+                                 calibration subset and keeps the fastest                      */
   QFLOW_SCHED_PER_CLASS = 1,  /* one grid-stride launch per size class                        */
   QFLOW_SCHED_PERSISTENT = 2  /* one persistent launch; warps take spaces of every class from a
                                  single work queue, 6e6o first                                 */
@@ -123,7 +123,9 @@ typedef struct {
                                  FP64: from the second), capture the sweep's device work in a
                                  CUDA graph and replay it (default 1)                        */
   int32_t form;               /* qflow_form: the downfolding form (default QFLOW_FORM_SESCC)  */
-  int32_t reserved[5];
+  int32_t warps;              /* mixed precision: spaces (warps) per CTA of the solver, 1..15;
+                                 0 = chosen by the autotuner (QFLOW_SCHED_AUTO) or 15        */
+  int32_t reserved[4];
 } qflow_options;
 
 /* Fill *opt with the defaults above for the given precision. */
@@ -256,11 +258,13 @@ int qflow_dressed(qflow_handle hnd, double* e0, double* F, double* W);
 int qflow_last_sweep_info(qflow_handle hnd, double* phase_ms, int64_t* kernel_launches);
 
 /* Launch schedule in use (tuned at the second sweep): persistent queue or per-class launches,
- * items per queue fetch, CTAs per SM (0 = occupancy limit), whether sweeps replay a CUDA
- * graph, and the autotuner's calibration times (milliseconds per candidate, up to 8; the
- * count is 0 when the schedule was fixed or came from the per-process cache).  Any output may
- * be NULL. */
-int qflow_schedule(qflow_handle hnd, int32_t* persistent, int32_t* chunk, int32_t* ctas_per_sm, int32_t* graph,
+ * items per queue fetch, warps (spaces) per CTA of the solver (one CTA per SM), whether sweeps
+ * replay a CUDA graph, and the autotuner's calibration times (milliseconds per candidate, up to
+ * QFLOW_TUNE_MAX; 0 for a candidate a fixed warps option skipped; the count is 0 before the
+ * calibration, when the schedule was fixed, or when it came from the per-process cache).  Any
+ * output may be NULL. */
+#define QFLOW_TUNE_MAX 8
+int qflow_schedule(qflow_handle hnd, int32_t* persistent, int32_t* chunk, int32_t* warps_per_cta, int32_t* graph,
                    float* candidate_ms, int32_t* n_candidates);
 
 /* Stream the handle works on (a cudaStream_t). */

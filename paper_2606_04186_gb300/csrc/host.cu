@@ -219,10 +219,10 @@ struct qflow_ctx {
   int64_t* rescue_items = nullptr;  // mixed path: positions of spaces the warp pass left unconverged
   unsigned long long* rescue_count = nullptr;  // and their count (device)
   // launch schedule of the mixed-precision solver: persistent queue or one launch per class
-  int sched_persistent = 1, sched_chunk = 4, sched_ctas = 0;
+  int sched_persistent = 1, sched_chunk = 4, sched_warps = 15;  // warps (spaces) per CTA
   bool tuned = false;
   int64_t sweeps = 0;  // sweeps run so far
-  float tune_ms[8] = {0};
+  float tune_ms[QFLOW_TUNE_MAX] = {0};
   int tune_count = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -305,6 +305,7 @@ void qflow_default_options(qflow_options* opt, int32_t precision) {
   opt->schedule = QFLOW_SCHED_AUTO;
   opt->graph = 1;
   opt->form = QFLOW_FORM_SESCC;
+  opt->warps = 0;
 }
 
 int qflow_plan(const double* h, const double* eri, int32_t n, int32_t nocc, const qflow_space* spaces,
@@ -358,6 +359,11 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     delete c;
     return QFLOW_ERR_ARG;
   }
+  if (c->opt.warps < 0 || c->opt.warps > 15) {
+    delete c;
+    return QFLOW_ERR_ARG;
+  }
+  if (c->opt.warps > 0) c->sched_warps = c->opt.warps;
   if (c->opt.form != QFLOW_FORM_SESCC && c->opt.form != QFLOW_FORM_DUCC) {
     delete c;
     return QFLOW_ERR_ARG;
@@ -553,10 +559,10 @@ cudaError_t enqueue_dress(qflow_ctx* c, int64_t* launches) {
 
 // The per-space solves with a given schedule; `count` > 0 limits every class to its first
 // `count` spaces (autotuner calibration).
-cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches,
+cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int warps, int64_t* launches,
                               bool calibrating);
 
-cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int64_t count, int64_t* launches) {
+cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int warps, int64_t count, int64_t* launches) {
   SolveArgs cls[4];
   for (int k = 1; k <= 3; ++k) {
     cls[k] = solve_args(c, k);
@@ -566,13 +572,13 @@ cudaError_t enqueue_solve(qflow_ctx* c, int persistent, int chunk, int ctas, int
       cls[k].root_out = nullptr;
     }
   }
-  return enqueue_solve_cls(c, cls, persistent, chunk, ctas, launches, count > 0);
+  return enqueue_solve_cls(c, cls, persistent, chunk, warps, launches, count > 0);
 }
 
 // The solves of the given per-class arguments (cls[1..3]) with a given schedule.  In the mixed
 // path the warp solver's pass stops at qf::kWarpIterCap steps; unless `calibrating`, the spaces it
 // leaves unconverged are then solved again by the FP64 solver within max_iter steps.
-cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int ctas, int64_t* launches,
+cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int chunk, int warps, int64_t* launches,
                               bool calibrating) {
   if (c->opt.precision != QFLOW_PREC_MIXED) {
     cudaError_t e = cudaSuccess;
@@ -591,12 +597,12 @@ cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int 
   cudaError_t e = cudaSuccess;
   if (persistent) {
     *launches += 2;  // queue reset + kernel
-    e = qf::launch_solve_persistent(warp, c->W32, c->queue, chunk, ctas, c->stream);
+    e = qf::launch_solve_persistent(warp, c->W32, c->queue, chunk, warps, c->stream);
   } else {
     for (int k = 3; k >= 1 && e == cudaSuccess; --k) {
       if (warp[k].nspaces == 0) continue;
       e = qf::launch_solve_warp(k, warp[k], c->W32, static_cast<const float*>(warp[k].guess),
-                                static_cast<float*>(warp[k].root_out), ctas, c->stream);
+                                static_cast<float*>(warp[k].root_out), warps, c->stream);
       ++*launches;
     }
   }
@@ -612,7 +618,7 @@ cudaError_t enqueue_solve_cls(qflow_ctx* c, SolveArgs* cls, int persistent, int 
 cudaError_t enqueue_solve_phase(qflow_ctx* c, int64_t* launches) {
   const size_t npool = (size_t)(c->n_t1 + c->n_t2);
   cudaError_t e = cudaMemcpyAsync(c->pool_new, c->pool, sizeof(double) * npool, cudaMemcpyDeviceToDevice, c->stream);
-  if (e == cudaSuccess) e = enqueue_solve(c, c->sched_persistent, c->sched_chunk, c->sched_ctas, 0, launches);
+  if (e == cudaSuccess) e = enqueue_solve(c, c->sched_persistent, c->sched_chunk, c->sched_warps, 0, launches);
   return e;
 }
 
@@ -718,16 +724,20 @@ cudaError_t autotune(qflow_ctx* c) {
     if (it != g_tune_cache.end()) {
       c->sched_persistent = it->second[0];
       c->sched_chunk = it->second[1];
-      c->sched_ctas = it->second[2];
+      c->sched_warps = it->second[2];
       c->tuned = true;
       return cudaSuccess;
     }
   }
-  // candidates: (persistent, chunk, CTAs per SM).  Only the persistent queue: one CTA of the
-  // warp solver fills an SM, and the per-class grid-stride launch, which can tie on a calibration
-  // prefix, loses its L2 locality over a whole list (n82: 90 ms against 76 ms).
-  constexpr int kCand = 5;
-  const int cand[kCand][3] = {{1, 1, 0}, {1, 2, 0}, {1, 4, 0}, {1, 8, 0}, {1, 16, 0}};
+  // candidates: (persistent, items per fetch, warps per CTA).  Only the persistent queue: the
+  // per-class grid-stride launch, which can tie on a calibration prefix, loses its L2 locality
+  // over a whole list (n82: 90 ms against 76 ms).  Fewer warps per CTA leave more of the SM's
+  // 256 KB to the L1 cache (the coupling tables and the gathered blocks) at the cost of latency
+  // hiding.  A fixed warps option (qflow_options.warps) keeps only its own candidates.
+  constexpr int kCand = 8;
+  const int cand[kCand][3] = {{1, 1, 15}, {1, 2, 15}, {1, 4, 15}, {1, 8, 15},
+                              {1, 1, 12}, {1, 2, 12}, {1, 4, 12}, {1, 8, 12}};
+  static_assert(kCand <= QFLOW_TUNE_MAX, "candidate times");
   // calibration prefix of every class: large enough that the warps' drift through the list
   // (which decides L2 reuse of the W blocks) shows, small next to a full solve
   const int64_t count = 262144;
@@ -739,6 +749,8 @@ cudaError_t autotune(qflow_ctx* c) {
   int64_t dummy = 0;
   for (int ci = 0; ci < kCand && e == cudaSuccess; ++ci) {
     float ms = 0.f;
+    c->tune_ms[ci] = 0.f;
+    if (c->opt.warps > 0 && cand[ci][2] != c->opt.warps) continue;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
       e = cudaEventRecord(t0, c->stream);
       if (e == cudaSuccess) e = enqueue_solve(c, cand[ci][0], cand[ci][1], cand[ci][2], count, &dummy);
@@ -747,7 +759,7 @@ cudaError_t autotune(qflow_ctx* c) {
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
     }
     c->tune_ms[ci] = ms;
-    if (ms < best) {
+    if (ms > 0.f && ms < best) {
       best = ms;
       bi = ci;
     }
@@ -758,10 +770,10 @@ cudaError_t autotune(qflow_ctx* c) {
   c->tune_count = kCand;
   c->sched_persistent = cand[bi][0];
   c->sched_chunk = cand[bi][1];
-  c->sched_ctas = cand[bi][2];
+  c->sched_warps = (c->opt.warps > 0) ? c->opt.warps : cand[bi][2];
   c->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_cache[key] = {c->sched_persistent, c->sched_chunk, c->sched_ctas};
+  g_tune_cache[key] = {c->sched_persistent, c->sched_chunk, c->sched_warps};
   return cudaSuccess;
 }
 
@@ -956,7 +968,7 @@ int qflow_sweep_waves(qflow_handle c, int64_t wave, double* d_e, double* max_dt,
       cls[k].t2_new = c->pool + c->n_t1;
     }
     if (e == cudaSuccess)
-      e = enqueue_solve_cls(c, cls, c->sched_persistent, c->sched_chunk, c->sched_ctas, &launches, false);
+      e = enqueue_solve_cls(c, cls, c->sched_persistent, c->sched_chunk, c->sched_warps, &launches, false);
   }
   if (e == cudaSuccess) e = mark(c, 2);
   if (e == cudaSuccess && c->diis) {
@@ -1082,12 +1094,12 @@ int qflow_dressed(qflow_handle c, double* e0, double* F, double* W) {
 
 void* qflow_stream(qflow_handle c) { return c ? (void*)c->stream : nullptr; }
 
-int qflow_schedule(qflow_handle c, int32_t* persistent, int32_t* chunk, int32_t* ctas_per_sm, int32_t* graph,
+int qflow_schedule(qflow_handle c, int32_t* persistent, int32_t* chunk, int32_t* warps_per_cta, int32_t* graph,
                    float* candidate_ms, int32_t* n_candidates) {
   if (!c) return QFLOW_ERR_ARG;
   if (persistent) *persistent = c->sched_persistent;
   if (chunk) *chunk = c->sched_chunk;
-  if (ctas_per_sm) *ctas_per_sm = c->sched_ctas;
+  if (warps_per_cta) *warps_per_cta = c->sched_warps;
   if (graph) *graph = c->graph_exec ? 1 : 0;
   if (candidate_ms)
     for (int i = 0; i < c->tune_count; ++i) candidate_ms[i] = c->tune_ms[i];

@@ -56,7 +56,7 @@ struct SolveArgs {
 // Launch the batched solver for spaces of size class k (1, 2 or 3) in the given precision.
 cudaError_t launch_solve(int k, int precision, const SolveArgs& a, cudaStream_t st);
 // Warp-per-space mixed-precision solvers (solve_warp.cu).  W32: optional FP32 copy of W (same
-// layout); NULL reads and converts the FP64 W.  ctas_per_sm: 0 = as many as fit.
+// layout); NULL reads and converts the FP64 W.
 // Iteration cap of the warp solver's pass in the mixed path: spaces still unconverged after it
 // (a few hard spaces whose Phi-dominant root has lower roots close by) are solved again by the
 // FP64 solver, whose larger subspace converges on them, within max_iter steps.
@@ -69,12 +69,13 @@ constexpr int kWarpIterCap = 16;
 cudaError_t launch_solve_rescue(int k, const SolveArgs& a, int64_t* items, unsigned long long* count,
                                 cudaStream_t st);
 
+// Warp solver launches: `warps` spaces (warps) per CTA, 1..15 (0 = 15); one CTA per SM.
 cudaError_t launch_solve_warp(int k, const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
-                              int ctas_per_sm, cudaStream_t st);
+                              int warps, cudaStream_t st);
 // One persistent launch over every size class (cls[k], k = 1..3; guesses from cls[k].guess):
 // warps take `chunk` work items per atomic from `queue` (zeroed by the call), 6e6o first.
 cudaError_t launch_solve_persistent(const SolveArgs* cls, const float* W32, unsigned long long* queue, int chunk,
-                                    int ctas_per_sm, cudaStream_t st);
+                                    int warps, cudaStream_t st);
 // FP32 copy of the dressed two-body integrals for the mixed-precision solver.
 cudaError_t launch_to_f32(const double* W, float* W32, size_t count, cudaStream_t st);
 

@@ -45,7 +45,12 @@ namespace qf {
 namespace {
 
 constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
-constexpr int WARPS = 15;  // spaces (warps) per CTA: one CTA fills the shared memory of an SM
+// Spaces (warps) per CTA: a launch parameter up to kMaxWarps (the autotuner picks it); one CTA
+// fills the shared memory of an SM.  The register file is split over the SM's four
+// sub-partitions (16,384 registers each); 15 warps put four warps on some of them, so a thread
+// may hold at most 16,384 / (4 x 32) = 128 registers, which every smaller count allows too.
+constexpr int kMaxWarps = 15;
+constexpr int kMaxRegs = 128;
 
 template <int K>
 struct Dim {
@@ -469,35 +474,37 @@ union alignas(16) AnyWarpState {
   WarpState<1> w1;
 };
 
-struct alignas(16) CtaSmem {
+// Shared memory of a CTA: the string tables, then one AnyWarpState per warp.
+struct alignas(16) CtaTabs {
   Tabs<3> t3;
   Tabs<2> t2;
   Tabs<1> t1;
   unsigned short pair3[Dim<3>::NPAIR];  // (P, R) with P <= R, packed P | R << 8
-  AnyWarpState w[WARPS];
 };
+constexpr size_t kTabsBytes = (sizeof(CtaTabs) + 15) / 16 * 16;
+__host__ __device__ constexpr size_t cta_smem_bytes(int warps) { return kTabsBytes + (size_t)warps * sizeof(AnyWarpState); }
 
 static_assert(sizeof(WarpState<3>) % 16 == 0 && offsetof(WarpState<3>, S) % 16 == 0 &&
                   offsetof(WarpState<3>, Wt) % 16 == 0 && offsetof(WarpState<3>, Hs) % 16 == 0 &&
                   offsetof(WarpState<3>, dh) % 16 == 0 && offsetof(WarpState<3>, Jc) % 16 == 0 &&
                   (2 * Dim<3>::NDET * sizeof(float)) % 16 == 0,
               "float4 rows of the 6e6o state");
-static_assert(offsetof(CtaSmem, w) % 16 == 0 && sizeof(AnyWarpState) % 16 == 0, "warp state alignment");
-static_assert(sizeof(CtaSmem) <= 232448, "one CTA within the 227 KB of shared memory a block may use");
+static_assert(kTabsBytes % 16 == 0 && sizeof(AnyWarpState) % 16 == 0, "warp state alignment");
+static_assert(cta_smem_bytes(kMaxWarps) <= 232448, "one CTA within the 227 KB of shared memory a block may use");
 
 // Entries of the 6e6o coupling tables (read-only global data, cached on the SM).  A per-CTA
 // shared-memory copy was measured slower: it costs one of the 15 warps an SM holds.
-__device__ __forceinline__ unsigned phi_entry(const CtaSmem&, int i) { return __ldg(&g_phi_table.e[i]); }
-__device__ __forceinline__ unsigned hs_entry(const CtaSmem&, int i) { return __ldg(&g_hs_table.e[i]); }
+__device__ __forceinline__ unsigned phi_entry(const CtaTabs&, int i) { return __ldg(&g_phi_table.e[i]); }
+__device__ __forceinline__ unsigned hs_entry(const CtaTabs&, int i) { return __ldg(&g_hs_table.e[i]); }
 
 template <int K>
-__device__ Tabs<K>& tabs(CtaSmem& cs);
+__device__ Tabs<K>& tabs(CtaTabs& cs);
 template <>
-__device__ __forceinline__ Tabs<3>& tabs<3>(CtaSmem& cs) { return cs.t3; }
+__device__ __forceinline__ Tabs<3>& tabs<3>(CtaTabs& cs) { return cs.t3; }
 template <>
-__device__ __forceinline__ Tabs<2>& tabs<2>(CtaSmem& cs) { return cs.t2; }
+__device__ __forceinline__ Tabs<2>& tabs<2>(CtaTabs& cs) { return cs.t2; }
 template <>
-__device__ __forceinline__ Tabs<1>& tabs<1>(CtaSmem& cs) { return cs.t1; }
+__device__ __forceinline__ Tabs<1>& tabs<1>(CtaTabs& cs) { return cs.t1; }
 
 template <int K>
 __device__ WarpState<K>& state(AnyWarpState& a);
@@ -586,7 +593,7 @@ __device__ void build_tabs(Tabs<K>& t) {
   }
 }
 
-__device__ void build_all_tabs(CtaSmem& cs) {
+__device__ void build_all_tabs(CtaTabs& cs) {
   if (threadIdx.x == 0) build_tabs<3>(cs.t3);
   if (threadIdx.x == 32) build_tabs<2>(cs.t2);
   if (threadIdx.x == 64) build_tabs<1>(cs.t1);
@@ -622,15 +629,16 @@ __device__ __forceinline__ void coulomb_rows(std::integer_sequence<int, B...>, f
 __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, const float* __restrict__ c,
                                      float* __restrict__ out, int lane) {
   constexpr int NS = 20, NSG = 12, NF = 36;
+  constexpr int kSplit = 8;  // alpha-beta: lanes < 20 take replacements [0, 8) of their string
+  float acc[NS];
+#pragma unroll
+  for (int b = 0; b < NS; ++b) acc[b] = 0.f;
   if (lane < NS) {
     const int Ia = lane;
     constexpr unsigned kRows = (1u << NS) - 1u;  // lanes 0..19
-    float acc[NS];
     // alpha-alpha: A[Ia][b] = sum_J Hs[Ia][J] c[J][b].  The vectors are symmetric under the spin
     // flip (c[a][b] = c[b][a]: Phi is, and the spin-free operator commutes with the flip), so the
     // beta-beta part is A^T: row Ia of A goes through `out` and comes back as column Ia.
-#pragma unroll
-    for (int b = 0; b < NS; ++b) acc[b] = 0.f;
 #pragma unroll 4
     for (int J = 0; J < NS; ++J) {
       const float hj = ws.Hs[Ia * NS + J];
@@ -670,37 +678,61 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
         acc[4 * q + 3] += out[(4 * q + 3) * NS + Ia] + (dha + dv.w + (jab[4 * q + 3] - jz)) * cv.w;
       }
     }
-    __syncwarp(kRows);  // every column read before a row of out is written again
-    // alpha-beta: the 12 replacements into Ia, register tiles of W and C rows
-#pragma unroll 1
-    for (int u = 0; u < NSG; ++u) {
-      const int e = Ia * NSG + u;
-      const int pq = tb.pq[e], Ja = tb.J[e];
-      const float su = (float)tb.sg[e];
-      float wr[NF], cr[NS];
-      const float4* wrow = reinterpret_cast<const float4*>(ws.Wt + pq * NF);
-#pragma unroll
-      for (int q = 0; q < NF / 4; ++q) {
-        const float4 v = wrow[q];
-        wr[4 * q] = v.x;
-        wr[4 * q + 1] = v.y;
-        wr[4 * q + 2] = v.z;
-        wr[4 * q + 3] = v.w;
-      }
-      const float4* crow = reinterpret_cast<const float4*>(c + Ja * NS);
-#pragma unroll
-      for (int q = 0; q < NS / 4; ++q) {
-        const float4 v = crow[q];
-        cr[4 * q] = su * v.x;
-        cr[4 * q + 1] = su * v.y;
-        cr[4 * q + 2] = su * v.z;
-        cr[4 * q + 3] = su * v.w;
-      }
-      ab_terms(std::make_integer_sequence<int, NS * NSG>{}, acc, wr, cr);
-    }
-    float4* orow = reinterpret_cast<float4*>(out + Ia * NS);
+  }
+  __syncwarp();  // every column of out read before lanes write rows of it again
+  // alpha-beta: the 12 replacements into each string Ia, register tiles of W and C rows, on all
+  // 32 lanes: lane Ia < 20 takes replacements [0, 8) of string Ia into its row; lane 20 + j takes
+  // replacements [8, 12) of string j (first) and of string 12 + j (then, for j < 8), and passes
+  // each partial row to its owner through `out` (row Ia is written by exactly one such lane).
+  const int j = lane - NS;
+  auto flush = [&](int row) {
+    float4* orow = reinterpret_cast<float4*>(out + row * NS);
 #pragma unroll
     for (int q = 0; q < NS / 4; ++q) orow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+#pragma unroll
+    for (int b = 0; b < NS; ++b) acc[b] = 0.f;
+  };
+#pragma unroll 1
+  for (int it = 0; it < kSplit; ++it) {
+    int Ia = lane, u = it;
+    if (lane >= NS) {
+      if (it == NSG - kSplit) flush(j);  // the first string's partial row is complete
+      Ia = (it < NSG - kSplit) ? j : ((j < NS - NSG) ? NSG + j : 0);  // lanes 28..31: unused second pass
+      u = kSplit + (it % (NSG - kSplit));
+    }
+    const int e = Ia * NSG + u;
+    const int pq = tb.pq[e], Ja = tb.J[e];
+    const float su = (float)tb.sg[e];
+    float wr[NF], cr[NS];
+    const float4* wrow = reinterpret_cast<const float4*>(ws.Wt + pq * NF);
+#pragma unroll
+    for (int q = 0; q < NF / 4; ++q) {
+      const float4 v = wrow[q];
+      wr[4 * q] = v.x;
+      wr[4 * q + 1] = v.y;
+      wr[4 * q + 2] = v.z;
+      wr[4 * q + 3] = v.w;
+    }
+    const float4* crow = reinterpret_cast<const float4*>(c + Ja * NS);
+#pragma unroll
+    for (int q = 0; q < NS / 4; ++q) {
+      const float4 v = crow[q];
+      cr[4 * q] = su * v.x;
+      cr[4 * q + 1] = su * v.y;
+      cr[4 * q + 2] = su * v.z;
+      cr[4 * q + 3] = su * v.w;
+    }
+    ab_terms(std::make_integer_sequence<int, NS * NSG>{}, acc, wr, cr);
+  }
+  if (lane >= NS && j < NS - NSG) flush(NSG + j);  // second string's partial row (lanes 20..27)
+  __syncwarp();
+  if (lane < NS) {  // own row + the partial row of replacements [8, 12)
+    float4* orow = reinterpret_cast<float4*>(out + lane * NS);
+#pragma unroll
+    for (int q = 0; q < NS / 4; ++q) {
+      const float4 v = orow[q];
+      orow[q] = make_float4(acc[4 * q] + v.x, acc[4 * q + 1] + v.y, acc[4 * q + 2] + v.z, acc[4 * q + 3] + v.w);
+    }
   }
   __syncwarp();
 }
@@ -983,7 +1015,7 @@ __device__ __noinline__ int small_eig_rr(const DF* G, int k, DF shift, float* y,
 
 // Solve space s of the class list in `a` (s: index in that list) with the warp's state `ws`.
 template <int K>
-__device__ void solve_one(const Tabs<K>& tb, const CtaSmem& cs, WarpState<K>& ws,
+__device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws,
                           const SolveArgs& a, const float* __restrict__ W32, const float* __restrict__ guess_in,
                           float* __restrict__ guess_out, int64_t s, int lane) {
   using D = Dim<K>;
@@ -1605,16 +1637,17 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaSmem& cs, WarpState<K>& ws
 // ---- kernels --------------------------------------------------------------------------------------
 
 template <int K>
-__global__ void __launch_bounds__(32 * WARPS) solve_class_kernel(SolveArgs a, const float* __restrict__ W32,
+__global__ void __maxnreg__(kMaxRegs) solve_class_kernel(SolveArgs a, const float* __restrict__ W32,
                                                                   const float* __restrict__ guess_in,
                                                                   float* __restrict__ guess_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CtaSmem& cs = *reinterpret_cast<CtaSmem*>(smem_raw);
+  CtaTabs& cs = *reinterpret_cast<CtaTabs*>(smem_raw);
+  AnyWarpState* wst = reinterpret_cast<AnyWarpState*>(smem_raw + kTabsBytes);
   build_all_tabs(cs);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpState<K>& ws = state<K>(cs.w[warp]);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  WarpState<K>& ws = state<K>(wst[warp]);
 #pragma unroll 1
-  for (int64_t s = (int64_t)blockIdx.x * WARPS + warp; s < a.nspaces; s += (int64_t)gridDim.x * WARPS)
+  for (int64_t s = (int64_t)blockIdx.x * nw + warp; s < a.nspaces; s += (int64_t)gridDim.x * nw)
     solve_one<K>(tabs<K>(cs), cs, ws, a, W32, guess_in, guess_out, a.items ? a.items[s] : s, lane);
 }
 
@@ -1626,9 +1659,10 @@ struct PersistentArgs {
 };
 
 // One queue over every size class: items [0, n3) are 6e6o spaces, then 4e4o, then 2e2o.
-__global__ void __maxnreg__(128) solve_persistent_kernel(PersistentArgs p) {
+__global__ void __maxnreg__(kMaxRegs) solve_persistent_kernel(PersistentArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CtaSmem& cs = *reinterpret_cast<CtaSmem*>(smem_raw);
+  CtaTabs& cs = *reinterpret_cast<CtaTabs*>(smem_raw);
+  AnyWarpState* wst = reinterpret_cast<AnyWarpState*>(smem_raw + kTabsBytes);
   build_all_tabs(cs);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n3 = p.cls[3].nspaces, n2 = p.cls[2].nspaces, n1 = p.cls[1].nspaces;
@@ -1647,17 +1681,17 @@ __global__ void __maxnreg__(128) solve_persistent_kernel(PersistentArgs p) {
       const int64_t it = (int64_t)item;
       if (it < n3) {
         const SolveArgs& a = p.cls[3];
-        solve_one<3>(cs.t3, cs, state<3>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+        solve_one<3>(cs.t3, cs, state<3>(wst[warp]), a, p.W32, static_cast<const float*>(a.guess),
                      static_cast<float*>(a.root_out), a.items ? a.items[it] : it, lane);
       } else if (it < n3 + n2) {
         const SolveArgs& a = p.cls[2];
         const int64_t l = it - n3;
-        solve_one<2>(cs.t2, cs, state<2>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+        solve_one<2>(cs.t2, cs, state<2>(wst[warp]), a, p.W32, static_cast<const float*>(a.guess),
                      static_cast<float*>(a.root_out), a.items ? a.items[l] : l, lane);
       } else {
         const SolveArgs& a = p.cls[1];
         const int64_t l = it - n3 - n2;
-        solve_one<1>(cs.t1, cs, state<1>(cs.w[warp]), a, p.W32, static_cast<const float*>(a.guess),
+        solve_one<1>(cs.t1, cs, state<1>(wst[warp]), a, p.W32, static_cast<const float*>(a.guess),
                      static_cast<float*>(a.root_out), a.items ? a.items[l] : l, lane);
       }
     }
@@ -1665,19 +1699,18 @@ __global__ void __maxnreg__(128) solve_persistent_kernel(PersistentArgs p) {
 }
 
 template <typename Kern>
-cudaError_t grid_for(Kern kern, int ctas_per_sm, int* grid) {
-  const size_t smem = sizeof(CtaSmem);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t grid_for(Kern kern, int warps, int* grid) {
+  const size_t smem = cta_smem_bytes(warps);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cta_smem_bytes(kMaxWarps));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WARPS, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   *grid = sms * per_sm;
   return cudaSuccess;
 }
@@ -1685,30 +1718,31 @@ cudaError_t grid_for(Kern kern, int ctas_per_sm, int* grid) {
 }  // namespace
 
 cudaError_t launch_solve_warp(int k, const SolveArgs& a, const float* W32, const float* guess_in, float* guess_out,
-                              int ctas_per_sm, cudaStream_t st) {
+                              int warps, cudaStream_t st) {
   if (a.nspaces <= 0) return cudaSuccess;
+  if (warps < 1 || warps > kMaxWarps) warps = kMaxWarps;
   int grid = 0;
   cudaError_t e;
-  const int64_t need = (a.nspaces + WARPS - 1) / WARPS;
+  const int64_t need = (a.nspaces + warps - 1) / warps;
   switch (k) {
-    case 1: e = grid_for(solve_class_kernel<1>, ctas_per_sm, &grid); break;
-    case 2: e = grid_for(solve_class_kernel<2>, ctas_per_sm, &grid); break;
-    case 3: e = grid_for(solve_class_kernel<3>, ctas_per_sm, &grid); break;
+    case 1: e = grid_for(solve_class_kernel<1>, warps, &grid); break;
+    case 2: e = grid_for(solve_class_kernel<2>, warps, &grid); break;
+    case 3: e = grid_for(solve_class_kernel<3>, warps, &grid); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
   if (grid > need) grid = (int)need;
-  const size_t smem = sizeof(CtaSmem);
+  const size_t smem = cta_smem_bytes(warps);
   switch (k) {
-    case 1: solve_class_kernel<1><<<grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out); break;
-    case 2: solve_class_kernel<2><<<grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out); break;
-    default: solve_class_kernel<3><<<grid, 32 * WARPS, smem, st>>>(a, W32, guess_in, guess_out); break;
+    case 1: solve_class_kernel<1><<<grid, 32 * warps, smem, st>>>(a, W32, guess_in, guess_out); break;
+    case 2: solve_class_kernel<2><<<grid, 32 * warps, smem, st>>>(a, W32, guess_in, guess_out); break;
+    default: solve_class_kernel<3><<<grid, 32 * warps, smem, st>>>(a, W32, guess_in, guess_out); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve_persistent(const SolveArgs* cls, const float* W32, unsigned long long* queue, int chunk,
-                                    int ctas_per_sm, cudaStream_t st) {
+                                    int warps, cudaStream_t st) {
   PersistentArgs p{};
   int64_t total = 0;
   for (int k = 1; k <= 3; ++k) {
@@ -1716,17 +1750,18 @@ cudaError_t launch_solve_persistent(const SolveArgs* cls, const float* W32, unsi
     total += cls[k].nspaces;
   }
   if (total <= 0) return cudaSuccess;
+  if (warps < 1 || warps > kMaxWarps) warps = kMaxWarps;
   p.W32 = W32;
   p.queue = queue;
   p.chunk = chunk < 1 ? 1 : chunk;
   int grid = 0;
-  cudaError_t e = grid_for(solve_persistent_kernel, ctas_per_sm, &grid);
+  cudaError_t e = grid_for(solve_persistent_kernel, warps, &grid);
   if (e != cudaSuccess) return e;
-  const int64_t need = (total + WARPS - 1) / WARPS;
+  const int64_t need = (total + warps - 1) / warps;
   if (grid > need) grid = (int)need;
   e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  solve_persistent_kernel<<<grid, 32 * WARPS, sizeof(CtaSmem), st>>>(p);
+  solve_persistent_kernel<<<grid, 32 * warps, cta_smem_bytes(warps), st>>>(p);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ class QFlowError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("diis", C.c_int32), ("guess", C.c_int32), ("schedule", C.c_int32), ("graph", C.c_int32),
-                ("form", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("form", C.c_int32), ("warps", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 _lib = None
@@ -177,7 +177,7 @@ class Flow:
 
     def __init__(self, h, eri, nocc: int, spaces, precision: str = "fp64", max_iter: int | None = None,
                  tol: float | None = None, guess: str = "phi", diis: int = 0, schedule: str = "auto",
-                 graph: bool = True, form: str = "ses"):
+                 graph: bool = True, form: str = "ses", warps: int = 0):
         h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
         self.n, self.nocc = h.shape[0], nocc
         self.nvir = self.n - nocc
@@ -192,6 +192,7 @@ class Flow:
         opt.schedule = {"auto": 0, "per_class": 1, "persistent": 2}[schedule]
         opt.graph = int(graph)
         opt.form = {"ses": 0, "ducc": 1}[form]
+        opt.warps = warps
         self._h = C.c_void_p()
         code = lib().qflow_init(C.byref(self._h), _ptr(h), _ptr(eri), self.n, nocc, _ptr(sp), len(sp), C.byref(opt))
         self.init_status = _check(code, "qflow_init")
@@ -296,10 +297,10 @@ class Flow:
 
     def schedule(self) -> dict:
         p, ch, ct, gr, nc = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-        ms = (C.c_float * 8)()
+        ms = (C.c_float * 8)()  # QFLOW_TUNE_MAX
         _check(lib().qflow_schedule(self._h, C.byref(p), C.byref(ch), C.byref(ct), C.byref(gr), ms, C.byref(nc)),
                "qflow_schedule")
-        return {"persistent": bool(p.value), "chunk": ch.value, "ctas_per_sm": ct.value, "graph": bool(gr.value),
+        return {"persistent": bool(p.value), "chunk": ch.value, "warps_per_cta": ct.value, "graph": bool(gr.value),
                 "candidate_ms": [float(ms[i]) for i in range(nc.value)]}
 
     def stream(self) -> int:

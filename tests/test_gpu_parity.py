@@ -247,6 +247,8 @@ def test_schedules_and_graph_replay_agree(qf):
     runs = {}
     for name, kw in [("per_class", dict(schedule="per_class", graph=False)),
                      ("persistent", dict(schedule="persistent", graph=False)),
+                     ("persistent_12_warps", dict(schedule="persistent", graph=False, warps=12)),
+                     ("per_class_7_warps", dict(schedule="per_class", graph=False, warps=7)),
                      ("graph", dict(schedule="persistent", graph=True))]:
         f = qf.Flow(h, g, 6, sp, precision="mixed", **kw)
         per = []
@@ -258,10 +260,11 @@ def test_schedules_and_graph_replay_agree(qf):
         runs[name] = (np.array(per), f.amplitudes(), f.schedule())
         f.close()
     ref = runs["per_class"]
-    for name in ("persistent", "graph"):
-        assert np.array_equal(runs[name][0], ref[0])
-        assert np.array_equal(runs[name][1][1], ref[1][1])
+    for name in ("persistent", "persistent_12_warps", "per_class_7_warps", "graph"):
+        assert np.array_equal(runs[name][0], ref[0]), name
+        assert np.array_equal(runs[name][1][1], ref[1][1]), name
     assert runs["graph"][2]["graph"] and runs["graph"][2]["persistent"]
+    assert runs["persistent_12_warps"][2]["warps_per_cta"] == 12 and runs["per_class_7_warps"][2]["warps_per_cta"] == 7
 
 
 def test_autotuner_times_candidates(qf):
@@ -272,6 +275,6 @@ def test_autotuner_times_candidates(qf):
     assert f.schedule()["candidate_ms"] == []     # calibration happens at the second sweep
     f.sweep()
     sch = f.schedule()
-    assert len(sch["candidate_ms"]) == 5 and min(sch["candidate_ms"]) > 0
-    assert sch["persistent"] and sch["chunk"] in (1, 2, 4, 8, 16)
+    assert len(sch["candidate_ms"]) == 8 and min(sch["candidate_ms"]) > 0
+    assert sch["persistent"] and sch["chunk"] in (1, 2, 4, 8) and sch["warps_per_cta"] in (12, 15)
     f.close()
