@@ -125,7 +125,10 @@ typedef struct {
   int32_t form;               /* qflow_form: the downfolding form (default QFLOW_FORM_SESCC)  */
   int32_t warps;              /* mixed precision: spaces (warps) per CTA of the solver, 1..15;
                                  0 = chosen by the autotuner (QFLOW_SCHED_AUTO) or 15        */
-  int32_t reserved[4];
+  int32_t chunk;              /* mixed precision, persistent queue: consecutive spaces a warp
+                                 takes per fetch, 1..16; 0 = chosen by the autotuner
+                                 (QFLOW_SCHED_AUTO) or 1                                     */
+  int32_t reserved[3];
 } qflow_options;
 
 /* Fill *opt with the defaults above for the given precision. */
@@ -249,7 +252,10 @@ int qflow_space_order(qflow_handle hnd, int64_t* perm);
 int qflow_space_stats(qflow_handle hnd, int32_t* iterations, int32_t* status);
 
 /* The dressed integrals of the current pool (what the next sweep will use): e0 (1),
- * F[n*n], W[n^4] copied to host buffers (any may be NULL). */
+ * F[n*n], W[n^4] copied to host buffers (any may be NULL).  With QFLOW_PREC_MIXED the vvvv
+ * block of W is dressed only where at most three of its four virtual indices differ (every
+ * element a (k, k) space with k <= 3 reads); its other elements hold the T1-transformed
+ * integrals.  qflow_dress_device dresses every element. */
 int qflow_dressed(qflow_handle hnd, double* e0, double* F, double* W);
 
 /* Timing of the last sweep from CUDA events recorded on the handle's stream:

@@ -13,6 +13,8 @@
 //   2. f~ = h~ + sum_k [2 g~_pqkk - g~_pkkq], E~ = <Phi|H~|Phi>.
 //   3. T2 through its connected contractions with H~ (one- and two-body parts of [H~, T2];
 //      the quadratic term 1/2 [[H~,T2],T2] only reaches the doubly excited (vo|vo) block).
+//      The mixed path adds the vvvv block's term only where at most three of the four
+//      virtual indices differ: every element a (k, k) space with k <= 3 reads.
 // Index names: occupied i j k l m n, virtual a b e f (absolute index nocc + a).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -553,6 +555,7 @@ struct Work {
   double *ht, *foo, *fvv, *wo, *r1, *r2, *A, *B, *Cq, *D, *t2f;  // A..D, t2f hold T values
   double* epart;  // energy partials
   float* acc;     // mixed path: FP32 GEMM results (v^3 o floats)
+  float* f32;     // mixed path: FP32 copies of f~ (n^2), Foo (o^2), Fvv (v^2) for the FP32 finishing sums
   int* err;       // mixed path: set by a GEMM tile that gave up waiting
   float* arena;   // mixed path: packed GEMM operands and partial products
 };
@@ -572,12 +575,15 @@ size_t carve(void* base, int n, int o, Work* w, bool mixed = false) {
     off += ((sizes[k] * sizeof(double) + 255) / 256) * 256;
   }
   w->acc = nullptr;
+  w->f32 = nullptr;
   w->err = nullptr;
   w->arena = nullptr;
   if (mixed && v > 0 && o > 0) {
     const size_t na = (size_t)v * v * v * o > (size_t)o * o * v * v ? (size_t)v * v * v * o : (size_t)o * o * v * v;
     if (base) w->acc = reinterpret_cast<float*>(static_cast<char*>(base) + off);
     off += ((na * sizeof(float) + 255) / 256) * 256;
+    if (base) w->f32 = reinterpret_cast<float*>(static_cast<char*>(base) + off);
+    off += (((size_t)n * n + (size_t)o * o + (size_t)v * v) * sizeof(float) + 255) / 256 * 256;
     if (base) w->err = reinterpret_cast<int*>(static_cast<char*>(base) + off);
     off += 256;
     if (base) w->arena = reinterpret_cast<float*>(static_cast<char*>(base) + off);
@@ -611,9 +617,9 @@ size_t dress_workspace_bytes_mixed(int n, int nocc) {
 
 int dress_launch_count(int n, int nocc, bool mixed) {
   // copy, 4 T1 passes, h~, f~, 2 energy, u, small blocks, finalize; T2 terms: 7 SIMT kernels
-  // (FP64) or 2 FP32 copies + 29 operand packs + 8 GEMM launches + 3 finalize kernels + error
-  // check (mixed)
-  return (n - nocc > 0 && nocc > 0) ? (mixed ? 12 + 43 : 12 + 7) : 5;
+  // (FP64) or 2 FP32 copies + 35 operand packs + 10 GEMM launches + FP32 Fock copies + 4 finalize
+  // kernels + error check (mixed)
+  return (n - nocc > 0 && nocc > 0) ? (mixed ? 12 + 53 : 12 + 7) : 5;
 }
 
 namespace {
@@ -689,6 +695,29 @@ struct StoreRows {
       if (j < cnt) q[j] = v[j];
   }
 };
+
+// Woooo (mixed path): rows (k, l), cols (i, j), k = (e, f):  sum_ef g~_kelf t_ij^ef, split K
+// into kWoSplit partial maps summed in order onto the FP64 base g~_kilj by k_wo_fin
+constexpr int kWoSplit = 8;
+struct LWOA {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const { return c.G(r / c.o, c.o + k / c.v, r % c.o, c.o + k % c.v); }
+};
+struct LWOB {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const { return c.T(col / c.o, col % c.o, k / c.v, k % c.v); }
+};
+__global__ void k_wo_fin(const double* __restrict__ W, const float* __restrict__ part, double* __restrict__ wo,
+                         Dims d) {
+  const int o = d.o, oo = o * o;
+  const int m_all = oo * oo;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;  // wo index [k i l j]
+  if (x >= m_all) return;
+  const int k = x / (o * oo), i = (x / oo) % o, l = (x / o) % o, j = x % o;
+  float v = 0.f;
+  for (int z = 0; z < kWoSplit; ++z) v += part[(size_t)z * m_all + (k * o + l) * oo + i * o + j];
+  wo[x] = W[gi(d, k, i, l, j)] + (double)v;
+}
 
 // r2, ladder + oooo: rows (i, j), cols (a, b), k = (e, f) then (m, n)
 struct LR2G1A {
@@ -822,14 +851,20 @@ struct LV4B {
     return c.G(k / c.o, c.o + col / c.v, k % c.o, c.o + col % c.v);
   }
 };
+// (the mixed path's flows only read elements with at most three distinct virtual indices among
+// a, e, b, f: the store skips the others, about 94 % of the block's read-modify-writes at v = 100)
 struct StoreV4 {  // rows (e, f), cols (a, b): consecutive lanes write consecutive f
   double* W;
   int n, o, v;
+  __device__ static bool read3(int a, int e, int b, int f) {  // at most three distinct indices
+    return a == e || a == b || a == f || e == b || e == f || b == f;
+  }
   // all 32 old values are loaded before any is written back, so the read-modify-writes do not
   // wait on one another (the addresses are distinct)
   __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
     const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
-    const size_t base = (size_t)(o + r / v) * n2 + (size_t)(o + r % v);
+    const int e = r / v, f = r % v;
+    const size_t base = (size_t)(o + e) * n2 + (size_t)(o + f);
     const int a0 = col / v, b0 = col % v;
     double old[32];
     {
@@ -837,7 +872,7 @@ struct StoreV4 {  // rows (e, f), cols (a, b): consecutive lanes write consecuti
       size_t x = base + (size_t)(o + a) * n3 + (size_t)(o + b) * n1;
 #pragma unroll
       for (int t = 0; t < 32; ++t) {
-        old[t] = (t < cnt) ? W[x] : 0.0;
+        old[t] = (t < cnt && read3(a, e, b, f)) ? W[x] : 0.0;
         x += n1;
         if (++b == v) {
           b = 0;
@@ -850,7 +885,7 @@ struct StoreV4 {  // rows (e, f), cols (a, b): consecutive lanes write consecuti
     size_t x = base + (size_t)(o + a) * n3 + (size_t)(o + b) * n1;
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
-      if (t < cnt) W[x] = old[t] + (double)val[t];
+      if (t < cnt && read3(a, e, b, f)) W[x] = old[t] + (double)val[t];
       x += n1;
       if (++b == v) {
         b = 0;
@@ -983,6 +1018,36 @@ struct StoreOVO {
   }
 };
 
+// oovo, the O(o v) terms, k = (n, e):
+//   rows (m, i), cols (b, j), k twice:  sum_ne g~_mine u_jn^be  - sum_ne g~_meni t_jn^be
+//   rows (m, j), cols (b, i):          -sum_ne g~_menj t_in^eb
+// (each into a row-major [rows][o v] buffer, added by k_oovo_fin)
+struct LOV2A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const {
+    const int ov = c.o * c.v, m = r / c.o, i = r % c.o;
+    if (k < ov) return c.G(m, i, k / c.v, c.o + k % c.v);
+    const int kk = k - ov;
+    return -c.G(m, c.o + kk % c.v, kk / c.v, i);
+  }
+};
+struct LOV2B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const {
+    const int ov = c.o * c.v, b = col / c.o, j = col % c.o;
+    const int kk = k < ov ? k : k - ov, nn = kk / c.v, e = kk % c.v;
+    return k < ov ? c.U(j, nn, b, e) : c.T(j, nn, b, e);
+  }
+};
+struct LOV3A {
+  TcCtx c;
+  __device__ float operator()(int r, int k) const { return -c.G(r / c.o, c.o + k % c.v, k / c.v, r % c.o); }
+};
+struct LOV3B {
+  TcCtx c;
+  __device__ float operator()(int col, int k) const { return c.T(col % c.o, k / c.v, k % c.v, col / c.o); }
+};
+
 // vvvo: acc[a e b i] from three GEMMs
 struct LVV1A {  // rows (a, e), k = (m, f) twice: g[m F A E], -g[m E A F]
   TcCtx c;
@@ -1041,8 +1106,17 @@ struct StoreVV {  // each job its own buffer
 
 // r2 = bare vo|vo + GEMM parts (ladder/oooo in acc, four ring maps in part[0..3]) + the O(v)
 // Fock terms (FP32), added in FP64
-__global__ void k_r2_fin(const double* __restrict__ W, const float* __restrict__ t2, const double* __restrict__ foo,
-                         const double* __restrict__ fvv, const float* __restrict__ acc, const float* __restrict__ part,
+// FP32 copies of f~, Foo and Fvv (the finishing kernels' O(v) sums multiply them with FP32 t2;
+// converting once keeps those loops off the FP64 pipe, with the same rounded values).
+__global__ void k_fock_f32(const double* __restrict__ F, const double* __restrict__ foo, const double* __restrict__ fvv,
+                           float* __restrict__ out, Dims d) {
+  const int nf = d.n * d.n, no = d.o * d.o, nv = d.v * d.v;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nf + no + nv; x += gridDim.x * blockDim.x)
+    out[x] = (float)(x < nf ? F[x] : (x < nf + no ? foo[x - nf] : fvv[x - nf - no]));
+}
+
+__global__ void k_r2_fin(const double* __restrict__ W, const float* __restrict__ t2, const float* __restrict__ foo,
+                         const float* __restrict__ fvv, const float* __restrict__ acc, const float* __restrict__ part,
                          double* __restrict__ r2, Dims d) {
   const size_t m_all = (size_t)d.o * d.o * d.v * d.v;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -1051,15 +1125,15 @@ __global__ void k_r2_fin(const double* __restrict__ W, const float* __restrict__
   const int a = (int)((x / d.v) % d.v), b = (int)(x % d.v);
   float v = acc[x] + part[x] + part[m_all + x] + part[2 * m_all + x] + part[3 * m_all + x];
   for (int e = 0; e < d.v; ++e)
-    v += (float)fvv[b * d.v + e] * t2[ti(d, i, j, a, e)] + (float)fvv[a * d.v + e] * t2[ti(d, i, j, e, b)];
+    v += fvv[b * d.v + e] * t2[ti(d, i, j, a, e)] + fvv[a * d.v + e] * t2[ti(d, i, j, e, b)];
   for (int m = 0; m < d.o; ++m)
-    v -= (float)foo[m * d.o + j] * t2[ti(d, i, m, a, b)] + (float)foo[m * d.o + i] * t2[ti(d, m, j, a, b)];
+    v -= foo[m * d.o + j] * t2[ti(d, i, m, a, b)] + foo[m * d.o + i] * t2[ti(d, m, j, a, b)];
   r2[x] = W[gi(d, d.o + a, i, d.o + b, j)] + (double)v;
 }
 
 // oovo: the GEMM's v^2 term plus the O(v) and O(ov) terms, onto the FP64 base and its mirror
-__global__ void k_oovo_fin(double* __restrict__ W, const float* __restrict__ G, const double* __restrict__ F,
-                           const float* __restrict__ t2, const float* __restrict__ part, int nsplit, Dims d) {
+__global__ void k_oovo_fin(double* __restrict__ W, const float* __restrict__ F, const float* __restrict__ t2,
+                           const float* __restrict__ part, int nsplit, Dims d) {
   const size_t m_all = (size_t)d.o * d.o * d.v * d.o;
   const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (x >= m_all) return;
@@ -1068,20 +1142,17 @@ __global__ void k_oovo_fin(double* __restrict__ W, const float* __restrict__ G, 
   const int B_ = d.o + b;
   float v = 0.f;
   for (int z = 0; z < nsplit; ++z) v += part[(size_t)z * m_all + x];  // split-K partials, in order
-  for (int e = 0; e < d.v; ++e) {
-    const int E_ = d.o + e;
-    v += (float)F[m * d.n + E_] * t2[ti(d, i, j, e, b)];
-    for (int nn = 0; nn < d.o; ++nn)
-      v += G[gi(d, m, i, nn, E_)] * Ut(t2, d, j, nn, b, e) - G[gi(d, m, E_, nn, i)] * t2[ti(d, j, nn, b, e)] -
-           G[gi(d, m, E_, nn, j)] * t2[ti(d, i, nn, e, b)];
-  }
+  // the O(o v) maps: [m i][b j] (same order as x) and [m j][b i]
+  v += part[(size_t)nsplit * m_all + x];
+  v += part[(size_t)(nsplit + 1) * m_all + (((size_t)m * d.o + j) * d.v + b) * d.o + i];
+  for (int e = 0; e < d.v; ++e) v += F[m * d.n + d.o + e] * t2[ti(d, i, j, e, b)];
   const double w = W[gi(d, m, i, B_, j)] + (double)v;
   W[gi(d, m, i, B_, j)] = w;
   W[gi(d, B_, j, m, i)] = w;
 }
 
 // vvvo: GEMM part minus the f~ term, onto the FP64 base and its mirror
-__global__ void k_vvvo_fin(double* __restrict__ W, const double* __restrict__ F, const float* __restrict__ t2,
+__global__ void k_vvvo_fin(double* __restrict__ W, const float* __restrict__ F, const float* __restrict__ t2,
                            const float* __restrict__ acc, const float* __restrict__ p1, const float* __restrict__ p2,
                            Dims d) {
   const size_t m_all = (size_t)d.v * d.v * d.v * d.o;
@@ -1091,7 +1162,7 @@ __global__ void k_vvvo_fin(double* __restrict__ W, const double* __restrict__ F,
   const int b = (int)((x / d.o) % d.v), i = (int)(x % d.o);
   const int A_ = d.o + a, E_ = d.o + e, B_ = d.o + b;
   float v = acc[x] + p1[x] + p2[x];
-  for (int m = 0; m < d.o; ++m) v -= (float)F[m * d.n + E_] * t2[ti(d, m, i, a, b)];
+  for (int m = 0; m < d.o; ++m) v -= F[m * d.n + E_] * t2[ti(d, m, i, a, b)];
   const double w = W[gi(d, A_, E_, B_, i)] + (double)v;
   W[gi(d, A_, E_, B_, i)] = w;
   W[gi(d, B_, i, A_, E_)] = w;
@@ -1181,6 +1252,22 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
   do {                                  \
     if (e == cudaSuccess) e = (x);      \
   } while (0)
+  // Woooo first: the ladder + oooo map reads it
+  {
+    ar.reset();
+    Op a, b;
+    QF_TRY(pack_op(LWOA{c}, oo, vv, kTileM, ar, &a, st));
+    QF_TRY(pack_op(LWOB{c}, oo, vv, 32, ar, &b, st));
+    float* wp = ar.take((size_t)oo * oo * kWoSplit);
+    tc::PackedJobs<StoreRows> js{};
+    for (int z = 0; z < kWoSplit; ++z) js.j[z] = job(a, b, StoreRows{wp + (run ? (size_t)oo * oo * z : 0), oo}, z, kWoSplit);
+    js.count = kWoSplit;
+    QF_TRY((run_jobs<32>(js, ar, err, st)));
+    if (run && e == cudaSuccess) {
+      k_wo_fin<<<blocks_for((size_t)oo * oo), TPB, 0, st>>>(W, wp, w.wo, d);
+      e = cudaGetLastError();
+    }
+  }
   // ring intermediates: one launch of four jobs sharing packed operands
   {
     ar.reset();
@@ -1232,12 +1319,15 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
     js.count = 4;
     QF_TRY((run_jobs<64>(js, ar, err, st)));
     if (run && e == cudaSuccess) {
-      k_r2_fin<<<blocks_for(n_r2), TPB, 0, st>>>(W, t2, w.foo, w.fvv, acc, part, w.r2, d);
+      const float* f32 = w.f32;
+      k_fock_f32<<<blocks_for((size_t)d.n * d.n + oo + vv), TPB, 0, st>>>(F, w.foo, w.fvv, w.f32, d);
+      k_r2_fin<<<blocks_for(n_r2), TPB, 0, st>>>(W, t2, f32 + (size_t)d.n * d.n, f32 + (size_t)d.n * d.n + oo, acc, part,
+                                                  w.r2, d);
       e = cudaGetLastError();
     }
   }
   // blocks written in place (their bases are read from W by the store of their single job)
-  {
+  {  // vvvv: the product on the tensor cores, stored only where (k, k) spaces read it
     ar.reset();
     Op a, b;
     QF_TRY(pack_op(LV4B{c}, vv, oo, kTileM, ar, &a, st));
@@ -1275,14 +1365,24 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
     QF_TRY(pack_op(LOVOA{c}, ov, vv, kTileM, ar, &a, st));
     QF_TRY(pack_op(LOVOB{c}, oo, vv, 32, ar, &b, st));
     const size_t n_ovo = (size_t)oo * v * o;
-    part = ar.take(n_ovo * kOvoSplit);
+    part = ar.take(n_ovo * (kOvoSplit + 2));  // + the two O(o v) maps
     tc::PackedJobs<StoreOVO> js{};
     for (int z = 0; z < kOvoSplit; ++z) js.j[z] = job(a, b, StoreOVO{part + (run ? n_ovo * z : 0), o, v}, z, kOvoSplit);
     js.count = kOvoSplit;
     QF_TRY((run_jobs<32>(js, ar, err, st)));
+    Op a2, b2, a3, b3;
+    QF_TRY(pack_op(LOV2A{c}, oo, 2 * ov, kTileM, ar, &a2, st));
+    QF_TRY(pack_op(LOV2B{c}, ov, 2 * ov, 32, ar, &b2, st));
+    QF_TRY(pack_op(LOV3A{c}, oo, ov, kTileM, ar, &a3, st));
+    QF_TRY(pack_op(LOV3B{c}, ov, ov, 32, ar, &b3, st));
+    tc::PackedJobs<StoreRows> jr{};
+    jr.j[0] = job(a2, b2, StoreRows{part + (run ? n_ovo * kOvoSplit : 0), ov});
+    jr.j[1] = job(a3, b3, StoreRows{part + (run ? n_ovo * (kOvoSplit + 1) : 0), ov});
+    jr.count = 2;
+    QF_TRY((run_jobs<32>(jr, ar, err, st)));
   }
   if (run && e == cudaSuccess) {
-    k_oovo_fin<<<blocks_for((size_t)oo * v * o), TPB, 0, st>>>(W, G, F, t2, part, kOvoSplit, d);
+    k_oovo_fin<<<blocks_for((size_t)oo * v * o), TPB, 0, st>>>(W, w.f32, t2, part, kOvoSplit, d);
     e = cudaGetLastError();
   }
   // vvvo: three output maps, one launch; each job its own buffer, summed by k_vvvo_fin
@@ -1306,7 +1406,7 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
     // 128-column tiles: half the re-reads of the v^2-row operand from L2
     QF_TRY((run_jobs<128>(js, ar, err, st)));
     if (run && e == cudaSuccess) {
-      k_vvvo_fin<<<blocks_for(n_vvvo), TPB, 0, st>>>(W, F, t2, acc, p1, p2, d);
+      k_vvvo_fin<<<blocks_for(n_vvvo), TPB, 0, st>>>(W, w.f32, t2, acc, p1, p2, d);
       e = cudaGetLastError();
     }
   }
@@ -1349,8 +1449,10 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
   if (v > 0 && o > 0) {
     // U lives in the r2 slot until the doubles residual is written there
     k_make_u<<<blocks_for(o * o * v * v), TPB, 0, st>>>(t2, w.r2, d);
-    k_small_blocks<<<(unsigned)(o * o + v * v + v * o + o * o * o * o), TPB, 0, st>>>(F, W, w.r2, t2, w.foo, w.fvv,
-                                                                                     w.r1, w.wo, d);
+    // the mixed path forms Woooo (a W block) on the tensor cores with its other T2 terms; the
+    // Fock-like blocks stay FP64 sums
+    const unsigned nsb = (unsigned)(o * o + v * v + v * o + (g32 ? 0 : o * o * o * o));
+    k_small_blocks<<<nsb, TPB, 0, st>>>(F, W, w.r2, t2, w.foo, w.fvv, w.r1, w.wo, d);
     if (g32) {  // contractions of the T2 terms in FP32 (mixed precision), bases kept in FP64
       float* t2f = reinterpret_cast<float*>(w.t2f);
       const unsigned gg = blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4);

@@ -201,6 +201,7 @@ struct qflow_ctx {
   double* energy = nullptr;
   int32_t *status = nullptr, *iters = nullptr;
   int32_t *own1 = nullptr, *own2 = nullptr;
+  uint8_t* owns = nullptr;  // [device slot]: 1 if the space there owns an amplitude
   qflow_space* spaces = nullptr;  // grouped by class, sorted within a class
   int64_t* sorted_index = nullptr;
   void* dwork = nullptr;
@@ -219,7 +220,7 @@ struct qflow_ctx {
   int64_t* rescue_items = nullptr;  // mixed path: positions of spaces the warp pass left unconverged
   unsigned long long* rescue_count = nullptr;  // and their count (device)
   // launch schedule of the mixed-precision solver: persistent queue or one launch per class
-  int sched_persistent = 1, sched_chunk = 4, sched_warps = 15;  // warps (spaces) per CTA
+  int sched_persistent = 1, sched_chunk = 1, sched_warps = 15;  // items per fetch, warps (spaces) per CTA
   bool tuned = false;
   int64_t sweeps = 0;  // sweeps run so far
   float tune_ms[QFLOW_TUNE_MAX] = {0};
@@ -266,7 +267,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_ctx(qflow_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->h, c->eri, c->pool, c->pool_new, c->e0, c->F, c->W, c->energy, c->status, c->iters,
-                  c->own1, c->own2, c->spaces, c->sorted_index, c->dwork, c->rwork, c->red};
+                  c->own1, c->own2, c->owns, c->spaces, c->sorted_index, c->dwork, c->rwork, c->red};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->guess)
@@ -364,6 +365,11 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     return QFLOW_ERR_ARG;
   }
   if (c->opt.warps > 0) c->sched_warps = c->opt.warps;
+  if (c->opt.chunk < 0 || c->opt.chunk > 16) {
+    delete c;
+    return QFLOW_ERR_ARG;
+  }
+  if (c->opt.chunk > 0) c->sched_chunk = c->opt.chunk;
   if (c->opt.form != QFLOW_FORM_SESCC && c->opt.form != QFLOW_FORM_DUCC) {
     delete c;
     return QFLOW_ERR_ARG;
@@ -414,6 +420,7 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
   if (e == cudaSuccess) e = dalloc(&c->iters, (size_t)std::max<int64_t>(nspaces, 1));
   if (e == cudaSuccess) e = dalloc(&c->own1, (size_t)c->n_t1);
   if (e == cudaSuccess) e = dalloc(&c->own2, (size_t)c->n_t2);
+  if (e == cudaSuccess) e = dalloc(&c->owns, (size_t)std::max<int64_t>(nspaces, 1));
   if (e == cudaSuccess) e = dalloc(&c->spaces, (size_t)std::max<int64_t>(nspaces, 1));
   if (e == cudaSuccess) e = dalloc(&c->sorted_index, (size_t)std::max<int64_t>(nspaces, 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->dwork, c->dwork_bytes);
@@ -458,6 +465,16 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     e = cudaMemcpyAsync(c->own1, pl.own1.data(), sizeof(int32_t) * pl.own1.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->own2, pl.own2.data(), sizeof(int32_t) * pl.own2.size(), cudaMemcpyHostToDevice, c->stream);
+  // owner flags by device slot (the solver reads them beside the space record, without waiting
+  // for the sorted index)
+  std::vector<uint8_t> owns_s((size_t)std::max<int64_t>(nspaces, 1), 0), owns((size_t)std::max<int64_t>(nspaces, 1), 0);
+  for (int32_t o : pl.own1)
+    if (o >= 0) owns_s[(size_t)o] = 1;
+  for (int32_t o : pl.own2)
+    if (o >= 0) owns_s[(size_t)o] = 1;
+  for (int64_t d = 0; d < nspaces; ++d) owns[(size_t)d] = owns_s[(size_t)gidx[(size_t)d]];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->owns, owns.data(), owns.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && nspaces > 0)
     e = cudaMemcpyAsync(c->spaces, grouped.data(), sizeof(qflow_space) * (size_t)nspaces, cudaMemcpyHostToDevice,
                         c->stream);
@@ -492,6 +509,7 @@ qf::SolveArgs solve_args(qflow_ctx* c, int k) {
   a.sorted_index = c->sorted_index + c->cls_off[k] + lo;
   a.owner1 = c->own1;
   a.owner2 = c->own2;
+  a.owns = c->owns + c->cls_off[k] + lo;
   a.t1_old = c->pool;
   a.t2_old = c->pool + c->n_t1;
   a.t1_new = c->pool_new;
@@ -751,6 +769,7 @@ cudaError_t autotune(qflow_ctx* c) {
     float ms = 0.f;
     c->tune_ms[ci] = 0.f;
     if (c->opt.warps > 0 && cand[ci][2] != c->opt.warps) continue;
+    if (c->opt.chunk > 0 && cand[ci][1] != c->opt.chunk) continue;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
       e = cudaEventRecord(t0, c->stream);
       if (e == cudaSuccess) e = enqueue_solve(c, cand[ci][0], cand[ci][1], cand[ci][2], count, &dummy);
@@ -769,7 +788,7 @@ cudaError_t autotune(qflow_ctx* c) {
   if (e != cudaSuccess) return e;
   c->tune_count = kCand;
   c->sched_persistent = cand[bi][0];
-  c->sched_chunk = cand[bi][1];
+  c->sched_chunk = (c->opt.chunk > 0) ? c->opt.chunk : cand[bi][1];
   c->sched_warps = (c->opt.warps > 0) ? c->opt.warps : cand[bi][2];
   c->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);

@@ -34,6 +34,8 @@ struct SolveArgs {
   const int64_t* items;         // nullable: item i of a launch is space items[i]; else space i
   const int32_t* owner1;
   const int32_t* owner2;
+  const uint8_t* owns;  // nullable: owns[s] != 0 iff spaces[s] owns an amplitude (the mixed
+                        // solver forms no increment for a space that owns none)
   const double* t1_old;
   const double* t2_old;
   double* t1_new;
@@ -84,7 +86,9 @@ size_t dress_workspace_bytes(int n, int nocc);
 size_t dress_workspace_bytes_mixed(int n, int nocc);  // + FP32 GEMM scratch of the mixed path
 int dress_launch_count(int n, int nocc, bool mixed);  // kernels one launch_dress issues
 // g32: NULL for FP64 contractions; else n^4 floats of scratch, and the T2 terms are contracted
-// in FP32 (mixed precision).
+// in FP32 (mixed precision); the mixed form adds the T2 term of the vvvv block only where at most
+// three of its four virtual indices differ (all a (k, k) space with k <= 3 reads), the other
+// vvvv elements keep their T1-transformed values.
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
                          double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st,
                          float* g32 = nullptr);

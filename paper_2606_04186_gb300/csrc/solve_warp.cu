@@ -359,7 +359,6 @@ template <int K>
 struct SetupF32 {
   using D = Dim<K>;
   float F[D::NF];     // F block
-  float J[D::NF];     // J_pr = W_pprr (the block's diagonal-only entries)
   float hd[D::NORB];  // folded one-body diagonal h_pp
 };
 
@@ -781,15 +780,22 @@ constexpr float kImagMin = 1e-5f;
 // taken (the space's root is the eigenvector with the largest |c_Phi|); shifted inverse
 // iteration from `shift` is the fallback when the closed forms fail.  Returns 1 when a complex
 // pair carries more Phi weight than every real root (the real candidate is still returned),
-// else 0.  The projected matrix is built from FP32 vectors, so it is solved in FP32 too.
-__device__ __noinline__ int small_eig(const float* G, int k, float shift, float* y, float* theta) {
+// else 0.  The closed forms run in FP32 on the rounded double-float matrix; `theta` is the
+// previous root (the fallback's second shift).  G and y are the warp state's (shared memory),
+// the root comes back by value, so lane 0 makes no local-memory round trips here.
+struct EigOut {
+  float theta;
+  int cx;
+};
+__device__ __noinline__ EigOut small_eig(const DF* Gd, int k, float shift, float theta, float* y) {
   int cx = 0;
+  auto G = [Gd](int i) { return df_f(Gd[i]); };
   // The closed forms below lose absolute accuracy to cancellation (the root sought is small next
   // to the other diagonal entries).  The chosen root is therefore polished with the Phi row of
   // G y = lambda y, lambda = (G y)_0 / y_0 (exact for an eigenpair; G_00 = Phi . sigma(Phi)),
   // alternating with the eigenvector twice: the error shrinks by about |G_0j| / gap per pass.
   if (k == 2) {
-    const float g00 = G[0], g01 = G[1], g10 = G[KM], g11 = G[KM + 1];
+    const float g00 = G(0), g01 = G(1), g10 = G(KM), g11 = G(KM + 1);
     const float tr = 0.5f * (g00 + g11), df = 0.5f * (g00 - g11);
     const float disc = df * df + g01 * g10;
     // eigenvector of G for root lam: the better conditioned of the two rows of (G - lam) y = 0
@@ -824,15 +830,13 @@ __device__ __noinline__ int small_eig(const float* G, int k, float shift, float*
         const float sc = ((y0 < 0.f) ? -1.f : 1.f) / nrm;
         y[0] = sc * y0;
         y[1] = sc * y1;
-        *theta = lam;
-        return cx;
+        return EigOut{lam, cx};
       }
     }
   }
   if (k == 3) {  // roots of the characteristic cubic; eigenvectors from cross products
-    const float* g = G;
-    const float g00 = g[0], g01 = g[1], g02 = g[2], g10 = g[KM], g11 = g[KM + 1], g12 = g[KM + 2];
-    const float g20 = g[2 * KM], g21 = g[2 * KM + 1], g22 = g[2 * KM + 2];
+    const float g00 = G(0), g01 = G(1), g02 = G(2), g10 = G(KM), g11 = G(KM + 1), g12 = G(KM + 2);
+    const float g20 = G(2 * KM), g21 = G(2 * KM + 1), g22 = G(2 * KM + 2);
     auto cross = [](const float* u, const float* w, float* o) {
       o[0] = u[1] * w[2] - u[2] * w[1];
       o[1] = u[2] * w[0] - u[0] * w[2];
@@ -913,15 +917,14 @@ __device__ __noinline__ int small_eig(const float* G, int k, float shift, float*
       y[0] = sc * vb[0];
       y[1] = sc * vb[1];
       y[2] = sc * vb[2];
-      *theta = lam;
-      return cx;
+      return EigOut{lam, cx};
     }
   }
   float a[KM * KM], z[KM];
   for (int phase = 0; phase < 5; ++phase) {
-    const float sg = (phase < 2) ? shift : *theta;
+    const float sg = (phase < 2) ? shift : theta;
     for (int i = 0; i < k; ++i)
-      for (int j = 0; j < k; ++j) a[i * KM + j] = G[i * KM + j] - ((i == j) ? sg : 0.f);
+      for (int j = 0; j < k; ++j) a[i * KM + j] = G(i * KM + j) - ((i == j) ? sg : 0.f);
     for (int i = 0; i < k; ++i) z[i] = y[i];
     for (int col = 0; col < k; ++col) {
       int piv = col;
@@ -965,12 +968,12 @@ __device__ __noinline__ int small_eig(const float* G, int k, float shift, float*
     float num = 0.f;
     for (int i = 0; i < k; ++i) {
       float gy = 0.f;
-      for (int j = 0; j < k; ++j) gy += G[i * KM + j] * y[j];
+      for (int j = 0; j < k; ++j) gy += G(i * KM + j) * y[j];
       num += y[i] * gy;
     }
-    *theta = num;
+    theta = num;
   }
-  return cx;
+  return EigOut{theta, cx};
 }
 
 // The Phi-dominant eigenpair of the projected matrix to FP64 accuracy: the FP32 closed forms
@@ -978,17 +981,18 @@ __device__ __noinline__ int small_eig(const float* G, int k, float shift, float*
 // vectors); one Newton step on the characteristic polynomial of the double-float matrix, with the
 // polynomial in double-float arithmetic and the FP32 derivative (the step is a small correction),
 // refines the root.  A step that is not finite or moves the root by more than 1e-3 is dropped.
+// G, y and theta are the warp state's (shared memory).
 __device__ __noinline__ int small_eig_rr(const DF* G, int k, DF shift, float* y, DF* theta) {
-  float Gf[KM * KM];
-  for (int i = 0; i < KM * KM; ++i) Gf[i] = df_f(G[i]);
-  float th = df_f(*theta);
-  const int cx = small_eig(Gf, k, df_f(shift), y, &th);
+  const EigOut r = small_eig(G, k, df_f(shift), df_f(*theta), y);
+  const int cx = r.cx;
+  const float th = r.theta;
+  auto Gf = [G](int i) { return df_f(G[i]); };
   float delta = 0.f;
   const DF lam{th, 0.f};
   if (k == 2) {  // det(lam - G) = (lam - g00)(lam - g11) - g01 g10
     const DF a = df_add(lam, df_neg(G[0])), b = df_add(lam, df_neg(G[KM + 1]));
     const DF f = df_add(df_mul(a, b), df_neg(df_mul(G[1], G[KM])));
-    const float fp = 2.f * th - Gf[0] - Gf[KM + 1];
+    const float fp = 2.f * th - Gf(0) - Gf(KM + 1);
     delta = -df_f(f) / fp;
   } else if (k == 3) {  // det(lam - G) by the rule of Sarrus on the double-float entries of lam - G
     DF m[9];
@@ -998,10 +1002,9 @@ __device__ __noinline__ int small_eig_rr(const DF* G, int k, DF shift, float* y,
     DF f = df_add(df_add(t3(0, 4, 8), t3(1, 5, 6)), t3(2, 3, 7));
     f = df_add(f, df_neg(df_add(df_add(t3(2, 4, 6), t3(0, 5, 7)), t3(1, 3, 8))));
     // d/dlam det(lam - G) = sum of the principal 2 x 2 minors of (lam - G), in FP32
-    const float* g = Gf;
-    const float d00 = th - g[0], d11 = th - g[KM + 1], d22 = th - g[2 * KM + 2];
-    const float fp = (d11 * d22 - g[KM + 2] * g[2 * KM + 1]) + (d00 * d22 - g[2] * g[2 * KM]) +
-                     (d00 * d11 - g[1] * g[KM]);
+    const float d00 = th - Gf(0), d11 = th - Gf(KM + 1), d22 = th - Gf(2 * KM + 2);
+    const float fp = (d11 * d22 - Gf(KM + 2) * Gf(2 * KM + 1)) + (d00 * d22 - Gf(2) * Gf(2 * KM)) +
+                     (d00 * d11 - Gf(1) * Gf(KM));
     delta = -df_f(f) / fp;
   }
   if (isfinite(delta) && fabsf(delta) <= 1e-3f * (1.f + fabsf(th)))
@@ -1025,20 +1028,26 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
   const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
   const float tol = (float)a.tol;
   // ---- validate -------------------------------------------------------------------------
+  // (the sorted index and the owner flag are loaded beside the record: neither waits on it)
+  const int64_t sidx = a.sorted_index ? a.sorted_index[s] : a.space_base + s;
+  const int64_t oidx = a.sorted_index ? sidx : s;
+  // only a space that owns an amplitude forms its increment (loaded here, used at the merge)
+  const bool owner = !a.owns || a.owns[s] != 0;
   if (lane == 0) {
     const qflow_space& q = a.spaces[s];
-    int ok = (q.no == K && q.nv == K);
+    int ok = (q.no == K && q.nv == K), same = (K == 3);
     for (int t = 0; t < NORB; ++t) {
       const int o = q.orb[t];
+      if (t < NORB - 1) same &= (o == ws.orb[t]);
       ws.orb[t] = o;
       if (t < K) ok &= (o >= 0 && o < a.nocc);
       else ok &= (o >= a.nocc && o < a.n);
     }
+    if (!ok) ws.orb[0] = -1;  // the W block below is not this record's: nothing to reuse next
     ws.ctrl[1] = ok;
+    ws.ctrl[0] = same && ok;
   }
   __syncwarp();
-  const int64_t sidx = a.sorted_index ? a.sorted_index[s] : a.space_base + s;
-  const int64_t oidx = a.sorted_index ? sidx : s;
   if (!ws.ctrl[1]) {
     if (lane == 0) {
       a.energy[oidx] = 0.0;
@@ -1071,6 +1080,10 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
       f1 = a.F32 ? a.F32[g] : (float)a.F[g];
     }
     if constexpr (K == 3) {  // the 666 unique elements of the pair-symmetric block
+      // A space whose first five orbitals are those of this warp's previous space (consecutive
+      // spaces of the sorted list differ in the last virtual) keeps the 325 elements without
+      // orbital 5 from it: W_t and J_c still hold them.
+      const bool reuse = ws.ctrl[0] != 0;
       constexpr int PER = (D::NPAIR + 31) / 32;
       float wv[PER];
 #pragma unroll
@@ -1079,8 +1092,10 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         wv[k] = 0.f;
         if (t < D::NPAIR) {
           const int pr = pair3[t], P = pr & 255, R = pr >> 8;
-          const size_t g = (size_t)(off[P] + off[NF + R]);
-          wv[k] = W32 ? W32[g] : (float)a.W[g];
+          if (!reuse || P % NORB == NORB - 1 || P >= NF - NORB || R % NORB == NORB - 1 || R >= NF - NORB) {
+            const size_t g = (size_t)(off[P] + off[NF + R]);
+            wv[k] = W32 ? W32[g] : (float)a.W[g];
+          }
         }
       }
 #pragma unroll
@@ -1088,15 +1103,17 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         const int t = lane + 32 * k;
         if (t < D::NPAIR) {
           const int pr = pair3[t], P = pr & 255, R = pr >> 8;
-          const int p = P / NORB, r = R / NORB;
-          const bool jj = (P == p * (NORB + 1)) && (R == r * (NORB + 1));  // W_pprr: diagonal only
-          if (jj) {
-            su.J[p * NORB + r] = wv[k];
-            su.J[r * NORB + p] = wv[k];
+          if (!reuse || P % NORB == NORB - 1 || P >= NF - NORB || R % NORB == NORB - 1 || R >= NF - NORB) {
+            const int p = P / NORB, r = R / NORB;
+            const bool jj = (P == p * (NORB + 1)) && (R == r * (NORB + 1));  // W_pprr: diagonal only
+            if (jj) {
+              ws.Jc[p * NORB + r] = wv[k];
+              ws.Jc[r * NORB + p] = wv[k];
+            }
+            const float wf = jj ? 0.f : wv[k];
+            ws.Wt[P * NF + R] = wf;
+            ws.Wt[R * NF + P] = wf;
           }
-          const float wf = jj ? 0.f : wv[k];
-          ws.Wt[P * NF + R] = wf;
-          ws.Wt[R * NF + P] = wf;
         }
       }
     } else {
@@ -1106,7 +1123,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         const int p = P / NORB, r = R / NORB;
         const bool jj = (P == p * (NORB + 1)) && (R == r * (NORB + 1));
         const float w = W32 ? W32[g] : (float)a.W[g];
-        if (jj) su.J[p * NORB + r] = w;
+        if (jj) ws.Jc[p * NORB + r] = w;
         ws.Wt[t] = jj ? 0.f : w;
       }
     }
@@ -1121,8 +1138,8 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
     const int p = lane;
     float v = su.F[p * (NORB + 1)];
     for (int k = 0; k < K; ++k) {
-      const float kx = (k == p) ? su.J[p * NORB + p] : ws.Wt[(p * NORB + k) * NF + k * NORB + p];
-      v -= 2.f * su.J[p * NORB + k] - kx;
+      const float kx = (k == p) ? ws.Jc[p * NORB + p] : ws.Wt[(p * NORB + k) * NF + k * NORB + p];
+      v -= 2.f * ws.Jc[p * NORB + k] - kx;
     }
     su.hd[p] = v;
   }
@@ -1145,7 +1162,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
 #pragma unroll
         for (int l = j + 1; l < K; ++l) {
           const int r = tb.occ[lane][l];
-          hs += su.J[p * NORB + r] - ws.Wt[(p * NORB + r) * NF + r * NORB + p];
+          hs += ws.Jc[p * NORB + r] - ws.Wt[(p * NORB + r) * NF + r * NORB + p];
         }
       }
     }
@@ -1213,6 +1230,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
             hc = fmaf(0.5f * s1 * (float)tb.c0sg[Kk][v], ws.Wt[pq * NF + tb.c0pq[Kk][v]], hc);
         }
       }
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) ws.S[d] = 0.f;
       __syncwarp();
       // alpha-beta couplings: both strings are Phi or single replacements of it; same-spin
@@ -1235,6 +1253,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
       }
       __syncwarp();
       float rr = 0.f;
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) rr = fmaf(ws.S[d], ws.S[d], rr);
       rphi = sqrtf(wsum(rr));
     }
@@ -1245,17 +1264,17 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         if (a.iters) a.iters[oidx] = 0;
       }
       if (guess_out)
+        #pragma unroll 1
         for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (d == 0) ? 1.f : 0.f;
       __syncwarp();
       return;
     }
-    // the diagonal relative to <Phi|H|Phi> (diag_at) needs the J block for its alpha-beta
-    // Coulomb sum J(Ia, Ib) = sum_{p in Ia, r in Ib} J_pr (the set-up slot is reused later)
-    for (int t = lane; t < NF; t += 32) ws.Jc[t] = su.J[t];
+    // the diagonal relative to <Phi|H|Phi> (diag_at) takes its alpha-beta Coulomb sum
+    // J(Ia, Ib) = sum_{p in Ia, r in Ib} J_pr from J_c; j0 is that sum at Phi
     if (lane == 0) {
       float j0 = 0.f;
       for (int l = 0; l < K; ++l)
-        for (int m = 0; m < K; ++m) j0 += su.J[tb.occ[0][l] * NORB + tb.occ[0][m]];
+        for (int m = 0; m < K; ++m) j0 += ws.Jc[tb.occ[0][l] * NORB + tb.occ[0][m]];
       ws.j0 = j0;
     }
     __syncwarp();
@@ -1263,12 +1282,24 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
       float nn = 0.f;
       float* v1 = ws.V;
       if constexpr (K == 3) {  // nonzero only where the column is (the diagonal is symmetric too)
-#pragma unroll
+        // the diagonal from per-string Coulomb rows jrow[I][r] = sum_{p in I} J_pr, summed as the
+        // 6e6o sigma sums them (scratch in the S_1 slot, free until sigma(V_1))
+        float* jrow = ws.S + NDET;
+        for (int t = lane; t < NS * NORB; t += 32) {
+          const int I = t / NORB, r = t % NORB;
+          jrow[t] = ws.Jc[tb.occ[I][0] * NORB + r] + ws.Jc[tb.occ[I][1] * NORB + r] + ws.Jc[tb.occ[I][2] * NORB + r];
+        }
+        __syncwarp();
+        const float j0 = ws.j0;
+#pragma unroll 1
         for (int k = 0; k < kPhiLen; ++k) {
           const unsigned e = phi_entry(cs, k * 32 + lane);
           if (e & (1u << 20)) {
             const int d = (int)((e >> 11) & 511u);
-            float den = -diag_at<K>(tb, ws, d / NS, d % NS);
+            const int ia = d / NS, ib = d % NS;
+            const float* jr = jrow + ia * NORB;
+            const float jab = (jr[tb.occ[ib][0]] + jr[tb.occ[ib][1]]) + jr[tb.occ[ib][2]];
+            float den = -(ws.dh[ia] + ws.dh[ib] + (jab - j0));
             if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
             const float v = ws.S[d] / den;
             v1[d] = v;
@@ -1281,6 +1312,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
           }
         }
       } else {
+        #pragma unroll 1
         for (int d = lane; d < NDET; d += 32) {
           float den = -diag_at<K>(tb, ws, d / NS, d % NS);
           if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
@@ -1298,6 +1330,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
           if (a.iters) a.iters[oidx] = 0;
         }
         if (guess_out && st == kSpaceOk)
+          #pragma unroll 1
           for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = (d == 0) ? 1.f : 0.f;
         __syncwarp();
         return;
@@ -1344,6 +1377,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
   if (guess_in && KM >= 2) {
     float* v1 = ws.V;
     float p = 0.f;
+    #pragma unroll 1
     for (int d = lane; d < NDET; d += 32) {  // spin-flip symmetric part (where the Phi root lies)
       const int dt = (d % NS) * NS + d / NS;
       const float gv = (d == 0) ? 0.f : 0.5f * (guess_in[(size_t)s * NDET + d] + guess_in[(size_t)s * NDET + dt]);
@@ -1353,11 +1387,13 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
     const float nr = sqrtf(wsum(p));
     if (nr > 1e-6f) {  // an all-Phi (or zero) guess adds nothing
       const float inv = 1.f / nr;
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) v1[d] *= inv;
       __syncwarp();
       float* s1 = ws.S + NDET;
       sigma<K>(tb, ws, v1, s1, lane);
       RRAcc a10, a11;
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) {
         a10.add(v1[d], ws.S[d]);
         a11.add(v1[d], s1[d]);
@@ -1369,12 +1405,9 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         ws.G[1] = g01;
         ws.G[KM] = g10;
         ws.G[KM + 1] = g11;
-        float yn[KM];
-        for (int j = 0; j < KM; ++j) yn[j] = (j == 0) ? 1.f : 0.f;
-        DF thn{0.f, 0.f};
-        ws.ctrl[1] = small_eig_rr(ws.G, 2, DF{-1e-2f, 0.f}, yn, &thn);
-        for (int j = 0; j < KM; ++j) ws.yf[j] = yn[j];
-        ws.theta = thn;
+        for (int j = 0; j < KM; ++j) ws.yf[j] = (j == 0) ? 1.f : 0.f;
+        ws.theta = DF{0.f, 0.f};
+        ws.ctrl[1] = small_eig_rr(ws.G, 2, DF{-1e-2f, 0.f}, ws.yf, &ws.theta);
         ws.ctrl[0] = 2;
       }
       it0 = 1;
@@ -1391,6 +1424,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
     if (k == KMX) {  // restart on {Phi, Ritz vector}: x = y_0 Phi + x', x' = sum_{j>=1} y_j V_j is
                      // already orthogonal to Phi, and sigma(x') = sum_{j>=1} y_j S_j
       RRAcc apv, ap0, ap1;
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) {
         float xv = 0.f, sv = 0.f;
         for (int j = 1; j < k; ++j) {
@@ -1405,6 +1439,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
       }
       const DF pv = apv.total(), p0 = ap0.total(), p1 = ap1.total();
       const float nx = sqrtf(df_f(pv)), inv = 1.f / nx;
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) {
         ws.V[d] *= inv;
         ws.S[NDET + d] *= inv;
@@ -1425,6 +1460,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
     float vn = vn_phi;  // first step from Phi: V1 already holds the preconditioned residual
     if (!(it == 0 && !guess_in)) {
       float rr = 0.f;
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) {
         float xv = (d == 0) ? ws.yf[0] : 0.f, sv = ws.yf[0] * ws.S[d];
         for (int j = 1; j < k; ++j) {
@@ -1449,6 +1485,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         __syncwarp();
         break;
       }
+      #pragma unroll 1
       for (int d = lane; d < NDET; d += 32) {  // diagonal preconditioner r / (theta - D)
         float den = th - diag_at<K>(tb, ws, d / NS, d % NS);
         if (fabsf(den) < 1e-4f) den = (den < 0.f) ? -1e-4f : 1e-4f;
@@ -1462,6 +1499,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
 #pragma unroll 1
       for (int attempt = 0; attempt < 2; ++attempt) {
         if (attempt == 1) {
+          #pragma unroll 1
           for (int d = lane; d < NDET; d += 32) {
             float xv = (d == 0) ? ws.yf[0] : 0.f, sv = ws.yf[0] * ws.S[d];
             for (int j = 1; j < k; ++j) {
@@ -1475,6 +1513,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         for (int pass = 0; pass < 2; ++pass) {  // against Phi: drop component 0
           RRAcc acf[KM];
           float cf[KM];
+          #pragma unroll 1
           for (int d = lane; d < NDET; d += 32) {
             const float v = vk[d];
 #pragma unroll
@@ -1483,6 +1522,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
           }
 #pragma unroll
           for (int j = 0; j < KM; ++j) cf[j] = (j >= 1 && j < k) ? df_f(acf[j].total()) : 0.f;
+          #pragma unroll 1
           for (int d = lane; d < NDET; d += 32) {
             float v = vk[d];
 #pragma unroll
@@ -1493,6 +1533,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
           __syncwarp();
         }
         float nn = 0.f;
+        #pragma unroll 1
         for (int d = lane; d < NDET; d += 32) nn = fmaf(vk[d], vk[d], nn);
         vn = sqrtf(wsum(nn));
         if (vn > 1e-6f || rnorm < 100.f * tol) break;
@@ -1507,11 +1548,13 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
       }
     }
     const float inv = 1.f / vn;
+    #pragma unroll 1
     for (int d = lane; d < NDET; d += 32) vk[d] *= inv;
     __syncwarp();
     float* sk = ws.S + k * NDET;
     sigma<K>(tb, ws, vk, sk, lane);
     RRAcc agc[KM], agr[KM], akk;
+    #pragma unroll 1
     for (int d = lane; d < NDET; d += 32) {
       const float vkd = vk[d], skd = sk[d];
       akk.add(vkd, skd);
@@ -1539,12 +1582,8 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
       }
       ws.G[k * KM + k] = gkk;
       const int kk = k + 1;
-      float yn[KM];
-      for (int j = 0; j < kk; ++j) yn[j] = (j < k) ? ws.yf[j] : 0.f;
-      DF thn = ws.theta;
-      const int cx = small_eig_rr(ws.G, kk, df_add(ws.theta, DF{-1e-2f, 0.f}), yn, &thn);
-      for (int j = 0; j < kk; ++j) ws.yf[j] = yn[j];
-      ws.theta = thn;
+      ws.yf[k] = 0.f;
+      const int cx = small_eig_rr(ws.G, kk, df_add(ws.theta, DF{-1e-2f, 0.f}), ws.yf, &ws.theta);
       ws.ctrl[0] = kk;
       ws.ctrl[3] = it + 1 + it0;
       ws.ctrl[1] = cx ? ws.ctrl[1] + 1 : 0;
@@ -1561,7 +1600,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
   int32_t own1 = -1, own2[R2];
   double old1 = 0.0, old2[R2];
   size_t g1 = 0, g2[R2];
-  if (a.owner1 && lane < K * K) {
+  if (owner && a.owner1 && lane < K * K) {
     g1 = (size_t)ws.orb[lane / K] * a.nvir + (ws.orb[K + lane % K] - a.nocc);
     own1 = a.owner1[g1];
     old1 = a.t1_old[g1];
@@ -1572,7 +1611,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
     own2[r] = -1;
     old2[r] = 0.0;
     g2[r] = 0;
-    if (a.owner2 && idx < K4) {
+    if (owner && a.owner2 && idx < K4) {
       const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
       g2[r] = (((size_t)ws.orb[i] * a.nocc + ws.orb[j]) * a.nvir + (ws.orb[K + aa] - a.nocc)) * a.nvir +
               (ws.orb[K + b] - a.nocc);
@@ -1582,6 +1621,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
   }
   const int k = ws.ctrl[0];
   float xx = 0.f;
+  #pragma unroll 1
   for (int d = lane; d < NDET; d += 32) {
     float xv = (d == 0) ? ws.yf[0] : 0.f;
     for (int j = 1; j < k; ++j) xv = fmaf(ws.yf[j], ws.V[(j - 1) * NDET + d], xv);
@@ -1598,31 +1638,34 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
   if (!isfinite(c0) || !isfinite(df_f(ws.theta))) st = kSpaceNonFinite;
   const float inv0 = (st == kSpaceOk || st == kSpaceNoConv) ? 1.f / c0 : 0.f;
   if (guess_out && st == kSpaceOk)
+    #pragma unroll 1
     for (int d = lane; d < NDET; d += 32) guess_out[(size_t)s * NDET + d] = ws.S[d] * inv0;
-  float* x1 = ws.V;  // V is free now: K^2 + K^4 floats of scratch
-  float* x2 = x1 + K * K;
-  if (lane < K * K) {
-    const int J = tb.xJ[lane];
-    const float f = (tb.xs[lane] < 0) ? -inv0 : inv0;
-    x1[lane] = 0.5f * f * (ws.S[J * NS] + ws.S[J]);
-  }
-  __syncwarp();
+  if (owner) {  // the increment, written where this space owns the amplitude
+    float* x1 = ws.V;  // V is free now: K^2 + K^4 floats of scratch
+    float* x2 = x1 + K * K;
+    if (lane < K * K) {
+      const int J = tb.xJ[lane];
+      const float f = (tb.xs[lane] < 0) ? -inv0 : inv0;
+      x1[lane] = 0.5f * f * (ws.S[J * NS] + ws.S[J]);
+    }
+    __syncwarp();
 #pragma unroll 1
-  for (int idx = lane; idx < K4; idx += 32) {
-    const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
-    const int xa = i * K + aa, xb = j * K + b;
-    const float f = (tb.xs[xa] != tb.xs[xb]) ? -inv0 : inv0;
-    x2[idx] = f * ws.S[tb.xJ[xa] * NS + tb.xJ[xb]] - x1[xa] * x1[xb];
-  }
-  __syncwarp();
-  if (st == kSpaceOk && a.owner1 && lane < K * K && own1 == sidx) a.t1_new[g1] = old1 + (double)x1[lane];
-  if (st == kSpaceOk && a.owner2) {
+    for (int idx = lane; idx < K4; idx += 32) {
+      const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
+      const int xa = i * K + aa, xb = j * K + b;
+      const float f = (tb.xs[xa] != tb.xs[xb]) ? -inv0 : inv0;
+      x2[idx] = f * ws.S[tb.xJ[xa] * NS + tb.xJ[xb]] - x1[xa] * x1[xb];
+    }
+    __syncwarp();
+    if (st == kSpaceOk && a.owner1 && lane < K * K && own1 == sidx) a.t1_new[g1] = old1 + (double)x1[lane];
+    if (st == kSpaceOk && a.owner2) {
 #pragma unroll
-    for (int r = 0; r < R2; ++r) {
-      const int idx = lane + 32 * r;
-      if (idx < K4 && own2[r] == sidx) {
-        const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
-        a.t2_new[g2[r]] = old2[r] + (double)(0.5f * (x2[idx] + x2[((j * K + i) * K + b) * K + aa]));
+      for (int r = 0; r < R2; ++r) {
+        const int idx = lane + 32 * r;
+        if (idx < K4 && own2[r] == sidx) {
+          const int i = idx / (K * K * K), j = (idx / (K * K)) % K, aa = (idx / K) % K, b = idx % K;
+          a.t2_new[g2[r]] = old2[r] + (double)(0.5f * (x2[idx] + x2[((j * K + i) * K + b) * K + aa]));
+        }
       }
     }
   }
@@ -1646,6 +1689,7 @@ __global__ void __maxnreg__(kMaxRegs) solve_class_kernel(SolveArgs a, const floa
   build_all_tabs(cs);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   WarpState<K>& ws = state<K>(wst[warp]);
+  if (lane == 0) ws.orb[0] = -1;  // no previous space: nothing to reuse
 #pragma unroll 1
   for (int64_t s = (int64_t)blockIdx.x * nw + warp; s < a.nspaces; s += (int64_t)gridDim.x * nw)
     solve_one<K>(tabs<K>(cs), cs, ws, a, W32, guess_in, guess_out, a.items ? a.items[s] : s, lane);
@@ -1665,6 +1709,9 @@ __global__ void __maxnreg__(kMaxRegs) solve_persistent_kernel(PersistentArgs p) 
   AnyWarpState* wst = reinterpret_cast<AnyWarpState*>(smem_raw + kTabsBytes);
   build_all_tabs(cs);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // no previous 6e6o space: nothing to reuse (a warp's items only increase, so after its first
+  // smaller space it never meets a 6e6o space again)
+  if (lane == 0) state<3>(wst[warp]).orb[0] = -1;
   const int64_t n3 = p.cls[3].nspaces, n2 = p.cls[2].nspaces, n1 = p.cls[1].nspaces;
   const unsigned long long total = (unsigned long long)(n3 + n2 + n1);
   // each pass takes `chunk` new items, so the loop ends after at most total / chunk + 1 passes

@@ -33,7 +33,8 @@ class QFlowError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("diis", C.c_int32), ("guess", C.c_int32), ("schedule", C.c_int32), ("graph", C.c_int32),
-                ("form", C.c_int32), ("warps", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("form", C.c_int32), ("warps", C.c_int32), ("chunk", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 _lib = None
@@ -177,7 +178,7 @@ class Flow:
 
     def __init__(self, h, eri, nocc: int, spaces, precision: str = "fp64", max_iter: int | None = None,
                  tol: float | None = None, guess: str = "phi", diis: int = 0, schedule: str = "auto",
-                 graph: bool = True, form: str = "ses", warps: int = 0):
+                 graph: bool = True, form: str = "ses", warps: int = 0, chunk: int = 0):
         h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
         self.n, self.nocc = h.shape[0], nocc
         self.nvir = self.n - nocc
@@ -193,6 +194,7 @@ class Flow:
         opt.graph = int(graph)
         opt.form = {"ses": 0, "ducc": 1}[form]
         opt.warps = warps
+        opt.chunk = chunk
         self._h = C.c_void_p()
         code = lib().qflow_init(C.byref(self._h), _ptr(h), _ptr(eri), self.n, nocc, _ptr(sp), len(sp), C.byref(opt))
         self.init_status = _check(code, "qflow_init")

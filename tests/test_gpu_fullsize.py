@@ -14,7 +14,7 @@ import pytest
 from oracle import cas, ccsd, flow
 from paper_2606_04186_gb300 import synth
 
-from gpu_util import library
+from gpu_util import mixed_flow_w, library
 
 pytestmark = pytest.mark.gpu
 
@@ -153,6 +153,9 @@ def test_mixed_dressing_elementwise_n82(qf):
     assert abs(e0 - e0r) < 1e-9
     assert np.abs(F - Fr).max() < 1e-9
     o, v = slice(0, no), slice(no, s.n)
+    # the flow's mixed dressing adds the vvvv block's T2 term where at most three of the four
+    # virtual indices differ (what (k, k) spaces with k <= 3 read)
+    W = mixed_flow_w(W, Wr, no)
     for name, blk in [("oooo", (o, o, o, o)), ("vvvv", (v, v, v, v)), ("vovo", (v, o, v, o)), ("ovov", (o, v, o, v)),
                       ("vvoo", (v, v, o, o)), ("vvvo", (v, v, v, o)), ("vovv", (v, o, v, v)), ("ooov", (o, o, o, v)),
                       ("vooo", (v, o, o, o)), ("voov", (v, o, o, v))]:
