@@ -103,11 +103,14 @@ def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12
     400*(4j+4), precondition 400*8, orthogonalise in two passes 400*(4j)*2 and normalise 400*3.
     Each iteration applies sigma, 400 * (2*NSG^2 + 2*NS + 3) = 132,400 flop (alpha-beta, the
     alpha-alpha product whose transpose is the beta-beta part, the transpose added, the diagonal
-    term), and forms the new
+    term); the first one, on the first-order vector (nonzero only on the 117 determinants of the
+    Phi column), takes only the products against its nonzeros: 2 * 16,848 alpha-beta, 2 * 20 * 117
+    alpha-alpha, 3 * 400 transpose and diagonal = 39,576 flop.  Each iteration forms the new
     row and column of the projected matrix 400*2*(2j+1); the subspace restarts at kmax.  The
     convergence test after the last iteration forms one more residual.
     """
     sig = ndet * (2 * nsg * nsg + 2 * ns + 3)
+    sig1 = 2 * 16848 + 2 * ns * 117 + 3 * ndet  # sigma of the first-order vector
     nz = 117
     phi = 2 * 153 + 2 * nz
     first = 2 * 6 * ns * k + nz * 8 + 2 * 1980
@@ -119,10 +122,10 @@ def solver_flops(iters: np.ndarray, ndet: int = 400, ns: int = 20, nsg: int = 12
             tot += ndet * (4 * kmax + 6)          # restart: Ritz vector + its sigma combination + norms
             j = 1
         if m == 1:
-            tot += ndet
+            tot += ndet + sig1
         else:
-            tot += ndet * (4 * j + 4) + ndet * 8 + ndet * 8 * j + ndet * 3
-        tot += sig + ndet * 2 * (2 * j + 1)
+            tot += ndet * (4 * j + 4) + ndet * 8 + ndet * 8 * j + ndet * 3 + sig
+        tot += ndet * 2 * (2 * j + 1)
         j += 1
         cum[m] = tot + ndet * (4 * j + 4)         # + the residual of the convergence test
     it = np.clip(iters, 0, m_max)
@@ -655,6 +658,9 @@ def run_ours(args):
                      if args.precision == "mixed" else ("solve_kernel<K,double,DUCC>" if args.form == "ducc"
                                                         else "solve_kernel<K,double>"),
                      "flops_per_launch": flops, "launch_ms": solve_ms,
+                     "flops_note": ("products the steps need (solver_flops): sigma of the first-order "
+                                    "vector counts only its 117-determinant support, as the kernel "
+                                    "computes it; the kernel is latency- and issue-bound (profiles/)"),
                      "peak_note": ("measured FP32 FMA peak of this GPU" if args.precision == "mixed"
                                    else "measured FP64 FMA peak of this GPU") + " (" + peaks["method"] + ")",
                      "peaks_measured": {k: v for k, v in peaks.items() if k != "method"}},

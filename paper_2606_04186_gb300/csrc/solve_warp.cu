@@ -336,6 +336,128 @@ __device__ __forceinline__ void ab_terms(std::integer_sequence<int, I...>, float
   (ab_term<I / 12, I % 12>(acc, wr, cr), ...);
 }
 
+// ---- sigma of the first expansion vector (6e6o) --------------------------------------------
+// The first vector is the first-order correction r / (0 - D) on the Phi column's support: the
+// determinants (Ia, Ib) whose strings together carry one or two excitations (117 of 400; the
+// type of a string is its number of virtual orbitals, 0 for the Phi string).  In the alpha-beta
+// part a source row Ja of type 0 then meets columns of types 1, 2 only, type 1 columns of types
+// 0, 1, type 2 the Phi string's column, type 3 nothing: 16,848 products instead of 57,600.  The
+// (row, replacement) pairs are scheduled at compile time in type-uniform steps (1 step of type 0,
+// 4 of type 1, 4 of type 2), so every lane runs the same compile-time product list in a step:
+// lane Ia < 20 takes pairs of its own row; lanes 20..31 take a row's remaining pairs of a phase
+// and leave their partial row in a scratch slot, which the row's lane adds at the end.
+__host__ __device__ constexpr int str_type(int J) { return popc6(TabHolder::value.mask[J] & 0x38); }
+__host__ __device__ constexpr bool first_support(int ta, int tb) { return ta + tb >= 1 && ta + tb <= 2; }
+
+constexpr int kFirstSteps = 9;            // step 0: type 0, steps 1-4: type 1, steps 5-8: type 2
+constexpr int kFirstSlots = 24;           // helper partial rows (V_2: 20 rows, S_2: 4 rows)
+struct FirstSched {
+  int e[kFirstSteps][32];    // (Ia << 4) | u of the pair a lane takes in a step, or -1
+  int hslot[3][12];          // slot helper h fills at the end of phase t, or -1
+  int rslot[20][6];          // slots added to row Ia, in order
+  int rcount[20];
+  bool ok;
+};
+__host__ __device__ constexpr FirstSched make_first_sched() {
+  FirstSched f{};
+  const Tab3 t = TabHolder::value;
+  for (int k = 0; k < kFirstSteps; ++k)
+    for (int l = 0; l < 32; ++l) f.e[k][l] = -1;
+  for (int ph = 0; ph < 3; ++ph)
+    for (int h = 0; h < 12; ++h) f.hslot[ph][h] = -1;
+  for (int r = 0; r < 20; ++r) f.rcount[r] = 0;
+  f.ok = true;
+  const int first[3] = {0, 1, 5}, steps[3] = {1, 4, 4};
+  int slot = 0;
+  for (int ph = 0; ph < 3; ++ph) {
+    int helper = 0;
+    for (int Ia = 0; Ia < 20; ++Ia) {
+      int list[12] = {}, n = 0;
+      for (int u = 0; u < 12; ++u)
+        if (str_type(t.J[Ia][u]) == ph) list[n++] = u;
+      int taken = 0;
+      for (; taken < n && taken < steps[ph]; ++taken) f.e[first[ph] + taken][Ia] = (Ia << 4) | list[taken];
+      while (taken < n) {  // a helper lane takes up to steps[ph] of this row's remaining pairs
+        if (helper >= 12 || slot >= kFirstSlots || f.rcount[Ia] >= 6) {
+          f.ok = false;
+          return f;
+        }
+        for (int k = 0; k < steps[ph] && taken < n; ++k, ++taken)
+          f.e[first[ph] + k][20 + helper] = (Ia << 4) | list[taken];
+        f.hslot[ph][helper] = slot;
+        f.rslot[Ia][f.rcount[Ia]++] = slot;
+        ++slot;
+        ++helper;
+      }
+    }
+  }
+  return f;
+}
+struct FirstHolder {
+  static constexpr FirstSched value = make_first_sched();
+};
+static_assert(FirstHolder::value.ok, "first-vector sigma schedule");
+__device__ const FirstSched g_first = make_first_sched();
+
+// Compile-time product lists: the alpha-beta terms (B, V) of a source row of type T (target
+// strings J(B, V) of the types first_support allows), and the same-spin terms (J, b) of the
+// first vector's support.
+template <int T>
+struct AbFirst {
+  int B[216], V[216], n;
+};
+template <int T>
+__host__ __device__ constexpr AbFirst<T> make_ab_first() {
+  AbFirst<T> a{};
+  a.n = 0;
+  for (int B = 0; B < 20; ++B)
+    for (int V = 0; V < 12; ++V)
+      if (first_support(T, str_type(TabHolder::value.J[B][V]))) {
+        a.B[a.n] = B;
+        a.V[a.n] = V;
+        ++a.n;
+      }
+  return a;
+}
+template <int T>
+struct AbFirstHolder {
+  static constexpr AbFirst<T> value = make_ab_first<T>();
+};
+template <int T, int... I>
+__device__ __forceinline__ void ab_first_terms(std::integer_sequence<int, I...>, float (&acc)[20], const float (&wr)[36],
+                                               const float (&cr)[20]) {
+  (ab_term<AbFirstHolder<T>::value.B[I], AbFirstHolder<T>::value.V[I]>(acc, wr, cr), ...);
+}
+struct AaFirst {
+  int J[117], b[117], n;
+};
+__host__ __device__ constexpr AaFirst make_aa_first() {
+  AaFirst a{};
+  a.n = 0;
+  for (int b = 0; b < 20; ++b)
+    for (int J = 0; J < 20; ++J)
+      if (first_support(str_type(J), str_type(b))) {
+        a.J[a.n] = J;
+        a.b[a.n] = b;
+        ++a.n;
+      }
+  return a;
+}
+struct AaFirstHolder {
+  static constexpr AaFirst value = make_aa_first();
+};
+static_assert(AbFirstHolder<0>::value.n == 216 && AbFirstHolder<1>::value.n == 120 && AbFirstHolder<2>::value.n == 12 &&
+                  AaFirstHolder::value.n == 117,
+              "first-vector product lists");
+template <int... I>
+__device__ __forceinline__ void aa_first_terms(std::integer_sequence<int, I...>, float (&acc)[20], const float (&h)[20],
+                                               const float* __restrict__ c) {
+  ((acc[AaFirstHolder::value.b[I]] =
+        fmaf(h[AaFirstHolder::value.J[I]], c[AaFirstHolder::value.J[I] * 20 + AaFirstHolder::value.b[I]],
+             acc[AaFirstHolder::value.b[I]])),
+   ...);
+}
+
 // ---- shared memory -------------------------------------------------------------------------
 
 template <int K>
@@ -732,6 +854,132 @@ __device__ __noinline__ void sigma33(const Tabs<3>& tb, const WarpState<3>& ws, 
       const float4 v = orow[q];
       orow[q] = make_float4(acc[4 * q] + v.x, acc[4 * q + 1] + v.y, acc[4 * q + 2] + v.z, acc[4 * q + 3] + v.w);
     }
+  }
+  __syncwarp();
+}
+
+// sigma of the first expansion vector (c on the Phi column's support, spin-flip symmetric): the
+// same terms as sigma33 with the products against c's zeros left out (see AbFirst / FirstSched).
+// scratch: 480 floats the call may overwrite (the second vector slot and the third sigma slot,
+// unused until sigma of the second vector).
+__device__ __noinline__ void sigma33_first(const Tabs<3>& tb, const WarpState<3>& ws, const float* __restrict__ c,
+                                           float* __restrict__ out, float* __restrict__ scr_a,
+                                           float* __restrict__ scr_b, int lane) {
+  constexpr int NS = 20, NF = 36;
+  float acc[NS];
+#pragma unroll
+  for (int b = 0; b < NS; ++b) acc[b] = 0.f;
+  if (lane < NS) {
+    const int Ia = lane;
+    constexpr unsigned kRows = (1u << NS) - 1u;
+    // alpha-alpha: A[Ia][b] = sum_J Hs[Ia][J] c[J][b] over c's support (J ascending per b, as the
+    // dense product adds them), then A^T and the diagonal as in sigma33
+    float h[NS];
+    {
+      const float4* hr = reinterpret_cast<const float4*>(ws.Hs + Ia * NS);
+#pragma unroll
+      for (int q = 0; q < NS / 4; ++q) {
+        const float4 v = hr[q];
+        h[4 * q] = v.x;
+        h[4 * q + 1] = v.y;
+        h[4 * q + 2] = v.z;
+        h[4 * q + 3] = v.w;
+      }
+    }
+    aa_first_terms(std::make_integer_sequence<int, 117>{}, acc, h, c);
+    {
+      float4* orow = reinterpret_cast<float4*>(out + Ia * NS);
+#pragma unroll
+      for (int q = 0; q < NS / 4; ++q) orow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+    __syncwarp(kRows);
+    {
+      float jp[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+        jp[r] = ws.Jc[tb.occ[Ia][0] * 6 + r] + ws.Jc[tb.occ[Ia][1] * 6 + r] + ws.Jc[tb.occ[Ia][2] * 6 + r];
+      float jab[NS];
+      coulomb_rows(std::make_integer_sequence<int, NS>{}, jab, jp);
+      const float4* dhr = reinterpret_cast<const float4*>(ws.dh);
+      const float4* crow = reinterpret_cast<const float4*>(c + Ia * NS);
+      const float dha = ws.dh[Ia], jz = ws.j0;
+#pragma unroll
+      for (int q = 0; q < NS / 4; ++q) {
+        const float4 dv = dhr[q], cv = crow[q];
+        acc[4 * q + 0] += out[(4 * q + 0) * NS + Ia] + (dha + dv.x + (jab[4 * q + 0] - jz)) * cv.x;
+        acc[4 * q + 1] += out[(4 * q + 1) * NS + Ia] + (dha + dv.y + (jab[4 * q + 1] - jz)) * cv.y;
+        acc[4 * q + 2] += out[(4 * q + 2) * NS + Ia] + (dha + dv.z + (jab[4 * q + 2] - jz)) * cv.z;
+        acc[4 * q + 3] += out[(4 * q + 3) * NS + Ia] + (dha + dv.w + (jab[4 * q + 3] - jz)) * cv.w;
+      }
+    }
+  }
+  __syncwarp();  // every column of out read before rows are written again
+  // alpha-beta over the compile-time schedule: one step adds the products of one (row, source)
+  // pair; a helper lane (20..31) hands its partial row to a scratch slot at the end of a phase
+  auto slot_ptr = [&](int sl) { return sl < 20 ? scr_a + sl * NS : scr_b + (sl - 20) * NS; };
+  auto step = [&](auto type_tag, int k) {
+    constexpr int T = decltype(type_tag)::value;
+    const int e = (int)__ldg(&g_first.e[k][lane]);
+    if (e < 0) return;
+    const int x = (e >> 4) * 12 + (e & 15);
+    const int pq = tb.pq[x], Ja = tb.J[x];
+    const float su = (float)tb.sg[x];
+    float wr[NF], cr[NS];
+    const float4* wrow = reinterpret_cast<const float4*>(ws.Wt + pq * NF);
+#pragma unroll
+    for (int q = 0; q < NF / 4; ++q) {
+      const float4 v = wrow[q];
+      wr[4 * q] = v.x;
+      wr[4 * q + 1] = v.y;
+      wr[4 * q + 2] = v.z;
+      wr[4 * q + 3] = v.w;
+    }
+    const float4* crow = reinterpret_cast<const float4*>(c + Ja * NS);
+#pragma unroll
+    for (int q = 0; q < NS / 4; ++q) {
+      const float4 v = crow[q];
+      cr[4 * q] = su * v.x;
+      cr[4 * q + 1] = su * v.y;
+      cr[4 * q + 2] = su * v.z;
+      cr[4 * q + 3] = su * v.w;
+    }
+    ab_first_terms<T>(std::make_integer_sequence<int, AbFirstHolder<T>::value.n>{}, acc, wr, cr);
+  };
+  auto flush = [&](int ph) {  // helpers: the phase's partial row to its slot
+    if (lane < NS) return;
+    const int sl = (int)__ldg(&g_first.hslot[ph][lane - NS]);
+    if (sl < 0) return;
+    float4* orow = reinterpret_cast<float4*>(slot_ptr(sl));
+#pragma unroll
+    for (int q = 0; q < NS / 4; ++q) orow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+#pragma unroll
+    for (int b = 0; b < NS; ++b) acc[b] = 0.f;
+  };
+  step(std::integral_constant<int, 0>{}, 0);
+  flush(0);
+#pragma unroll 1
+  for (int k = 1; k < 5; ++k) step(std::integral_constant<int, 1>{}, k);
+  flush(1);
+#pragma unroll 1
+  for (int k = 5; k < 9; ++k) step(std::integral_constant<int, 2>{}, k);
+  flush(2);
+  __syncwarp();
+  if (lane < NS) {  // own row + the helpers' partial rows, in slot order
+    const int nsl = (int)__ldg(&g_first.rcount[lane]);
+    for (int i = 0; i < nsl; ++i) {
+      const float4* prow = reinterpret_cast<const float4*>(slot_ptr((int)__ldg(&g_first.rslot[lane][i])));
+#pragma unroll
+      for (int q = 0; q < NS / 4; ++q) {
+        const float4 v = prow[q];
+        acc[4 * q] += v.x;
+        acc[4 * q + 1] += v.y;
+        acc[4 * q + 2] += v.z;
+        acc[4 * q + 3] += v.w;
+      }
+    }
+    float4* orow = reinterpret_cast<float4*>(out + lane * NS);
+#pragma unroll
+    for (int q = 0; q < NS / 4; ++q) orow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
   }
   __syncwarp();
 }
@@ -1552,7 +1800,14 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
     for (int d = lane; d < NDET; d += 32) vk[d] *= inv;
     __syncwarp();
     float* sk = ws.S + k * NDET;
-    sigma<K>(tb, ws, vk, sk, lane);
+    if constexpr (K == 3) {
+      if (it == 0 && !guess_in)  // the first-order vector: nonzero only on the Phi column's support
+        sigma33_first(tb, ws, vk, sk, ws.V + NDET, ws.S + 2 * NDET, lane);
+      else
+        sigma33(tb, ws, vk, sk, lane);
+    } else {
+      sigma<K>(tb, ws, vk, sk, lane);
+    }
     RRAcc agc[KM], agr[KM], akk;
     #pragma unroll 1
     for (int d = lane; d < NDET; d += 32) {
