@@ -152,6 +152,40 @@ __global__ void k_t1_creator_fast(double* __restrict__ W, const double* __restri
   }
 }
 
+// The first pass of the fast form also copies: it reads the bare integrals and writes every row
+// of W (occupied rows unchanged, virtual rows corrected), so no separate copy pass reads and
+// writes W first.  Same arithmetic as k_t1_creator_fast at POS 0.
+template <typename A>
+__global__ void k_t1_creator_copy(const double* __restrict__ src, double* __restrict__ W, const double* __restrict__ t1,
+                                  Dims d) {
+  extern __shared__ double t1raw[];
+  A* t1s = reinterpret_cast<A*>(t1raw);
+  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = to_acc<A>(t1[x]);
+  __syncthreads();
+  const size_t m = (size_t)d.n * d.n * d.n;
+  for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
+    A wi[kT1Omax];
+#pragma unroll
+    for (int i = 0; i < kT1Omax; ++i) {
+      wi[i] = (A)0;
+      if (i < d.o) {
+        const size_t g = t1_index<A, 0>(d, i, rest);
+        const double x = src[g];
+        W[g] = x;
+        wi[i] = to_acc<A>(x);
+      }
+    }
+    for (int a = 0; a < d.v; ++a) {
+      A acc = 0;
+#pragma unroll
+      for (int i = 0; i < kT1Omax; ++i)
+        if (i < d.o) acc += t1s[i * d.v + a] * wi[i];
+      const size_t g = t1_index<A, 0>(d, d.o + a, rest);
+      W[g] = src[g] - from_acc<A>(acc);
+    }
+  }
+}
+
 template <typename A, int POS>
 __global__ void k_t1_annihilator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
   extern __shared__ double t1raw[];
@@ -176,16 +210,19 @@ __global__ void k_t1_annihilator_fast(double* __restrict__ W, const double* __re
 }
 
 template <typename A>
-void t1_passes(double* W, const double* t1, const Dims& d, cudaStream_t st) {
+void t1_passes(const double* eri, double* W, const double* t1, const Dims& d, cudaStream_t st) {
   const size_t mc = (size_t)d.v * d.n * d.n * d.n, ma = (size_t)d.o * d.n * d.n * d.n;
+  const size_t n3 = (size_t)d.n * d.n * d.n;
   if (d.o <= kT1Omax) {
-    const size_t n3 = (size_t)d.n * d.n * d.n, sm = sizeof(double) * d.o * d.v;
+    const size_t sm = sizeof(double) * d.o * d.v;
     const unsigned g = blocks_for(n3) > 152u * 16u ? 152u * 16u : blocks_for(n3);
-    k_t1_creator_fast<A, 0><<<g, TPB, sm, st>>>(W, t1, d);
+    k_t1_creator_copy<A><<<g, TPB, sm, st>>>(eri, W, t1, d);
     k_t1_creator_fast<A, 2><<<g, TPB, sm, st>>>(W, t1, d);
     k_t1_annihilator_fast<A, 1><<<g, TPB, sm, st>>>(W, t1, d);
     k_t1_annihilator_fast<A, 3><<<g, TPB, sm, st>>>(W, t1, d);
   } else {
+    const size_t n4 = n3 * d.n;
+    k_copy<<<blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
     k_t1_creator<A><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 0);
     k_t1_creator<A><<<blocks_for(mc), TPB, 0, st>>>(W, t1, d, 2);
     k_t1_annihilator<A><<<blocks_for(ma), TPB, 0, st>>>(W, t1, d, 1);
@@ -616,10 +653,13 @@ size_t dress_workspace_bytes_mixed(int n, int nocc) {
 }
 
 int dress_launch_count(int n, int nocc, bool mixed) {
-  // copy, 4 T1 passes, h~, f~, 2 energy, u, small blocks, finalize; T2 terms: 7 SIMT kernels
-  // (FP64) or 2 FP32 copies + 35 operand packs + 10 GEMM launches + FP32 Fock copies + 4 finalize
+  // 4 T1 passes (the first one copies; for nocc > kT1Omax a separate copy + 4), h~, f~, 2 energy,
+  // u, small blocks, finalize; T2 terms: 7 SIMT kernels (FP64) or 2 FP32 copies + 33 operand
+  // packs + 9 GEMM launches + the vvvv pack and two product kernels + FP32 Fock copies + 4 finalize
   // kernels + error check (mixed)
-  return (n - nocc > 0 && nocc > 0) ? (mixed ? 12 + 53 : 12 + 7) : 5;
+  if (!(n - nocc > 0 && nocc > 0)) return 5;
+  const int front = (nocc <= kT1Omax ? 4 : 5) + 7;
+  return front + (mixed ? 53 : 7);
 }
 
 namespace {
@@ -837,62 +877,6 @@ struct LR2G6B {
   __device__ float operator()(int col, int k) const {
     const int ov = c.o * c.v, kk = k % ov, i = col / c.v, a = col % c.v, m = kk / c.v, e = kk % c.v;
     return (k < ov) ? c.G(m, c.o + e, c.o + a, i) : -c.G(m, i, c.o + a, c.o + e);
-  }
-};
-
-// vvvv: rows (a, b), cols (e, f), k = (m, n); W[a e b f] += D
-struct LV4A {
-  TcCtx c;
-  __device__ float operator()(int r, int k) const { return c.T(k / c.o, k % c.o, r / c.v, r % c.v); }
-};
-struct LV4B {
-  TcCtx c;
-  __device__ float operator()(int col, int k) const {
-    return c.G(k / c.o, c.o + col / c.v, k % c.o, c.o + col % c.v);
-  }
-};
-// (the mixed path's flows only read elements with at most three distinct virtual indices among
-// a, e, b, f: the store skips the others, about 94 % of the block's read-modify-writes at v = 100)
-struct StoreV4 {  // rows (e, f), cols (a, b): consecutive lanes write consecutive f
-  double* W;
-  int n, o, v;
-  __device__ static bool read3(int a, int e, int b, int f) {  // at most three distinct indices
-    return a == e || a == b || a == f || e == b || e == f || b == f;
-  }
-  // all 32 old values are loaded before any is written back, so the read-modify-writes do not
-  // wait on one another (the addresses are distinct)
-  __device__ void run(int r, int col, const float (&val)[32], int cnt) const {
-    const size_t n1 = (size_t)n, n2 = n1 * n1, n3 = n2 * n1;
-    const int e = r / v, f = r % v;
-    const size_t base = (size_t)(o + e) * n2 + (size_t)(o + f);
-    const int a0 = col / v, b0 = col % v;
-    double old[32];
-    {
-      int a = a0, b = b0;
-      size_t x = base + (size_t)(o + a) * n3 + (size_t)(o + b) * n1;
-#pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        old[t] = (t < cnt && read3(a, e, b, f)) ? W[x] : 0.0;
-        x += n1;
-        if (++b == v) {
-          b = 0;
-          ++a;
-          x = base + (size_t)(o + a) * n3 + (size_t)o * n1;
-        }
-      }
-    }
-    int a = a0, b = b0;
-    size_t x = base + (size_t)(o + a) * n3 + (size_t)(o + b) * n1;
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      if (t < cnt && read3(a, e, b, f)) W[x] = old[t] + (double)val[t];
-      x += n1;
-      if (++b == v) {
-        b = 0;
-        ++a;
-        x = base + (size_t)(o + a) * n3 + (size_t)o * n1;
-      }
-    }
   }
 };
 
@@ -1175,6 +1159,130 @@ __global__ void k_gemm_check(const int* __restrict__ err, double* __restrict__ e
 
 // Scratch for packed operands: a bump allocator over one region, reset between phases; a dry
 // run (base == nullptr) only records the peak, which sizes the workspace.
+// vvvv block restricted to what (k, k) spaces with k <= 3 read: W[A E B F] with at most three
+// distinct virtual indices among a, e, b, f (about 6 v^3 of the v^4 elements), each getting the
+// ladder-type term  D = sum_mn g~_menf t_mn^ab  (FP32 products and sums, added in FP64).  Operands
+// packed once as rows of o^2:  Gt[(e v + f)][m o + n] = g~[m][o+e][n][o+f],
+// Tt[(a v + b)][m o + n] = t2[m][n][a][b].  The restricted set is the disjoint union of six
+// families, each a batch of v products C_x = T_x G_x^T (v x v, K = o^2) over rows of Tt and Gt:
+//   0  a = b (all e, f):            x = a, C[e][f] = Tt(a,a).Gt(e,f)  -> W[A E A F]
+//   1  e = a != b (all f):          x = a, C[b][f] = Tt(a,b).Gt(a,f)  -> W[A A B F]
+//   2  e = b != a (all f):          x = b, C[a][f] = Tt(a,b).Gt(b,f)  -> W[A B B F]
+//   3  f = a, a != b, e not in {a, b}: x = a, C[b][e] = Tt(a,b).Gt(e,a) -> W[A E B A]
+//   4  f = b, a != b, e not in {a, b}: x = b, C[a][e] = Tt(a,b).Gt(e,b) -> W[A E B B]
+//   5  e = f, a != b, e not in {a, b}: x = a, C[b][e] = Tt(a,b).Gt(e,e) -> W[A E B E]
+__global__ void k_pack_vvvv(const float* __restrict__ g, const float* __restrict__ t2, float* __restrict__ Gt,
+                            float* __restrict__ Tt, Dims d) {
+  const int o = d.o, v = d.v, oo = o * o;
+  const size_t m_all = (size_t)v * v * oo;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < m_all; x += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(x % oo), ef = (int)(x / oo);
+    const int m = k / o, nn = k % o, e = ef / v, f = ef % v;
+    Gt[x] = g[gi(d, m, o + e, nn, o + f)];
+    Tt[x] = t2[ti(d, m, nn, e, f)];
+  }
+}
+
+constexpr int kV4Tile = 128;  // v <= 128: one CTA holds a family's whole v x v product
+constexpr int kV4K = 32;      // K chunk staged in shared memory
+
+__global__ void __launch_bounds__(256) k_vvvv_restricted(double* __restrict__ W, const float* __restrict__ Gt,
+                                                         const float* __restrict__ Tt, Dims d) {
+  __shared__ float ts[kV4K][kV4Tile + 4], gs[kV4K][kV4Tile + 4];  // [k][row]
+  const int o = d.o, v = d.v, oo = o * o;
+  const int fam = 1 + blockIdx.x / v, x = blockIdx.x % v;  // families 1..5 (0: k_vvvv_diag)
+  const size_t n1 = d.n, n2 = n1 * n1, n3 = n2 * n1;
+  // row selectors of the batch: T row i, G row j
+  auto trow = [&](int i) -> int { return (fam == 1 || fam == 3 || fam == 5) ? x * v + i : i * v + x; };
+  auto grow = [&](int j) -> int {
+    switch (fam) {
+      case 1: case 2: return x * v + j;
+      case 3: case 4: return j * v + x;
+      default: return j * (v + 1);  // 5
+    }
+  };
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;  // 16 x 16 threads, 8 x 8 outputs each
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  for (int k0 = 0; k0 < oo; k0 += kV4K) {
+    __syncthreads();
+    for (int t = tid; t < kV4K * kV4Tile; t += 256) {
+      const int kk = t / kV4Tile, r = t % kV4Tile, k = k0 + kk;
+      float tv = 0.f, gv = 0.f;
+      if (r < v && k < oo) {
+        tv = Tt[(size_t)trow(r) * oo + k];
+        gv = Gt[(size_t)grow(r) * oo + k];
+      }
+      ts[kk][r] = tv;
+      gs[kk][r] = gv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kV4K; ++kk) {
+      float a[8], b[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) a[r] = ts[kk][ty * 8 + r];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) b[c] = gs[kk][tx * 8 + c];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = ty * 8 + r;
+    if (i >= v) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = tx * 8 + c;
+      if (j >= v) continue;
+      int a, e, b, f;
+      bool keep;
+      switch (fam) {
+        case 1: a = x; b = i; e = x; f = j; keep = (i != x); break;
+        case 2: a = i; b = x; e = x; f = j; keep = (i != x); break;
+        case 3: a = x; b = i; e = j; f = x; keep = (i != x && j != x && j != i); break;
+        case 4: a = i; b = x; e = j; f = x; keep = (i != x && j != x && j != i); break;
+        default: a = x; b = i; e = j; f = j; keep = (i != x && j != x && j != i); break;
+      }
+      if (keep) {
+        const size_t w = (size_t)(o + a) * n3 + (size_t)(o + e) * n2 + (size_t)(o + b) * n1 + (size_t)(o + f);
+        W[w] += (double)acc[r][c];
+      }
+    }
+  }
+}
+
+// Family 0 (a = b, every (e, f)): C[e][f] = Tt(a,a).Gt(e v + f), a warp per output streaming
+// Gt's rows (contiguous) with Tt(a,a) in registers; kV4Diag blocks share one a.
+constexpr int kV4Diag = 8;
+__global__ void __launch_bounds__(256) k_vvvv_diag(double* __restrict__ W, const float* __restrict__ Gt,
+                                                   const float* __restrict__ Tt, Dims d) {
+  const int o = d.o, v = d.v, oo = o * o, lane = threadIdx.x & 31;
+  const int a = blockIdx.x / kV4Diag, part = blockIdx.x % kV4Diag;
+  const size_t n1 = d.n, n2 = n1 * n1, n3 = n2 * n1;
+  const float* trow = Tt + (size_t)(a * v + a) * oo;
+  const int rows = v * v, per = (rows + kV4Diag - 1) / kV4Diag;
+  const int r1 = (part + 1) * per < rows ? (part + 1) * per : rows;
+  for (int r = part * per + (int)(threadIdx.x >> 5); r < r1; r += (int)(blockDim.x >> 5)) {
+    const float* gr = Gt + (size_t)r * oo;
+    float acc = 0.f;
+    for (int k = lane; k < oo; k += 32) acc = fmaf(trow[k], gr[k], acc);
+#pragma unroll
+    for (int s2 = 16; s2 > 0; s2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s2);
+    if (lane == 0) {
+      const int e = r / v, f = r % v;
+      const size_t w = (size_t)(o + a) * n3 + (size_t)(o + e) * n2 + (size_t)(o + a) * n1 + (size_t)(o + f);
+      W[w] += (double)acc;
+    }
+  }
+}
+
 struct Arena {
   float* base;
   size_t used = 0, peak = 0;
@@ -1327,15 +1435,18 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
     }
   }
   // blocks written in place (their bases are read from W by the store of their single job)
-  {  // vvvv: the product on the tensor cores, stored only where (k, k) spaces read it
+  {  // vvvv: only the elements (k, k) spaces read, six batched SIMT products (v <= 128)
+    static_assert(kV4Tile >= 128, "n <= 128 orbitals: v fits one tile");
     ar.reset();
-    Op a, b;
-    QF_TRY(pack_op(LV4B{c}, vv, oo, kTileM, ar, &a, st));
-    QF_TRY(pack_op(LV4A{c}, vv, oo, 128, ar, &b, st));
-    tc::PackedJobs<StoreV4> js{};
-    js.j[0] = job(a, b, StoreV4{W, d.n, o, v});
-    js.count = 1;
-    QF_TRY((run_jobs<128>(js, ar, err, st)));
+    float* Gt = ar.take((size_t)vv * oo);
+    float* Tt = ar.take((size_t)vv * oo);
+    if (run && e == cudaSuccess) {
+      const size_t m_all = (size_t)vv * oo;
+      k_pack_vvvv<<<blocks_for(m_all) > 152u * 32u ? 152u * 32u : blocks_for(m_all), TPB, 0, st>>>(G, t2, Gt, Tt, d);
+      k_vvvv_diag<<<kV4Diag * v, 256, 0, st>>>(W, Gt, Tt, d);
+      k_vvvv_restricted<<<5 * v, 256, 0, st>>>(W, Gt, Tt, d);
+      e = cudaGetLastError();
+    }
   }
   {
     ar.reset();
@@ -1437,10 +1548,11 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
   Dims d{n, nocc, n - nocc};
   const size_t n4 = (size_t)n * n * n * n;
   const size_t o = nocc, v = n - nocc;
-  k_copy<<<blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
-  if (v > 0 && o > 0) {
-    if (mixed) t1_passes<float>(W, t1, d, st);  // FP32 correction sums onto the FP64 elements
-    else t1_passes<double>(W, t1, d, st);
+  if (v > 0 && o > 0) {  // W = the bare integrals with T1 applied (the first pass copies them)
+    if (mixed) t1_passes<float>(eri, W, t1, d, st);  // FP32 correction sums onto the FP64 elements
+    else t1_passes<double>(eri, W, t1, d, st);
+  } else {
+    k_copy<<<blocks_for(n4) > 152u * 64u ? 152u * 64u : blocks_for(n4), TPB, 0, st>>>(eri, W, n4);
   }
   k_h_tilde<<<blocks_for((size_t)n * n), TPB, 0, st>>>(h, t1, w.ht, d);
   k_fock<<<blocks_for((size_t)n * n), TPB, 0, st>>>(w.ht, W, F, d);
