@@ -20,94 +20,59 @@
 #include <stdint.h>
 
 #include "qflow_internal.h"
+#include "tc_gemm.cuh"
 
 namespace qf {
 namespace {
 
-// ---- FP32 tiled matrix product with fused epilogues ---------------------------------------
-constexpr int GT = 64;   // tile rows and columns
-constexpr int GK = 16;   // tile depth
-constexpr int GPAD = 4;  // shared-memory row padding (keeps float4 alignment)
-constexpr int GTHREADS = 256;
-
+// ---- matrix products on the tensor cores, with fused epilogues --------------------------------
+// C[M][N] = op(A) op(B) through the repo's tcgen05 engine (three-term TF32 products, FP32
+// accumulation in tensor memory: FP32-accurate): op(A) is A[M][K] (lda) or, when TA, A stored
+// [K][M]; op(B) is B[K][N] (ldb) or, when TB, B stored [N][K].  Epilogues: kBiasTanh
+// C = tanh(acc + bias[n]); kBias C = acc + bias[n]; kTanhGrad C = acc * (1 - aux[m][n]^2) (aux has
+// C's layout).  `err` is set by a tile that gave up waiting on its operands (k_mlp_check then
+// makes the first output NaN, so a failed product cannot pass silently).
 enum Epi { kStore = 0, kBiasTanh = 1, kBias = 2, kTanhGrad = 3 };
 
-// C[M][N] = op(A) op(B): op(A) is A[M][K] (lda) or, when TA, A stored [K][M]; op(B) is B[K][N]
-// (ldb) or, when TB, B stored [N][K].  Epilogues: kBiasTanh C = tanh(acc + bias[n]);
-// kBias C = acc + bias[n]; kTanhGrad C = acc * (1 - aux[m][n]^2) (aux has C's layout).
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(GTHREADS) k_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
-                                                   const float* __restrict__ B, int ldb, float* __restrict__ C,
-                                                   int ldc, const float* __restrict__ bias,
-                                                   const float* __restrict__ aux) {
-  __shared__ __align__(16) float As[GK][GT + GPAD];
-  __shared__ __align__(16) float Bs[GK][GT + GPAD];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-#pragma unroll
-    for (int r = 0; r < (GT * GK) / GTHREADS; ++r) {
-      const int e = tid + r * GTHREADS;
-      const int mm = TA ? e % GT : e / GK, kk = TA ? e / GT : e % GK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      float v = 0.f;
-      if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-      As[kk][mm] = v;
-    }
-#pragma unroll
-    for (int r = 0; r < (GT * GK) / GTHREADS; ++r) {
-      const int e = tid + r * GTHREADS;
-      const int nn = TB ? e / GK : e % GT, kk = TB ? e % GK : e / GT;
-      const int gk = k0 + kk, gn = n0 + nn;
-      float v = 0.f;
-      if (gk < K && gn < N) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-      Bs[kk][nn] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
+template <bool T>
+struct LoadOp {  // element (r, k) of op(X): X[r][k] (T = false) or X stored [k][r] (T = true)
+  const float* p;
+  int ld;
+  __device__ float operator()(int r, int k) const { return T ? p[(size_t)k * ld + r] : p[(size_t)r * ld + k]; }
+};
+template <int EPI>
+struct StoreEpi {
+  float* C;
+  int ldc;
+  const float* bias;
+  const float* aux;
+  __device__ void operator()(int m, int n, float v) const {
+    const size_t x = (size_t)m * ldc + n;
+    if (EPI == kBiasTanh) v = tanhf(v + bias[n]);
+    else if (EPI == kBias) v = v + bias[n];
+    else if (EPI == kTanhGrad) v = v * (1.f - aux[x] * aux[x]);
+    C[x] = v;
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + ty * 4 + i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx * 4 + j;
-      if (gn >= N) continue;
-      float v = acc[i][j];
-      if (EPI == kBiasTanh) v = tanhf(v + bias[gn]);
-      if (EPI == kBias) v += bias[gn];
-      if (EPI == kTanhGrad) {
-        const float hv = aux[(size_t)gm * ldc + gn];
-        v *= 1.f - hv * hv;
-      }
-      C[(size_t)gm * ldc + gn] = v;
-    }
-  }
+};
+
+__global__ void k_mlp_check(const int* __restrict__ err, float* __restrict__ y) {
+  if (threadIdx.x == 0 && *err) y[0] = __int_as_float(0x7fc00000);
 }
 
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                 const float* bias, const float* aux, cudaStream_t st) {
+                 const float* bias, const float* aux, int* err, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT));
-  k_gemm<TA, TB, EPI><<<grid, GTHREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux);
-  return cudaGetLastError();
+  // the engine forms sum_k a(m, k) b(n, k): op(B)^T element (n, k) is B[k][n], or B[n][k] when TB.
+  // Tile width: the widest that N fills while the tiles still cover every SM (op(A) streamed
+  // fewer times); products with few 128-row tiles (the weight gradients, K = rows) take 64.
+  const LoadOp<TA> la{A, lda};
+  const LoadOp<!TB> lb{B, ldb};
+  const StoreEpi<EPI> sv{C, ldc, bias, aux};
+  const int mt = (M + 127) / 128;
+  if (N > 128 && mt * ((N + 255) / 256) >= 152) return tc::gemm_tf32x3<256>(M, N, K, la, lb, sv, err, st);
+  if (N > 64 && mt * ((N + 127) / 128) >= 152) return tc::gemm_tf32x3<128>(M, N, K, la, lb, sv, err, st);
+  return tc::gemm_tf32x3<64>(M, N, K, la, lb, sv, err, st);
 }
 
 // out[c] = sum over rows r (ascending) of X[r][c]
@@ -454,7 +419,11 @@ int64_t mlp_param_count(int I, int H, int O) { return (int64_t)I * H + H + (int6
 size_t mlp_workspace_bytes(int I, int H, int O, int64_t rows) {
   (void)I;
   // H1, H2, dZ (rows x H each), Y, dY (rows x O each), loss partials + loss
-  return sizeof(float) * ((size_t)rows * (3 * (size_t)H + 2 * (size_t)O) + LGRID + 4) + 256;
+  return sizeof(float) * ((size_t)rows * (3 * (size_t)H + 2 * (size_t)O) + LGRID + 4) + 512;
+}
+// the products' timeout flag: the workspace's last 256 bytes
+int* mlp_err(void* work, int I, int H, int O, int64_t rows) {
+  return reinterpret_cast<int*>(static_cast<char*>(work) + mlp_workspace_bytes(I, H, O, rows) - 256);
 }
 
 cudaError_t mlp_forward(int I, int H, int O, const float* params, const float* x, int64_t rows, float* y, void* work,
@@ -463,9 +432,15 @@ cudaError_t mlp_forward(int I, int H, int O, const float* params, const float* x
   float* H1 = static_cast<float*>(work);
   float* H2 = H1 + (size_t)rows * H;
   const int R = (int)rows;
-  cudaError_t e = gemm<false, false, kBiasTanh>(R, H, I, x, I, net.W1, H, H1, H, net.b1, nullptr, st);
-  if (e == cudaSuccess) e = gemm<false, false, kBiasTanh>(R, H, H, H1, H, net.W2, H, H2, H, net.b2, nullptr, st);
-  if (e == cudaSuccess) e = gemm<false, false, kBias>(R, O, H, H2, H, net.W3, O, y, O, net.b3, nullptr, st);
+  int* err = mlp_err(work, I, H, O, rows);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = gemm<false, false, kBiasTanh>(R, H, I, x, I, net.W1, H, H1, H, net.b1, nullptr, err, st);
+  if (e == cudaSuccess) e = gemm<false, false, kBiasTanh>(R, H, H, H1, H, net.W2, H, H2, H, net.b2, nullptr, err, st);
+  if (e == cudaSuccess) e = gemm<false, false, kBias>(R, O, H, H2, H, net.W3, O, y, O, net.b3, nullptr, err, st);
+  if (e == cudaSuccess && R > 0) {
+    k_mlp_check<<<1, 32, 0, st>>>(err, y);
+    e = cudaGetLastError();
+  }
   return e;
 }
 
@@ -485,26 +460,29 @@ cudaError_t mlp_loss_grad(int I, int H, int O, const float* params, const float*
   float* gb2 = gW2 + (size_t)H * H;
   float* gW3 = gb2 + H;
   float* gb3 = gW3 + (size_t)H * O;
-  cudaError_t e = gemm<false, false, kBiasTanh>(R, H, I, x, I, net.W1, H, H1, H, net.b1, nullptr, st);
-  if (e == cudaSuccess) e = gemm<false, false, kBiasTanh>(R, H, H, H1, H, net.W2, H, H2, H, net.b2, nullptr, st);
-  if (e == cudaSuccess) e = gemm<false, false, kBias>(R, O, H, H2, H, net.W3, O, Y, O, net.b3, nullptr, st);
+  int* err = mlp_err(work, I, H, O, rows);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = gemm<false, false, kBiasTanh>(R, H, I, x, I, net.W1, H, H1, H, net.b1, nullptr, err, st);
+  if (e == cudaSuccess) e = gemm<false, false, kBiasTanh>(R, H, H, H1, H, net.W2, H, H2, H, net.b2, nullptr, err, st);
+  if (e == cudaSuccess) e = gemm<false, false, kBias>(R, O, H, H2, H, net.W3, O, Y, O, net.b3, nullptr, err, st);
   if (e != cudaSuccess) return e;
   k_loss_grad<<<LGRID, LB, 0, st>>>(Y, t, mask, R, O, dY, part);
   k_loss_final<<<1, 32, 0, st>>>(part, R, loss);
   // layer 3: gW3 = H2^T dY, gb3 = colsum dY, dZ2 = (dY W3^T) (1 - H2^2)
-  e = gemm<true, false, kStore>(H, O, R, H2, H, dY, O, gW3, O, nullptr, nullptr, st);
+  e = gemm<true, false, kStore>(H, O, R, H2, H, dY, O, gW3, O, nullptr, nullptr, err, st);
   if (e != cudaSuccess) return e;
   k_colsum<<<grid1(O, 128), 128, 0, st>>>(dY, R, O, gb3);
-  e = gemm<false, true, kTanhGrad>(R, H, O, dY, O, net.W3, O, dZ, H, nullptr, H2, st);
+  e = gemm<false, true, kTanhGrad>(R, H, O, dY, O, net.W3, O, dZ, H, nullptr, H2, err, st);
   // layer 2: gW2 = H1^T dZ2, gb2 = colsum dZ2, dZ1 = (dZ2 W2^T) (1 - H1^2) (into H2's buffer)
-  if (e == cudaSuccess) e = gemm<true, false, kStore>(H, H, R, H1, H, dZ, H, gW2, H, nullptr, nullptr, st);
+  if (e == cudaSuccess) e = gemm<true, false, kStore>(H, H, R, H1, H, dZ, H, gW2, H, nullptr, nullptr, err, st);
   if (e != cudaSuccess) return e;
   k_colsum<<<grid1(H, 128), 128, 0, st>>>(dZ, R, H, gb2);
-  e = gemm<false, true, kTanhGrad>(R, H, H, dZ, H, net.W2, H, H2, H, nullptr, H1, st);
+  e = gemm<false, true, kTanhGrad>(R, H, H, dZ, H, net.W2, H, H2, H, nullptr, H1, err, st);
   // layer 1: gW1 = X^T dZ1, gb1 = colsum dZ1
-  if (e == cudaSuccess) e = gemm<true, false, kStore>(I, H, R, x, I, H2, H, gW1, H, nullptr, nullptr, st);
+  if (e == cudaSuccess) e = gemm<true, false, kStore>(I, H, R, x, I, H2, H, gW1, H, nullptr, nullptr, err, st);
   if (e != cudaSuccess) return e;
   k_colsum<<<grid1(H, 128), 128, 0, st>>>(H2, R, H, gb1);
+  k_mlp_check<<<1, 32, 0, st>>>(err, loss);  // a failed product shows as a NaN loss
   return cudaGetLastError();
 }
 

@@ -1876,17 +1876,21 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
   }
   const int k = ws.ctrl[0];
   float xx = 0.f;
-  #pragma unroll 1
-  for (int d = lane; d < NDET; d += 32) {
-    float xv = (d == 0) ? ws.yf[0] : 0.f;
-    for (int j = 1; j < k; ++j) xv = fmaf(ws.yf[j], ws.V[(j - 1) * NDET + d], xv);
-    ws.S[d] = xv;
-    xx = fmaf(xv, xv, xx);
+  if (owner || guess_out) {  // the Ritz vector itself: the increment and the saved root read it
+#pragma unroll 1
+    for (int d = lane; d < NDET; d += 32) {
+      float xv = (d == 0) ? ws.yf[0] : 0.f;
+      for (int j = 1; j < k; ++j) xv = fmaf(ws.yf[j], ws.V[(j - 1) * NDET + d], xv);
+      ws.S[d] = xv;
+      xx = fmaf(xv, xv, xx);
+    }
+    xx = wsum(xx);
+    __syncwarp();
+  } else {  // only its norm (root test): the stored vectors are orthonormal and orthogonal to Phi
+    for (int j = 0; j < k; ++j) xx = fmaf(ws.yf[j], ws.yf[j], xx);
   }
-  xx = wsum(xx);
-  __syncwarp();
   const float xn = sqrtf(xx);
-  const float c0 = ws.S[0];
+  const float c0 = ws.yf[0];  // component 0 of the Ritz vector (every stored vector has a zero there)
   int st = ws.ctrl[2];
   if (st == kSpaceNoConv && ws.ctrl[1] > 0) st = kSpaceRoot;  // stopped on a complex projected root
   if (st == kSpaceOk && !(fabsf(c0) >= 1e-3f * xn)) st = kSpaceRoot;
