@@ -218,8 +218,9 @@ int qflow_sweep_waves(qflow_handle hnd, int64_t wave, double* d_e, double* max_d
  * launches (no graph replay).  nranks = 1 makes the three-call form cover the whole list. */
 int qflow_set_shard(qflow_handle hnd, int32_t rank, int32_t nranks);
 
-/* Length (FP64 elements) of the exchange vector: pool (nocc*nvir + nocc^2*nvir^2), then
- * energy, status and Davidson iterations per space (3 * nspaces, sorted order). */
+/* Length (FP64 elements) of the exchange vector: pool (nocc*nvir + nocc^2*nvir^2), then the
+ * energy and a code per space (2 * nspaces, sorted order), code = status * 2^20 + Davidson
+ * iterations (an exact integer in FP64). */
 int64_t qflow_exchange_size(qflow_handle hnd);
 
 /* Dressing + this shard's solves; fills exchange[qflow_exchange_size] (device pointer, caller

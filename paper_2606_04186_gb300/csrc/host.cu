@@ -1008,7 +1008,7 @@ int qflow_sweep_waves(qflow_handle c, int64_t wave, double* d_e, double* max_dt,
 }
 
 int64_t qflow_exchange_size(qflow_handle c) {
-  return c ? c->n_t1 + c->n_t2 + 3 * c->nspaces : 0;
+  return c ? c->n_t1 + c->n_t2 + 2 * c->nspaces : 0;
 }
 
 int qflow_sweep_shard_begin(qflow_handle c, double* exchange) {

@@ -85,22 +85,25 @@ __global__ void k_final(const Partial* __restrict__ in, int64_t ns, double* __re
   }
 }
 
-// Exchange vector of a sharded sweep: [pool (np) | energy (ns) | status (ns) | iterations (ns)].
+// Exchange vector of a sharded sweep: [pool (np) | energy (ns) | code (ns)], code = status * 2^20
+// + Davidson iterations (an exact integer in FP64; both fields are small and non-negative).
 // Entries this shard did not produce hold -0.0, the identity of floating-point addition for every
 // value (x + (-0.0) = x, also for x = +0.0 and -0.0), so the element-wise sum over the ranks
 // reproduces each produced entry exactly, in any summation order.
+constexpr int kCodeShift = 20;  // iterations below 2^20
 __global__ void k_exchange_pack(const double* __restrict__ pool_new, const uint8_t* __restrict__ pool_mask, int64_t np,
                                 const double* __restrict__ energy, const int32_t* __restrict__ status,
                                 const int32_t* __restrict__ iters, const uint8_t* __restrict__ space_mask, int64_t ns,
                                 double* __restrict__ x) {
-  const int64_t total = np + 3 * ns;
+  const int64_t total = np + 2 * ns;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     double v = -0.0;
     if (i < np) {
       if (pool_mask[i]) v = pool_new[i];
     } else {
       const int64_t j = (i - np) % ns, seg = (i - np) / ns;
-      if (space_mask[j]) v = (seg == 0) ? energy[j] : (double)((seg == 1) ? status[j] : iters[j]);
+      if (space_mask[j])
+        v = (seg == 0) ? energy[j] : (double)(((int64_t)status[j] << kCodeShift) + (int64_t)iters[j]);
     }
     x[i] = v;
   }
@@ -112,16 +115,20 @@ __global__ void k_exchange_unpack(const double* __restrict__ x, const int32_t* _
                                   const int32_t* __restrict__ own2, int64_t n2, double* __restrict__ pool_new,
                                   double* __restrict__ energy, int32_t* __restrict__ status,
                                   int32_t* __restrict__ iters, int64_t ns) {
-  const int64_t np = n1 + n2, total = np + 3 * ns;
+  const int64_t np = n1 + n2, total = np + 2 * ns;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < np) {
       const int32_t o = (i < n1) ? own1[i] : own2[i - n1];
       if (o >= 0) pool_new[i] = x[i];
     } else {
       const int64_t j = (i - np) % ns, seg = (i - np) / ns;
-      if (seg == 0) energy[j] = x[i];
-      else if (seg == 1) status[j] = (int32_t)x[i];
-      else iters[j] = (int32_t)x[i];
+      if (seg == 0) {
+        energy[j] = x[i];
+      } else {
+        const int64_t c = (int64_t)x[i];
+        status[j] = (int32_t)(c >> kCodeShift);
+        iters[j] = (int32_t)(c & ((1 << kCodeShift) - 1));
+      }
     }
   }
 }
@@ -131,7 +138,7 @@ __global__ void k_exchange_unpack(const double* __restrict__ x, const int32_t* _
 cudaError_t launch_exchange_pack(const double* pool_new, const uint8_t* pool_mask, int64_t np, const double* energy,
                                  const int32_t* status, const int32_t* iters, const uint8_t* space_mask, int64_t ns,
                                  double* x, cudaStream_t st) {
-  const int64_t total = np + 3 * ns;
+  const int64_t total = np + 2 * ns;
   if (total == 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((total + RB - 1) / RB, 152 * 16);
   k_exchange_pack<<<(unsigned)blocks, RB, 0, st>>>(pool_new, pool_mask, np, energy, status, iters, space_mask, ns, x);
@@ -141,7 +148,7 @@ cudaError_t launch_exchange_pack(const double* pool_new, const uint8_t* pool_mas
 cudaError_t launch_exchange_unpack(const double* x, const int32_t* own1, int64_t n1, const int32_t* own2, int64_t n2,
                                    double* pool_new, double* energy, int32_t* status, int32_t* iters, int64_t ns,
                                    cudaStream_t st) {
-  const int64_t total = n1 + n2 + 3 * ns;
+  const int64_t total = n1 + n2 + 2 * ns;
   if (total == 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((total + RB - 1) / RB, 152 * 16);
   k_exchange_unpack<<<(unsigned)blocks, RB, 0, st>>>(x, own1, n1, own2, n2, pool_new, energy, status, iters, ns);

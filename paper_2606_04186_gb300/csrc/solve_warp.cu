@@ -44,6 +44,11 @@
 namespace qf {
 namespace {
 
+// Loop unrolling of the table-driven set-up steps (measured: the same-spin table at 11 steps per
+// iteration, the first-order vector rolled; 22, 66 and a fully unrolled first-order loop were not
+// faster)
+constexpr int kHsUnroll = 11;
+constexpr int kFoUnroll = 1;
 constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
 // Spaces (warps) per CTA: a launch parameter up to kMaxWarps (the autotuner picks it); one CTA
 // fills the shared memory of an SM.  The register file is split over the SM's four
@@ -1539,7 +1544,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         }
         __syncwarp();
         const float j0 = ws.j0;
-#pragma unroll 1
+#pragma unroll kFoUnroll
         for (int k = 0; k < kPhiLen; ++k) {
           const unsigned e = phi_entry(cs, k * 32 + lane);
           if (e & (1u << 20)) {
@@ -1591,7 +1596,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
     for (int q = lane; q < NS * NS / 4; q += 32) reinterpret_cast<float4*>(ws.Hs)[q] = z4;
     __syncwarp();
     float acc = 0.f;
-#pragma unroll 11
+#pragma unroll kHsUnroll
     for (int k = 0; k < kHsLen; ++k) {
       const unsigned e = hs_entry(cs, k * 32 + lane);
       acc = fmaf(__uint_as_float(e & 0xff800000u), ws.Wt[e & 2047u], acc);

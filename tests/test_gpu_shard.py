@@ -48,7 +48,7 @@ def test_sharded_sweeps_bitwise(qf, name, precision, R, diis, guess):
     for r, f in enumerate(flows):
         f.set_shard(r, R)
     n = flows[0].exchange_size()
-    assert n == s.nocc * (s.n - s.nocc) + (s.nocc * (s.n - s.nocc)) ** 2 + 3 * len(sp)
+    assert n == s.nocc * (s.n - s.nocc) + (s.nocc * (s.n - s.nocc)) ** 2 + 2 * len(sp)
     bufs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(R)]
     for sweep in range(3):
         de, dt, nf, code = ref.sweep()

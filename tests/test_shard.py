@@ -3,7 +3,8 @@ reconstruction of the partition, and a two-rank gloo run of the sharded sweep pr
 oracle doing each rank's per-space work.
 
 The protocol under test: every rank dresses the same pool, solves the spaces of its shard,
-writes the exchange vector [owned pool entries | energy | status | iterations] with -0.0 in every
+writes the exchange vector [owned pool entries | energy | code] (code = status * 2^20 + Davidson
+iterations, an exact integer in FP64) with -0.0 in every
 entry it did not produce, the ranks sum the vectors (allreduce), and every rank merges the sum.
 Owners are unique (Numerical Implementation: each amplitude belongs to exactly one space), so the
 result must equal an unsharded sweep bit for bit.
@@ -94,10 +95,10 @@ def _pack(t1n, t2n, res, smask, pmask):
     """Exchange vector of one rank; -0.0 where the rank produced nothing."""
     ns = len(res)
     pool = np.concatenate([t1n.ravel(), t2n.ravel()])
-    x = np.full(pool.size + 3 * ns, -0.0)
+    x = np.full(pool.size + 2 * ns, -0.0)
     x[:pool.size] = np.where(pmask == 1, pool, -0.0)
     e = np.array([r[0] if r is not None else 0.0 for r in res])
-    st = np.array([float(r[3]) if r is not None else 0.0 for r in res])
+    st = np.array([float(int(r[3]) << 20) if r is not None else 0.0 for r in res])
     x[pool.size:pool.size + ns] = np.where(smask == 1, e, -0.0)
     x[pool.size + ns:pool.size + 2 * ns] = np.where(smask == 1, st, -0.0)
     return x
