@@ -401,7 +401,12 @@ __host__ __device__ constexpr FirstSched make_first_sched() {
 struct FirstHolder {
   static constexpr FirstSched value = make_first_sched();
 };
-static_assert(FirstHolder::value.ok, "first-vector sigma schedule");
+__host__ __device__ constexpr int max_row_slots(const FirstSched& f) {
+  int m = 0;
+  for (int r = 0; r < 20; ++r) m = f.rcount[r] > m ? f.rcount[r] : m;
+  return m;
+}
+static_assert(FirstHolder::value.ok && max_row_slots(FirstHolder::value) <= 4, "first-vector sigma schedule");
 __device__ const FirstSched g_first = make_first_sched();
 
 // Compile-time product lists: the alpha-beta terms (B, V) of a source row of type T (target
@@ -871,6 +876,19 @@ __device__ __noinline__ void sigma33_first(const Tabs<3>& tb, const WarpState<3>
                                            float* __restrict__ out, float* __restrict__ scr_a,
                                            float* __restrict__ scr_b, int lane) {
   constexpr int NS = 20, NF = 36;
+  // this lane's schedule, loaded up front (its latency runs under the alpha-alpha part)
+  int ent[kFirstSteps];
+#pragma unroll
+  for (int k = 0; k < kFirstSteps; ++k) ent[k] = (int)__ldg(&g_first.e[k][lane]);
+  int hsl[3] = {-1, -1, -1}, rsl[4] = {0, 0, 0, 0}, rcnt = 0;
+  if (lane >= NS) {
+#pragma unroll
+    for (int ph = 0; ph < 3; ++ph) hsl[ph] = (int)__ldg(&g_first.hslot[ph][lane - NS]);
+  } else {
+    rcnt = (int)__ldg(&g_first.rcount[lane]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) rsl[i] = (int)__ldg(&g_first.rslot[lane][i]);
+  }
   float acc[NS];
 #pragma unroll
   for (int b = 0; b < NS; ++b) acc[b] = 0.f;
@@ -922,9 +940,8 @@ __device__ __noinline__ void sigma33_first(const Tabs<3>& tb, const WarpState<3>
   // alpha-beta over the compile-time schedule: one step adds the products of one (row, source)
   // pair; a helper lane (20..31) hands its partial row to a scratch slot at the end of a phase
   auto slot_ptr = [&](int sl) { return sl < 20 ? scr_a + sl * NS : scr_b + (sl - 20) * NS; };
-  auto step = [&](auto type_tag, int k) {
+  auto step = [&](auto type_tag, int e) {
     constexpr int T = decltype(type_tag)::value;
-    const int e = (int)__ldg(&g_first.e[k][lane]);
     if (e < 0) return;
     const int x = (e >> 4) * 12 + (e & 15);
     const int pq = tb.pq[x], Ja = tb.J[x];
@@ -950,29 +967,28 @@ __device__ __noinline__ void sigma33_first(const Tabs<3>& tb, const WarpState<3>
     }
     ab_first_terms<T>(std::make_integer_sequence<int, AbFirstHolder<T>::value.n>{}, acc, wr, cr);
   };
-  auto flush = [&](int ph) {  // helpers: the phase's partial row to its slot
-    if (lane < NS) return;
-    const int sl = (int)__ldg(&g_first.hslot[ph][lane - NS]);
-    if (sl < 0) return;
+  auto flush = [&](int sl) {  // helpers: the phase's partial row to its slot
+    if (lane < NS || sl < 0) return;
     float4* orow = reinterpret_cast<float4*>(slot_ptr(sl));
 #pragma unroll
     for (int q = 0; q < NS / 4; ++q) orow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 #pragma unroll
     for (int b = 0; b < NS; ++b) acc[b] = 0.f;
   };
-  step(std::integral_constant<int, 0>{}, 0);
-  flush(0);
-#pragma unroll 1
-  for (int k = 1; k < 5; ++k) step(std::integral_constant<int, 1>{}, k);
-  flush(1);
-#pragma unroll 1
-  for (int k = 5; k < 9; ++k) step(std::integral_constant<int, 2>{}, k);
-  flush(2);
+  step(std::integral_constant<int, 0>{}, ent[0]);
+  flush(hsl[0]);
+#pragma unroll
+  for (int k = 1; k < 5; ++k) step(std::integral_constant<int, 1>{}, ent[k]);
+  flush(hsl[1]);
+#pragma unroll
+  for (int k = 5; k < 9; ++k) step(std::integral_constant<int, 2>{}, ent[k]);
+  flush(hsl[2]);
   __syncwarp();
   if (lane < NS) {  // own row + the helpers' partial rows, in slot order
-    const int nsl = (int)__ldg(&g_first.rcount[lane]);
-    for (int i = 0; i < nsl; ++i) {
-      const float4* prow = reinterpret_cast<const float4*>(slot_ptr((int)__ldg(&g_first.rslot[lane][i])));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i >= rcnt) break;
+      const float4* prow = reinterpret_cast<const float4*>(slot_ptr(rsl[i]));
 #pragma unroll
       for (int q = 0; q < NS / 4; ++q) {
         const float4 v = prow[q];
