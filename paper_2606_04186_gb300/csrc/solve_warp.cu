@@ -44,11 +44,9 @@
 namespace qf {
 namespace {
 
-// Loop unrolling of the table-driven set-up steps (measured: the same-spin table at 11 steps per
-// iteration, the first-order vector rolled; 22, 66 and a fully unrolled first-order loop were not
+// Loop unrolling of the same-spin table loop (measured: 11 steps per iteration; 22 and 66 were not
 // faster)
 constexpr int kHsUnroll = 11;
-constexpr int kFoUnroll = 1;
 constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
 // Spaces (warps) per CTA: a launch parameter up to kMaxWarps (the autotuner picks it); one CTA
 // fills the shared memory of an SM.  The register file is split over the SM's four
@@ -1459,7 +1457,10 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
   float vn_phi = 0.f;
   {
     float rphi;
+    unsigned pe[kPhiLen];  // this lane's Phi-table entries, kept for the first-order vector
     if constexpr (K == 3) {  // the column from its coupling table, each unique element once
+#pragma unroll
+      for (int k = 0; k < kPhiLen; ++k) pe[k] = phi_entry(cs, k * 32 + lane);
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int q = lane; q < NDET / 4; q += 32) {
         reinterpret_cast<float4*>(ws.S)[q] = z4;  // S0 = sigma(Phi)
@@ -1469,7 +1470,7 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
       float acc = 0.f, rr = 0.f;
 #pragma unroll
       for (int k = 0; k < kPhiLen; ++k) {
-        const unsigned e = phi_entry(cs, k * 32 + lane);
+        const unsigned e = pe[k];
         acc = fmaf(__uint_as_float(e & 0xff800000u), ws.Wt[e & 2047u], acc);
         if (e & (1u << 20)) {
           const int d = (int)((e >> 11) & 511u);
@@ -1560,9 +1561,9 @@ __device__ void solve_one(const Tabs<K>& tb, const CtaTabs& cs, WarpState<K>& ws
         }
         __syncwarp();
         const float j0 = ws.j0;
-#pragma unroll kFoUnroll
+#pragma unroll
         for (int k = 0; k < kPhiLen; ++k) {
-          const unsigned e = phi_entry(cs, k * 32 + lane);
+          const unsigned e = pe[k];
           if (e & (1u << 20)) {
             const int d = (int)((e >> 11) & 511u);
             const int ia = d / NS, ib = d % NS;
