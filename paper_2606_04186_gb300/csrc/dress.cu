@@ -118,7 +118,32 @@ __global__ void k_t1_annihilator(double* __restrict__ W, const double* __restric
 // The same four passes with each element read once per pass: thread per index triple (the
 // three positions other than the transformed one), t1 in shared memory, the occupied-index
 // values (creator) or the o accumulators (annihilator) in registers.  Used when o <= kT1Omax.
+// Shared t1 is stored transposed, t1s[a][i] with rows padded to kT1Omax (zeros), so the o
+// coefficients of one virtual index come in 16-byte loads that every lane shares.
 constexpr int kT1Omax = 16;
+// FP32 sums: resident CTAs per SM the register budget keeps (5 x 256 threads; the creator
+// pass, which holds no accumulators, 6)
+constexpr int kT1Blocks = 5;
+
+template <typename A>
+__device__ __forceinline__ void load_t1_t(const double* __restrict__ t1, A* t1s, const Dims& d) {
+  for (int x = threadIdx.x; x < d.v * kT1Omax; x += blockDim.x) {
+    const int a = x / kT1Omax, i = x % kT1Omax;
+    t1s[x] = (i < d.o) ? to_acc<A>(t1[i * d.v + a]) : (A)0;
+  }
+  __syncthreads();
+}
+// the kT1Omax coefficients t1[0..o)[a] (then zeros) of virtual index a
+template <typename A>
+__device__ __forceinline__ void t1_row(const A* t1s, int a, A (&c)[kT1Omax]) {
+  static_assert(kT1Omax * sizeof(A) % 16 == 0, "16-byte rows");
+  const uint4* r = reinterpret_cast<const uint4*>(t1s + a * kT1Omax);
+#pragma unroll
+  for (int q = 0; q < kT1Omax * (int)sizeof(A) / 16; ++q) {
+    const uint4 u = r[q];
+    memcpy(reinterpret_cast<unsigned char*>(c) + 16 * q, &u, 16);
+  }
+}
 
 template <typename A, int POS>
 __device__ __forceinline__ size_t t1_index(const Dims& d, int p, size_t rest) {
@@ -132,21 +157,22 @@ __device__ __forceinline__ size_t t1_index(const Dims& d, int p, size_t rest) {
 }
 
 template <typename A, int POS>
-__global__ void k_t1_creator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
-  extern __shared__ double t1raw[];  // [o][v], converted once to the accumulation type
+__global__ void __launch_bounds__(TPB, sizeof(A) == 4 ? kT1Blocks + 1 : 1) k_t1_creator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
+  extern __shared__ __align__(16) double t1raw[];  // [v][kT1Omax], in the accumulation type
   A* t1s = reinterpret_cast<A*>(t1raw);
-  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = to_acc<A>(t1[x]);
-  __syncthreads();
+  load_t1_t<A>(t1, t1s, d);
   const size_t m = (size_t)d.n * d.n * d.n;
   for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
     A wi[kT1Omax];
 #pragma unroll
     for (int i = 0; i < kT1Omax; ++i) wi[i] = (i < d.o) ? to_acc<A>(W[t1_index<A, POS>(d, i, rest)]) : (A)0;
     for (int a = 0; a < d.v; ++a) {
+      A c[kT1Omax];
+      t1_row<A>(t1s, a, c);
       A acc = 0;
 #pragma unroll
       for (int i = 0; i < kT1Omax; ++i)
-        if (i < d.o) acc += t1s[i * d.v + a] * wi[i];
+        if (i < d.o) acc += c[i] * wi[i];
       W[t1_index<A, POS>(d, d.o + a, rest)] -= from_acc<A>(acc);
     }
   }
@@ -156,12 +182,11 @@ __global__ void k_t1_creator_fast(double* __restrict__ W, const double* __restri
 // of W (occupied rows unchanged, virtual rows corrected), so no separate copy pass reads and
 // writes W first.  Same arithmetic as k_t1_creator_fast at POS 0.
 template <typename A>
-__global__ void k_t1_creator_copy(const double* __restrict__ src, double* __restrict__ W, const double* __restrict__ t1,
+__global__ void __launch_bounds__(TPB, sizeof(A) == 4 ? kT1Blocks : 1) k_t1_creator_copy(const double* __restrict__ src, double* __restrict__ W, const double* __restrict__ t1,
                                   Dims d) {
-  extern __shared__ double t1raw[];
+  extern __shared__ __align__(16) double t1raw[];  // [v][kT1Omax], in the accumulation type
   A* t1s = reinterpret_cast<A*>(t1raw);
-  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = to_acc<A>(t1[x]);
-  __syncthreads();
+  load_t1_t<A>(t1, t1s, d);
   const size_t m = (size_t)d.n * d.n * d.n;
   for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
     A wi[kT1Omax];
@@ -176,10 +201,12 @@ __global__ void k_t1_creator_copy(const double* __restrict__ src, double* __rest
       }
     }
     for (int a = 0; a < d.v; ++a) {
+      A c[kT1Omax];
+      t1_row<A>(t1s, a, c);
       A acc = 0;
 #pragma unroll
       for (int i = 0; i < kT1Omax; ++i)
-        if (i < d.o) acc += t1s[i * d.v + a] * wi[i];
+        if (i < d.o) acc += c[i] * wi[i];
       const size_t g = t1_index<A, 0>(d, d.o + a, rest);
       W[g] = src[g] - from_acc<A>(acc);
     }
@@ -187,11 +214,10 @@ __global__ void k_t1_creator_copy(const double* __restrict__ src, double* __rest
 }
 
 template <typename A, int POS>
-__global__ void k_t1_annihilator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
-  extern __shared__ double t1raw[];
+__global__ void __launch_bounds__(TPB, sizeof(A) == 4 ? kT1Blocks : 1) k_t1_annihilator_fast(double* __restrict__ W, const double* __restrict__ t1, Dims d) {
+  extern __shared__ __align__(16) double t1raw[];  // [v][kT1Omax], in the accumulation type
   A* t1s = reinterpret_cast<A*>(t1raw);
-  for (int x = threadIdx.x; x < d.o * d.v; x += blockDim.x) t1s[x] = to_acc<A>(t1[x]);
-  __syncthreads();
+  load_t1_t<A>(t1, t1s, d);
   const size_t m = (size_t)d.n * d.n * d.n;
   for (size_t rest = blockIdx.x * (size_t)blockDim.x + threadIdx.x; rest < m; rest += (size_t)gridDim.x * blockDim.x) {
     A acc[kT1Omax];
@@ -199,9 +225,11 @@ __global__ void k_t1_annihilator_fast(double* __restrict__ W, const double* __re
     for (int q = 0; q < kT1Omax; ++q) acc[q] = 0;
     for (int a = 0; a < d.v; ++a) {
       const A wa = to_acc<A>(W[t1_index<A, POS>(d, d.o + a, rest)]);
+      A c[kT1Omax];
+      t1_row<A>(t1s, a, c);
 #pragma unroll
       for (int q = 0; q < kT1Omax; ++q)
-        if (q < d.o) acc[q] += t1s[q * d.v + a] * wa;
+        if (q < d.o) acc[q] += c[q] * wa;
     }
 #pragma unroll
     for (int q = 0; q < kT1Omax; ++q)
@@ -214,7 +242,7 @@ void t1_passes(const double* eri, double* W, const double* t1, const Dims& d, cu
   const size_t mc = (size_t)d.v * d.n * d.n * d.n, ma = (size_t)d.o * d.n * d.n * d.n;
   const size_t n3 = (size_t)d.n * d.n * d.n;
   if (d.o <= kT1Omax) {
-    const size_t sm = sizeof(double) * d.o * d.v;
+    const size_t sm = sizeof(A) * kT1Omax * d.v;
     const unsigned g = blocks_for(n3) > 152u * 16u ? 152u * 16u : blocks_for(n3);
     k_t1_creator_copy<A><<<g, TPB, sm, st>>>(eri, W, t1, d);
     k_t1_creator_fast<A, 2><<<g, TPB, sm, st>>>(W, t1, d);
