@@ -360,51 +360,85 @@ __global__ void k_make_u(const double* __restrict__ t2, double* __restrict__ U, 
   }
 }
 
+// Index walk of a grid-stride loop over t = (x0 n1 + x1) n2 + x2 (x2 fastest) in steps of
+// `step`: the digits advance by the step's own digits with carries instead of three divisions
+// per term (the same t sequence, so the same summation order).
+struct Walk3 {
+  int x0, x1, x2, s0, s1, s2, n1, n2;
+  __device__ Walk3(int t, int step, int n1_, int n2_) : n1(n1_), n2(n2_) {
+    x2 = t % n2;
+    x1 = (t / n2) % n1;
+    x0 = t / (n1 * n2);
+    s2 = step % n2;
+    s1 = (step / n2) % n1;
+    s0 = step / (n1 * n2);
+  }
+  __device__ __forceinline__ void next() {
+    x2 += s2;
+    int c = x2 >= n2;
+    x2 -= c ? n2 : 0;
+    x1 += s1 + c;
+    c = x1 >= n1;
+    x1 -= c ? n1 : 0;
+    x0 += s0 + c;
+  }
+};
+
 __global__ void k_small_blocks(const double* __restrict__ F, const double* __restrict__ W,
                                const double* __restrict__ U, const double* __restrict__ t2, double* __restrict__ foo, double* __restrict__ fvv,
                                double* __restrict__ r1, double* __restrict__ wo, Dims d) {
   __shared__ double red[TPB];
   const int o = d.o, v = d.v;
+  const size_t n1 = d.n, n2 = n1 * n1, n3 = n2 * n1;
   const int x = blockIdx.x;
   double acc = 0.0;
   if (x < o * o) {
     const int m = x / o, i = x % o;
-    for (int t = threadIdx.x; t < o * v * v; t += TPB) {
-      const int nn = t / (v * v), e = (t / v) % v, f = t % v;
-      acc += W[gi(d, m, o + e, nn, o + f)] * U[ti(d, i, nn, e, f)];
+    // t = (nn, e, f): W[m, o+e, nn, o+f] U[i, nn, e, f]
+    for (Walk3 w(threadIdx.x, TPB, v, v); w.x0 < o; w.next()) {
+      const int nn = w.x0, e = w.x1, f = w.x2;
+      acc += W[(size_t)m * n3 + (size_t)(o + e) * n2 + (size_t)nn * n1 + (o + f)] *
+             U[((i * o + nn) * v + e) * v + f];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) foo[x] = F[m * d.n + i] + acc;
   } else if (x < o * o + v * v) {
     const int y = x - o * o, a = y / v, e = y % v;
-    for (int t = threadIdx.x; t < o * o * v; t += TPB) {
-      const int m = t / (o * v), nn = (t / v) % o, f = t % v;
-      acc -= W[gi(d, m, o + e, nn, o + f)] * U[ti(d, m, nn, a, f)];
+    // t = (m, nn, f): W[m, o+e, nn, o+f] U[m, nn, a, f]
+    for (Walk3 w(threadIdx.x, TPB, o, v); w.x0 < o; w.next()) {
+      const int m = w.x0, nn = w.x1, f = w.x2;
+      acc -= W[(size_t)m * n3 + (size_t)(o + e) * n2 + (size_t)nn * n1 + (o + f)] *
+             U[((m * o + nn) * v + a) * v + f];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) fvv[y] = F[(o + a) * d.n + o + e] + acc;
   } else if (x < o * o + v * v + v * o) {
     const int y = x - o * o - v * v, a = y / o, i = y % o;
-    for (int t = threadIdx.x; t < o * v * v; t += TPB) {
-      const int m = t / (v * v), e = (t / v) % v, f = t % v;
-      acc += W[gi(d, o + a, o + e, m, o + f)] * U[ti(d, i, m, e, f)];
+    // t = (m, e, f): W[o+a, o+e, m, o+f] U[i, m, e, f]
+    for (Walk3 w(threadIdx.x, TPB, v, v); w.x0 < o; w.next()) {
+      const int m = w.x0, e = w.x1, f = w.x2;
+      acc += W[(size_t)(o + a) * n3 + (size_t)(o + e) * n2 + (size_t)m * n1 + (o + f)] *
+             U[((i * o + m) * v + e) * v + f];
     }
-    for (int t = threadIdx.x; t < o * o * v; t += TPB) {
-      const int m = t / (o * v), nn = (t / v) % o, e = t % v;
-      acc -= W[gi(d, m, i, nn, o + e)] * U[ti(d, m, nn, a, e)];
+    // t = (m, nn, e): W[m, i, nn, o+e] U[m, nn, a, e]
+    for (Walk3 w(threadIdx.x, TPB, o, v); w.x0 < o; w.next()) {
+      const int m = w.x0, nn = w.x1, e = w.x2;
+      acc -= W[(size_t)m * n3 + (size_t)i * n2 + (size_t)nn * n1 + (o + e)] * U[((m * o + nn) * v + a) * v + e];
     }
-    for (int t = threadIdx.x; t < o * v; t += TPB) {
-      const int m = t / v, e = t % v;
-      acc += F[m * d.n + o + e] * U[ti(d, i, m, a, e)];
+    // t = (m, e): F[m, o+e] U[i, m, a, e]
+    for (Walk3 w(threadIdx.x, TPB, o, v); w.x0 < 1; w.next()) {
+      const int m = w.x1, e = w.x2;
+      acc += F[m * d.n + o + e] * U[((i * o + m) * v + a) * v + e];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) r1[y] = F[(o + a) * d.n + i] + acc;
   } else {
     const int y = x - o * o - v * v - v * o;
     const int k = y / (o * o * o), i = (y / (o * o)) % o, l = (y / o) % o, j = y % o;
-    for (int t = threadIdx.x; t < v * v; t += TPB) {
-      const int e = t / v, f = t % v;
-      acc += W[gi(d, k, o + e, l, o + f)] * t2[ti(d, i, j, e, f)];
+    // t = (e, f): W[k, o+e, l, o+f] t2[i, j, e, f]
+    for (Walk3 w(threadIdx.x, TPB, v, v); w.x0 < 1; w.next()) {
+      const int e = w.x1, f = w.x2;
+      acc += W[(size_t)k * n3 + (size_t)(o + e) * n2 + (size_t)l * n1 + (o + f)] * t2[((i * o + j) * v + e) * v + f];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) wo[y] = W[gi(d, k, i, l, j)] + acc;

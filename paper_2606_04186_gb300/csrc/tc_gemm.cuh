@@ -305,15 +305,23 @@ namespace tc {
 constexpr int PTHREADS = 256;  // threads of a packed-engine CTA
 
 // out_hi/out_lo[r][k] = split(L(r, k)) for r < rows, k < K; zero in the padding.
+// (r, k) of the grid-stride index x = r Kp + k advance by the stride's own digits with a carry,
+// so no 64-bit division runs per element.
 template <class L>
 __global__ void k_pack(L ld, int rows, int K, int rows_p, int Kp, float* __restrict__ hi, float* __restrict__ lo) {
   const size_t total = (size_t)rows_p * Kp;
-  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(x / Kp), k = (int)(x % Kp);
+  const size_t x0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+  int r = (int)(x0 / Kp), k = (int)(x0 % Kp);
+  const int sr = (int)(step / Kp), sk = (int)(step % Kp);
+  for (size_t x = x0; x < total; x += step) {
     const float v = (r < rows && k < K) ? ld(r, k) : 0.f;
     const float h = tf32_round(v);
     hi[x] = h;
     lo[x] = tf32_round(v - h);
+    k += sk;
+    const int c = k >= Kp;
+    k -= c ? Kp : 0;
+    r += sr + c;
   }
 }
 
