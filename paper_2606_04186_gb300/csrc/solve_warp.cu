@@ -973,13 +973,21 @@ __device__ __noinline__ void sigma33_first(const Tabs<3>& tb, const WarpState<3>
 #pragma unroll
     for (int b = 0; b < NS; ++b) acc[b] = 0.f;
   };
+  // one body per step type (a rolled loop: the kernel's hot code stays small), the lane's entry
+  // for step k selected from its registers
+  auto entry = [&](int k) {
+    int e = ent[0];
+#pragma unroll
+    for (int j = 1; j < kFirstSteps; ++j) e = (k == j) ? ent[j] : e;
+    return e;
+  };
   step(std::integral_constant<int, 0>{}, ent[0]);
   flush(hsl[0]);
-#pragma unroll
-  for (int k = 1; k < 5; ++k) step(std::integral_constant<int, 1>{}, ent[k]);
+#pragma unroll 1
+  for (int k = 1; k < 5; ++k) step(std::integral_constant<int, 1>{}, entry(k));
   flush(hsl[1]);
-#pragma unroll
-  for (int k = 5; k < 9; ++k) step(std::integral_constant<int, 2>{}, ent[k]);
+#pragma unroll 1
+  for (int k = 5; k < 9; ++k) step(std::integral_constant<int, 2>{}, entry(k));
   flush(hsl[2]);
   __syncwarp();
   if (lane < NS) {  // own row + the helpers' partial rows, in slot order
