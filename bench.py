@@ -521,6 +521,7 @@ def run_ours(args):
     it, st = fl.stats()
     e_mean = fl.energy()
     sched = fl.schedule()
+    sched["dress_ladder"] = fl.dress_schedule()  # tile width of the ladder + oooo product
     if dist is not None:
         tt = torch.tensor([elapsed_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)

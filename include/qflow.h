@@ -128,7 +128,11 @@ typedef struct {
   int32_t chunk;              /* mixed precision, persistent queue: consecutive spaces a warp
                                  takes per fetch, 1..16; 0 = chosen by the autotuner
                                  (QFLOW_SCHED_AUTO) or 1                                     */
-  int32_t reserved[3];
+  int32_t ladder_bn;          /* mixed precision, SES-CC form: tile width (columns) of the
+                                 dressing's ladder + oooo tensor-core product, 32, 64 or 128;
+                                 0 = chosen by the autotuner (QFLOW_SCHED_AUTO) or 64.  Every
+                                 width gives the same products bit for bit.                  */
+  int32_t reserved[2];
 } qflow_options;
 
 /* Fill *opt with the defaults above for the given precision. */
@@ -273,6 +277,13 @@ int qflow_last_sweep_info(qflow_handle hnd, double* phase_ms, int64_t* kernel_la
 #define QFLOW_TUNE_MAX 8
 int qflow_schedule(qflow_handle hnd, int32_t* persistent, int32_t* chunk, int32_t* warps_per_cta, int32_t* graph,
                    float* candidate_ms, int32_t* n_candidates);
+
+/* Tile width in use for the mixed dressing's ladder + oooo product (QFLOW_SCHED_AUTO times
+ * 32, 64 and 128 columns at the second sweep, beside the solver's candidates) and the times of
+ * those three candidates in milliseconds (count 0 when the width was fixed, came from the
+ * per-process cache, or before the calibration).  Any output may be NULL. */
+#define QFLOW_LADDER_TUNE_MAX 3
+int qflow_dress_schedule(qflow_handle hnd, int32_t* ladder_bn, float* candidate_ms, int32_t* n_candidates);
 
 /* Stream the handle works on (a cudaStream_t). */
 void* qflow_stream(qflow_handle hnd);

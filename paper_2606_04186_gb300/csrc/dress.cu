@@ -1403,11 +1403,34 @@ cudaError_t run_jobs(tc::PackedJobs<Store>& jobs, const Arena& ar, int* err, cud
   return tc::gemm_packed<BN>(jobs, err, st);
 }
 
+// The ladder + oooo product's tile width is a run-time choice among kLadderBN (timed by
+// tune_ladder); its B operand is padded to the widest candidate so any of them can run on it.
+constexpr int kLadderBN[3] = {32, 64, 128};
+constexpr int kLadderPad = 128;
+constexpr int kLadderDefault = 64;  // one wave of 81 tiles at o = 10 (v^2 = 5184)
+
+cudaError_t run_ladder(tc::PackedJobs<StoreR2>& js, const Arena& ar, int* err, int bn, cudaStream_t st) {
+  switch (bn) {
+    case 32: return run_jobs<32>(js, ar, err, st);
+    case 128: return run_jobs<128>(js, ar, err, st);
+    default: return run_jobs<64>(js, ar, err, st);
+  }
+}
+
+// The packed operands of the ladder + oooo product: rows (i, j), cols (a, b), k = (e, f) then
+// (m, n).
+cudaError_t pack_ladder(const TcCtx& c, int o, int v, Arena& ar, Op* a1, Op* b1, cudaStream_t st) {
+  const int oo = o * o, vv = v * v;
+  cudaError_t e = pack_op(LR2G1A{c}, oo, vv + oo, kTileM, ar, a1, st);
+  if (e == cudaSuccess) e = pack_op(LR2G1B{c}, vv, vv + oo, kLadderPad, ar, b1, st);
+  return e;
+}
+
 constexpr int kOvoSplit = 6;  // split K of the oovo v^2 product (720 x 100 x v^2)
 
 // The T2 terms of the mixed path; with ar.base == nullptr only sizes the packed scratch.
 cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* F, const float* t2, const Work& w,
-                        double* e0, Arena& ar, cudaStream_t st) {
+                        double* e0, Arena& ar, cudaStream_t st, int ladder_bn = kLadderDefault) {
   const int o = d.o, v = d.v, ov = o * v, vv = v * v, oo = o * o;
   const bool run = ar.base != nullptr;
   float* A = run ? reinterpret_cast<float*>(w.A) : nullptr;
@@ -1459,13 +1482,11 @@ cudaError_t t2_terms_tc(const Dims& d, double* W, const float* G, const double* 
   {
     ar.reset();
     Op a1, b1;
-    QF_TRY(pack_op(LR2G1A{c}, oo, vv + oo, kTileM, ar, &a1, st));
-    QF_TRY(pack_op(LR2G1B{c}, vv, vv + oo, 64, ar, &b1, st));
+    QF_TRY(pack_ladder(c, o, v, ar, &a1, &b1, st));
     tc::PackedJobs<StoreR2> js{};
     js.j[0] = job(a1, b1, StoreR2{acc, o, v, 4});
     js.count = 1;
-    // 64-column tiles: v^2 / 64 tiles fit one wave of CTAs at o = 10 (162 tiles of 32 took two)
-    QF_TRY((run_jobs<64>(js, ar, err, st)));
+    QF_TRY(run_ladder(js, ar, err, ladder_bn, st));
   }
   // r2: rings (four output maps, one launch)
   {
@@ -1602,7 +1623,7 @@ size_t tc_arena_floats(int n, int nocc) {
 
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
                          double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st,
-                         float* g32) {
+                         float* g32, int ladder_bn) {
   Work w;
   const bool mixed = g32 != nullptr;
   if (work_bytes < carve(nullptr, n, nocc, &w, mixed)) return cudaErrorInvalidValue;
@@ -1633,7 +1654,7 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
       k_to_f32<<<gg, TPB, 0, st>>>(W, g32, n4);
       k_to_f32<<<blocks_for(o * o * v * v), TPB, 0, st>>>(t2, t2f, o * o * v * v);
       Arena ar{w.arena};
-      cudaError_t e = t2_terms_tc(d, W, g32, F, t2f, w, e0, ar, st);
+      cudaError_t e = t2_terms_tc(d, W, g32, F, t2f, w, e0, ar, st, ladder_bn > 0 ? ladder_bn : kLadderDefault);
       if (e != cudaSuccess) return e;
     } else {
       t2_terms<double>(d, W, W, F, t2, w, st);
@@ -1642,6 +1663,48 @@ cudaError_t launch_dress(const double* h, const double* eri, const double* t1, c
     k_finalize<<<blocks_for(nf), TPB, 0, st>>>(W, F, w.foo, w.fvv, w.r1, w.wo, w.r2, d);
   }
   return cudaGetLastError();
+}
+
+// Times the ladder + oooo product with each tile width of kLadderBN on the workspace of a mixed
+// dressing that has run (its packed scratch and FP32 copies are overwritten, its results are
+// not read): each candidate runs twice on the stream, the second run timed with CUDA events.
+// *best = the fastest width; ms[3] = the candidates' times.  Not capturable (it synchronises).
+cudaError_t tune_ladder(int n, int nocc, const float* g32, void* work, size_t work_bytes, cudaStream_t st, int* best,
+                        float* ms) {
+  *best = kLadderDefault;
+  for (int i = 0; i < 3; ++i) ms[i] = 0.f;
+  const int o = nocc, v = n - nocc;
+  if (!(o > 0 && v > 0) || !g32) return cudaSuccess;
+  Work w;
+  if (work_bytes < carve(nullptr, n, nocc, &w, true)) return cudaErrorInvalidValue;
+  carve(work, n, nocc, &w, true);
+  TcCtx c{g32, reinterpret_cast<const float*>(w.t2f), nullptr, nullptr, nullptr, nullptr, w.wo, n, o, v};
+  Arena ar{w.arena};
+  Op a1, b1;
+  cudaError_t e = pack_ladder(c, o, v, ar, &a1, &b1, st);
+  tc::PackedJobs<StoreR2> js{};
+  js.j[0] = job(a1, b1, StoreR2{w.acc, o, v, 4});
+  js.count = 1;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float bt = 0.f;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(t0, st);
+      if (e == cudaSuccess) e = run_ladder(js, ar, w.err, kLadderBN[i], st);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], t0, t1);
+    }
+    if (e == cudaSuccess && ms[i] > 0.f && (bt == 0.f || ms[i] < bt)) {
+      bt = ms[i];
+      *best = kLadderBN[i];
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  return e;
 }
 
 }  // namespace qf

@@ -225,6 +225,11 @@ struct qflow_ctx {
   int64_t sweeps = 0;  // sweeps run so far
   float tune_ms[QFLOW_TUNE_MAX] = {0};
   int tune_count = 0;
+  // tile width of the mixed dressing's ladder + oooo product (0 = the default until tuned) and
+  // the tuner's times for 32, 64 and 128 columns
+  int ladder_bn = 0;
+  float ladder_ms[QFLOW_LADDER_TUNE_MAX] = {0};
+  int ladder_count = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches = 0;
@@ -370,6 +375,11 @@ int qflow_init(qflow_handle* out, const double* h, const double* eri, int32_t n,
     return QFLOW_ERR_ARG;
   }
   if (c->opt.chunk > 0) c->sched_chunk = c->opt.chunk;
+  if (c->opt.ladder_bn != 0 && c->opt.ladder_bn != 32 && c->opt.ladder_bn != 64 && c->opt.ladder_bn != 128) {
+    delete c;
+    return QFLOW_ERR_ARG;
+  }
+  c->ladder_bn = c->opt.ladder_bn;
   if (c->opt.form != QFLOW_FORM_SESCC && c->opt.form != QFLOW_FORM_DUCC) {
     delete c;
     return QFLOW_ERR_ARG;
@@ -552,7 +562,7 @@ cudaError_t dress_pool(qflow_ctx* c, const double* t1, const double* t2) {
     return qf::launch_dress_ducc(c->h, c->eri, t1, t2, c->n, c->nocc, c->e0, c->F, c->W, c->F0, c->dwork,
                                  c->dwork_bytes, c->stream);
   return qf::launch_dress(c->h, c->eri, t1, t2, c->n, c->nocc, c->e0, c->F, c->W, c->dwork, c->dwork_bytes, c->stream,
-                          c->W32);
+                          c->W32, c->ladder_bn);
 }
 
 int dress_pool_launches(const qflow_ctx* c) {
@@ -683,7 +693,7 @@ struct TuneKey {
     return c3 < o.c3;
   }
 };
-std::map<TuneKey, std::array<int, 3>> g_tune_cache;
+std::map<TuneKey, std::array<int, 4>> g_tune_cache;  // persistent, chunk, warps, ladder width
 std::mutex g_tune_mu;
 
 // Model layout: parameters, then mu_x[708], s_x[708], mu_y[54], sd_y[54].
@@ -743,6 +753,7 @@ cudaError_t autotune(qflow_ctx* c) {
       c->sched_persistent = it->second[0];
       c->sched_chunk = it->second[1];
       c->sched_warps = it->second[2];
+      if (c->opt.ladder_bn == 0 && c->opt.form == QFLOW_FORM_SESCC) c->ladder_bn = it->second[3];
       c->tuned = true;
       return cudaSuccess;
     }
@@ -786,13 +797,22 @@ cudaError_t autotune(qflow_ctx* c) {
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if (e != cudaSuccess) return e;
+  // the dressing's ladder + oooo tile width, on the workspace of this sweep's dressing (which
+  // has run: the tuner only overwrites its scratch)
+  if (c->opt.ladder_bn == 0 && c->opt.form == QFLOW_FORM_SESCC && c->W32) {
+    int bn = 0;
+    e = qf::tune_ladder(c->n, c->nocc, c->W32, c->dwork, c->dwork_bytes, c->stream, &bn, c->ladder_ms);
+    if (e != cudaSuccess) return e;
+    c->ladder_bn = bn;
+    c->ladder_count = QFLOW_LADDER_TUNE_MAX;
+  }
   c->tune_count = kCand;
   c->sched_persistent = cand[bi][0];
   c->sched_chunk = (c->opt.chunk > 0) ? c->opt.chunk : cand[bi][1];
   c->sched_warps = (c->opt.warps > 0) ? c->opt.warps : cand[bi][2];
   c->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_cache[key] = {c->sched_persistent, c->sched_chunk, c->sched_warps};
+  g_tune_cache[key] = {c->sched_persistent, c->sched_chunk, c->sched_warps, c->ladder_bn};
   return cudaSuccess;
 }
 
@@ -1123,6 +1143,15 @@ int qflow_schedule(qflow_handle c, int32_t* persistent, int32_t* chunk, int32_t*
   if (candidate_ms)
     for (int i = 0; i < c->tune_count; ++i) candidate_ms[i] = c->tune_ms[i];
   if (n_candidates) *n_candidates = c->tune_count;
+  return QFLOW_OK;
+}
+
+int qflow_dress_schedule(qflow_handle c, int32_t* ladder_bn, float* candidate_ms, int32_t* n_candidates) {
+  if (!c) return QFLOW_ERR_ARG;
+  if (ladder_bn) *ladder_bn = c->ladder_bn > 0 ? c->ladder_bn : 64;
+  if (candidate_ms)
+    for (int i = 0; i < c->ladder_count; ++i) candidate_ms[i] = c->ladder_ms[i];
+  if (n_candidates) *n_candidates = c->ladder_count;
   return QFLOW_OK;
 }
 

@@ -89,9 +89,15 @@ int dress_launch_count(int n, int nocc, bool mixed);  // kernels one launch_dres
 // in FP32 (mixed precision); the mixed form adds the T2 term of the vvvv block only where at most
 // three of its four virtual indices differ (all a (k, k) space with k <= 3 reads), the other
 // vvvv elements keep their T1-transformed values.
+// ladder_bn: tile width (32, 64 or 128 columns) of the mixed path's ladder + oooo product; 0 = 64.
 cudaError_t launch_dress(const double* h, const double* eri, const double* t1, const double* t2, int n, int nocc,
                          double* e0, double* F, double* W, void* work, size_t work_bytes, cudaStream_t st,
-                         float* g32 = nullptr);
+                         float* g32 = nullptr, int ladder_bn = 0);
+// Times the ladder + oooo product at each tile width on the workspace of a mixed dressing that
+// has run (scratch overwritten; synchronises the stream): *best = the fastest, ms[3] = the times
+// of 32, 64 and 128 columns.
+cudaError_t tune_ladder(int n, int nocc, const float* g32, void* work, size_t work_bytes, cudaStream_t st, int* best,
+                        float* ms);
 
 // Step (a) in the Hermitian (DUCC) form (ducc.cu): e0, F, W of the part G common to every space,
 // and F0 = the bare Fock matrix (the per-space part needs it).  FP64.

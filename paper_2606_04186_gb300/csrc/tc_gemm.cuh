@@ -505,15 +505,22 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_gemm_packed(const __grid_consta
   __syncthreads();
   tc_fence_after();
   const bool ok = (sm.abort == 0);
-  if (ok && nslab > 0) {
+  // A job whose K range is empty (a split-K part past the last slab) stores zeros: its partial
+  // output is summed like the others.
+  if (ok) {
     const int quad = warp & 3;  // accumulator lanes 32 quad .. 32 quad + 31
     const int m = m0 + quad * 32 + (tid & 31);
 #pragma unroll 1
     for (int c = (warp >> 2) * 32; c < BN; c += 64) {
       float v[32], w[32];
       const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-      tmem_ld32(tmem + lane_base + (uint32_t)c, v);
-      tmem_ld32(tmem + lane_base + (uint32_t)(BN + c), w);
+      if (nslab > 0) {  // uniform over the CTA: every warp takes the collective loads or none
+        tmem_ld32(tmem + lane_base + (uint32_t)c, v);
+        tmem_ld32(tmem + lane_base + (uint32_t)(BN + c), w);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = w[j] = 0.f;
+      }
       if (m < jb.M && n0 + c < jb.N) {
         // 32 consecutive columns of row m in one call, so the store can walk its output indices
         // instead of splitting every column index

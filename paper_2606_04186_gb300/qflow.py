@@ -34,7 +34,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("diis", C.c_int32), ("guess", C.c_int32), ("schedule", C.c_int32), ("graph", C.c_int32),
                 ("form", C.c_int32), ("warps", C.c_int32), ("chunk", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("ladder_bn", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 _lib = None
@@ -63,6 +63,7 @@ def lib() -> C.CDLL:
         "qflow_stream": (V, [P]),
         "qflow_last_sweep_info": (I32, [P, P, P]),
         "qflow_schedule": (I32, [P, P, P, P, P, P, P]),
+        "qflow_dress_schedule": (I32, [P, P, P, P]),
         "qflow_destroy": (None, [P]),
         "qflow_strerror": (C.c_char_p, [C.c_int]),
         "qflow_dress_workspace": (C.c_size_t, [I32, I32]),
@@ -178,7 +179,8 @@ class Flow:
 
     def __init__(self, h, eri, nocc: int, spaces, precision: str = "fp64", max_iter: int | None = None,
                  tol: float | None = None, guess: str = "phi", diis: int = 0, schedule: str = "auto",
-                 graph: bool = True, form: str = "ses", warps: int = 0, chunk: int = 0):
+                 graph: bool = True, form: str = "ses", warps: int = 0, chunk: int = 0,
+                 ladder_bn: int = 0):
         h, eri, sp = _f64(h), _f64(eri), _spaces(spaces)
         self.n, self.nocc = h.shape[0], nocc
         self.nvir = self.n - nocc
@@ -195,6 +197,7 @@ class Flow:
         opt.form = {"ses": 0, "ducc": 1}[form]
         opt.warps = warps
         opt.chunk = chunk
+        opt.ladder_bn = ladder_bn
         self._h = C.c_void_p()
         code = lib().qflow_init(C.byref(self._h), _ptr(h), _ptr(eri), self.n, nocc, _ptr(sp), len(sp), C.byref(opt))
         self.init_status = _check(code, "qflow_init")
@@ -304,6 +307,14 @@ class Flow:
                "qflow_schedule")
         return {"persistent": bool(p.value), "chunk": ch.value, "warps_per_cta": ct.value, "graph": bool(gr.value),
                 "candidate_ms": [float(ms[i]) for i in range(nc.value)]}
+
+    def dress_schedule(self) -> dict:
+        """Tile width of the mixed dressing's ladder + oooo product and the autotuner's times for
+        32, 64 and 128 columns (empty when the width was fixed or cached)."""
+        bn, nc = C.c_int32(), C.c_int32()
+        ms = (C.c_float * 3)()  # QFLOW_LADDER_TUNE_MAX
+        _check(lib().qflow_dress_schedule(self._h, C.byref(bn), ms, C.byref(nc)), "qflow_dress_schedule")
+        return {"ladder_bn": bn.value, "candidate_ms": [float(ms[i]) for i in range(nc.value)]}
 
     def stream(self) -> int:
         return lib().qflow_stream(self._h) or 0

@@ -92,7 +92,8 @@ def test_init_rejects_bad_arguments_before_any_device_work(qf):
     bad = rows.copy()
     bad[0, 5], bad[0, 6] = bad[0, 6], bad[0, 5]   # virtual orbitals out of ascending order
     assert init(10, 3, bad, None) == (qf.ERR_ARG, None)
-    for field, value in (("precision", 5), ("diis", 1), ("diis", -1), ("guess", 9)):
+    for field, value in (("precision", 5), ("diis", 1), ("diis", -1), ("guess", 9), ("warps", 16), ("chunk", 17),
+                         ("ladder_bn", 48), ("ladder_bn", -64)):
         opt = qf.default_options("mixed")
         setattr(opt, field, value)
         assert init(10, 3, rows, opt) == (qf.ERR_ARG, None), field

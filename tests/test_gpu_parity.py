@@ -270,6 +270,29 @@ def test_schedules_and_graph_replay_agree(qf):
     assert runs["persistent_chunk_4"][2]["chunk"] == 4
 
 
+def test_ladder_tile_widths_agree(qf):
+    """The mixed dressing's ladder + oooo tensor-core product at 32, 64 and 128 columns per tile
+    gives the same dressed operator and the same sweeps, bit for bit (each output element sums
+    its K slabs in the same order whatever the tile width)."""
+    eps, h, g, sp = synth.system_inputs("n40")
+    runs = {}
+    for bn in (32, 64, 128):
+        f = qf.Flow(h, g, 6, sp, precision="mixed", schedule="persistent", graph=False, ladder_bn=bn)
+        per = []
+        for _ in range(2):
+            f.sweep()
+            per.append(f.energy(per_space=True)[1])
+        e0, F, W = f.dressed()
+        runs[bn] = (np.array(per), e0, F, W, f.dress_schedule())
+        f.close()
+    for bn in (32, 128):
+        assert np.array_equal(runs[bn][0], runs[64][0]), bn
+        assert runs[bn][1] == runs[64][1] and np.array_equal(runs[bn][2], runs[64][2]), bn
+        assert np.array_equal(runs[bn][3], runs[64][3]), bn
+    for bn in (32, 64, 128):
+        assert runs[bn][4] == {"ladder_bn": bn, "candidate_ms": []}
+
+
 def test_consecutive_spaces_reuse_the_gathered_block(qf):
     """A warp that takes consecutive spaces of the sorted list keeps the couplings of the five
     orbitals they share and gathers only those of the last virtual: every (3, 3) space of n24
@@ -300,4 +323,7 @@ def test_autotuner_times_candidates(qf):
     sch = f.schedule()
     assert len(sch["candidate_ms"]) == 8 and min(sch["candidate_ms"]) > 0
     assert sch["persistent"] and sch["chunk"] in (1, 2, 4, 8) and sch["warps_per_cta"] in (12, 15)
+    ds = f.dress_schedule()   # the dressing's ladder tile width is timed beside the solver's candidates
+    assert len(ds["candidate_ms"]) == 3 and min(ds["candidate_ms"]) > 0 and ds["ladder_bn"] in (32, 64, 128)
+    assert ds["ladder_bn"] == (32, 64, 128)[int(np.argmin(ds["candidate_ms"]))]
     f.close()
