@@ -145,7 +145,7 @@ def dress_gemm_flops(o: int, v: int) -> float:
 
 
 # solve-kernel DRAM traffic per space, sweep 3 (ncu capture of the 477,120-space n82 subset)
-TRAFFIC_PER_SPACE = {"n82": 150.3}
+TRAFFIC_PER_SPACE = {"n82": 151.1}
 
 
 # ---- clocks ------------------------------------------------------------------------------------
