@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=3000, help="spaces solved by the oracle for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "persistent", "per_class"])
+    ap.add_argument("--ladder-bn", type=int, default=0, choices=[0, 32, 64, 128],
+                    help="tile width of the dressing's ladder + oooo GEMM (0 = timed by the autotuner, else 64 "
+                         "under a fixed schedule)")
     ap.add_argument("--sampler", type=int, default=-1,
                     help="space list from Algorithm 1 (greedy coverage cycle of (3,3) spaces) with this seed")
     ap.add_argument("--waves", type=int, default=0,
@@ -456,7 +459,8 @@ def run_ours(args):
     t_init = time.perf_counter()
     if args.form == "ducc":
         args.precision = "fp64"   # the DUCC form is FP64 throughout; its FP64 leg is the run itself
-    fl = qflow.Flow(h, g, no, sp, precision=args.precision, schedule=args.schedule, form=args.form)
+    fl = qflow.Flow(h, g, no, sp, precision=args.precision, schedule=args.schedule, form=args.form,
+                    ladder_bn=args.ladder_bn if args.precision == "mixed" and args.form == "ses" else 0)
     t_init = time.perf_counter() - t_init
     stream = torch.cuda.ExternalStream(fl.stream())
     log(f"init {t_init:.1f} s")
