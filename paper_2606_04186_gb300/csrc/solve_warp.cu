@@ -44,8 +44,8 @@
 namespace qf {
 namespace {
 
-// Loop unrolling of the same-spin table loop (measured: 11 steps per iteration; 22 and 66 were not
-// faster)
+// Loop unrolling of the same-spin table loop (measured: 11 steps per iteration; 6, 22 and 66 were
+// not faster)
 constexpr int kHsUnroll = 11;
 constexpr int KM = 3;     // Davidson subspace limit (restart on the Ritz vector)
 // Spaces (warps) per CTA: a launch parameter up to kMaxWarps (the autotuner picks it); one CTA
