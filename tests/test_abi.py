@@ -97,3 +97,13 @@ def test_init_rejects_bad_arguments_before_any_device_work(qf):
         opt = qf.default_options("mixed")
         setattr(opt, field, value)
         assert init(10, 3, rows, opt) == (qf.ERR_ARG, None), field
+
+
+def test_queries_reject_a_null_handle(qf):
+    """Every handle query answers QFLOW_ERR_ARG for a null handle and writes nothing (no GPU)."""
+    import ctypes as C
+    L = qf.lib()
+    i32, f32 = C.c_int32(-7), (C.c_float * 8)()
+    assert L.qflow_schedule(None, C.byref(i32), C.byref(i32), C.byref(i32), C.byref(i32), f32, C.byref(i32)) == qf.ERR_ARG
+    assert L.qflow_dress_schedule(None, C.byref(i32), f32, C.byref(i32)) == qf.ERR_ARG
+    assert i32.value == -7
